@@ -1,0 +1,257 @@
+"""FP64 CPU oracle for POD-augmented CG — TEST INFRASTRUCTURE ONLY.
+
+Plain, slow, obviously correct reference implementation (see ``pod_cg_oracle.c``) of
+what the GPU library computes, used only by the test suite, the package smoke check and
+the benchmark's CPU-baseline leg. It shares no code with the CUDA library and imports
+nothing from it. Inputs are plain numpy arrays (CSR as ``row_ptr``/``col``/``val``,
+n-by-k blocks as Fortran-ordered float64 arrays).
+
+The sequence driver (:class:`OracleSequence`) is the paper's overall algorithm
+(Section 4.4, Algorithm 3) reduced to the recycled-solution form: the POD basis for
+system j is computed (Algorithm 4, identity metric, unit weights) from the last
+``s_max`` solutions, stage one (Algorithm 2) solves on it directly, then augmented PCG
+(Algorithm 1) iterates to the tolerance.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pod_cg_oracle.c")
+_LOCK = threading.Lock()
+_LIBS: dict[int, ctypes.CDLL] = {}
+
+STATUS = {0: "ok", 1: "arg", 2: "not_spd", 3: "breakdown", 4: "maxit", 5: "nonfinite"}
+
+
+def lib_path(mutant: int = 0, out_dir: str | None = None) -> str:
+    d = out_dir or os.path.join(_HERE, "_build")
+    name = "liborc.so" if mutant == 0 else f"liborc_mut{mutant}.so"
+    return os.path.join(d, name)
+
+
+def build(mutant: int = 0, out_dir: str | None = None, force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, portable flags) and return the .so path.
+
+    ``mutant`` > 0 plants the numbered mistake (``-DORC_MUTANT=k``) for the pin-sensitivity
+    tests; the normal build uses 0.
+    """
+    out = lib_path(mutant, out_dir)
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", f"-DORC_MUTANT={int(mutant)}",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("w", ctypes.c_int),
+                ("chol_failed", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("stage1_relres", ctypes.c_double), ("final_relres", ctypes.c_double),
+                ("cond_gram", ctypes.c_double)]
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64) if np.ndim(a) <= 1 else np.asfortranarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Oracle:
+    """ctypes front end of one oracle build (``mutant`` selects a planted-mistake build)."""
+
+    def __init__(self, mutant: int = 0, out_dir: str | None = None):
+        with _LOCK:
+            path = build(mutant, out_dir)
+            lib = ctypes.CDLL(path)
+        self.lib = lib
+        vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        lib.orc_spmv.argtypes = [ci, vp, vp, vp, vp, vp]
+        lib.orc_dot.argtypes = [ci, vp, vp]
+        lib.orc_dot.restype = cd
+        lib.orc_gram.argtypes = [ci, ci, vp, ci, vp, vp]
+        lib.orc_spmm.argtypes = [ci, vp, vp, vp, ci, vp, vp]
+        lib.orc_cholesky.argtypes = [ci, vp, vp]
+        lib.orc_chol_solve.argtypes = [ci, vp, vp, vp]
+        lib.orc_jacobi_eig.argtypes = [ci, vp, vp, vp, ci]
+        lib.orc_pod_evd.argtypes = [ci, ci, vp, cd, ci, cd, vp, vp]
+        lib.orc_stage_one.argtypes = [ci, vp, vp, vp, vp, ci, vp, vp, vp]
+        lib.orc_aug_pcg.argtypes = [ci, vp, vp, vp, vp, ci, vp, vp, vp, cd, ci, ci, vp,
+                                    ctypes.POINTER(_Info), vp, vp, ci]
+        lib.orc_pcg.argtypes = [ci, vp, vp, vp, vp, vp, cd, ci, vp, ctypes.POINTER(ci)]
+        lib.orc_solve_system.argtypes = [ci, vp, vp, vp, vp, ci, vp, cd, ci, ci, vp,
+                                         ctypes.POINTER(_Info), vp, vp, ci]
+
+    # -- Section 2 / basic kernels -------------------------------------------------
+    def spmv(self, A, x):
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        n = len(rp) - 1
+        x = _f64(x)
+        y = np.empty(n)
+        self.lib.orc_spmv(n, _p(rp), _p(col), _p(val), _p(x), _p(y))
+        return y
+
+    def dot(self, a, b):
+        a, b = _f64(a), _f64(b)
+        return self.lib.orc_dot(len(a), _p(a), _p(b))
+
+    def gram(self, X, Y):
+        X, Y = _f64(X), _f64(Y)
+        n, p = X.shape
+        q = Y.shape[1]
+        G = np.empty((p, q))
+        self.lib.orc_gram(n, p, _p(X), q, _p(Y), _p(G))
+        return G
+
+    def spmm(self, A, W):
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        W = _f64(W)
+        n, w = W.shape
+        AW = np.empty((n, w), order="F")
+        self.lib.orc_spmm(n, _p(rp), _p(col), _p(val), w, _p(W), _p(AW))
+        return AW
+
+    # -- small dense -------------------------------------------------------------------
+    def cholesky(self, G):
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        w = G.shape[0]
+        R = np.empty((w, w))
+        st = self.lib.orc_cholesky(w, _p(G), _p(R))
+        return R, st
+
+    def chol_solve(self, R, c):
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        c = _f64(c)
+        y = np.empty(len(c))
+        self.lib.orc_chol_solve(len(c), _p(R), _p(c), _p(y))
+        return y
+
+    def jacobi_eig(self, G, max_sweeps: int = 60):
+        G = np.ascontiguousarray(G, dtype=np.float64)
+        s = G.shape[0]
+        ev = np.empty(s)
+        V = np.empty((s, s))
+        sweeps = self.lib.orc_jacobi_eig(s, _p(G), _p(ev), _p(V), max_sweeps)
+        return ev, V, sweeps
+
+    # -- Algorithm 4 ----------------------------------------------------------------------
+    def pod_evd(self, S, energy: float, w_max: int, rank_tol: float = 1e-13):
+        S = _f64(S)
+        n, s = S.shape
+        W = np.zeros((n, max(w_max, 1)), order="F")
+        sig2 = np.empty(max(s, 1))
+        w = self.lib.orc_pod_evd(n, s, _p(S), energy, w_max, rank_tol, _p(W), _p(sig2))
+        return np.asfortranarray(W[:, :w]), w, sig2[:s]
+
+    # -- Algorithm 2 ----------------------------------------------------------------------
+    def stage_one(self, A, b, W):
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        W = _f64(W)
+        n, w = W.shape
+        b = _f64(b)
+        R = np.zeros((w, w))
+        what = np.zeros(w)
+        st = self.lib.orc_stage_one(n, _p(rp), _p(col), _p(val), _p(b), w, _p(W), _p(R), _p(what))
+        return what, R, st
+
+    # -- Algorithm 1 ----------------------------------------------------------------------
+    def aug_pcg(self, A, b, W, R, xhat0, tol_abs, kmax=100000, max_refine=5, p_cap=0):
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        n = len(rp) - 1
+        b = _f64(b)
+        if W is None:
+            W = np.zeros((n, 0), order="F")
+        W = _f64(W)
+        w = W.shape[1]
+        R = np.ascontiguousarray(R if R is not None else np.zeros((max(w, 1), max(w, 1))), dtype=np.float64)
+        xhat0 = _f64(xhat0 if xhat0 is not None else np.zeros(max(w, 1)))
+        x = np.empty(n)
+        info = _Info()
+        P = np.zeros((n, p_cap), order="F") if p_cap else None
+        g = np.zeros(p_cap) if p_cap else None
+        self.lib.orc_aug_pcg(n, _p(rp), _p(col), _p(val), _p(b), w, _p(W), _p(R), _p(xhat0),
+                             tol_abs, kmax, max_refine, _p(x), ctypes.byref(info), _p(P), _p(g), p_cap)
+        return x, _info_dict(info), P, g
+
+    def pcg(self, A, b, x0, tol_abs, kmax=100000):
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        n = len(rp) - 1
+        b = _f64(b)
+        x0 = _f64(x0) if x0 is not None else None
+        x = np.empty(n)
+        k = ctypes.c_int(0)
+        st = self.lib.orc_pcg(n, _p(rp), _p(col), _p(val), _p(b), _p(x0), tol_abs, kmax, _p(x), ctypes.byref(k))
+        return x, k.value, st
+
+    def solve_system(self, A, b, W, tol_rel, kmax=100000, max_refine=5, p_cap=0):
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        n = len(rp) - 1
+        b = _f64(b)
+        if W is None:
+            W = np.zeros((n, 0), order="F")
+        W = _f64(W)
+        x = np.empty(n)
+        info = _Info()
+        P = np.zeros((n, p_cap), order="F") if p_cap else None
+        g = np.zeros(p_cap) if p_cap else None
+        self.lib.orc_solve_system(n, _p(rp), _p(col), _p(val), _p(b), W.shape[1], _p(W), tol_rel,
+                                  kmax, max_refine, _p(x), ctypes.byref(info), _p(P), _p(g), p_cap)
+        return x, _info_dict(info), P, g
+
+
+def _info_dict(info: _Info) -> dict:
+    return {"status": STATUS.get(info.status, str(info.status)), "iters": info.iters,
+            "refinements": info.refinements, "w": info.w, "chol_failed": bool(info.chol_failed),
+            "stage1_relres": info.stage1_relres, "final_relres": info.final_relres,
+            "cond_gram": info.cond_gram}
+
+
+class OracleSequence:
+    """Sequence driver: POD of the last ``s_max`` solutions → stage one → Algorithm 1.
+
+    ``solve(A, b, tol)`` solves the next system and records its solution as a snapshot;
+    ``add_snapshot(x)`` records an externally supplied solution instead.
+    """
+
+    def __init__(self, n: int, s_max: int = 40, w_max: int = 32, energy: float = 0.9999,
+                 kmax: int = 100000, max_refine: int = 5, oracle: Oracle | None = None):
+        self.n, self.s_max, self.w_max, self.energy = n, s_max, w_max, energy
+        self.kmax, self.max_refine = kmax, max_refine
+        self.orc = oracle or Oracle()
+        self.snaps: list[np.ndarray] = []
+
+    def add_snapshot(self, x):
+        self.snaps.append(np.array(x, dtype=np.float64))
+        if len(self.snaps) > self.s_max:
+            self.snaps.pop(0)
+
+    def basis(self):
+        if not self.snaps:
+            return np.zeros((self.n, 0), order="F"), 0, np.zeros(0)
+        S = np.asfortranarray(np.stack(self.snaps, axis=1))
+        return self.orc.pod_evd(S, self.energy, self.w_max)
+
+    def solve(self, A, b, tol_rel, record: bool = True):
+        W, w, sig2 = self.basis()
+        x, info, _, _ = self.orc.solve_system(A, b, W, tol_rel, self.kmax, self.max_refine)
+        info["s"] = len(self.snaps)
+        if record:
+            self.add_snapshot(x)
+        return x, info

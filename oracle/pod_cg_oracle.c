@@ -1,0 +1,470 @@
+/*
+ * FP64 CPU oracle for POD-augmented conjugate gradient
+ * (Carlberg, Forstall & Tuminaro, "Krylov-subspace recycling via the
+ * POD-augmented conjugate-gradient method").
+ *
+ * TEST INFRASTRUCTURE, NOT PART OF THE LIBRARY. This is the plain, slow, obviously
+ * correct reference the GPU library is checked against. Only the test suite, the
+ * package smoke check and the benchmark's CPU-baseline leg load it. It shares no
+ * source, header, table or helper with the CUDA library, and includes nothing from it.
+ *
+ * Everything is double precision, single threaded, in the order the paper states the
+ * steps. Matrices are CSR with 32-bit indices (row_ptr[n+1], col[nnz], val[nnz],
+ * columns sorted within each row); dense n-by-k blocks are column-major (column j
+ * starts at j*n); small k-by-k matrices are row-major.
+ *
+ * Readings where the paper is silent (also listed in the design notes):
+ *  - stopping test: ||r||_2 <= tol_abs, tol_abs = tol_rel * ||b||_2, checked on r0 before
+ *    the loop and after every update; at exit the true residual b - A x is formed and,
+ *    if it is above tol_abs, the iteration restarts from it (residual replacement);
+ *  - POD with identity metric and unit weights; numerical rank = #{lambda_i > 1e-13 lambda_1};
+ *  - a Cholesky failure of W^T A W drops the basis for that system (plain PCG).
+ *
+ * Compile-time mistake planting: building with -DORC_MUTANT=k (k >= 1) plants one
+ * plausible mistake so the pin tests can show they catch it. The normal build has
+ * ORC_MUTANT = 0 and every MUT(k) is false.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
+#define MUT(k) (ORC_MUTANT == (k))
+
+enum { ORC_OK = 0, ORC_NOT_SPD = 2, ORC_BREAKDOWN = 3, ORC_MAXIT = 4, ORC_NONFINITE = 5, ORC_ARG = 1 };
+
+typedef struct {
+    int status;          /* ORC_* code */
+    int iters;           /* Algorithm 1 loop passes, summed over restarts */
+    int refinements;     /* residual-replacement restarts */
+    int w;               /* basis dimension actually used (0 after a Cholesky failure) */
+    int chol_failed;     /* 1 if W^T A W was not numerically SPD */
+    int pad_;
+    double stage1_relres;   /* ||b - A x0||/||b|| after stage one */
+    double final_relres;    /* ||b - A x||/||b|| at exit (true residual) */
+    double cond_gram;       /* lambda_max/lambda_min of W^T A W (Jacobi EVD), 0 if w = 0 */
+} orc_info;
+
+/* ---------------------------------------------------------------- basic linear algebra */
+
+/* y = A x (CSR). */
+void orc_spmv(int n, const int* rp, const int* ci, const double* va, const double* x, double* y)
+{
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int k = rp[i] + (MUT(10) ? 1 : 0); k < rp[i + 1]; ++k) s += va[k] * x[ci[k]];
+        y[i] = s;
+    }
+}
+
+double orc_dot(int n, const double* a, const double* b)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+/* G = X^T Y for column-major X (n x p) and Y (n x q); G row-major p x q. */
+void orc_gram(int n, int p, const double* X, int q, const double* Y, double* G)
+{
+    for (int a = 0; a < p; ++a)
+        for (int c = 0; c < q; ++c) G[a * q + c] = orc_dot(n, X + (size_t)a * n, Y + (size_t)c * n);
+}
+
+/* AW = A W, one column at a time (w matrix-vector products). */
+void orc_spmm(int n, const int* rp, const int* ci, const double* va, int w, const double* W, double* AW)
+{
+    for (int j = 0; j < w; ++j) orc_spmv(n, rp, ci, va, W + (size_t)j * n, AW + (size_t)j * n);
+}
+
+/* Upper Cholesky G = R^T R of a symmetric w x w matrix (row-major; only the upper
+ * triangle of G is read). Returns 0, or ORC_NOT_SPD if a pivot is not positive. */
+int orc_cholesky(int w, const double* G, double* R)
+{
+    memset(R, 0, sizeof(double) * (size_t)w * w);
+    for (int i = 0; i < w; ++i) {
+        double d = G[i * w + i];
+        for (int k = 0; k < i; ++k) d -= R[k * w + i] * R[k * w + i];
+        if (!(d > 0.0)) return ORC_NOT_SPD;
+        double rii = sqrt(d);
+        R[i * w + i] = rii;
+        for (int j = i + 1; j < w; ++j) {
+            double s = MUT(7) ? G[j * w + i] * 0.5 : G[i * w + j];
+            for (int k = 0; k < i; ++k) s -= R[k * w + i] * R[k * w + j];
+            R[i * w + j] = s / rii;
+        }
+    }
+    return ORC_OK;
+}
+
+/* Solve R^T R y = c (forward then backward substitution). */
+void orc_chol_solve(int w, const double* R, const double* c, double* y)
+{
+    double* t = (double*)malloc(sizeof(double) * (w > 0 ? w : 1));
+    for (int i = 0; i < w; ++i) {            /* R^T t = c */
+        double s = c[i];
+        for (int k = 0; k < i; ++k) s -= R[k * w + i] * t[k];
+        t[i] = s / R[i * w + i];
+    }
+    for (int i = w - 1; i >= 0; --i) {       /* R y = t */
+        double s = t[i];
+        for (int k = i + 1; k < w; ++k) s -= R[i * w + k] * y[k];
+        y[i] = s / R[i * w + i];
+    }
+    free(t);
+}
+
+/* Cyclic-by-row Jacobi eigensolver for a symmetric s x s matrix (Golub & Van Loan,
+ * "Matrix Computations", section 8.5: two-sided rotations chosen by the 2x2 symmetric
+ * Schur decomposition). G is row-major; on return evals[i] are the eigenvalues sorted in
+ * decreasing order and column i of the row-major V is the matching unit eigenvector,
+ * signed so that its entry of largest magnitude is positive. Returns the sweep count. */
+int orc_jacobi_eig(int s, const double* G, double* evals, double* V, int max_sweeps)
+{
+    double* A = (double*)malloc(sizeof(double) * (size_t)s * s + 8);
+    double* U = (double*)malloc(sizeof(double) * (size_t)s * s + 8);
+    memcpy(A, G, sizeof(double) * (size_t)s * s);
+    for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j) U[i * s + j] = (i == j) ? 1.0 : 0.0;
+    double fro = 0.0;
+    for (int i = 0; i < s * s; ++i) fro += A[i] * A[i];
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < s; ++i)
+            for (int j = 0; j < s; ++j)
+                if (i != j) off += A[i * s + j] * A[i * s + j];
+        if (off <= 1e-32 * fro || off == 0.0) break;
+        for (int p = 0; p < s - 1; ++p) {
+            for (int q = p + 1; q < s; ++q) {
+                double apq = A[p * s + q];
+                if (apq == 0.0) continue;
+                double theta = (A[q * s + q] - A[p * s + p]) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+                /* A <- J^T A J with J the rotation in the (p, q) plane */
+                for (int k = 0; k < s; ++k) {       /* columns p and q */
+                    double akp = A[k * s + p], akq = A[k * s + q];
+                    A[k * s + p] = c * akp - sn * akq;
+                    A[k * s + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < s; ++k) {       /* rows p and q */
+                    double apk = A[p * s + k], aqk = A[q * s + k];
+                    A[p * s + k] = c * apk - sn * aqk;
+                    A[q * s + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < s; ++k) {       /* V <- V J */
+                    double ukp = U[k * s + p], ukq = U[k * s + q];
+                    U[k * s + p] = c * ukp - sn * ukq;
+                    U[k * s + q] = (MUT(9) ? -sn : sn) * ukp + c * ukq;
+                }
+            }
+        }
+    }
+    /* sort by decreasing eigenvalue (selection sort keeps it obvious) */
+    int* order = (int*)malloc(sizeof(int) * (s > 0 ? s : 1));
+    for (int i = 0; i < s; ++i) order[i] = i;
+    for (int i = 0; i < s; ++i) {
+        int best = i;
+        for (int j = i + 1; j < s; ++j)
+            if (A[order[j] * s + order[j]] > A[order[best] * s + order[best]]) best = j;
+        int tmp = order[i]; order[i] = order[best]; order[best] = tmp;
+    }
+    for (int i = 0; i < s; ++i) {
+        int src = order[i];
+        evals[i] = A[src * s + src];
+        int arg = 0;
+        for (int k = 1; k < s; ++k)
+            if (fabs(U[k * s + src]) > fabs(U[arg * s + src])) arg = k;
+        double sg = U[arg * s + src] < 0.0 ? -1.0 : 1.0;
+        for (int k = 0; k < s; ++k) V[k * s + i] = sg * U[k * s + src];
+    }
+    free(order); free(U); free(A);
+    return sweep;
+}
+
+/* ------------------------------------------------------------------ POD (Algorithm 4) */
+
+/* POD by the eigenvalue decomposition (Appendix, Algorithm 4) with identity metric and
+ * unit weights, i.e. the basis of the POD definition (Section 3.1, eigenproblem
+ * S^T S V = V Sigma^2 and W = S [v_1/sigma_1 ... v_w/sigma_w]):
+ *   step 1  Kbar = S^T S
+ *   step 2  Kbar = V Sigma^2 V^T (symmetric EVD, decreasing eigenvalues)
+ *   step 3  w = min{ i <= rank(Kbar) : sum_{k<=i} sigma_k^2 / sum_l sigma_l^2 >= energy },
+ *           then capped at w_max
+ *   step 4  W = S [v_1/sigma_1 ... v_w/sigma_w]
+ * S is column-major n x s. W_out (column-major, room for w_max columns) receives the
+ * basis, sigma2_out (length s) all eigenvalues. Returns w. */
+int orc_pod_evd(int n, int s, const double* S, double energy, int w_max, double rank_tol,
+                double* W_out, double* sigma2_out)
+{
+    if (s <= 0) return 0;
+    double* K = (double*)malloc(sizeof(double) * (size_t)s * s);
+    double* V = (double*)malloc(sizeof(double) * (size_t)s * s);
+    orc_gram(n, s, S, s, S, K);                                  /* step 1 */
+    orc_jacobi_eig(s, K, sigma2_out, V, 60);                     /* step 2 */
+    double lam1 = sigma2_out[0];
+    int rank = 0;
+    if (lam1 > 0.0)
+        for (int i = 0; i < s; ++i)
+            if (sigma2_out[i] > rank_tol * lam1) rank = i + 1;
+    double total = 0.0;
+    for (int i = 0; i < s; ++i) total += (MUT(6) ? sqrt(fmax(sigma2_out[i], 0.0)) : fmax(sigma2_out[i], 0.0));
+    int w = rank;                                                /* step 3 */
+    double cum = 0.0;
+    for (int i = 0; i < rank; ++i) {
+        cum += MUT(6) ? sqrt(sigma2_out[i]) : sigma2_out[i];
+        if (cum / total >= energy) { w = i + 1; break; }
+    }
+    if (w > w_max) w = w_max;
+    for (int j = 0; j < w; ++j) {                                /* step 4 */
+        double inv_sigma = MUT(5) ? 1.0 : 1.0 / sqrt(sigma2_out[j]);
+        double* wj = W_out + (size_t)j * n;
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < s; ++k) acc += S[(size_t)k * n + i] * V[k * s + j];
+            wj[i] = acc * inv_sigma;
+        }
+    }
+    free(V); free(K);
+    return w;
+}
+
+/* ------------------------------------------------------------- stage one (Algorithm 2) */
+
+/* Direct reduced solve (Section 4.1, Algorithm 2) with initial guess xbar = 0:
+ *   Ahat = W^T A W, bhat = W^T b, Ahat = R^T R (Cholesky), Ahat what = bhat.
+ * W column-major n x w. R (w x w row-major upper) and what (w) are outputs.
+ * Returns ORC_OK or ORC_NOT_SPD when Ahat is not numerically SPD. */
+int orc_stage_one(int n, const int* rp, const int* ci, const double* va, const double* b,
+                  int w, const double* W, double* R, double* what)
+{
+    if (w <= 0) return ORC_OK;
+    double* AW = (double*)malloc(sizeof(double) * (size_t)n * w);
+    double* Ahat = (double*)malloc(sizeof(double) * (size_t)w * w);
+    double* bhat = (double*)malloc(sizeof(double) * (size_t)w);
+    orc_spmm(n, rp, ci, va, w, W, AW);
+    orc_gram(n, w, W, w, AW, Ahat);
+    for (int a = 0; a < w; ++a) bhat[a] = orc_dot(n, MUT(3) ? AW + (size_t)a * n : W + (size_t)a * n, b);
+    int st = orc_cholesky(w, Ahat, R);
+    if (st == ORC_OK) orc_chol_solve(w, R, bhat, what);
+    free(bhat); free(Ahat); free(AW);
+    return st;
+}
+
+/* ----------------------------------------------------- augmented PCG (Algorithm 1) */
+
+/* mu = (W^T A W)^{-1} W^T A z, with W^T A W = R^T R from stage one (Section 4.3 reuses the
+ * stage-one factor). The right-hand side is formed literally as W^T (A z). */
+static void orc_aug_component(int n, const int* rp, const int* ci, const double* va, int w,
+                              const double* W, const double* R, const double* z, double* Az,
+                              double* rhs, double* mu)
+{
+    if (w <= 0) return;
+    orc_spmv(n, rp, ci, va, z, Az);
+    for (int a = 0; a < w; ++a) rhs[a] = orc_dot(n, W + (size_t)a * n, Az);
+    orc_chol_solve(w, R, rhs, mu);
+}
+
+/* Augmented preconditioned CG (Section 2.2, Algorithm 1) with augmenting basis Y = W,
+ * preconditioner M = diag(A) (Jacobi) and initial reduced coordinates xhat0:
+ *   x0 = W xhat0, r0 = b - A x0, z0 = M^{-1} r0, solve W^T A W mu0 = W^T A z0, p0 = z0 - W mu0
+ *   loop: gamma = (A p, p), alpha = (r, z)/gamma, x += alpha p, r -= alpha A p,
+ *         z = M^{-1} r, beta = (r_new, z_new)/(r, z), solve W^T A W mu = W^T A z,
+ *         p = z + beta p - W mu, exit when ||r|| <= tol_abs.
+ * The residual test is also applied to r0 (zero iterations allowed). After the loop the
+ * true residual b - A x is formed; if it is above tol_abs the loop restarts from it
+ * (at most max_refine times). With w = 0 the W terms vanish and this is plain PCG.
+ * P_out (optional, column-major n x p_cap) receives the search directions p_k in the
+ * order used; gamma_out (optional, p_cap) the matching (A p_k, p_k).
+ * x (length n) is the output. Returns the status; info->iters counts loop passes. */
+int orc_aug_pcg(int n, const int* rp, const int* ci, const double* va, const double* b,
+                int w, const double* W, const double* R, const double* xhat0,
+                double tol_abs, int kmax, int max_refine, double* x, orc_info* info,
+                double* P_out, double* gamma_out, int p_cap)
+{
+    size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    double* r = (double*)malloc(nb);
+    double* z = (double*)malloc(nb);
+    double* p = (double*)malloc(nb);
+    double* Ap = (double*)malloc(nb);
+    double* Az = (double*)malloc(nb);
+    double* dinv = (double*)malloc(nb);
+    double* rhs = (double*)malloc(sizeof(double) * (w > 0 ? w : 1));
+    double* mu = (double*)malloc(sizeof(double) * (w > 0 ? w : 1));
+    int status = ORC_OK, iters = 0, refinements = 0;
+
+    for (int i = 0; i < n; ++i) {                     /* M = diag(A) */
+        double d = 0.0;
+        for (int k = rp[i]; k < rp[i + 1]; ++k)
+            if (ci[k] == i) d += va[k];
+        if (!(d > 0.0)) { status = ORC_NOT_SPD; goto done; }
+        dinv[i] = MUT(4) ? d : 1.0 / d;
+    }
+    for (int i = 0; i < n; ++i) x[i] = 0.0;           /* x0 = W xhat0 (xbar = 0) */
+    for (int a = 0; a < w; ++a)
+        for (int i = 0; i < n; ++i) x[i] += W[(size_t)a * n + i] * xhat0[a];
+    orc_spmv(n, rp, ci, va, x, Ap);                   /* r0 = b - A x0 */
+    for (int i = 0; i < n; ++i) r[i] = b[i] - Ap[i];
+
+    for (;;) {   /* one pass of Algorithm 1 from the current (true) residual r */
+        for (int i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+        orc_aug_component(n, rp, ci, va, w, W, R, z, Az, rhs, mu);
+        for (int i = 0; i < n; ++i) p[i] = z[i];
+        for (int a = 0; a < w; ++a)
+            for (int i = 0; i < n; ++i) p[i] -= W[(size_t)a * n + i] * mu[a];
+        double rz = orc_dot(n, r, z);
+        double rnorm = sqrt(orc_dot(n, r, r));
+        if (!isfinite(rnorm)) { status = ORC_NONFINITE; break; }
+        while (rnorm > tol_abs) {
+            if (iters >= kmax) { status = ORC_MAXIT; break; }
+            orc_spmv(n, rp, ci, va, p, Ap);
+            double gamma = orc_dot(n, Ap, p);
+            if (P_out && iters < p_cap) {
+                memcpy(P_out + (size_t)iters * n, p, nb);
+                if (gamma_out) gamma_out[iters] = gamma;
+            }
+            if (!isfinite(gamma)) { status = ORC_NONFINITE; break; }
+            if (!(gamma > 0.0)) { status = ORC_BREAKDOWN; break; }
+            double alpha = rz / gamma;
+            for (int i = 0; i < n; ++i) x[i] += alpha * p[i];
+            for (int i = 0; i < n; ++i) r[i] -= alpha * (MUT(8) ? p[i] : Ap[i]);
+            for (int i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+            double rz_new = orc_dot(n, r, z);
+            double beta = rz_new / rz;
+            orc_aug_component(n, rp, ci, va, w, W, R, z, Az, rhs, mu);
+            for (int i = 0; i < n; ++i) p[i] = z[i] + (MUT(1) ? 0.0 : beta) * p[i];
+            for (int a = 0; a < w; ++a)
+                for (int i = 0; i < n; ++i)
+                    p[i] += (MUT(2) ? 1.0 : -1.0) * W[(size_t)a * n + i] * mu[a];
+            rz = rz_new;
+            rnorm = sqrt(orc_dot(n, r, r));
+            ++iters;
+            if (!isfinite(rnorm)) { status = ORC_NONFINITE; break; }
+        }
+        if (status != ORC_OK) break;
+        orc_spmv(n, rp, ci, va, x, Ap);               /* true residual */
+        for (int i = 0; i < n; ++i) r[i] = b[i] - Ap[i];
+        if (sqrt(orc_dot(n, r, r)) <= tol_abs) break;
+        if (refinements >= max_refine) { status = ORC_MAXIT; break; }
+        ++refinements;                                /* residual replacement */
+    }
+done:
+    info->status = status;
+    info->iters = iters;
+    info->refinements = refinements;
+    free(mu); free(rhs); free(dinv); free(Az); free(Ap); free(p); free(z); free(r);
+    return status;
+}
+
+/* Plain Jacobi-preconditioned CG from x0 (Section 2.1, optimality (KrylovSolve)), written
+ * on its own so that Algorithm 1 with an empty basis can be checked against it. */
+int orc_pcg(int n, const int* rp, const int* ci, const double* va, const double* b,
+            const double* x0, double tol_abs, int kmax, double* x, int* iters_out)
+{
+    size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    double* r = (double*)malloc(nb);
+    double* z = (double*)malloc(nb);
+    double* p = (double*)malloc(nb);
+    double* q = (double*)malloc(nb);
+    double* dinv = (double*)malloc(nb);
+    int status = ORC_OK, k = 0;
+    for (int i = 0; i < n; ++i) x[i] = x0 ? x0[i] : 0.0;
+    orc_spmv(n, rp, ci, va, x, q);
+    for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    for (int i = 0; i < n; ++i) {                     /* M = diag(A) */
+        double d = 0.0;
+        for (int kk = rp[i]; kk < rp[i + 1]; ++kk)
+            if (ci[kk] == i) d += va[kk];
+        if (!(d > 0.0)) { status = ORC_NOT_SPD; goto out; }
+        dinv[i] = 1.0 / d;
+    }
+    for (int i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+    for (int i = 0; i < n; ++i) p[i] = z[i];
+    double rz = orc_dot(n, r, z);
+    while (sqrt(orc_dot(n, r, r)) > tol_abs) {
+        if (k >= kmax) { status = ORC_MAXIT; break; }
+        orc_spmv(n, rp, ci, va, p, q);
+        double pq = orc_dot(n, q, p);
+        if (!(pq > 0.0)) { status = ORC_BREAKDOWN; break; }
+        double alpha = rz / pq;
+        for (int i = 0; i < n; ++i) x[i] += alpha * p[i];
+        for (int i = 0; i < n; ++i) r[i] -= alpha * q[i];
+        for (int i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+        double rz_new = orc_dot(n, r, z);
+        double beta = rz_new / rz;
+        for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+        rz = rz_new;
+        ++k;
+    }
+out:
+    *iters_out = k;
+    free(dinv); free(q); free(p); free(z); free(r);
+    return status;
+}
+
+/* --------------------------------------------------------------- one system, end to end */
+
+/* Solve system j of the sequence (Section 2, (sequenceInexact)) with augmenting basis W:
+ * stage one (Algorithm 2) when w > 0, then Algorithm 1 started from the stage-one
+ * coordinates, with tol_abs = tol_rel ||b||_2. If W^T A W is not numerically SPD the basis
+ * is dropped for this system (info->chol_failed = 1) and plain PCG runs instead.
+ * cond_gram is the 2-norm condition number of W^T A W from the Jacobi eigensolver
+ * (the diagnostic of Section 5.2's reduced-matrix conditioning). */
+int orc_solve_system(int n, const int* rp, const int* ci, const double* va, const double* b,
+                     int w, const double* W, double tol_rel, int kmax, int max_refine,
+                     double* x, orc_info* info, double* P_out, double* gamma_out, int p_cap)
+{
+    memset(info, 0, sizeof(*info));
+    double bnorm = sqrt(orc_dot(n, b, b));
+    double tol_abs = tol_rel * bnorm;
+    double* R = (double*)malloc(sizeof(double) * (size_t)(w > 0 ? w * w : 1));
+    double* what = (double*)calloc((size_t)(w > 0 ? w : 1), sizeof(double));
+    int wu = w;
+    if (w > 0) {
+        int st = orc_stage_one(n, rp, ci, va, b, w, W, R, what);
+        if (st != ORC_OK) { info->chol_failed = 1; wu = 0; }
+        else {
+            double* AW = (double*)malloc(sizeof(double) * (size_t)n * w);
+            double* G = (double*)malloc(sizeof(double) * (size_t)w * w);
+            double* ev = (double*)malloc(sizeof(double) * (size_t)w);
+            double* V = (double*)malloc(sizeof(double) * (size_t)w * w);
+            orc_spmm(n, rp, ci, va, w, W, AW);
+            orc_gram(n, w, W, w, AW, G);
+            for (int a = 0; a < w; ++a)          /* symmetric part, upper triangle as read */
+                for (int c = 0; c < a; ++c) G[a * w + c] = G[c * w + a];
+            orc_jacobi_eig(w, G, ev, V, 60);
+            info->cond_gram = ev[w - 1] > 0.0 ? ev[0] / ev[w - 1] : INFINITY;
+            free(V); free(ev); free(G); free(AW);
+        }
+    }
+    info->w = wu;
+    /* stage-one residual */
+    {
+        double* x0 = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        double* r0 = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        for (int a = 0; a < wu; ++a)
+            for (int i = 0; i < n; ++i) x0[i] += W[(size_t)a * n + i] * what[a];
+        orc_spmv(n, rp, ci, va, x0, r0);
+        for (int i = 0; i < n; ++i) r0[i] = b[i] - r0[i];
+        info->stage1_relres = bnorm > 0.0 ? sqrt(orc_dot(n, r0, r0)) / bnorm : 0.0;
+        free(r0); free(x0);
+    }
+    int chol = info->chol_failed;
+    double cond = info->cond_gram, s1 = info->stage1_relres;
+    int st = orc_aug_pcg(n, rp, ci, va, b, wu, W, R, what, tol_abs, kmax, max_refine, x, info,
+                         P_out, gamma_out, p_cap);
+    info->chol_failed = chol; info->cond_gram = cond; info->stage1_relres = s1; info->w = wu;
+    {
+        double* q = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        orc_spmv(n, rp, ci, va, x, q);
+        double rr = 0.0;
+        for (int i = 0; i < n; ++i) rr += (b[i] - q[i]) * (b[i] - q[i]);
+        info->final_relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+        free(q);
+    }
+    free(what); free(R);
+    return st;
+}

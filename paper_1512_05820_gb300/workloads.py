@@ -1,0 +1,321 @@
+"""Seeded synthetic workloads: sequences of sparse SPD systems A_j x_j = b_j.
+
+This module only generates inputs (CSR matrices and right-hand sides). It holds none of
+the solver's arithmetic and is shared by the GPU path, the oracle-based tests and the
+benchmark. The paper's systems (Sierra/SolidMechanics exports, Section 5.1) are not
+available; these stand in for them with the shapes of the benchmark configurations:
+
+* ``diffusion2d_drift``   64x64 5-point variable-coefficient diffusion, 10 systems,
+  A_j = A_0 + diag(0.01 j u), drifting Gaussian-bump sources (w <= 8, FP64).
+* ``diffusion3d_moving``  128^3 7-point diffusion, 50 systems, log-coefficients
+  perturbed by 0.5% per step, a heat source moving on a circle (s <= 40, w <= 32).
+* ``diffusion3d_theta``   96^3 7-point diffusion parameterised by per-cell
+  log-coefficients theta (the differentiation workload), 20 systems.
+
+Discretisation (cell-centred finite volumes, unit spacing): the conductance of the face
+between cells a and b is the harmonic mean 2 k_a k_b / (k_a + k_b); every boundary face
+is a homogeneous Dirichlet face at half-cell distance with conductance 2 k_a. Row a of A
+holds the sum of its face conductances on the diagonal and -k_f for each neighbour.
+Cells are numbered x fastest, then y, then z; CSR columns are sorted within each row.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class CSR:
+    """CSR matrix with 32-bit indices (row_ptr[n+1], col[nnz]) and float64 values."""
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.row_ptr[-1])
+
+    def arrays(self):
+        return self.row_ptr, self.col, self.val
+
+    def todense(self) -> np.ndarray:
+        D = np.zeros((self.n, self.n))
+        rows = np.repeat(np.arange(self.n), np.diff(self.row_ptr))
+        np.add.at(D, (rows, self.col), self.val)
+        return D
+
+
+def _hm(a, b):
+    return 2.0 * a * b / (a + b)
+
+
+class DiffusionOperator:
+    """Sparsity pattern and value assembly of the 2D 5-point / 3D 7-point operator.
+
+    ``shape`` is (my, mx) or (mz, my, mx). The pattern is built once; ``values(k, d)``
+    assembles the CSR values for cell coefficients ``k`` (length n) plus an optional extra
+    diagonal ``d``.
+    """
+
+    def __init__(self, shape):
+        shape = tuple(int(s) for s in shape)
+        if len(shape) == 2:
+            shape = (1,) + shape
+        self.shape3 = shape
+        self.dim = 2 if shape[0] == 1 else 3
+        mz, my, mx = shape
+        n = mx * my * mz
+        self.n = n
+        iz, iy, ix = np.meshgrid(np.arange(mz), np.arange(my), np.arange(mx), indexing="ij")
+        ix, iy, iz = ix.ravel(), iy.ravel(), iz.ravel()
+        i = np.arange(n, dtype=np.int64)
+        # slots in ascending column order: z-1, y-1, x-1, self, x+1, y+1, z+1
+        steps = [mx * my, mx, 1]
+        valid = [iz > 0, iy > 0, ix > 0, np.ones(n, bool), ix < mx - 1, iy < my - 1, iz < mz - 1]
+        cols = [i - steps[0], i - steps[1], i - steps[2], i, i + steps[2], i + steps[1], i + steps[0]]
+        if self.dim == 2:
+            keep = [1, 2, 3, 4, 5]
+            valid = [valid[s] for s in keep]
+            cols = [cols[s] for s in keep]
+        self.slots = len(valid)
+        self.mask = np.stack(valid, axis=1)
+        colmat = np.stack(cols, axis=1)
+        self.col = colmat[self.mask].astype(np.int32)
+        counts = self.mask.sum(axis=1)
+        self.row_ptr = np.zeros(n + 1, dtype=np.int32)
+        np.cumsum(counts, out=self.row_ptr[1:])
+        self.nnz = int(self.row_ptr[-1])
+
+    def face_conductances(self, k):
+        """Interior face conductances per axis: (fx, fy, fz) on the face grids."""
+        K = np.asarray(k, dtype=np.float64).reshape(self.shape3)
+        fx = _hm(K[:, :, :-1], K[:, :, 1:])
+        fy = _hm(K[:, :-1, :], K[:, 1:, :])
+        fz = _hm(K[:-1, :, :], K[1:, :, :])
+        return fx, fy, fz
+
+    def values(self, k, extra_diag=None) -> np.ndarray:
+        K = np.asarray(k, dtype=np.float64).reshape(self.shape3)
+        fx, fy, fz = self.face_conductances(K)
+        mz, my, mx = self.shape3
+        diag = np.zeros(self.shape3)
+        diag[:, :, :-1] += fx
+        diag[:, :, 1:] += fx
+        diag[:, :, 0] += 2.0 * K[:, :, 0]
+        diag[:, :, -1] += 2.0 * K[:, :, -1]
+        diag[:, :-1, :] += fy
+        diag[:, 1:, :] += fy
+        diag[:, 0, :] += 2.0 * K[:, 0, :]
+        diag[:, -1, :] += 2.0 * K[:, -1, :]
+        if self.dim == 3:
+            diag[:-1, :, :] += fz
+            diag[1:, :, :] += fz
+            diag[0, :, :] += 2.0 * K[0, :, :]
+            diag[-1, :, :] += 2.0 * K[-1, :, :]
+        d = diag.ravel()
+        if extra_diag is not None:
+            d = d + np.asarray(extra_diag, dtype=np.float64)
+        n = self.n
+        V = np.zeros((n, 7))
+
+        def put(slot, arr, sl):
+            tmp = np.zeros(self.shape3)
+            tmp[sl] = -arr
+            V[:, slot] = tmp.ravel()
+
+        # each interior face couples its two cells; place -k_f in both rows
+        put(0, fz, (slice(1, None), slice(None), slice(None)))   # z-1 neighbour
+        put(1, fy, (slice(None), slice(1, None), slice(None)))   # y-1
+        put(2, fx, (slice(None), slice(None), slice(1, None)))   # x-1
+        V[:, 3] = d
+        put(4, fx, (slice(None), slice(None), slice(None, -1)))  # x+1
+        put(5, fy, (slice(None), slice(None, -1), slice(None)))  # y+1
+        put(6, fz, (slice(None, -1), slice(None), slice(None)))  # z+1
+        if self.dim == 2:
+            V = V[:, 1:6]
+        return V[self.mask]
+
+    def csr(self, k, extra_diag=None) -> CSR:
+        return CSR(self.n, self.row_ptr, self.col, self.values(k, extra_diag))
+
+    def gaussian(self, center, sigma, amplitude=1.0) -> np.ndarray:
+        """Gaussian bump sampled at cell indices; ``center`` is (x, y[, z]) in cell units."""
+        mz, my, mx = self.shape3
+        iz, iy, ix = np.meshgrid(np.arange(mz), np.arange(my), np.arange(mx), indexing="ij")
+        c = list(center) + [0.0] * (3 - len(center))
+        r2 = (ix - c[0]) ** 2 + (iy - c[1]) ** 2 + ((iz - c[2]) ** 2 if self.dim == 3 else 0.0)
+        return (amplitude * np.exp(-r2 / (2.0 * sigma * sigma))).ravel()
+
+
+@dataclass
+class Sequence:
+    """A sequence of systems sharing one sparsity pattern, plus its solver settings."""
+    name: str
+    op: DiffusionOperator
+    p: int
+    tol: float
+    s_max: int
+    w_max: int
+    energy: float
+    seed: int
+    recipe: dict = field(default_factory=dict)
+    _gen: object = None
+
+    @property
+    def n(self):
+        return self.op.n
+
+    @property
+    def nnz(self):
+        return self.op.nnz
+
+    @property
+    def row_ptr(self):
+        return self.op.row_ptr
+
+    @property
+    def col(self):
+        return self.op.col
+
+    def systems(self):
+        """Yield (j, val_j, b_j) for j = 1..p in order (values float64, length nnz / n)."""
+        return self._gen(self)
+
+    def all_systems(self):
+        return list(self.systems())
+
+
+def _drift2d_gen(seq: Sequence):
+    rng = np.random.default_rng(seq.seed)
+    n = seq.n
+    theta = rng.normal(0.0, seq.recipe["coef_sigma"], n)
+    u = rng.uniform(0.0, 1.0, n)
+    k = np.exp(theta)
+    my, mx = seq.op.shape3[1], seq.op.shape3[2]
+    for j in range(1, seq.p + 1):
+        val = seq.op.values(k, 0.01 * j * u)
+        cx = seq.recipe["x0"] + seq.recipe["drift"] * j
+        b = seq.op.gaussian((cx, my / 2.0), seq.recipe["sigma"])
+        yield j, val, b
+
+
+def diffusion2d_drift(m: int = 64, p: int = 10, seed: int = 1234, w_max: int = 8,
+                      s_max: int = 40, energy: float = 0.9999, tol: float = 1e-8) -> Sequence:
+    """2D 5-point diffusion on an m x m grid; lognormal(0, 0.5) cell coefficients,
+    A_j = A_0 + diag(0.01 j u) with u ~ U(0, 1), Gaussian bump (amplitude 1, sigma 3 cells)
+    centred at (m/4 + j, m/2), drifting one cell per system.
+
+    Random draws, in order, from ``numpy.random.default_rng(seed)``: theta ~ N(0, 0.5^2)
+    (n values), then u ~ U(0, 1) (n values)."""
+    op = DiffusionOperator((m, m))
+    recipe = {"coef_sigma": 0.5, "x0": m / 4.0, "drift": 1.0, "sigma": 3.0 * m / 64.0 if m < 64 else 3.0}
+    return Sequence("diffusion2d_drift", op, p, tol, s_max, w_max, energy, seed, recipe, _drift2d_gen)
+
+
+def _moving3d_gen(seq: Sequence):
+    rng = np.random.default_rng(seq.seed)
+    n = seq.n
+    r = seq.recipe
+    theta = rng.normal(0.0, r["coef_sigma"], n)
+    m = seq.op.shape3[2]
+    for j in range(1, seq.p + 1):
+        if j > 1:
+            xi = rng.normal(0.0, 1.0, n)
+            theta = theta + np.log1p(r["perturb"] * xi)
+        val = seq.op.values(np.exp(theta))
+        ang = 2.0 * np.pi * j / r["period"]
+        c = (m / 2.0 + m / 4.0 * np.cos(ang), m / 2.0 + m / 4.0 * np.sin(ang), m / 2.0)
+        b = seq.op.gaussian(c, r["sigma"])
+        yield j, val, b
+
+
+def diffusion3d_moving(m: int = 128, p: int = 50, seed: int = 1235, w_max: int = 32,
+                       s_max: int = 40, energy: float = 0.9999, tol: float = 1e-8,
+                       period: float | None = None) -> Sequence:
+    """3D 7-point diffusion on an m^3 grid; lognormal(0, 1) coefficients perturbed by
+    0.5% per system (theta <- theta + log(1 + 0.005 xi), xi ~ N(0, 1) per cell); a
+    Gaussian heat source (sigma 4 cells at m = 128, scaled with m) moving on the circle
+    (m/2 + m/4 cos(2 pi j/P), m/2 + m/4 sin(2 pi j/P), m/2) with P = 50.
+
+    Random draws, in order: theta_1 ~ N(0, 1) (n values); then for each j >= 2 one
+    xi ~ N(0, 1) draw of n values."""
+    op = DiffusionOperator((m, m, m))
+    recipe = {"coef_sigma": 1.0, "perturb": 0.005, "period": float(period or 50),
+              "sigma": max(1.5, 4.0 * m / 128.0)}
+    return Sequence("diffusion3d_moving", op, p, tol, s_max, w_max, energy, seed, recipe, _moving3d_gen)
+
+
+def _theta3d_gen(seq: Sequence):
+    r = seq.recipe
+    theta, u = r["theta"], r["u"]
+    m = seq.op.shape3[2]
+    k = np.exp(theta)
+    for j in range(1, seq.p + 1):
+        val = seq.op.values(k, 0.01 * j * u)
+        ang = 2.0 * np.pi * j / r["period"]
+        c = (m / 2.0 + m / 4.0 * np.cos(ang), m / 2.0 + m / 4.0 * np.sin(ang), m / 2.0)
+        b = seq.op.gaussian(c, r["sigma"])
+        yield j, val, b
+
+
+def diffusion3d_theta(m: int = 96, p: int = 20, seed: int = 1238, w_max: int = 32,
+                      s_max: int = 40, energy: float = 0.9999, tol: float = 1e-8,
+                      theta=None) -> Sequence:
+    """3D 7-point diffusion parameterised by per-cell log-coefficients theta
+    (k = exp(theta)), A_j(theta) = A(theta) + diag(0.01 j u), sources as in
+    ``diffusion3d_moving`` with period 50; loss L = sum_j c^T x_j with c ~ N(0, 1).
+
+    Random draws, in order: theta ~ N(0, 0.5^2) (n values), u ~ U(0, 1) (n values),
+    c ~ N(0, 1) (n values). ``theta`` may be given to override the drawn one."""
+    op = DiffusionOperator((m, m, m))
+    rng = np.random.default_rng(seed)
+    th = rng.normal(0.0, 0.5, op.n)
+    u = rng.uniform(0.0, 1.0, op.n)
+    c = rng.normal(0.0, 1.0, op.n)
+    recipe = {"theta": th if theta is None else np.asarray(theta, dtype=np.float64), "u": u, "c": c,
+              "period": 50.0, "sigma": max(1.5, 4.0 * m / 128.0)}
+    return Sequence("diffusion3d_theta", op, p, tol, s_max, w_max, energy, seed, recipe, _theta3d_gen)
+
+
+def random_spd_csr(n: int, density: float, seed: int, shift: float = 1.0, empty_rows: int = 0) -> CSR:
+    """Random sparse SPD matrix with ragged row lengths (symmetric pattern, strictly
+    diagonally dominant): used for edge-case tests (heavy-tailed rows, ``empty_rows``
+    rows holding only their diagonal)."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    lengths = np.minimum(n - 1, rng.zipf(1.6, n) * max(1, int(density * n)) // 4)
+    lengths[:empty_rows] = 0
+    for i in range(n):
+        if lengths[i] == 0:
+            continue
+        js = rng.choice(n, size=int(lengths[i]), replace=False)
+        js = js[js != i]
+        if empty_rows:
+            js = js[js >= empty_rows]
+        v = -rng.uniform(0.1, 1.0, len(js))
+        rows += [i] * len(js) + list(js)
+        cols += list(js) + [i] * len(js)
+        vals += list(v) + list(v)
+    rows = np.array(rows, dtype=np.int64)
+    cols = np.array(cols, dtype=np.int64)
+    vals = np.array(vals, dtype=np.float64)
+    # merge duplicates
+    key = rows * n + cols
+    uk, inv = np.unique(key, return_inverse=True)
+    acc = np.zeros(len(uk))
+    np.add.at(acc, inv, vals)
+    r_u, c_u = uk // n, uk % n
+    diag = np.zeros(n)
+    np.add.at(diag, r_u, np.abs(acc))
+    diag = diag + shift + rng.uniform(0.0, 1.0, n)
+    r_all = np.concatenate([r_u, np.arange(n)])
+    c_all = np.concatenate([c_u, np.arange(n)])
+    v_all = np.concatenate([acc, diag])
+    order = np.lexsort((c_all, r_all))
+    r_all, c_all, v_all = r_all[order], c_all[order], v_all[order]
+    row_ptr = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(row_ptr, r_all + 1, 1)
+    row_ptr = np.cumsum(row_ptr).astype(np.int32)
+    return CSR(n, row_ptr, c_all.astype(np.int32), v_all)

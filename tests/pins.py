@@ -1,0 +1,278 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each pin returns ``(ok, detail)`` so that the same checks serve two tests: against the
+normal oracle build every pin must hold, and against each build with a planted mistake
+(``-DORC_MUTANT=k``) at least one must fail. None of these re-types the oracle's own
+formula: they compare against dense LAPACK results (numpy), closed forms, invariants of
+the method (Galerkin orthogonality, A-orthogonality, optimality) and brute force.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_1512_05820_gb300.workloads import CSR, DiffusionOperator, random_spd_csr
+
+
+def dense_to_csr(D) -> CSR:
+    D = np.asarray(D, dtype=np.float64)
+    n = D.shape[0]
+    rp = [0]
+    cols, vals = [], []
+    for i in range(n):
+        nz = np.nonzero(D[i])[0]
+        cols += list(nz)
+        vals += list(D[i, nz])
+        rp.append(len(cols))
+    return CSR(n, np.array(rp, np.int32), np.array(cols, np.int32), np.array(vals))
+
+
+def small_diffusion(m=8, seed=0, dim=2):
+    rng = np.random.default_rng(seed)
+    op = DiffusionOperator((m,) * dim)
+    k = np.exp(rng.normal(0, 0.5, op.n))
+    return op.csr(k)
+
+
+def orth_basis(vectors):
+    Q, _ = np.linalg.qr(np.asarray(vectors).T if np.ndim(vectors) == 2 else vectors)
+    return np.asfortranarray(Q)
+
+
+def a_norm(D, v):
+    return float(np.sqrt(max(v @ (D @ v), 0.0)))
+
+
+# ---------------------------------------------------------------------------- pins
+
+
+def pin_spmv_dense(orc):
+    """y = A x against the dense product (ragged rows, diagonal-only rows)."""
+    A = random_spd_csr(60, 0.1, seed=3, empty_rows=4)
+    x = np.random.default_rng(1).normal(size=60)
+    y = orc.spmv(A.arrays(), x)
+    ref = A.todense() @ x
+    err = np.max(np.abs(y - ref)) / np.max(np.abs(ref))
+    return err < 1e-14, f"spmv rel err {err:.2e}"
+
+
+def pin_cholesky_numpy(orc):
+    """R^T R = G and R equals the transposed LAPACK lower factor; a non-SPD matrix fails."""
+    rng = np.random.default_rng(5)
+    B = rng.normal(size=(9, 9))
+    G = B @ B.T + 9 * np.eye(9)
+    R, st = orc.cholesky(G)
+    L = np.linalg.cholesky(G)
+    e1 = np.max(np.abs(R.T @ R - G)) / np.max(np.abs(G))
+    e2 = np.max(np.abs(R - L.T)) / np.max(np.abs(L))
+    G2 = G.copy()
+    G2[4, 4] = -1.0
+    _, st2 = orc.cholesky(G2)
+    y = orc.chol_solve(R, np.arange(9.0))
+    e3 = np.max(np.abs(G @ y - np.arange(9.0))) / 9.0
+    ok = st == 0 and e1 < 1e-14 and e2 < 1e-13 and st2 == 2 and e3 < 1e-12
+    return ok, f"chol st={st} recon {e1:.1e} vs lapack {e2:.1e} nonspd st={st2} solve {e3:.1e}"
+
+
+def pin_jacobi_closed_form(orc):
+    """Eigenvalues of the 1D Dirichlet Laplacian tridiag(-1, 2, -1) of order s are
+    2 - 2 cos(k pi/(s+1)); eigenvectors sin(i k pi/(s+1)) (closed form)."""
+    s = 12
+    T = 2 * np.eye(s) - np.eye(s, k=1) - np.eye(s, k=-1)
+    ev, V, sweeps = orc.jacobi_eig(T)
+    k = np.arange(1, s + 1)
+    ref = np.sort(2 - 2 * np.cos(k * np.pi / (s + 1)))[::-1]
+    e1 = np.max(np.abs(ev - ref))
+    # eigenvector for the largest eigenvalue (k = s): sin(i s pi/(s+1)), i = 1..s
+    i = np.arange(1, s + 1)
+    v = np.sin(i * s * np.pi / (s + 1))
+    v /= np.linalg.norm(v)
+    e2 = 1 - abs(v @ V[:, 0])
+    return e1 < 1e-13 and e2 < 1e-13, f"jacobi closed-form eig err {e1:.1e}, vec {e2:.1e}, sweeps {sweeps}"
+
+
+def pin_jacobi_vs_eigh(orc):
+    """Random symmetric matrix: eigenvalues match LAPACK eigh; G V = V diag(ev); V^T V = I;
+    largest-magnitude entry of every eigenvector is positive."""
+    rng = np.random.default_rng(11)
+    B = rng.normal(size=(20, 20))
+    G = B + B.T
+    ev, V, _ = orc.jacobi_eig(G)
+    ref = np.sort(np.linalg.eigvalsh(G))[::-1]
+    e1 = np.max(np.abs(ev - ref)) / np.max(np.abs(ref))
+    e2 = np.max(np.abs(G @ V - V * ev)) / np.max(np.abs(ref))
+    e3 = np.max(np.abs(V.T @ V - np.eye(20)))
+    sign_ok = all(V[np.argmax(np.abs(V[:, j])), j] > 0 for j in range(20))
+    return e1 < 1e-13 and e2 < 1e-12 and e3 < 1e-13 and sign_ok, \
+        f"eigh err {e1:.1e} resid {e2:.1e} orth {e3:.1e} sign {sign_ok}"
+
+
+def _snapshots(n=300, s=12, seed=2):
+    rng = np.random.default_rng(seed)
+    # decaying singular values so that the energy criterion bites
+    U, _ = np.linalg.qr(rng.normal(size=(n, s)))
+    V, _ = np.linalg.qr(rng.normal(size=(s, s)))
+    sig = 10.0 ** (-0.6 * np.arange(s))
+    return np.asfortranarray(U @ np.diag(sig) @ V.T), sig
+
+
+def pin_pod_svd(orc):
+    """POD (Section 3.1 / Algorithm 4, identity metric, unit weights):
+    eigenvalues of S^T S equal the squared singular values of S (LAPACK svd);
+    W^T W = I (Eq. podOrth with Theta = I); w is the smallest index whose energy fraction
+    reaches the criterion; Eckart-Young: sum_i ||s_i - W W^T s_i||^2 = sum_{k>w} sigma_k^2;
+    range(W) equals the span of the leading left singular vectors."""
+    S, _ = _snapshots()
+    energy = 0.9999
+    W, w, sig2 = orc.pod_evd(S, energy, 40)
+    U, sv, _ = np.linalg.svd(S, full_matrices=False)
+    e_sig = np.max(np.abs(sig2 - sv ** 2)) / sv[0] ** 2
+    frac = np.cumsum(sv ** 2) / np.sum(sv ** 2)
+    w_ref = int(np.argmax(frac >= energy)) + 1
+    e_orth = np.max(np.abs(W.T @ W - np.eye(w))) if w else 0.0
+    resid = S - W @ (W.T @ S)
+    ey = abs(np.sum(resid ** 2) - np.sum(sv[w:] ** 2)) / np.sum(sv ** 2)
+    cosines = np.linalg.svd(U[:, :w].T @ W, compute_uv=False) if w else np.ones(1)
+    ok = e_sig < 1e-13 and w == w_ref and e_orth < 1e-10 and ey < 1e-12 and cosines.min() > 1 - 1e-10
+    return ok, f"pod sig2 err {e_sig:.1e} w={w} ref={w_ref} orth {e_orth:.1e} EY {ey:.1e} cos {cosines.min():.12f}"
+
+
+def pin_pod_nested(orc):
+    """Nesting (Eq. podordering): the first w' columns do not depend on the cap w_max >= w'."""
+    S, _ = _snapshots(seed=4)
+    W8, w8, _ = orc.pod_evd(S, 1.0, 8)
+    W3, w3, _ = orc.pod_evd(S, 1.0, 3)
+    e = np.max(np.abs(W8[:, :w3] - W3))
+    return w3 == 3 and w8 == 8 and e < 1e-12, f"nesting w3={w3} w8={w8} err {e:.1e}"
+
+
+def pin_stage_one_exact(orc):
+    """If x* lies in range(W), the stage-one Galerkin solve (Algorithm 2) returns x*
+    (Section 4.1; the A-orthogonal projection of x* onto a space containing it is x*),
+    and the full solve needs zero Algorithm-1 iterations."""
+    A = small_diffusion(10, seed=1)
+    D = A.todense()
+    rng = np.random.default_rng(7)
+    xs = rng.normal(size=A.n)
+    b = D @ xs
+    W = orth_basis(np.stack([xs, rng.normal(size=A.n), rng.normal(size=A.n)]))
+    what, R, st = orc.stage_one(A.arrays(), b, W)
+    x1 = W @ what
+    e = np.linalg.norm(x1 - xs) / np.linalg.norm(xs)
+    x, info, _, _ = orc.solve_system(A.arrays(), b, W, 1e-10)
+    return st == 0 and e < 1e-12 and info["iters"] == 0, f"stage one exact err {e:.1e} iters {info['iters']}"
+
+
+def pin_stage_one_galerkin(orc):
+    """Galerkin orthogonality (Eq. equivalenceResidualOrth): W^T (b - A W what) = 0, and
+    the stage-one iterate is the A-orthogonal projection: equals the dense least-squares
+    solution of min ||A^{1/2}(x* - W y)||."""
+    A = small_diffusion(9, seed=2)
+    D = A.todense()
+    rng = np.random.default_rng(9)
+    b = rng.normal(size=A.n)
+    W = orth_basis(rng.normal(size=(5, A.n)))
+    what, R, st = orc.stage_one(A.arrays(), b, W)
+    r = b - D @ (W @ what)
+    e1 = np.max(np.abs(W.T @ r)) / np.linalg.norm(b)
+    xs = np.linalg.solve(D, b)
+    L = np.linalg.cholesky(D)
+    y_ref = np.linalg.lstsq(L.T @ W, L.T @ xs, rcond=None)[0]
+    e2 = np.max(np.abs(what - y_ref)) / np.max(np.abs(y_ref))
+    return st == 0 and e1 < 1e-13 and e2 < 1e-10, f"galerkin orth {e1:.1e} projection {e2:.1e}"
+
+
+def pin_empty_basis_is_pcg(orc):
+    """Algorithm 1 with an empty augmenting basis is plain PCG: bitwise equal iterate and
+    the same iteration count as the separately written PCG."""
+    A = small_diffusion(12, seed=3)
+    b = np.random.default_rng(4).normal(size=A.n)
+    tol = 1e-9 * np.linalg.norm(b)
+    x1, info, _, _ = orc.aug_pcg(A.arrays(), b, None, None, None, tol)
+    x2, k2, st2 = orc.pcg(A.arrays(), b, None, tol)
+    same = np.array_equal(x1, x2)
+    return same and info["iters"] == k2 and info["status"] == "ok", \
+        f"aug(W=0) vs pcg bitwise {same}, iters {info['iters']} vs {k2}"
+
+
+def _aug_problem(n_side=10, w=4, seed=5):
+    A = small_diffusion(n_side, seed=seed)
+    D = A.todense()
+    rng = np.random.default_rng(seed + 100)
+    xs = rng.normal(size=A.n)
+    b = D @ xs
+    # basis: POD-like vectors close to (but not containing) the solution
+    W = orth_basis(np.stack([xs + 0.3 * rng.normal(size=A.n) for _ in range(w)]))
+    return A, D, b, W
+
+
+def pin_dense_agreement(orc):
+    """Full solve at tol 1e-14 agrees with the dense direct solve in the A-norm."""
+    A, D, b, W = _aug_problem()
+    x, info, _, _ = orc.solve_system(A.arrays(), b, W, 1e-14)
+    xs = np.linalg.solve(D, b)
+    e = a_norm(D, x - xs) / a_norm(D, xs)
+    return info["status"] == "ok" and e < 1e-12, f"dense agreement {e:.1e} status {info['status']} iters {info['iters']}"
+
+
+def pin_a_orthogonality(orc):
+    """Directions stay A-orthogonal to W (Eq. Ajorthogonality: W^T A P = 0) and to each
+    other (P^T A P diagonal)."""
+    A, D, b, W = _aug_problem(seed=6)
+    x, info, P, g = orc.solve_system(A.arrays(), b, W, 1e-10, p_cap=400)
+    k = info["iters"]
+    P = P[:, :k]
+    AP = D @ P
+    pa = np.sqrt(np.einsum("ij,ij->j", P, AP))
+    wa = np.sqrt(np.einsum("ij,ij->j", W, D @ W))
+    e1 = np.max(np.abs(W.T @ AP) / np.outer(wa, pa)) if k else 0.0
+    C = (P.T @ AP) / np.outer(pa, pa)
+    off = C - np.diag(np.diag(C))
+    # loss of orthogonality in finite precision grows with k; check the first 15
+    e2 = np.max(np.abs(off[:15, :15])) if k else 0.0
+    e3 = np.max(np.abs(np.diag(P.T @ AP) - g[:k]) / g[:k]) if k else 0.0
+    return k > 5 and e1 < 1e-10 and e2 < 1e-8 and e3 < 1e-12, \
+        f"W^T A p {e1:.1e}, p_i^T A p_k {e2:.1e}, gamma {e3:.1e} (k={k})"
+
+
+def pin_optimality(orc):
+    """After k iterations the iterate minimises the A-norm error over
+    range(W) + span(p_0..p_{k-1}) (Eq. KrylovSolveAugment / Section 4.3's projection):
+    it equals the dense Galerkin solution on B = [W, P]."""
+    A, D, b, W = _aug_problem(n_side=12, seed=8)
+    x, info, P, g = orc.solve_system(A.arrays(), b, W, 1e-4, p_cap=400)
+    k = info["iters"]
+    B = np.concatenate([W, P[:, :k]], axis=1)
+    y = np.linalg.solve(B.T @ D @ B, B.T @ b)
+    xg = B @ y
+    e = a_norm(D, x - xg) / a_norm(D, xg)
+    return k >= 3 and e < 1e-9, f"optimality err {e:.1e} (k={k})"
+
+
+def pin_finite_termination(orc):
+    """CG terminates in at most as many steps as the preconditioned operator has distinct
+    eigenvalues. A symmetric circulant tridiagonal matrix of order 32 has a constant
+    diagonal (Jacobi = scaling) and 17 distinct eigenvalues a + 2 b cos(2 pi k/32)."""
+    n = 32
+    C = 4.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    C[0, -1] = C[-1, 0] = -1.0
+    A = dense_to_csr(C)
+    b = np.random.default_rng(1).normal(size=n)
+    x, info, _, _ = orc.aug_pcg(A.arrays(), b, None, None, None, 1e-11 * np.linalg.norm(b))
+    xs = np.linalg.solve(C, b)
+    e = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+    return info["iters"] <= 17 and e < 1e-10, f"finite termination iters {info['iters']} <= 17, err {e:.1e}"
+
+
+def pin_generator_2x2(orc=None):
+    """The 2x2 five-point operator with unit coefficients, assembled by hand: each cell has
+    two interior faces (conductance 1) and two Dirichlet faces (conductance 2)."""
+    op = DiffusionOperator((2, 2))
+    A = op.csr(np.ones(4)).todense()
+    ref = np.array([[6, -1, -1, 0], [-1, 6, 0, -1], [-1, 0, 6, -1], [0, -1, -1, 6]], float)
+    return np.array_equal(A, ref), "generator 2x2"
+
+
+ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
+            pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
+            pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
+            pin_finite_termination]
