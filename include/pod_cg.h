@@ -1,0 +1,193 @@
+/*
+ * pod_cg.h — C ABI of the GB300 (sm_103a) POD-augmented conjugate-gradient library.
+ *
+ * Method: K. Carlberg, V. Forstall, R. Tuminaro, "Krylov-subspace recycling via the
+ * POD-augmented conjugate-gradient method". A sequence of sparse SPD systems
+ * A_j x_j = b_j (Section 2, Eq. (sequence)) is solved to inexact tolerances
+ * ||b_j - A_j x_j||_2 <= tol ||b_j||_2 (Eq. (sequenceInexact), with a relative tolerance).
+ * For system j the library
+ *   1. computes a POD basis W_j of the retained snapshots (previous solutions) with the
+ *      eigenvalue route of Algorithm 4 (identity metric, unit weights): Gram S^T S,
+ *      symmetric eigensolve, energy truncation, lift W = S V Sigma^{-1};
+ *   2. stage one (Section 4.1, Algorithm 2): AW = A_j W, Ahat = W^T AW, Cholesky
+ *      Ahat = R^T R, Ahat what = W^T b, x0 = W what, r0 = b - AW what;
+ *   3. stage two (the paper's stage 3, Section 4.3, Algorithm 1 with Y = W): Jacobi-
+ *      preconditioned CG whose directions are A_j-orthogonalised against W through
+ *      mu = R^{-1} R^{-T} (AW)^T z and p = z + beta p - W mu.
+ * Every step runs in hand-written CUDA kernels; this header is the only interface.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments marked "device" are device pointers in the current CUDA context,
+ *    borrowed for the duration of the call (the library never frees them and keeps no
+ *    reference after the call returns). Arguments marked "host" are host pointers.
+ *  - CSR matrices use 32-bit indices: row_ptr[n+1], col[nnz] (sorted within each row,
+ *    diagonal present), val[nnz] float64; nnz < 2^31.
+ *  - n-by-k dense blocks are column-major with leading dimension n (column j starts at
+ *    element j*n). Small k-by-k matrices are row-major.
+ *  - Work is ordered on the CUDA stream given at creation (or per call for the stateless
+ *    step functions; NULL = the legacy default stream). Handle calls synchronise that
+ *    stream before returning, so host outputs (stats, w) are valid on return.
+ *  - Every function returns a pod_cg_status. On failure a message is available from
+ *    pod_cg_last_error(handle) (or pod_cg_last_error(NULL) for stateless calls); the
+ *    handle stays usable and solution outputs hold the best iterate reached.
+ */
+#ifndef POD_CG_H
+#define POD_CG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pod_cg_t pod_cg_t;
+
+typedef enum {
+    POD_CG_OK = 0,
+    POD_CG_ERR_ARG = 1,        /* invalid argument (sizes, NULL pointers, bad config) */
+    POD_CG_ERR_NOT_SPD = 2,    /* non-positive Jacobi diagonal */
+    POD_CG_ERR_BREAKDOWN = 3,  /* (A p, p) <= 0 during CG: matrix not SPD */
+    POD_CG_ERR_MAXIT = 4,      /* iteration or refinement cap reached above tolerance */
+    POD_CG_ERR_NONFINITE = 5,  /* NaN/Inf in a scalar of the iteration */
+    POD_CG_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+    POD_CG_ERR_TIMEOUT = 7,    /* a bounded device wait expired */
+    POD_CG_ERR_OOM = 8,        /* device allocation failed */
+    POD_CG_ERR_STATE = 9       /* call not valid in the handle's state (e.g. evicted system) */
+} pod_cg_status;
+
+enum { POD_CG_FP64 = 0, POD_CG_MIXED = 1 };
+
+/* Solver settings. Fill with pod_cg_config_default() and override fields. */
+typedef struct {
+    int    w_max;        /* cap on the POD basis dimension w (1..64) */
+    int    s_max;        /* snapshot window: the last s_max added snapshots are kept (1..64) */
+    double energy;       /* POD energy criterion (Algorithm 4 step 3), e.g. 0.9999 */
+    double rank_tol;     /* eigenvalues <= rank_tol * lambda_1 count as rank deficient (1e-13) */
+    int    k_max;        /* cap on CG iterations per solve, summed over restarts */
+    int    max_refine;   /* FP64: residual-replacement restarts; MIXED: FP64 refinement steps */
+    int    precision;    /* POD_CG_FP64, or POD_CG_MIXED (FP32 inner CG, FP64 refinement) */
+    double inner_tol;    /* MIXED: each inner solve reduces its residual by this factor */
+    int    use_tc_gram;  /* MIXED: stage-one Gram on tensor cores with split products */
+    int    cond_diag;    /* 1: compute cond_2(W^T A W) per solve (diagnostic, Section 5.2) */
+    int    keep_factors; /* systems whose W, AW, R are kept for pod_cg_solve_adjoint (0..) */
+} pod_cg_config;
+
+/* CSR matrix, device arrays, borrowed. */
+typedef struct {
+    int            n;
+    int64_t        nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const double*  val;
+} pod_cg_csr;
+
+/* Per-solve statistics (host). The paper's measures (Section 5.1): matrix-vector
+ * products, preconditioner applications (= stage-two iterations) and wall time. */
+typedef struct {
+    int    status;          /* pod_cg_status of the solve */
+    int    iters;           /* stage-two CG iterations (all restarts / inner solves) */
+    int    refinements;     /* FP64: residual-replacement restarts; MIXED: outer steps */
+    int    w;               /* POD basis dimension used (0 = plain PCG) */
+    int    s;               /* snapshots available */
+    int    chol_failed;     /* 1 if W^T A W was not numerically SPD (basis dropped) */
+    int    system_id;       /* id of this solve for pod_cg_solve_adjoint */
+    int    spmv_count;      /* sparse products: iters + w (stage one) + true-residual products */
+    double stage1_relres;   /* ||b - A x0||/||b|| after stage one */
+    double final_relres;    /* ||b - A x||/||b|| at exit, from an FP64 product */
+    double cond_gram;       /* cond_2(W^T A W) when cond_diag = 1, else 0 */
+    float  ms_pod;          /* device time of the POD update (eigensolve + lift) */
+    float  ms_stage1;       /* device time of stage one */
+    float  ms_stage2;       /* device time of the CG iteration */
+} pod_cg_stats;
+
+/* ------------------------------------------------------------------ handle lifecycle */
+
+/* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
+ * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0. */
+pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
+
+/* Create a solver for systems of order n (the problem statement of Section 2) whose work
+ * is ordered on `cuda_stream` (a cudaStream_t; NULL = legacy default stream). The handle
+ * owns the snapshot ring (s_max columns of n), the basis W and AW (w_max columns each),
+ * the stage-one factor and all CG vectors. Errors: ERR_ARG (n < 1, bad config), ERR_OOM. */
+pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg /* host, NULL = defaults */,
+                            void* cuda_stream, pod_cg_t** out /* host, out */);
+
+/* Release everything the handle owns. NULL is accepted. */
+pod_cg_status pod_cg_destroy(pod_cg_t* h);
+
+/* Message of the last failure on this handle (NULL: of the last stateless call on this
+ * thread). The string stays valid until the next call on the same handle/thread. */
+const char* pod_cg_last_error(const pod_cg_t* h);
+
+/* ---------------------------------------------------------------------- the sequence */
+
+/* Append m snapshots (columns of X, device, n-by-m column-major) to the snapshot set S
+ * (Section 3.1; here previous solutions, identity metric, unit weights). Once s_max
+ * snapshots are held the oldest is replaced. Updates the snapshot Gram S^T S by the new
+ * rows (Algorithm 4 step 1). Errors: ERR_ARG. */
+pod_cg_status pod_cg_add_snapshots(pod_cg_t* h, const double* X, int m);
+
+/* Forget all snapshots (the next solve is plain Jacobi PCG). */
+pod_cg_status pod_cg_clear_snapshots(pod_cg_t* h);
+
+/* Solve A x = b to ||b - A x||_2 <= tol ||b||_2 (Eq. (sequenceInexact)) with the
+ * POD-augmented method: POD of the current snapshots (Algorithm 4), stage one
+ * (Algorithm 2) and augmented PCG (Algorithm 1, Y = W), then a true-residual check in
+ * FP64 with residual replacement (FP64 mode) or FP64 iterative refinement around FP32
+ * inner solves (MIXED). A: device CSR of order n; b, x_out: device, length n (x_out is
+ * written, caller-owned; it may not alias b). st: host, may be NULL.
+ * Errors: ERR_ARG, ERR_NOT_SPD, ERR_BREAKDOWN, ERR_MAXIT, ERR_NONFINITE (x_out then holds
+ * the last iterate), ERR_CUDA. */
+pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, double tol,
+                           double* x_out, pod_cg_stats* st);
+
+/* Adjoint solve for a loss L(x_j): lambda = A_j^{-1} g (A_j symmetric, so A_j^{-T} = A_j^{-1}),
+ * by the same POD-augmented method reusing the basis W_j, A_j W_j and the stage-one factor
+ * R_j saved by the forward solve whose stats reported `system_id` (requires
+ * keep_factors > 0 and that the system is among the last keep_factors solves).
+ * A: the same matrix as that forward solve. g, lambda_out: device, length n.
+ * Errors: as pod_cg_solve, plus ERR_STATE when the factors were not kept. */
+pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr* A,
+                                   const double* g, double tol, double* lambda_out,
+                                   pod_cg_stats* st);
+
+/* Copy the basis W used by the last solve (device out, n-by-w column-major, room for
+ * w_max columns) and its dimension (host out). */
+pod_cg_status pod_cg_get_basis(pod_cg_t* h, double* W_out, int* w_out);
+
+/* ------------------------------------------------------ stateless steps of the path */
+
+/* y = A x (the product of Algorithm 1's gamma = (A p, p)); x, y device length n. */
+pod_cg_status pod_cg_spmv(const pod_cg_csr* A, const double* x, double* y, void* cuda_stream);
+
+/* AW = A W for a device n-by-w column-major W (the w products of Section 4's stage-one
+ * cost estimate). AW device n-by-w. */
+pod_cg_status pod_cg_spmm(const pod_cg_csr* A, const double* W, int w, double* AW,
+                          void* cuda_stream);
+
+/* Bytes of device workspace pod_cg_gram needs for an n-row, p-by-q product. */
+size_t pod_cg_gram_workspace(int n, int p, int q);
+
+/* G = X^T Y for device X (n-by-p) and Y (n-by-q), column-major; G device row-major p-by-q.
+ * This is the snapshot Gram S^T S (Algorithm 4 step 1) and the reduced matrix W^T (A W)
+ * (Algorithm 2 step 1). p, q <= 65. work: device, at least pod_cg_gram_workspace(n,p,q)
+ * bytes, caller-owned scratch (contents on return are unspecified). */
+pod_cg_status pod_cg_gram(int n, const double* X, int p, const double* Y, int q, double* G,
+                          void* work, size_t work_bytes, void* cuda_stream);
+
+/* POD by Algorithm 4 (identity metric, unit weights) of the device snapshot block S
+ * (n-by-s, column-major, s <= 64): symmetric Jacobi eigensolve of S^T S, eigenvalues in
+ * decreasing order, w = smallest index within the numerical rank whose energy fraction
+ * reaches `energy`, capped at w_max; W_out (device, n-by-w_max room) = S V_w Sigma_w^{-1};
+ * sigma2_out (device, s) = all eigenvalues; w_out (host). work as for pod_cg_gram with
+ * p = q = s. */
+pod_cg_status pod_cg_pod(int n, int s, const double* S, double energy, double rank_tol,
+                         int w_max, double* W_out, double* sigma2_out, int* w_out,
+                         void* work, size_t work_bytes, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* POD_CG_H */

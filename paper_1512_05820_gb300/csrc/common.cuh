@@ -1,0 +1,118 @@
+// Device-side helpers shared by the kernels of the POD-augmented CG library.
+//
+// Reductions are deterministic: each block reduces in a fixed shuffle/shared-memory
+// order, writes one partial per value, and the last block to finish (found with one
+// atomic ticket, no waiting) sums the partials in block order. Results are therefore
+// identical from run to run for a given launch shape; no floating-point atomics are used.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace podcg {
+
+constexpr int kBlock = 256;             // threads per block of every streaming kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kWMax = 64;               // largest basis dimension (w) supported
+constexpr int kSMax = 64;               // largest snapshot window (s) supported
+
+// Scalars of the iteration, resident in device memory for the whole solve so the loop
+// needs no host round trip. One instance per solve in flight.
+struct DevState {
+    double rho;        // (r, z)
+    double gamma;      // (A p, p)
+    double alpha, beta;
+    double rr;         // ||r||^2 of the recursive residual
+    double bb;         // ||b||^2
+    double tol2;       // (tol * ||b||)^2: the outer (true-residual) test
+    double tol2_in;    // the inner loop's test on the recursive residual
+    double rr_true;    // ||b - A x||^2 from the last true-residual product
+    double rr_stage1;  // ||b - A x0||^2 after stage one
+    double rr_outer;   // mixed precision: ||r||^2 of the current outer residual
+    double cond;       // cond_2(W^T A W) diagnostic
+    double mu[kWMax];  // reduced coordinates of the A-orthogonalisation (Algorithm 1)
+    double what[kWMax];// stage-one reduced solution
+    int w;             // basis dimension in use (0 = plain PCG)
+    int iters;         // CG iterations so far (all passes)
+    int k_max;
+    int restarts;      // residual replacements (FP64) / outer refinement steps (mixed)
+    int max_refine;
+    int status;        // pod_cg_status code
+    int done;          // inner loop finished
+    int chol_failed;
+    int pod_w;         // w chosen by the POD (before a possible Cholesky failure)
+    int outer_done;
+    int inner_iters;   // mixed precision: iterations of the current inner solve
+    int pad_;
+};
+
+// Borrowed problem pointers of the current solve, read by the kernels of a captured
+// graph so the graph can be replayed for every system of a sequence.
+struct ProbDesc {
+    const int32_t* rp;
+    const int32_t* col;
+    const double* val;
+    const float* val32;
+    const double* b;
+    double* x;
+    int n;
+    int ld;            // leading dimension of the n-by-k blocks (W, AW, S)
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-reduce acc[0..nv) (nv uniform over the grid, nv <= NV), store one partial per
+// block, and return true in the last block to finish, which then holds the grid totals
+// in s_tot[0..nv). Every thread of every block must call this exactly once per launch.
+// `counter` must be 0 on entry; the last block resets it.
+template <int NV>
+__device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], int nv,
+                                                     double* __restrict__ partials,
+                                                     unsigned int* counter, double* s_tot)
+{
+    __shared__ double s_w[kWarps][NV];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        if (v < nv) {
+            double t = warp_sum(acc[v]);
+            if (lane == 0) s_w[wid][v] = t;
+        }
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < kWarps; ++k) t += s_w[k][v];
+        partials[(size_t)blockIdx.x * NV + v] = t;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int ticket = atomicAdd(counter, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    for (int v = wid; v < nv; v += kWarps) {
+        double t = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&partials[(size_t)b * NV + v]);
+        t = warp_sum(t);
+        if (lane == 0) s_tot[v] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+}  // namespace podcg

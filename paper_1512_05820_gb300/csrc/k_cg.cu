@@ -1,0 +1,195 @@
+// Kernels of the augmented PCG iteration (Section 2.2, Algorithm 1 with Y = W and
+// M = diag(A)), in FP64 or FP32 (T), for a basis of at most WB columns (w <= WB read from
+// the device state so one captured graph serves every w of its bucket).
+//
+// One iteration is three launches:
+//   k_spmv_cg : q = A p, gamma = (q, p), alpha = (r, z)/gamma            (k_sparse.cu)
+//   k_update  : r -= alpha q, z = M^{-1} r, (r, z), ||r||^2, c = (A W)^T z;
+//               last block: beta, mu = R^{-1} R^{-T} c (stage-one factor reused,
+//               Section 4.3), iteration count, exit test -> graph condition
+//   k_dir     : x += alpha p, p = z + beta p - W mu  (z recomputed from r, never stored)
+// (A W)^T z equals the paper's W^T A z because A is symmetric.
+#include "common.cuh"
+#include "launch.h"
+
+namespace podcg {
+
+// mu = R^{-1} (R^{-T} c) for c in s_c[0..w) (shared), R^{-1} upper with row stride kWMax.
+__device__ __forceinline__ void apply_rinv(const double* __restrict__ Rinv, const double* s_c, double* s_t,
+                                           int w, double* mu_out)
+{
+    for (int a = threadIdx.x; a < w; a += blockDim.x) {
+        double v = 0.0;
+        for (int k = 0; k <= a; ++k) v += Rinv[k * kWMax + a] * s_c[k];
+        s_t[a] = v;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < w; a += blockDim.x) {
+        double v = 0.0;
+        for (int k = a; k < w; ++k) v += Rinv[a * kWMax + k] * s_t[k];
+        mu_out[a] = v;
+    }
+    __syncthreads();
+}
+
+// Start of a CG pass from the residual r: z0 = M^{-1} r, (r, z0), ||r||^2, c = (A W)^T z0,
+// mu0; the residual test on r0 (zero iterations allowed).
+template <int WB, typename T>
+__global__ void __launch_bounds__(kBlock) k_init(int n, int ld, const T* __restrict__ r, const T* __restrict__ dinv,
+                                                 const T* __restrict__ AW, const double* __restrict__ Rinv,
+                                                 double* __restrict__ partials, unsigned int* counter, DevState* st,
+                                                 cudaGraphConditionalHandle h_inner, int use_cond)
+{
+    const int w = st->w;
+    double acc[WB + 2];
+    T cl[WB > 0 ? WB : 1];
+#pragma unroll
+    for (int j = 0; j < WB; ++j) cl[j] = T(0);
+    T rho = T(0), rr = T(0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const T ri = r[i];
+        const T zi = dinv[i] * ri;
+        rho += ri * zi;
+        rr += ri * ri;
+#pragma unroll
+        for (int j = 0; j < WB; ++j)
+            if (j < w) cl[j] += __ldg(AW + (size_t)j * ld + i) * zi;
+    }
+    acc[0] = double(rho);
+    acc[1] = double(rr);
+#pragma unroll
+    for (int j = 0; j < WB; ++j) acc[2 + j] = double(cl[j]);
+    __shared__ double tot[WB + 2];
+    __shared__ double s_t[WB > 0 ? WB : 1];
+    if (reduce_to_last_block<WB + 2>(acc, 2 + w, partials, counter, tot)) {
+        apply_rinv(Rinv, tot + 2, s_t, w, st->mu);
+        if (threadIdx.x == 0) {
+            st->rho = tot[0];
+            st->rr = tot[1];
+            st->alpha = 0.0;
+            st->beta = 0.0;
+            if (st->status == 0 && !(isfinite(tot[0]) && isfinite(tot[1]))) st->status = 5;
+            const int done = (st->status != 0) || !(tot[1] > st->tol2_in);
+            st->done = done;
+            st->inner_iters = 0;
+            if (use_cond) cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+        }
+    }
+}
+
+template <int WB, typename T>
+__global__ void __launch_bounds__(kBlock) k_update(int n, int ld, T* __restrict__ r, const T* __restrict__ q,
+                                                   const T* __restrict__ dinv, const T* __restrict__ AW,
+                                                   const double* __restrict__ Rinv, double* __restrict__ partials,
+                                                   unsigned int* counter, DevState* st,
+                                                   cudaGraphConditionalHandle h_inner, int use_cond)
+{
+    const int w = st->w;
+    const T alpha = (st->status == 0) ? T(st->alpha) : T(0);
+    T cl[WB > 0 ? WB : 1];
+#pragma unroll
+    for (int j = 0; j < WB; ++j) cl[j] = T(0);
+    T rho = T(0), rr = T(0);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const T ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        const T zi = dinv[i] * ri;
+        rho += ri * zi;
+        rr += ri * ri;
+#pragma unroll
+        for (int j = 0; j < WB; ++j)
+            if (j < w) cl[j] += __ldg(AW + (size_t)j * ld + i) * zi;
+    }
+    double acc[WB + 2];
+    acc[0] = double(rho);
+    acc[1] = double(rr);
+#pragma unroll
+    for (int j = 0; j < WB; ++j) acc[2 + j] = double(cl[j]);
+    __shared__ double tot[WB + 2];
+    __shared__ double s_t[WB > 0 ? WB : 1];
+    if (reduce_to_last_block<WB + 2>(acc, 2 + w, partials, counter, tot)) {
+        apply_rinv(Rinv, tot + 2, s_t, w, st->mu);
+        if (threadIdx.x == 0) {
+            const double rho_new = tot[0];
+            st->beta = rho_new / st->rho;
+            st->rho = rho_new;
+            st->rr = tot[1];
+            st->iters += 1;
+            st->inner_iters += 1;
+            if (st->status == 0 && !(isfinite(rho_new) && isfinite(tot[1]))) st->status = 5;
+            int done = (st->status != 0) || !(tot[1] > st->tol2_in);
+            if (!done && st->iters >= st->k_max) {
+                st->status = 4;
+                done = 1;
+            }
+            st->done = done;
+            if (use_cond) cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+        }
+    }
+}
+
+// x += alpha p; then (unless the pass has finished) p = z + beta p - W mu with z = M^{-1} r.
+// FIRST: the initial direction p0 = z0 - W mu0 (x untouched).
+template <int WB, typename T, bool FIRST>
+__global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x, T* __restrict__ p,
+                                                const T* __restrict__ r, const T* __restrict__ dinv,
+                                                const T* __restrict__ W, const DevState* st)
+{
+    const int w = st->w;
+    const bool ok = st->status == 0;
+    const T alpha = ok ? T(st->alpha) : T(0);
+    const T beta = T(st->beta);
+    const bool upd_p = FIRST || (!st->done && ok);
+    __shared__ T s_mu[WB > 0 ? WB : 1];
+    for (int j = threadIdx.x; j < WB; j += blockDim.x) s_mu[j] = (j < w) ? T(st->mu[j]) : T(0);
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const T pi = p[i];
+        if (!FIRST) x[i] += alpha * pi;
+        if (upd_p) {
+            T v = dinv[i] * r[i];
+            if (!FIRST) v += beta * pi;
+#pragma unroll
+            for (int j = 0; j < WB; ++j)
+                if (j < w) v -= __ldg(W + (size_t)j * ld + i) * s_mu[j];
+            p[i] = v;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ kernel pointers
+
+template <typename T>
+static void pick(int wb, void** init, void** upd, void** dir0, void** dir)
+{
+#define PODCG_PICK(WW)                                   \
+    *init = (void*)k_init<WW, T>;                        \
+    *upd = (void*)k_update<WW, T>;                       \
+    *dir0 = (void*)k_dir<WW, T, true>;                   \
+    *dir = (void*)k_dir<WW, T, false>;
+    if (wb <= 0) { PODCG_PICK(0) }
+    else if (wb <= 8) { PODCG_PICK(8) }
+    else if (wb <= 16) { PODCG_PICK(16) }
+    else if (wb <= 32) { PODCG_PICK(32) }
+    else if (wb <= 48) { PODCG_PICK(48) }
+    else { PODCG_PICK(64) }
+#undef PODCG_PICK
+}
+
+void cg_kernels(int wb, bool fp32, void** init, void** upd, void** dir0, void** dir)
+{
+    if (fp32) pick<float>(wb, init, upd, dir0, dir);
+    else pick<double>(wb, init, upd, dir0, dir);
+}
+
+int wb_bucket(int w)
+{
+    if (w <= 0) return 0;
+    if (w <= 8) return 8;
+    if (w <= 16) return 16;
+    if (w <= 32) return 32;
+    if (w <= 48) return 48;
+    return 64;
+}
+
+}  // namespace podcg

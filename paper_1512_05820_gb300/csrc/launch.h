@@ -1,0 +1,49 @@
+// Internal host-side launchers and kernel pointers (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace podcg {
+
+struct DevState;
+struct ProbDesc;
+
+int grid_rows(int rows, int per_block, int sms);
+int spmv_lanes_for(double mean_row);
+int wb_bucket(int w);
+
+// sparse
+cudaError_t launch_spmv_plain(int L, const int32_t* rp, const int32_t* col, const double* val, const double* x,
+                              double* y, int n, int sms, cudaStream_t s);
+void* kernel_spmv_cg(int L, bool fp32);
+void* kernel_residual(int L);
+cudaError_t launch_spmm(const int32_t* rp, const int32_t* col, const double* val, const double* W, int ldw,
+                        double* AW, int lda, int n, int w, int sms, cudaStream_t s);
+cudaError_t launch_spmm_f32(const int32_t* rp, const int32_t* col, const float* val, const float* W, int ldw,
+                            float* AW, int lda, int n, int w, int sms, cudaStream_t s);
+cudaError_t launch_dinv(const ProbDesc* pd, int n, double* dinv, float* dinv32, DevState* st, int sms,
+                        cudaStream_t s);
+cudaError_t launch_to_f32(const double* a, float* b, size_t m, int sms, cudaStream_t s);
+cudaError_t launch_desc_val_to_f32(const ProbDesc* pd, float* v32, int64_t nnz, int sms, cudaStream_t s);
+
+// dense
+size_t gram_workspace_bytes(int n, int p, int q, int sms);
+cudaError_t launch_gram(int n, const double* X, int ldx, int p, const double* Y, int ldy, int qy,
+                        const double* extra, double* G, int ldg, int upper_only, double* work,
+                        size_t work_bytes, int sms, cudaStream_t s);
+cudaError_t launch_lift(int n, const double* S, int lds, int s, const double* C, const DevState* st,
+                        double* W, int ldw, int sms, cudaStream_t str);
+cudaError_t launch_stage1(int wb, const ProbDesc* pd, int n, const double* W, const double* AW, double* x,
+                          double* r, double* partials, unsigned int* counter, DevState* st, double tol, int sms,
+                          cudaStream_t s);
+cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, double rank_tol, int w_max, double* C,
+                           double* sigma2, DevState* st, cudaStream_t str);
+cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str);
+cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
+
+// CG iteration (k_cg.cu): kernel pointers for graph construction
+void cg_kernels(int wb, bool fp32, void** init, void** upd, void** dir0, void** dir);
+
+}  // namespace podcg

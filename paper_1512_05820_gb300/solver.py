@@ -1,0 +1,199 @@
+"""Python front end of the C ABI: torch tensors in, torch tensors out.
+
+PyTorch provides device memory and streams only; every step of the path runs in the
+library's CUDA kernels. n-by-k blocks are passed to the library column-major; in Python
+they are (n, k) tensors (any layout; they are made column-major before the call).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+
+class PodCGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int, handle=None):
+    if st != 0:
+        L = _lib.load()
+        msg = L.pod_cg_last_error(handle).decode(errors="replace")
+        raise PodCGError(st, msg)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _colmajor(X: torch.Tensor) -> torch.Tensor:
+    """(n, k) tensor → contiguous (k, n) buffer = column-major n-by-k."""
+    return X.t().contiguous()
+
+
+class DeviceCSR:
+    """A CSR matrix resident on the GPU (int32 indices, float64 values)."""
+
+    def __init__(self, row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor):
+        assert row_ptr.dtype == torch.int32 and col.dtype == torch.int32 and val.dtype == torch.float64
+        self.row_ptr, self.col, self.val = row_ptr, col, val
+        self.n = row_ptr.numel() - 1
+        self.nnz = col.numel()
+
+    @classmethod
+    def from_numpy(cls, row_ptr, col, val, device="cuda"):
+        return cls(torch.as_tensor(row_ptr, dtype=torch.int32, device=device),
+                   torch.as_tensor(col, dtype=torch.int32, device=device),
+                   torch.as_tensor(val, dtype=torch.float64, device=device))
+
+    def with_values(self, val: torch.Tensor) -> "DeviceCSR":
+        return DeviceCSR(self.row_ptr, self.col, val)
+
+    def struct(self) -> _lib.CSRStruct:
+        return _lib.CSRStruct(self.n, self.nnz, self.row_ptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr())
+
+
+DEFAULTS = dict(w_max=32, s_max=40, energy=0.9999, rank_tol=1e-13, k_max=100000, max_refine=5,
+                precision=0, inner_tol=1e-5, use_tc_gram=0, cond_diag=0, keep_factors=0)
+
+
+def make_config(**kw) -> _lib.Config:
+    L = _lib.load()
+    c = _lib.Config()
+    L.pod_cg_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": 0, "mixed": 1}[v]
+        setattr(c, k, v)
+    return c
+
+
+class PodCG:
+    """POD-augmented CG solver for a sequence of systems of order n (one handle)."""
+
+    def __init__(self, n: int, stream: torch.cuda.Stream | None = None, **config):
+        self.L = _lib.load()
+        self.n = n
+        self.stream = stream or torch.cuda.current_stream()
+        self.cfg = make_config(**config)
+        h = ctypes.c_void_p()
+        _check(self.L.pod_cg_create(n, ctypes.byref(self.cfg), ctypes.c_void_p(_stream_ptr(self.stream)),
+                                    ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            self.L.pod_cg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_snapshots(self, X: torch.Tensor):
+        """Append snapshots: X is a length-n vector or an (n, m) block."""
+        if X.dim() == 1:
+            X = X.view(-1, 1)
+        assert X.shape[0] == self.n and X.dtype == torch.float64 and X.is_cuda
+        Xc = _colmajor(X)
+        _check(self.L.pod_cg_add_snapshots(self.h, Xc.data_ptr(), X.shape[1]), self.h)
+
+    def clear_snapshots(self):
+        _check(self.L.pod_cg_clear_snapshots(self.h), self.h)
+
+    def solve(self, A: DeviceCSR, b: torch.Tensor, tol: float, x_out: torch.Tensor | None = None,
+              raise_on_error: bool = True):
+        """Solve A x = b to ||b - A x|| <= tol ||b||. Returns (x, stats dict)."""
+        assert b.dtype == torch.float64 and b.is_cuda and b.numel() == self.n
+        b = b.contiguous()
+        if x_out is None:
+            x_out = torch.empty_like(b)
+        st = _lib.Stats()
+        A_s = A.struct()
+        rc = self.L.pod_cg_solve(self.h, ctypes.byref(A_s), b.data_ptr(), float(tol), x_out.data_ptr(),
+                                 ctypes.byref(st))
+        if rc != 0 and (raise_on_error or rc not in (2, 3, 4, 5)):
+            _check(rc, self.h)
+        return x_out, st.as_dict()
+
+    def solve_adjoint(self, system_id: int, A: DeviceCSR, g: torch.Tensor, tol: float,
+                      lam_out: torch.Tensor | None = None):
+        g = g.contiguous()
+        if lam_out is None:
+            lam_out = torch.empty_like(g)
+        st = _lib.Stats()
+        A_s = A.struct()
+        _check(self.L.pod_cg_solve_adjoint(self.h, system_id, ctypes.byref(A_s), g.data_ptr(), float(tol),
+                                           lam_out.data_ptr(), ctypes.byref(st)), self.h)
+        return lam_out, st.as_dict()
+
+    def basis(self) -> torch.Tensor:
+        """The basis W of the last solve as an (n, w) tensor."""
+        w = ctypes.c_int(0)
+        buf = torch.empty((self.cfg.w_max, self.n), dtype=torch.float64, device="cuda")
+        _check(self.L.pod_cg_get_basis(self.h, buf.data_ptr(), ctypes.byref(w)), self.h)
+        return buf[: w.value].t()
+
+
+# ------------------------------------------------------------------ stateless steps
+
+
+def spmv(A: DeviceCSR, x: torch.Tensor, stream=None) -> torch.Tensor:
+    L = _lib.load()
+    y = torch.empty_like(x)
+    A_s = A.struct()
+    _check(L.pod_cg_spmv(ctypes.byref(A_s), x.contiguous().data_ptr(), y.data_ptr(),
+                         ctypes.c_void_p(_stream_ptr(stream))))
+    return y
+
+
+def spmm(A: DeviceCSR, W: torch.Tensor, stream=None) -> torch.Tensor:
+    L = _lib.load()
+    Wc = _colmajor(W)
+    AWc = torch.empty_like(Wc)
+    A_s = A.struct()
+    _check(L.pod_cg_spmm(ctypes.byref(A_s), Wc.data_ptr(), W.shape[1], AWc.data_ptr(),
+                         ctypes.c_void_p(_stream_ptr(stream))))
+    return AWc.t()
+
+
+def gram_workspace(n: int, p: int, q: int) -> int:
+    return int(_lib.load().pod_cg_gram_workspace(n, p, q))
+
+
+def gram(X: torch.Tensor, Y: torch.Tensor, stream=None) -> torch.Tensor:
+    """G = X^T Y for (n, p) and (n, q) float64 tensors."""
+    L = _lib.load()
+    n, p = X.shape
+    q = Y.shape[1]
+    Xc, Yc = _colmajor(X), _colmajor(Y)
+    G = torch.empty((p, q), dtype=torch.float64, device=X.device)
+    ws = gram_workspace(n, p, q)
+    work = torch.empty(max(ws, 8), dtype=torch.uint8, device=X.device)
+    _check(L.pod_cg_gram(n, Xc.data_ptr(), p, Yc.data_ptr(), q, G.data_ptr(), work.data_ptr(), ws,
+                         ctypes.c_void_p(_stream_ptr(stream))))
+    return G
+
+
+def pod(S: torch.Tensor, energy: float, w_max: int, rank_tol: float = 1e-13, stream=None):
+    """POD basis of the (n, s) snapshot block: returns (W (n, w), w, sigma^2 (s,))."""
+    L = _lib.load()
+    n, s = S.shape
+    Sc = _colmajor(S)
+    Wc = torch.zeros((w_max, n), dtype=torch.float64, device=S.device)
+    sig2 = torch.empty(s, dtype=torch.float64, device=S.device)
+    w = ctypes.c_int(0)
+    ws = gram_workspace(n, s, s)
+    work = torch.empty(max(ws, 8), dtype=torch.uint8, device=S.device)
+    _check(L.pod_cg_pod(n, s, Sc.data_ptr(), float(energy), float(rank_tol), int(w_max), Wc.data_ptr(),
+                        sig2.data_ptr(), ctypes.byref(w), work.data_ptr(), ws, ctypes.c_void_p(_stream_ptr(stream))))
+    torch.cuda.current_stream().synchronize()
+    return Wc[: w.value].t(), w.value, sig2
