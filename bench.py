@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark: systems solved/s and SpMV-equivalent GB/s, POD-augmented CG vs plain CG.
+
+Workload (default): the 128^3 seven-point variable-coefficient diffusion sequence of 50
+systems (lognormal(0, 1) coefficients perturbed 0.5% per system, moving heat source),
+POD of the last 40 solutions truncated at 99.99% energy to w <= 32, Jacobi
+preconditioner, relative residual 1e-8. One step = solving the whole sequence on the GPU
+(POD + stage one + stage two for each system, snapshots recorded as it goes), inputs
+resident in HBM. A_j values (117 MB each) and the basis blocks (~1 GB) exceed the 129 MB
+L2, so no L2 flush is needed between steps.
+
+Prints one JSON line on rank 0. ``--impl reference`` times the FP64 CPU oracle (the
+reference arm of this build) on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "systems solved/s and SpMV-equiv HBM GB/s to rel. residual 1e-8: POD-aug vs plain CG"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--grid", type=int, default=128, help="grid edge m (m^3 cells)")
+    ap.add_argument("--systems", type=int, default=50)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--kernel-reps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args):
+    from paper_1512_05820_gb300 import workloads as wl
+    return wl.diffusion3d_moving(m=args.grid, p=args.systems)
+
+
+def config_dict(seq, args, precision):
+    return {"workload": f"diffusion3d_moving {args.grid}^3 7-point, {seq.p} systems",
+            "n": seq.n, "nnz": seq.nnz, "systems": seq.p, "s_max": seq.s_max, "w_max": seq.w_max,
+            "energy": seq.energy, "tol": seq.tol, "precision": precision, "preconditioner": "jacobi",
+            "l2": "inputs larger than L2 (A_j values 117 MB each, W/AW/S blocks ~1.9 GB); no flush",
+            "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+def b_spmv(n, nnz, fp32=False):
+    """Bytes of one CSR SpMV that move once: values, column indices, row pointers, the
+    input vector and the output vector."""
+    return (8 * nnz + 4 * nnz + 4 * (n + 1) + 8 * n) if fp32 else (12 * nnz + 4 * (n + 1) + 16 * n)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        smax = [num(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(rows),
+                "reasons": reasons}
+
+
+def traffic_from_profiles(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from a committed ncu summary (profiles/*.txt lines
+    `traffic_bytes_per_launch <kernel> <bytes> <source-hash>`), or None."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for fn in sorted(os.listdir(d)):
+        if not fn.endswith(".txt"):
+            continue
+        with open(os.path.join(d, fn)) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 3 and parts[0] == "traffic_bytes_per_launch" and parts[1] == kernel:
+                    return float(parts[2])
+    return None
+
+
+# ----------------------------------------------------------------------- reference arm
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle (single thread) on a bounded sample of the workload: system 1
+    of the sequence (no snapshots yet, so Algorithm 1 with an empty basis)."""
+    if rank != 0:
+        return 0
+    from oracle import Oracle, OracleSequence
+    seq = workload(args)
+    j, val, b = next(iter(seq.systems()))
+    A = (seq.row_ptr, seq.col, val)
+    orc = Oracle()
+    times = []
+    info = None
+    for it in range(args.warmup + args.steps):
+        oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
+        t0 = time.perf_counter()
+        x, info = oseq.solve(A, b, seq.tol)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    value = 1.0 / t
+    sample = f"system 1 of {seq.p} (no snapshots: Algorithm 1 with an empty basis), {info['iters']} iterations"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(seq, args, "fp64"),
+            "cpu_baseline": {"value": value, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- ours
+
+
+def cpu_baseline(seq, systems):
+    from oracle import Oracle, OracleSequence
+    j, val, b = systems[0]
+    orc = Oracle()
+    oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
+    t0 = time.perf_counter()
+    x, info = oseq.solve((seq.row_ptr, seq.col, val), b, seq.tol)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "systems/s", "cores": 1, "kind": "oracle",
+            "sample": f"system 1 of {seq.p} at full size (no snapshots yet: Algorithm 1 with an empty basis, "
+                      f"{info['iters']} iterations, {dt:.1f} s); systems/s = 1/time"}
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
+    from paper_1512_05820_gb300.solver import PodCG
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    prec = 1 if args.precision == "mixed" else 0
+    seq = workload(args)
+    systems = seq.all_systems()
+    dseq = DeviceSequence(seq, systems=systems)
+    xs = [torch.empty(seq.n, dtype=torch.float64, device="cuda") for _ in range(dseq.p)]
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec)
+    stream = solver.stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        run_sequence(solver, dseq, xs)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    all_stats = []
+    for _ in range(args.steps):
+        all_stats.append(run_sequence(solver, dseq, xs))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms_total = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    systems_done = world * seq.p * args.steps
+    value = systems_done / (ms_total / 1e3)
+    last = all_stats[-1]
+    spmv_per_step = sum(s["spmv_count"] for s in last)
+    bsp = b_spmv(seq.n, seq.nnz)
+    spmv_gbs = world * spmv_per_step * bsp / (ms_step / 1e3) / 1e9
+    launches = sum(s["launches"] + 3 for st in all_stats for s in st)   # + add_snapshots (3 kernels)
+    iters = [s["iters"] for s in last]
+    ws = [s["w"] for s in last]
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    out = {"metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if prec == 0 else "f32+f64", "data": "synthetic",
+           "config": config_dict(seq, args, args.precision),
+           "spmv_equiv_gbs": spmv_gbs,
+           "pod_aug": {"systems_per_s": value, "mean_iters": float(np.mean(iters)), "iters_first": iters[0],
+                       "iters_last": iters[-1], "mean_w": float(np.mean(ws)),
+                       "max_final_relres": max(s["final_relres"] for s in last),
+                       "ms_pod_mean": float(np.mean([s["ms_pod"] for s in last])),
+                       "ms_stage1_mean": float(np.mean([s["ms_stage1"] for s in last])),
+                       "ms_stage2_mean": float(np.mean([s["ms_stage2"] for s in last])),
+                       "spmv_per_step": spmv_per_step}}
+
+    # plain Jacobi CG on the same GPU (no recycling), one timed pass
+    if not args.no_compare:
+        plain = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec)
+        run_sequence(plain, dseq, xs, recycle=False)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(plain.stream)
+        pst = run_sequence(plain, dseq, xs, recycle=False)
+        a1.record(plain.stream)
+        torch.cuda.synchronize()
+        pms = a0.elapsed_time(a1)
+        p_spmv = sum(s["spmv_count"] for s in pst)
+        out["plain_cg"] = {"systems_per_s": seq.p / (pms / 1e3), "ms_per_step": pms,
+                           "mean_iters": float(np.mean([s["iters"] for s in pst])),
+                           "spmv_equiv_gbs": p_spmv * bsp / (pms / 1e3) / 1e9,
+                           "max_final_relres": max(s["final_relres"] for s in pst)}
+        out["speedup_vs_plain_cg"] = value / world / out["plain_cg"]["systems_per_s"]
+        plain.close()
+
+    # per-kernel device times of one stage-two iteration (CUDA events, launching stream)
+    j_last = dseq.p - 1
+    run_sequence(solver, dseq, xs)
+    ms_k = solver.time_kernels(dseq.matrix(j_last), dseq.bs[j_last], reps=args.kernel_reps)
+    w_meas = solver.last_w
+    n, nnz = seq.n, seq.nnz
+    kbytes = {"spmv_cg": b_spmv(n, nnz), "update": 32 * n + 8 * w_meas * n, "direction": 48 * n + 8 * w_meas * n,
+              "residual": b_spmv(n, nnz) + 16 * n}
+    kms = dict(zip(["spmv_cg", "update", "direction", "residual"], ms_k))
+    it_total = sum(iters)
+    share = {k: kms[k] * it_total for k in ("spmv_cg", "update", "direction")}
+    dominant = max(share, key=share.get)
+    peak, peak_kind = peaks()
+    achieved = kbytes[dominant] / (kms[dominant] / 1e3) / 1e9
+    names = {"spmv_cg": "k_spmv_cg", "update": "k_update", "direction": "k_dir", "residual": "k_residual"}
+    out["roofline"] = {"bound": "hbm", "kernel": names[dominant], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "frac": achieved / peak, "peak_source": peak_kind,
+                       "traffic": traffic_from_profiles(names[dominant]),
+                       "algorithmic_bytes_per_launch": kbytes[dominant], "w": w_meas,
+                       "ms_per_launch": kms[dominant]}
+    out["kernels"] = {k: {"ms": kms[k], "GB/s": kbytes[k] / (kms[k] / 1e3) / 1e9,
+                          "frac_hbm": kbytes[k] / (kms[k] / 1e3) / 1e9 / peak} for k in kms}
+
+    # end to end through the public API from pinned host buffers
+    if not args.no_e2e:
+        import torch as T
+        h_vals = [T.as_tensor(v).pin_memory() for _, v, _ in systems]
+        h_bs = [T.as_tensor(b).pin_memory() for _, _, b in systems]
+        h_rp = T.as_tensor(seq.row_ptr).pin_memory()
+        h_col = T.as_tensor(seq.col).pin_memory()
+        h_xs = [T.empty(seq.n, dtype=T.float64).pin_memory() for _ in range(dseq.p)]
+        d_val = T.empty(seq.nnz, dtype=T.float64, device="cuda")
+        d_b = T.empty(seq.n, dtype=T.float64, device="cuda")
+        d_rp = T.empty_like(h_rp, device="cuda")
+        d_col = T.empty_like(h_col, device="cuda")
+        from paper_1512_05820_gb300.solver import DeviceCSR
+
+        def e2e_step():
+            solver.clear_snapshots()
+            with T.cuda.stream(stream):
+                d_rp.copy_(h_rp, non_blocking=True)
+                d_col.copy_(h_col, non_blocking=True)
+                A = DeviceCSR(d_rp, d_col, d_val)
+                for j in range(dseq.p):
+                    d_val.copy_(h_vals[j], non_blocking=True)
+                    d_b.copy_(h_bs[j], non_blocking=True)
+                    x, _ = solver.solve(A, d_b, seq.tol, x_out=xs[j])
+                    solver.add_snapshots(x)
+                    h_xs[j].copy_(x, non_blocking=True)
+            T.cuda.synchronize()
+
+        e2e_step()
+        t0 = time.perf_counter()
+        e2e_step()
+        dt = time.perf_counter() - t0
+        h2d = 4 * (seq.n + 1) + 4 * seq.nnz + dseq.p * (8 * seq.nnz + 8 * seq.n)
+        d2h = dseq.p * 8 * seq.n
+        out["e2e"] = {"value": world * seq.p / dt, "unit": "systems/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h}
+
+    out["gpu_launches"] = launches
+    out["clocks"] = clocks
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(seq, systems)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

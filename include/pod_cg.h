@@ -93,6 +93,8 @@ typedef struct {
     int    chol_failed;     /* 1 if W^T A W was not numerically SPD (basis dropped) */
     int    system_id;       /* id of this solve for pod_cg_solve_adjoint */
     int    spmv_count;      /* sparse products: iters + w (stage one) + true-residual products */
+    int    launches;        /* kernels launched by this solve (graph-internal ones included) */
+    int    pad_;
     double stage1_relres;   /* ||b - A x0||/||b|| after stage one */
     double final_relres;    /* ||b - A x||/||b|| at exit, from an FP64 product */
     double cond_gram;       /* cond_2(W^T A W) when cond_diag = 1, else 0 */
@@ -156,6 +158,16 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
 /* Copy the basis W used by the last solve (device out, n-by-w column-major, room for
  * w_max columns) and its dimension (host out). */
 pod_cg_status pod_cg_get_basis(pod_cg_t* h, double* W_out, int* w_out);
+
+/* Measurement support (no counterpart in the paper): time, with CUDA events on the
+ * handle's stream, `reps` separate launches of each kernel of one stage-two iteration
+ * (Algorithm 1's loop body) with the launch shapes the solve uses: [0] the CG product
+ * q = A p with (A p, p), [1] the update r -= alpha q, z = M^{-1} r, (r, z), ||r||^2,
+ * c = (A W)^T z, [2] the direction x += alpha p, p = z + beta p - W mu, [3] the FP64 true
+ * residual b - A x. Uses the basis of the last pod_cg_solve; A and b must be that solve's.
+ * ms_out (host, 4 floats) receives the mean milliseconds per launch. The handle's
+ * iteration vectors are overwritten (the next solve resets them). Errors: ERR_ARG, ERR_CUDA. */
+pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double* b, int reps, float* ms_out);
 
 /* ------------------------------------------------------ stateless steps of the path */
 

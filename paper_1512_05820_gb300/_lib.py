@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "not_spd", 3: "breakdown", 4: "maxit", 5: 
 # every function the header declares (checked by the symbol-export test)
 EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_last_error",
            "pod_cg_add_snapshots", "pod_cg_clear_snapshots", "pod_cg_solve", "pod_cg_solve_adjoint",
-           "pod_cg_get_basis", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram",
+           "pod_cg_get_basis", "pod_cg_time_kernels", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram",
            "pod_cg_pod"]
 
 
@@ -32,6 +32,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("w", ctypes.c_int), ("s", ctypes.c_int), ("chol_failed", ctypes.c_int),
                 ("system_id", ctypes.c_int), ("spmv_count", ctypes.c_int),
+                ("launches", ctypes.c_int), ("pad_", ctypes.c_int),
                 ("stage1_relres", ctypes.c_double), ("final_relres", ctypes.c_double),
                 ("cond_gram", ctypes.c_double), ("ms_pod", ctypes.c_float), ("ms_stage1", ctypes.c_float),
                 ("ms_stage2", ctypes.c_float)]
@@ -72,6 +73,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_solve.argtypes = [vp, P(CSRStruct), vp, cd, vp, P(Stats)]
     L.pod_cg_solve_adjoint.argtypes = [vp, ci, P(CSRStruct), vp, cd, vp, P(Stats)]
     L.pod_cg_get_basis.argtypes = [vp, vp, P(ci)]
+    L.pod_cg_time_kernels.argtypes = [vp, P(CSRStruct), vp, ci, P(ctypes.c_float)]
     L.pod_cg_spmv.argtypes = [P(CSRStruct), vp, vp, vp]
     L.pod_cg_spmm.argtypes = [P(CSRStruct), vp, ci, vp, vp]
     L.pod_cg_gram_workspace.argtypes = [ci, ci, ci]

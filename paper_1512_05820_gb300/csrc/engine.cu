@@ -377,7 +377,6 @@ pod_cg_status pod_cg_add_snapshots(pod_cg_t* h, const double* X, int m)
         PODCG_CK(h, launch_gram_scatter(h->grow, h->s_count, slot, h->GS, kSMax, h->stream));
     }
     if (m > 0) h->pod_dirty = true;
-    PODCG_CK(h, cudaStreamSynchronize(h->stream));
     return POD_CG_OK;
 }
 
@@ -419,8 +418,10 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
     PODCG_CK(h, launch_dinv(h->pd, n, h->dinv, h->dinv32, h->st, h->sms, s));
 
+    int launches = 2;   // dinv, stage-one lift
     // POD of the current snapshots (Algorithm 4)
     if (h->s_count > 0 && h->pod_dirty) {
+        launches += 2;
         PODCG_CK(h, launch_pod_eig(h->GS, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, h->cfg.w_max, h->C,
                                    h->sigma2, h->st, s));
         PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->W, h->ld, h->sms, s));
@@ -440,6 +441,7 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         PODCG_CK(h, launch_gram(n, h->W, h->ld, w, h->AW, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
                                 h->gram_work_bytes, h->sms, s));
         PODCG_CK(h, launch_chol(h->G, kWMax + 1, h->Rinv, h->st, h->cfg.cond_diag, s));
+        launches += 4;   // spmm, gram partial + reduce, cholesky
     }
     const int wb = wb_bucket(w);
     PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4, h->st, tol,
@@ -473,6 +475,8 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         stats->chol_failed = d.chol_failed;
         stats->system_id = sysid;
         stats->spmv_count = d.iters + w + d.restarts + 1;
+        // graph: per outer pass init + first direction + residual; per iteration 3 kernels
+        stats->launches = launches + 3 * (d.restarts + 1) + 3 * d.iters;
         stats->stage1_relres = d.bb > 0.0 ? std::sqrt(d.rr_stage1 / d.bb) : 0.0;
         stats->final_relres = d.bb > 0.0 ? std::sqrt(d.rr_true / d.bb) : 0.0;
         stats->cond_gram = d.cond;
@@ -494,6 +498,79 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
 {
     (void)system_id; (void)A; (void)g; (void)tol; (void)lambda_out; (void)st;
     return fail(h, POD_CG_ERR_STATE, "adjoint factors not kept");
+}
+
+pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double* b, int reps, float* ms_out)
+{
+    if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
+    pod_cg_status cs = check_csr(h, A, h->n);
+    if (cs != POD_CG_OK) return cs;
+    if (!b || !ms_out || reps < 1) return fail(h, POD_CG_ERR_ARG, "bad arguments");
+    const int n = h->n, ld = h->ld;
+    cudaStream_t s = h->stream;
+    *h->pd_host = ProbDesc{A->row_ptr, A->col, A->val, nullptr, b, nullptr, n, h->ld};
+    PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+    const int w = h->pod_w;
+    const int wb = wb_bucket(w);
+    const int L = spmv_lanes_for(n > 0 ? double(A->nnz) / n : 1.0);
+    const int grid = grid_rows(n, kBlock, h->sms);
+    const int grid_spmv = grid_rows(n, kBlock / L, h->sms);
+    void *k_init_f, *k_upd_f, *k_dir0_f, *k_dir_f;
+    cg_kernels(wb, false, &k_init_f, &k_upd_f, &k_dir0_f, &k_dir_f);
+    void* k_spmv_f = kernel_spmv_cg(L, false);
+    void* k_res_f = kernel_residual(L);
+    DevState tmpl;
+    std::memset(&tmpl, 0, sizeof(tmpl));
+    tmpl.rho = 1.0;
+    tmpl.alpha = 1e-30;
+    tmpl.beta = 0.5;
+    tmpl.w = w;
+    tmpl.pod_w = w;
+    tmpl.k_max = 1 << 30;
+    tmpl.max_refine = 1 << 30;
+    tmpl.tol2 = 0.0;
+    tmpl.tol2_in = -1.0;
+    *h->st_host = tmpl;
+    const double* cW = h->W;
+    const double* cAW = h->AW;
+    const double* cRinv = h->Rinv;
+    const double* cdinv = h->dinv;
+    const double* cr = h->r;
+    const double* cq = h->q;
+    const double* cp = h->p;
+    const double* cx = h->x;
+    const DevState* cst = h->st;
+    const ProbDesc* cpd = h->pd;
+    cudaGraphConditionalHandle h0 = 0;
+    int no_cond = 0, zero = 0;
+    double inner_tol = h->cfg.inner_tol;
+    unsigned int* c2 = h->counters + 2;
+    unsigned int* c3 = h->counters + 3;
+    unsigned int* c1 = h->counters + 1;
+    void* a_spmv[] = {(void*)&cpd, (void*)&cp, (void*)&h->q, (void*)&h->partials, (void*)&c2, (void*)&h->st};
+    void* a_upd[] = {(void*)&n, (void*)&ld, (void*)&h->r, (void*)&cq, (void*)&cdinv, (void*)&cAW, (void*)&cRinv,
+                     (void*)&h->partials, (void*)&c3, (void*)&h->st, (void*)&h0, (void*)&no_cond};
+    void* a_dir[] = {(void*)&n, (void*)&ld, (void*)&h->x, (void*)&h->p, (void*)&cr, (void*)&cdinv, (void*)&cW,
+                     (void*)&cst};
+    void* a_res[] = {(void*)&cpd, (void*)&cx, (void*)&h->r, (void*)&h->partials, (void*)&c1, (void*)&h->st,
+                     (void*)&zero, (void*)&inner_tol, (void*)&h0, (void*)&no_cond};
+    struct K { void* f; int g; void** a; } ks[4] = {{k_spmv_f, grid_spmv, a_spmv}, {k_upd_f, grid, a_upd},
+                                                   {k_dir_f, grid, a_dir}, {k_res_f, grid_spmv, a_res}};
+    for (int k = 0; k < 4; ++k) {
+        float total = 0.0f;
+        for (int rep = 0; rep < reps + 1; ++rep) {
+            PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
+            PODCG_CK(h, cudaEventRecord(h->ev[0], s));
+            PODCG_CK(h, cudaLaunchKernel(ks[k].f, dim3(ks[k].g), dim3(kBlock), ks[k].a, 0, s));
+            PODCG_CK(h, cudaEventRecord(h->ev[1], s));
+            PODCG_CK(h, cudaEventSynchronize(h->ev[1]));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+            if (rep > 0) total += ms;   // first launch is a warm-up
+        }
+        ms_out[k] = total / reps;
+    }
+    return POD_CG_OK;
 }
 
 // ----------------------------------------------------------------- stateless steps

@@ -104,6 +104,8 @@ class PodCG:
             X = X.view(-1, 1)
         assert X.shape[0] == self.n and X.dtype == torch.float64 and X.is_cuda
         Xc = _colmajor(X)
+        if Xc.data_ptr() != X.data_ptr():
+            Xc.record_stream(self.stream)   # the copy into the ring is stream-ordered
         _check(self.L.pod_cg_add_snapshots(self.h, Xc.data_ptr(), X.shape[1]), self.h)
 
     def clear_snapshots(self):
@@ -134,6 +136,21 @@ class PodCG:
         _check(self.L.pod_cg_solve_adjoint(self.h, system_id, ctypes.byref(A_s), g.data_ptr(), float(tol),
                                            lam_out.data_ptr(), ctypes.byref(st)), self.h)
         return lam_out, st.as_dict()
+
+    def time_kernels(self, A: DeviceCSR, b: torch.Tensor, reps: int = 20) -> list[float]:
+        """Mean ms per launch of the stage-two kernels [spmv_cg, update, direction, residual]
+        (CUDA events on the handle's stream), on the basis of the last solve."""
+        ms = (ctypes.c_float * 4)()
+        A_s = A.struct()
+        _check(self.L.pod_cg_time_kernels(self.h, ctypes.byref(A_s), b.contiguous().data_ptr(), int(reps), ms),
+               self.h)
+        return [float(v) for v in ms]
+
+    @property
+    def last_w(self) -> int:
+        w = ctypes.c_int(0)
+        _check(self.L.pod_cg_get_basis(self.h, None, ctypes.byref(w)), self.h)
+        return w.value
 
     def basis(self) -> torch.Tensor:
         """The basis W of the last solve as an (n, w) tensor."""

@@ -252,5 +252,9 @@ def test_arg_errors(dev):
         PodCG(10, w_max=65)
     s = PodCG(10)
     A = wl.DiffusionOperator((3, 3)).csr(np.ones(9))
-    with pytest.raises(PodCGError):
-        s.solve(dcsr(A, dev), to_dev(np.ones(9), dev), 1e-8)   # n mismatch
+    with pytest.raises(PodCGError) as e:
+        s.solve(dcsr(A, dev), to_dev(np.ones(10), dev), 1e-8)   # A of order 9, handle of order 10
+    assert e.value.status == 1
+    with pytest.raises(PodCGError) as e:
+        s.solve(dcsr(wl.DiffusionOperator((2, 5)).csr(np.ones(10)), dev), to_dev(np.ones(10), dev), -1.0)
+    assert e.value.status == 1
