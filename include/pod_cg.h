@@ -189,6 +189,22 @@ size_t pod_cg_gram_workspace(int n, int p, int q);
 pod_cg_status pod_cg_gram(int n, const double* X, int p, const double* Y, int q, double* G,
                           void* work, size_t work_bytes, void* cuda_stream);
 
+/* Allocation-free G = X^T Y (the paper has no counterpart: this is a deployment variant
+ * of pod_cg_gram). It is for callers that cannot allocate device memory at the point of
+ * use: latency-bound loops where cudaMalloc/cudaFree may synchronise the whole device, and
+ * host applications that hand out all device memory themselves under a fixed budget.
+ * Arguments as pod_cg_gram without the workspace: the scratch is a fixed 512 KiB array
+ * compiled into the library (held on every GPU that loads the library until exit); this
+ * call allocates nothing. p, q <= 65; a product whose scratch would exceed the array
+ * (possible only on a GPU with far more than 152 SMs) is rejected with ERR_ARG and a
+ * message naming both sizes. The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Every call shares the one array: calls that may overlap on the GPU
+ * (different streams, or different host threads) race on it and must be serialised by
+ * the caller. Each call overwrites all the scratch it reads, so no clearing is needed. */
+pod_cg_status pod_cg_gram_noalloc(int n, const double* X, int p, const double* Y, int q, double* G,
+                                  void* cuda_stream);
+
 /* POD by Algorithm 4 (identity metric, unit weights) of the device snapshot block S
  * (n-by-s, column-major, s <= 64): symmetric Jacobi eigensolve of S^T S, eigenvalues in
  * decreasing order, w = smallest index within the numerical rank whose energy fraction

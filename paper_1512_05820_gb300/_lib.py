@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "not_spd", 3: "breakdown", 4: "maxit", 5: 
 # every function the header declares (checked by the symbol-export test)
 EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_last_error",
            "pod_cg_add_snapshots", "pod_cg_clear_snapshots", "pod_cg_solve", "pod_cg_solve_adjoint",
-           "pod_cg_get_basis", "pod_cg_time_kernels", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram",
+           "pod_cg_get_basis", "pod_cg_time_kernels", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram", "pod_cg_gram_noalloc",
            "pod_cg_pod"]
 
 
@@ -79,6 +79,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_gram_workspace.argtypes = [ci, ci, ci]
     L.pod_cg_gram_workspace.restype = sz
     L.pod_cg_gram.argtypes = [ci, vp, ci, vp, ci, vp, vp, sz, vp]
+    L.pod_cg_gram_noalloc.argtypes = [ci, vp, ci, vp, ci, vp, vp]
     L.pod_cg_pod.argtypes = [ci, ci, vp, cd, cd, ci, vp, vp, P(ci), vp, sz, vp]
     for name in EXPORTS:
         if name not in ("pod_cg_last_error", "pod_cg_gram_workspace"):

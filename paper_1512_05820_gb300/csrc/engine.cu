@@ -239,6 +239,8 @@ cudaError_t dalloc(T** p, size_t count)
 
 }  // namespace
 
+void podcg::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 // ======================================================================== C ABI
 
 extern "C" {

@@ -5,12 +5,15 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace podcg {
 
 struct DevState;
 struct ProbDesc;
 
 int grid_rows(int rows, int per_block, int sms);
+void set_last_error(const std::string& msg);   // message for pod_cg_last_error(NULL)
 int spmv_lanes_for(double mean_row);
 int wb_bucket(int w);
 
