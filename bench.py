@@ -41,11 +41,15 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--grid", type=int, default=128, help="grid edge m (m^3 cells)")
     ap.add_argument("--systems", type=int, default=50)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-sequences measurement")
+    ap.add_argument("--batch-seqs", type=int, default=256)
+    ap.add_argument("--loop-mode", choices=["graph", "chunked"], default="graph",
+                    help="graph: conditional CUDA graph; chunked: plain graphs of 16 iterations (profilable)")
     return ap.parse_args()
 
 
@@ -71,8 +75,9 @@ def config_dict(seq, args, precision):
 
 def b_spmv(n, nnz, fp32=False):
     """Bytes of one CSR SpMV that move once: values, column indices, row pointers, the
-    input vector and the output vector."""
-    return (8 * nnz + 4 * nnz + 4 * (n + 1) + 8 * n) if fp32 else (12 * nnz + 4 * (n + 1) + 16 * n)
+    input vector and the output vector (FP64: 12 nnz + 4(n+1) + 16 n; FP32 values and
+    vectors: 8 nnz + 4(n+1) + 8 n)."""
+    return (8 * nnz + 4 * (n + 1) + 8 * n) if fp32 else (12 * nnz + 4 * (n + 1) + 16 * n)
 
 
 def peaks():
@@ -193,6 +198,64 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------- ours
 
 
+def batch_section(args):
+    """Many independent sequences (256 x 8 systems, n log-uniform in [2k, 260k], 2D/3D mixed,
+    w_max in [4, 24]) in one persistent launch under a CUDA graph, cluster size autotuned,
+    FP32 inner + FP64 refinement; compared with the single-sequence engine in FP64 on the
+    first 32 sequences at the same tolerance."""
+    import torch
+    from paper_1512_05820_gb300 import workloads as wl
+    from paper_1512_05820_gb300.batch import BatchSolver
+    from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
+    from paper_1512_05820_gb300.solver import PodCG
+    seqs = wl.batch_sequences(nseq=args.batch_seqs)
+    systems = [s.all_systems() for s in seqs]
+    t0 = time.perf_counter()
+    bs = BatchSolver(seqs, systems=systems, cluster=0)
+    tune_s = time.perf_counter() - t0
+    bs.solve()
+    times, stats = [], None
+    for _ in range(max(1, args.steps)):
+        stats, ms = bs.solve()
+        times.append(ms)
+    ms = statistics.median(times)
+    total = len(stats)
+    ok = sum(1 for s in stats if s["status"] == "ok")
+    info = bs.info()
+    out = {"workload": f"{len(seqs)} sequences x {seqs[0].p} systems, n in [2k, 260k] log-uniform, 2D/3D",
+           "rows_per_layer": int(sum(s.n for s in seqs)), "systems": total, "converged": ok,
+           "systems_per_s": total / (ms / 1e3), "ms_per_batch": ms,
+           "max_final_relres": max(s["final_relres"] for s in stats),
+           "mean_iters": float(np.mean([s["iters"] for s in stats])),
+           "cluster": info["cluster"], "workers": info["workers"],
+           "autotune_ms": {str(k): v for k, v in info["tune_ms"].items()}, "setup_s": tune_s}
+    bs.close()
+    # single-sequence engine, FP64, same tolerance, first 32 sequences
+    sub = seqs[:32]
+    t_single, n_single = 0.0, 0
+    for seq, sy in zip(sub, systems[:32]):
+        dseq = DeviceSequence(seq, systems=sy)
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=0)
+        run_sequence(solver, dseq)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(solver.stream)
+        run_sequence(solver, dseq)
+        e1.record(solver.stream)
+        torch.cuda.synchronize()
+        t_single += e0.elapsed_time(e1)
+        n_single += dseq.p
+        solver.close()
+    sub_sys = sum(len(sy) for sy in systems[:32])
+    frac = sub_sys / total
+    out["single_sequence_fp64"] = {"systems_per_s": n_single / (t_single / 1e3), "sample": "first 32 sequences",
+                                   "ms": t_single}
+    out["speedup_vs_single_fp64"] = out["systems_per_s"] / out["single_sequence_fp64"]["systems_per_s"]
+    del frac
+    return out
+
+
 def cpu_baseline(seq, systems):
     from oracle import Oracle, OracleSequence
     j, val, b = systems[0]
@@ -227,7 +290,8 @@ def main():
     systems = seq.all_systems()
     dseq = DeviceSequence(seq, systems=systems)
     xs = [torch.empty(seq.n, dtype=torch.float64, device="cuda") for _ in range(dseq.p)]
-    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec)
+    loop_mode = 0 if args.loop_mode == "graph" else 1
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec, loop_mode=loop_mode)
     stream = solver.stream
 
     def barrier():
@@ -286,25 +350,34 @@ def main():
                        "ms_stage2_mean": float(np.mean([s["ms_stage2"] for s in last])),
                        "spmv_per_step": spmv_per_step}}
 
-    # plain Jacobi CG on the same GPU (no recycling), one timed pass
-    if not args.no_compare:
-        plain = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec)
-        run_sequence(plain, dseq, xs, recycle=False)
+    # one timed pass each: POD-aug in the other precision, plain Jacobi CG (no recycling)
+    # in both precisions, same GPU, same tolerance
+    def one_pass(precision, recycle):
+        sv = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=precision,
+                   loop_mode=loop_mode)
+        run_sequence(sv, dseq, xs, recycle=recycle)
         torch.cuda.synchronize()
         a0 = torch.cuda.Event(enable_timing=True)
         a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(plain.stream)
-        pst = run_sequence(plain, dseq, xs, recycle=False)
-        a1.record(plain.stream)
+        a0.record(sv.stream)
+        pst = run_sequence(sv, dseq, xs, recycle=recycle)
+        a1.record(sv.stream)
         torch.cuda.synchronize()
         pms = a0.elapsed_time(a1)
-        p_spmv = sum(s["spmv_count"] for s in pst)
-        out["plain_cg"] = {"systems_per_s": seq.p / (pms / 1e3), "ms_per_step": pms,
-                           "mean_iters": float(np.mean([s["iters"] for s in pst])),
-                           "spmv_equiv_gbs": p_spmv * bsp / (pms / 1e3) / 1e9,
-                           "max_final_relres": max(s["final_relres"] for s in pst)}
-        out["speedup_vs_plain_cg"] = value / world / out["plain_cg"]["systems_per_s"]
-        plain.close()
+        sv.close()
+        return {"systems_per_s": seq.p / (pms / 1e3), "ms_per_step": pms,
+                "mean_iters": float(np.mean([s["iters"] for s in pst])),
+                "spmv_equiv_gbs": sum(s["spmv_count"] for s in pst) * bsp / (pms / 1e3) / 1e9,
+                "max_final_relres": max(s["final_relres"] for s in pst)}
+
+    if not args.no_compare:
+        other = 0 if prec == 1 else 1
+        out["pod_aug_" + ("fp64" if other == 0 else "mixed")] = one_pass(other, True)
+        out["plain_cg_fp64"] = one_pass(0, False)
+        out["plain_cg_mixed"] = one_pass(1, False)
+        same = out["plain_cg_mixed" if prec == 1 else "plain_cg_fp64"]
+        out["speedup_vs_plain_cg_same_precision"] = value / world / same["systems_per_s"]
+        out["speedup_vs_fp64_pod_aug"] = (value / world / out["pod_aug_fp64"]["systems_per_s"]) if prec == 1 else 1.0
 
     # per-kernel device times of one stage-two iteration (CUDA events, launching stream)
     j_last = dseq.p - 1
@@ -312,8 +385,12 @@ def main():
     ms_k = solver.time_kernels(dseq.matrix(j_last), dseq.bs[j_last], reps=args.kernel_reps)
     w_meas = solver.last_w
     n, nnz = seq.n, seq.nnz
-    kbytes = {"spmv_cg": b_spmv(n, nnz), "update": 32 * n + 8 * w_meas * n, "direction": 48 * n + 8 * w_meas * n,
-              "residual": b_spmv(n, nnz) + 16 * n}
+    # algorithmic bytes per launch (each datum once): FP64 or FP32 vectors/panels
+    e = 4 if prec == 1 else 8
+    kbytes = {"spmv_cg": b_spmv(n, nnz, fp32=(prec == 1)),
+              "update": 4 * e * n + e * w_meas * n,          # read r, q, dinv, AW; write r
+              "direction": 6 * e * n + e * w_meas * n,       # read x, p, r, dinv, W; write x, p
+              "residual": b_spmv(n, nnz) + 16 * n}           # FP64 always; + read b, write r
     kms = dict(zip(["spmv_cg", "update", "direction", "residual"], ms_k))
     it_total = sum(iters)
     share = {k: kms[k] * it_total for k in ("spmv_cg", "update", "direction")}
@@ -365,6 +442,12 @@ def main():
         d2h = dseq.p * 8 * seq.n
         out["e2e"] = {"value": world * seq.p / dt, "unit": "systems/s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h}
+
+    if not args.no_batch:
+        try:
+            out["batch"] = batch_section(args)
+        except Exception as e:  # reported, not fatal to the headline measurement
+            out["batch"] = {"error": repr(e)[:300]}
 
     out["gpu_launches"] = launches
     out["clocks"] = clocks

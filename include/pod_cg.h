@@ -71,6 +71,9 @@ typedef struct {
     int    use_tc_gram;  /* MIXED: stage-one Gram on tensor cores with split products */
     int    cond_diag;    /* 1: compute cond_2(W^T A W) per solve (diagnostic, Section 5.2) */
     int    keep_factors; /* systems whose W, AW, R are kept for pod_cg_solve_adjoint (0..) */
+    int    loop_mode;    /* 0: the CG loop is one conditional CUDA graph (no host round trip);
+                            1: plain graphs of 16 unrolled iterations, host check per chunk
+                            (same kernels; a form that kernel profilers can attribute) */
 } pod_cg_config;
 
 /* CSR matrix, device arrays, borrowed. */
@@ -106,7 +109,8 @@ typedef struct {
 /* ------------------------------------------------------------------ handle lifecycle */
 
 /* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
- * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0. */
+ * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
+ * loop_mode 0. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 
 /* Create a solver for systems of order n (the problem statement of Section 2) whose work
@@ -214,6 +218,86 @@ pod_cg_status pod_cg_gram_noalloc(int n, const double* X, int p, const double* Y
 pod_cg_status pod_cg_pod(int n, int s, const double* S, double energy, double rank_tol,
                          int w_max, double* W_out, double* sigma2_out, int* w_out,
                          void* work, size_t work_bytes, void* cuda_stream);
+
+/* ------------------------------------------- many independent sequences in one launch */
+
+typedef struct pod_cg_batch_t pod_cg_batch_t;
+
+/* One sequence of a batch (device arrays, borrowed for the batch handle's lifetime): p
+ * systems sharing one CSR pattern of order n; val holds the p value arrays back to back
+ * (system j at j*nnz), b the p right-hand sides (j*n), x receives the p solutions. */
+typedef struct {
+    int            n;
+    int64_t        nnz;
+    int            p;
+    int            w_max;     /* POD basis cap, 1..32 */
+    int            s_max;     /* snapshot window, 1..16 */
+    double         tol;       /* relative residual target, Eq. (sequenceInexact) */
+    double         energy;    /* POD energy criterion (Algorithm 4) */
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const double*  val;
+    const double*  b;
+    double*        x;
+} pod_cg_batch_seq;
+
+typedef struct {
+    int    status;          /* pod_cg_status of this system */
+    int    iters;           /* FP32 inner CG iterations, all refinement steps */
+    int    refinements;     /* FP64 refinement steps */
+    int    w;               /* POD basis dimension used */
+    double final_relres;    /* FP64 ||b - A x||/||b|| at exit */
+    double stage1_relres;   /* after stage one */
+} pod_cg_batch_sysstat;
+
+/* Prepare a batch of nseq independent sequences (the problem of Section 2, many at once)
+ * solved by one persistent launch captured in a CUDA graph: each worker (a thread-block
+ * cluster) takes whole sequences, longest estimated work first, and runs the recycled-
+ * solution form of the overall algorithm (Section 4.4) on each: POD of the previous
+ * solutions (Algorithm 4), stage one (Algorithm 2), FP32 augmented PCG (Algorithm 1)
+ * inside FP64 refinement. cfg supplies k_max, max_refine, inner_tol, rank_tol (NULL =
+ * defaults). cluster: CTAs per worker, 1, 2, 4 or 8, or 0 to autotune (each candidate
+ * 2, 4, 8 runs the whole batch once; the fastest is kept). The handle owns the workspace.
+ * Errors: ERR_ARG (a bad sequence is named in the message), ERR_OOM, ERR_CUDA. */
+pod_cg_status pod_cg_batch_create(const pod_cg_batch_seq* seqs /* host, nseq */, int nseq,
+                                  const pod_cg_config* cfg, int cluster, void* cuda_stream,
+                                  pod_cg_batch_t** out);
+
+/* Solve every system of every sequence (one graph launch; synchronises). stats (host,
+ * may be NULL) receives one entry per system, sequences in the order given and systems
+ * in order within each; ms (host, may be NULL) the device time of the launch. Returns
+ * the first non-OK system status, if any. */
+pod_cg_status pod_cg_batch_solve(pod_cg_batch_t* h, pod_cg_batch_sysstat* stats, float* ms);
+
+/* Chosen cluster size, number of concurrent workers and the autotuner's timings (ms of
+ * the whole batch for cluster 2, 4, 8; 0 when not tuned, -1 when not schedulable). */
+pod_cg_status pod_cg_batch_info(const pod_cg_batch_t* h, int* cluster, int* workers, float* tune_ms3);
+const char* pod_cg_batch_last_error(const pod_cg_batch_t* h);
+pod_cg_status pod_cg_batch_destroy(pod_cg_batch_t* h);
+
+/* --------------------------------------- differentiation through a sequence of solves */
+
+/* Values of the cell-centred finite-volume diffusion operator A(theta) + diag(extra) on an
+ * mx x my x mz grid (mz = 1: five-point 2D), k = exp(theta) per cell, interior faces with
+ * the harmonic-mean conductance 2 k_a k_b/(k_a + k_b), Dirichlet boundary faces with 2 k_a.
+ * This is the operator whose parameters the adjoint gradient differentiates (the
+ * differentiation workload of the sequence problem, Section 2). Cells are numbered x
+ * fastest; row i of the CSR pattern (row_ptr, device, n+1) lists the z-1, y-1, x-1
+ * neighbours, the cell itself, then x+1, y+1, z+1 (absent ones omitted); val_out (device,
+ * nnz) receives the values in that order. theta, extra_diag (nullable): device, length n. */
+pod_cg_status pod_cg_diffusion_assemble(int mx, int my, int mz, const double* theta, const double* extra_diag,
+                                        const int32_t* row_ptr, double* val_out, void* cuda_stream);
+
+/* Accumulate grad -= sum_j lambda_j^T (dA/dtheta) x_j for nsys systems of the operator
+ * above: for each cell c, the sum over its faces of dk_f/dtheta_c (lambda_c - lambda_m)
+ * (x_c - x_m) with dk_f/dtheta_c = k_f k_m/(k_c + k_m), plus 2 k_c lambda_c x_c per
+ * boundary face. With lambda_j the adjoint solutions (pod_cg_solve_adjoint) of a loss
+ * L(x_1..x_p), this is dL/dtheta (A_j symmetric). lambdas and xs: device, nsys x n
+ * row-major (system j at offset j*n); theta, grad: device, length n (grad accumulated).
+ * One pass over all checkpoints. Errors: ERR_ARG, ERR_CUDA. */
+pod_cg_status pod_cg_diffusion_theta_grad(int mx, int my, int mz, const double* theta, int nsys,
+                                          const double* lambdas, const double* xs, double* grad,
+                                          void* cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,9 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "not_spd", 3: "breakdown", 4: "maxit", 5: 
 # every function the header declares (checked by the symbol-export test)
 EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_last_error",
            "pod_cg_add_snapshots", "pod_cg_clear_snapshots", "pod_cg_solve", "pod_cg_solve_adjoint",
-           "pod_cg_get_basis", "pod_cg_time_kernels", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram", "pod_cg_gram_noalloc",
+           "pod_cg_get_basis", "pod_cg_time_kernels", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram", "pod_cg_gram_noalloc", "pod_cg_diffusion_assemble",
+           "pod_cg_diffusion_theta_grad", "pod_cg_batch_create", "pod_cg_batch_solve", "pod_cg_batch_info",
+           "pod_cg_batch_last_error", "pod_cg_batch_destroy",
            "pod_cg_pod"]
 
 
@@ -20,12 +22,24 @@ class Config(ctypes.Structure):
     _fields_ = [("w_max", ctypes.c_int), ("s_max", ctypes.c_int), ("energy", ctypes.c_double),
                 ("rank_tol", ctypes.c_double), ("k_max", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("use_tc_gram", ctypes.c_int),
-                ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int)]
+                ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int), ("loop_mode", ctypes.c_int)]
 
 
 class CSRStruct(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_int64), ("row_ptr", ctypes.c_void_p),
                 ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class BatchSeq(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("nnz", ctypes.c_int64), ("p", ctypes.c_int), ("w_max", ctypes.c_int),
+                ("s_max", ctypes.c_int), ("tol", ctypes.c_double), ("energy", ctypes.c_double),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p),
+                ("b", ctypes.c_void_p), ("x", ctypes.c_void_p)]
+
+
+class BatchSysStat(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("w", ctypes.c_int), ("final_relres", ctypes.c_double), ("stage1_relres", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -80,9 +94,17 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_gram_workspace.restype = sz
     L.pod_cg_gram.argtypes = [ci, vp, ci, vp, ci, vp, vp, sz, vp]
     L.pod_cg_gram_noalloc.argtypes = [ci, vp, ci, vp, ci, vp, vp]
+    L.pod_cg_diffusion_assemble.argtypes = [ci, ci, ci, vp, vp, vp, vp, vp]
+    L.pod_cg_diffusion_theta_grad.argtypes = [ci, ci, ci, vp, ci, vp, vp, vp, vp]
+    L.pod_cg_batch_create.argtypes = [P(BatchSeq), ci, P(Config), ci, vp, P(vp)]
+    L.pod_cg_batch_solve.argtypes = [vp, P(BatchSysStat), P(ctypes.c_float)]
+    L.pod_cg_batch_info.argtypes = [vp, P(ci), P(ci), P(ctypes.c_float)]
+    L.pod_cg_batch_last_error.argtypes = [vp]
+    L.pod_cg_batch_last_error.restype = ctypes.c_char_p
+    L.pod_cg_batch_destroy.argtypes = [vp]
     L.pod_cg_pod.argtypes = [ci, ci, vp, cd, cd, ci, vp, vp, P(ci), vp, sz, vp]
     for name in EXPORTS:
-        if name not in ("pod_cg_last_error", "pod_cg_gram_workspace"):
+        if name not in ("pod_cg_last_error", "pod_cg_gram_workspace", "pod_cg_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L

@@ -31,6 +31,7 @@ struct DevState {
     double rr_outer;   // mixed precision: ||r||^2 of the current outer residual
     double cond;       // cond_2(W^T A W) diagnostic
     double mu[kWMax];  // reduced coordinates of the A-orthogonalisation (Algorithm 1)
+    double c[kWMax];   // (A W)^T z of the current iterate; mu = R^{-1} R^{-T} c
     double what[kWMax];// stage-one reduced solution
     int w;             // basis dimension in use (0 = plain PCG)
     int iters;         // CG iterations so far (all passes)
@@ -43,7 +44,9 @@ struct DevState {
     int pod_w;         // w chosen by the POD (before a possible Cholesky failure)
     int outer_done;
     int inner_iters;   // mixed precision: iterations of the current inner solve
-    int pad_;
+    int dir_pending;   // the direction kernel of this iteration has work (chunked loops)
+    int mixed;         // FP32 inner loop: a breakdown ends the inner pass instead of the solve
+    int inner_break;   // set by an FP32 inner breakdown (mixed mode)
 };
 
 // Borrowed problem pointers of the current solve, read by the kernels of a captured
@@ -66,6 +69,10 @@ __device__ __forceinline__ T warp_sum(T v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+// Stride between the partials of two values: partials are stored value-major
+// (partials[v * kPartialStride + block]) so the last block reads them coalesced.
+constexpr int kPartialStride = 4096;   // >= any grid of a reducing kernel
 
 // Block-reduce acc[0..nv) (nv uniform over the grid, nv <= NV), store one partial per
 // block, and return true in the last block to finish, which then holds the grid totals
@@ -91,7 +98,7 @@ __device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], in
         double t = 0.0;
 #pragma unroll
         for (int k = 0; k < kWarps; ++k) t += s_w[k][v];
-        partials[(size_t)blockIdx.x * NV + v] = t;
+        partials[(size_t)v * kPartialStride + blockIdx.x] = t;
     }
     __threadfence();
     __syncthreads();
@@ -102,10 +109,19 @@ __device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], in
     __syncthreads();
     if (!s_last) return false;
     __threadfence();
+    const int G = gridDim.x;
     for (int v = wid; v < nv; v += kWarps) {
-        double t = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(&partials[(size_t)b * NV + v]);
-        t = warp_sum(t);
+        const double* pv = partials + (size_t)v * kPartialStride;
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        int b = lane;
+        for (; b + 96 < G; b += 128) {
+            t0 += __ldcg(pv + b);
+            t1 += __ldcg(pv + b + 32);
+            t2 += __ldcg(pv + b + 64);
+            t3 += __ldcg(pv + b + 96);
+        }
+        for (; b < G; b += 32) t0 += __ldcg(pv + b);
+        double t = warp_sum((t0 + t1) + (t2 + t3));
         if (lane == 0) s_tot[v] = t;
     }
     if (threadIdx.x == 0) *counter = 0u;

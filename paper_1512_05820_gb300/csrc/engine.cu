@@ -2,23 +2,27 @@
 //
 // A handle owns the snapshot ring S (column-major, leading dimension ld = n rounded up to
 // 32), its Gram S^T S (kept up to date one row per added snapshot), the POD basis W, A W,
-// the stage-one factor R^{-1}, the CG vectors, reduction scratch and the captured graphs.
+// the stage-one Gram and R^{-1}, the CG vectors, reduction scratch and the captured graphs.
 //
 // pod_cg_solve enqueues, on the handle's stream:
 //   POD (when the snapshots changed): Jacobi eigensolve of S^T S, truncation, lift W = S C
 //   stage one: A W, W^T [A W, b], Cholesky + R^{-1} + what, x0 = W what, r0 = b - A W what
-//   one graph launch: outer while (residual replacement / refinement) {
-//       init pass: z0, mu0, p0; inner while (CG) { q = A p; update; direction };
-//       true residual b - A x in FP64 (sets the outer condition) }
-// The loop runs entirely on the device (conditional graph nodes); the host synchronises
-// once to learn w (which selects the graph of the basis-width bucket) and once at the end.
+//   the stage-two loop, either
+//     loop_mode 0: one graph launch with two nested conditional while-nodes
+//        FP64 : outer (residual replacement) { init; first direction;
+//                 inner { q = A p; update; direction }; true residual }
+//        mixed: outer (refinement) { FP64 residual; projection of the correction onto W;
+//                 FP32 init; first direction; inner { ... in FP32 }; x += d }
+//     loop_mode 1: the same kernels, the inner loop as a plain graph of 16 unrolled
+//        iterations (later ones return at once after convergence), host check per chunk.
+// The host synchronises once to learn w (which selects the kernel width bucket) and once
+// at the end for the statistics.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +35,7 @@ using namespace podcg;
 namespace {
 
 thread_local std::string g_last_error;
+constexpr int kChunk = 16;   // iterations per plain graph in loop_mode 1
 
 int device_sms()
 {
@@ -46,6 +51,45 @@ int device_sms()
     return cache[dev];
 }
 
+// Kernel arguments stored by value with stable addresses (a spec is built in place and
+// never copied, so the pointer array stays valid for graph-node creation and launches).
+struct KArgs {
+    alignas(16) unsigned char buf[512];
+    size_t off = 0;
+    void* ptrs[24];
+    int count = 0;
+    template <typename T>
+    void add(T v)
+    {
+        off = (off + alignof(T) - 1) & ~(alignof(T) - 1);
+        std::memcpy(buf + off, &v, sizeof(T));
+        ptrs[count++] = buf + off;
+        off += sizeof(T);
+    }
+};
+
+struct KSpec {
+    void* f = nullptr;
+    int grid = 1;
+    KArgs a;
+    KSpec() = default;
+    KSpec(const KSpec&) = delete;
+    KSpec& operator=(const KSpec&) = delete;
+    template <typename... Args>
+    void set(void* func, int g, Args... args)
+    {
+        f = func;
+        grid = g;
+        a.off = 0;
+        a.count = 0;
+        (a.add(args), ...);
+    }
+};
+
+struct Plan {
+    KSpec init, dir0, spmv, upd, dir, res, mxproj, mxstart, mxaccum;
+};
+
 struct GraphSlot {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -53,19 +97,14 @@ struct GraphSlot {
     bool valid = false;
 };
 
-// Add a kernel node: the arguments are passed by value and must match the kernel's
-// parameter types in size and order.
-template <typename... Args>
-cudaError_t add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, void* func, int grid,
-                       int block, cudaGraphNode_t* out, Args... args)
+cudaError_t add_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, KSpec& k, cudaGraphNode_t* out)
 {
-    void* ptrs[] = {(void*)&args...};
     cudaKernelNodeParams p = {};
-    p.func = func;
-    p.gridDim = dim3(grid);
-    p.blockDim = dim3(block);
+    p.func = k.f;
+    p.gridDim = dim3(k.grid);
+    p.blockDim = dim3(kBlock);
     p.sharedMemBytes = 0;
-    p.kernelParams = ptrs;
+    p.kernelParams = k.a.ptrs;
     p.extra = nullptr;
     return cudaGraphAddKernelNode(out, g, deps, ndeps, &p);
 }
@@ -83,16 +122,23 @@ cudaError_t add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, 
     return e;
 }
 
+cudaError_t launch_spec(KSpec& k, cudaStream_t s)
+{
+    return cudaLaunchKernel(k.f, dim3(k.grid), dim3(kBlock), k.a.ptrs, 0, s);
+}
+
 }  // namespace
 
 struct pod_cg_t {
     int n = 0, ld = 0, sms = 1, device = 0;
+    bool mixed = false;
     pod_cg_config cfg{};
     cudaStream_t stream = nullptr;
     std::string err;
 
     // snapshots and POD
     double* S = nullptr;        // ld x s_max
+    float* S32 = nullptr;       // ld x s_max (mixed)
     double* GS = nullptr;       // kSMax x kSMax row-major (slot order)
     double* grow = nullptr;     // one Gram row (kSMax)
     double* C = nullptr;        // kSMax x kWMax lift coefficients
@@ -104,12 +150,17 @@ struct pod_cg_t {
     // basis and stage one
     double* W = nullptr;        // ld x w_max
     double* AW = nullptr;       // ld x w_max
+    float* W32 = nullptr;       // mixed
+    float* AW32 = nullptr;      // mixed
     double* G = nullptr;        // kWMax x (kWMax + 1) row-major
     double* Rinv = nullptr;     // kWMax x kWMax
 
-    // CG vectors (FP64)
+    // vectors
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr;
     float* dinv32 = nullptr;
+    float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr;   // mixed
+    float* val32 = nullptr;     // mixed: FP32 copy of A's values
+    int64_t val32_cap = 0;
 
     // reductions
     double* partials = nullptr;
@@ -122,7 +173,15 @@ struct pod_cg_t {
     ProbDesc* pd = nullptr;
     ProbDesc* pd_host = nullptr;        // pinned
 
-    GraphSlot graphs[6][2];             // [width bucket][precision]
+    // factors kept for the adjoint
+    double* kW = nullptr;
+    double* kAW = nullptr;
+    double* kG = nullptr;
+    std::vector<int> k_id, k_w;
+    int k_next = 0;
+
+    GraphSlot graphs[6];                // conditional graphs [width bucket]
+    GraphSlot chunks[6];                // plain chunk graphs [width bucket]
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int system_counter = 0;
 };
@@ -142,9 +201,9 @@ pod_cg_status cuda_fail(pod_cg_t* h, const char* what, cudaError_t e)
     return fail(h, e == cudaErrorMemoryAllocation ? POD_CG_ERR_OOM : POD_CG_ERR_CUDA, m);
 }
 
-#define PODCG_CK(h, call)                                  \
-    do {                                                   \
-        cudaError_t e_ = (call);                           \
+#define PODCG_CK(h, call)                                      \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
         if (e_ != cudaSuccess) return cuda_fail(h, #call, e_); \
     } while (0)
 
@@ -170,58 +229,68 @@ pod_cg_status check_csr(pod_cg_t* h, const pod_cg_csr* A, int n)
     return POD_CG_OK;
 }
 
-// Build the FP64 solve graph for width bucket wb and SpMV lanes L.
-pod_cg_status build_graph_fp64(pod_cg_t* h, int wb, int L, GraphSlot& gs)
+// One wave: as many blocks as are resident at once (occupancy), never more than needed.
+int occ_grid(pod_cg_t* h, const void* f, int rows, int rows_per_block)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kBlock, 0) != cudaSuccess || nb < 1) nb = 1;
+    long long need = ((long long)rows + rows_per_block - 1) / rows_per_block;
+    long long cap = (long long)h->sms * nb;
+    long long g = std::min(need, cap);
+    g = std::min<long long>(g, kPartialStride);
+    return (int)std::max<long long>(g, 1);
+}
+
+void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphConditionalHandle h_inner,
+               cudaGraphConditionalHandle h_outer, Plan& P)
 {
     const int n = h->n, ld = h->ld;
-    const int grid = grid_rows(n, kBlock, h->sms);
-    const int grid_spmv = grid_rows(n, kBlock / L, h->sms);
-    void *k_init_f, *k_upd_f, *k_dir0_f, *k_dir_f;
-    cg_kernels(wb, false, &k_init_f, &k_upd_f, &k_dir0_f, &k_dir_f);
-    void* k_spmv_f = kernel_spmv_cg(L, false);
-    void* k_res_f = kernel_residual(L);
-
-    cudaGraph_t P = nullptr;
-    PODCG_CK(h, cudaGraphCreate(&P, 0));
-    cudaGraphConditionalHandle h_outer, h_inner;
-    PODCG_CK(h, cudaGraphConditionalHandleCreate(&h_outer, P, 1, cudaGraphCondAssignDefault));
-    cudaGraphNode_t n_outer;
-    cudaGraph_t O = nullptr, I = nullptr;
-    PODCG_CK(h, add_while(P, nullptr, 0, h_outer, &n_outer, &O));
-    PODCG_CK(h, cudaGraphConditionalHandleCreate(&h_inner, O, 0, 0));
-
-    const double* cW = h->W;
-    const double* cAW = h->AW;
-    const double* cRinv = h->Rinv;
-    const double* cdinv = h->dinv;
-    unsigned int* c0 = h->counters + 0;
-    unsigned int* c1 = h->counters + 1;
-    unsigned int* c2 = h->counters + 2;
-    unsigned int* c3 = h->counters + 3;
-    int use_cond = 1, zero = 0;
-    double inner_tol = h->cfg.inner_tol;
-
-    cudaGraphNode_t n1, n2, n3, n4, m1, m2, m3;
-    PODCG_CK(h, add_kernel(O, nullptr, 0, k_init_f, grid, kBlock, &n1, n, ld, (const double*)h->r, cdinv, cAW,
-                           cRinv, h->partials, c0, h->st, h_inner, use_cond));
-    PODCG_CK(h, add_kernel(O, &n1, 1, k_dir0_f, grid, kBlock, &n2, n, ld, h->x, h->p, (const double*)h->r, cdinv,
-                           cW, (const DevState*)h->st));
-    PODCG_CK(h, add_while(O, &n2, 1, h_inner, &n3, &I));
-    PODCG_CK(h, add_kernel(O, &n3, 1, k_res_f, grid_spmv, kBlock, &n4, (const ProbDesc*)h->pd,
-                           (const double*)h->x, h->r, h->partials, c1, h->st, zero, inner_tol, h_outer, use_cond));
-    PODCG_CK(h, add_kernel(I, nullptr, 0, k_spmv_f, grid_spmv, kBlock, &m1, (const ProbDesc*)h->pd,
-                           (const double*)h->p, h->q, h->partials, c2, h->st));
-    PODCG_CK(h, add_kernel(I, &m1, 1, k_upd_f, grid, kBlock, &m2, n, ld, h->r, (const double*)h->q, cdinv, cAW,
-                           cRinv, h->partials, c3, h->st, h_inner, use_cond));
-    PODCG_CK(h, add_kernel(I, &m2, 1, k_dir_f, grid, kBlock, &m3, n, ld, h->x, h->p, (const double*)h->r, cdinv, cW,
-                           (const DevState*)h->st));
-    cudaGraphExec_t exec = nullptr;
-    PODCG_CK(h, cudaGraphInstantiate(&exec, P, 0));
-    gs.graph = P;
-    gs.exec = exec;
-    gs.L = L;
-    gs.valid = true;
-    return POD_CG_OK;
+    void *f_init, *f_upd, *f_dir0, *f_dir;
+    cg_kernels(wb, mixed, use_cond != 0, &f_init, &f_upd, &f_dir0, &f_dir);
+    void* f_spmv = kernel_spmv_cg(L, mixed);
+    void* f_res = kernel_residual(L, use_cond != 0);
+    const int g_init = occ_grid(h, f_init, n, kBlock);
+    const int g_upd = occ_grid(h, f_upd, n, kBlock);
+    const int g_dir = occ_grid(h, f_dir, n, kBlock);
+    const int g_spmv = occ_grid(h, f_spmv, n, kBlock / L);
+    const int g_res = occ_grid(h, f_res, n, kBlock / L);
+    unsigned int* c = h->counters;
+    const ProbDesc* pd = h->pd;
+    DevState* st = h->st;
+    const DevState* cst = h->st;
+    const double* Rinv = h->Rinv;
+    const double inner_tol = h->cfg.inner_tol;
+    P.res.set(f_res, g_res, pd, (const double*)h->x, h->r, h->partials, c + 1, st, (int)mixed, inner_tol, h_outer,
+              use_cond);
+    if (!mixed) {
+        P.init.set(f_init, g_init, n, ld, (const double*)h->r, (const double*)h->dinv, (const double*)h->AW,
+                   h->partials, c + 0, st, h_inner, use_cond);
+        P.dir0.set(f_dir0, g_dir, n, ld, h->x, h->p, (const double*)h->r, (const double*)h->dinv,
+                   (const double*)h->W, Rinv, cst);
+        P.spmv.set(f_spmv, g_spmv, pd, (const double*)h->p, h->q, h->partials, c + 2, st);
+        P.upd.set(f_upd, g_upd, n, ld, h->r, (const double*)h->q, (const double*)h->dinv, (const double*)h->AW,
+                  h->partials, c + 3, st, h_inner, use_cond);
+        P.dir.set(f_dir, g_dir, n, ld, h->x, h->p, (const double*)h->r, (const double*)h->dinv,
+                  (const double*)h->W, Rinv, cst);
+    } else {
+        void *f_proj, *f_start;
+        mixed_kernels(wb, &f_proj, &f_start);
+        void* f_acc = kernel_mx_accum();
+        P.mxproj.set(f_proj, occ_grid(h, f_proj, n, kBlock), n, ld, (const double*)h->r, h->r32,
+                     (const float*)h->W32, h->partials, c + 5, st);
+        P.mxstart.set(f_start, occ_grid(h, f_start, n, kBlock), n, ld, h->d32, h->r32, (const float*)h->W32,
+                      (const float*)h->AW32, Rinv, cst);
+        P.init.set(f_init, g_init, n, ld, (const float*)h->r32, (const float*)h->dinv32, (const float*)h->AW32,
+                   h->partials, c + 0, st, h_inner, use_cond);
+        P.dir0.set(f_dir0, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
+                   (const float*)h->W32, Rinv, cst);
+        P.spmv.set(f_spmv, g_spmv, pd, (const float*)h->p32, h->q32, h->partials, c + 2, st);
+        P.upd.set(f_upd, g_upd, n, ld, h->r32, (const float*)h->q32, (const float*)h->dinv32,
+                  (const float*)h->AW32, h->partials, c + 3, st, h_inner, use_cond);
+        P.dir.set(f_dir, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
+                  (const float*)h->W32, Rinv, cst);
+        P.mxaccum.set(f_acc, occ_grid(h, f_acc, n, kBlock), n, h->x, (const float*)h->d32, cst);
+    }
 }
 
 void destroy_graph(GraphSlot& gs)
@@ -231,10 +300,181 @@ void destroy_graph(GraphSlot& gs)
     gs = GraphSlot();
 }
 
+// The whole stage-two loop as one graph with two nested conditional while-nodes.
+pod_cg_status build_conditional(pod_cg_t* h, int wb, int L, GraphSlot& gs)
+{
+    cudaGraph_t P = nullptr, O = nullptr, I = nullptr;
+    PODCG_CK(h, cudaGraphCreate(&P, 0));
+    cudaGraphConditionalHandle h_outer, h_inner;
+    PODCG_CK(h, cudaGraphConditionalHandleCreate(&h_outer, P, 1, cudaGraphCondAssignDefault));
+    cudaGraphNode_t n_outer;
+    PODCG_CK(h, add_while(P, nullptr, 0, h_outer, &n_outer, &O));
+    PODCG_CK(h, cudaGraphConditionalHandleCreate(&h_inner, O, 0, 0));
+    Plan pl;
+    make_plan(h, wb, L, h->mixed, 1, h_inner, h_outer, pl);
+    cudaGraphNode_t a, b, c, d, e, f, g, m1, m2, m3;
+    if (!h->mixed) {
+        PODCG_CK(h, add_node(O, nullptr, 0, pl.init, &a));
+        PODCG_CK(h, add_node(O, &a, 1, pl.dir0, &b));
+        PODCG_CK(h, add_while(O, &b, 1, h_inner, &c, &I));
+        PODCG_CK(h, add_node(O, &c, 1, pl.res, &d));
+    } else {
+        PODCG_CK(h, add_node(O, nullptr, 0, pl.res, &a));
+        PODCG_CK(h, add_node(O, &a, 1, pl.mxproj, &b));
+        PODCG_CK(h, add_node(O, &b, 1, pl.mxstart, &c));
+        PODCG_CK(h, add_node(O, &c, 1, pl.init, &d));
+        PODCG_CK(h, add_node(O, &d, 1, pl.dir0, &e));
+        PODCG_CK(h, add_while(O, &e, 1, h_inner, &f, &I));
+        PODCG_CK(h, add_node(O, &f, 1, pl.mxaccum, &g));
+    }
+    PODCG_CK(h, add_node(I, nullptr, 0, pl.spmv, &m1));
+    PODCG_CK(h, add_node(I, &m1, 1, pl.upd, &m2));
+    PODCG_CK(h, add_node(I, &m2, 1, pl.dir, &m3));
+    cudaGraphExec_t exec = nullptr;
+    PODCG_CK(h, cudaGraphInstantiate(&exec, P, 0));
+    gs.graph = P;
+    gs.exec = exec;
+    gs.L = L;
+    gs.valid = true;
+    return POD_CG_OK;
+}
+
+// kChunk unrolled inner iterations as a plain graph (no conditional nodes).
+pod_cg_status build_chunk(pod_cg_t* h, int wb, int L, GraphSlot& gs)
+{
+    cudaGraph_t P = nullptr;
+    PODCG_CK(h, cudaGraphCreate(&P, 0));
+    Plan pl;
+    make_plan(h, wb, L, h->mixed, 0, 0, 0, pl);
+    cudaGraphNode_t prev = nullptr, cur;
+    for (int it = 0; it < kChunk; ++it) {
+        PODCG_CK(h, add_node(P, prev ? &prev : nullptr, prev ? 1 : 0, pl.spmv, &cur));
+        prev = cur;
+        PODCG_CK(h, add_node(P, &prev, 1, pl.upd, &cur));
+        prev = cur;
+        PODCG_CK(h, add_node(P, &prev, 1, pl.dir, &cur));
+        prev = cur;
+    }
+    cudaGraphExec_t exec = nullptr;
+    PODCG_CK(h, cudaGraphInstantiate(&exec, P, 0));
+    gs.graph = P;
+    gs.exec = exec;
+    gs.L = L;
+    gs.valid = true;
+    return POD_CG_OK;
+}
+
+pod_cg_status read_state(pod_cg_t* h)
+{
+    PODCG_CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    PODCG_CK(h, cudaStreamSynchronize(h->stream));
+    return POD_CG_OK;
+}
+
+// Stage two: run the loop in the configured form.
+pod_cg_status run_loop(pod_cg_t* h, int wb, int L)
+{
+    const int bi = bucket_index(wb);
+    cudaStream_t s = h->stream;
+    if (h->cfg.loop_mode == 0) {
+        GraphSlot& gs = h->graphs[bi];
+        if (gs.valid && gs.L != L) destroy_graph(gs);
+        if (!gs.valid) {
+            pod_cg_status bs = build_conditional(h, wb, L, gs);
+            if (bs != POD_CG_OK) return bs;
+        }
+        PODCG_CK(h, cudaGraphLaunch(gs.exec, s));
+        return POD_CG_OK;
+    }
+    GraphSlot& gs = h->chunks[bi];
+    if (gs.valid && gs.L != L) destroy_graph(gs);
+    if (!gs.valid) {
+        pod_cg_status bs = build_chunk(h, wb, L, gs);
+        if (bs != POD_CG_OK) return bs;
+    }
+    Plan pl;
+    make_plan(h, wb, L, h->mixed, 0, 0, 0, pl);
+    const long long max_chunks = (long long)h->cfg.k_max / kChunk + 2;
+    for (int pass = 0; pass <= h->cfg.max_refine + 1; ++pass) {
+        if (h->mixed) {
+            PODCG_CK(h, launch_spec(pl.res, s));
+            PODCG_CK(h, launch_spec(pl.mxproj, s));
+            PODCG_CK(h, launch_spec(pl.mxstart, s));
+        }
+        PODCG_CK(h, launch_spec(pl.init, s));
+        PODCG_CK(h, launch_spec(pl.dir0, s));
+        pod_cg_status rs = read_state(h);
+        if (rs != POD_CG_OK) return rs;
+        for (long long c = 0; !h->st_host->done && c < max_chunks; ++c) {
+            PODCG_CK(h, cudaGraphLaunch(gs.exec, s));
+            rs = read_state(h);
+            if (rs != POD_CG_OK) return rs;
+        }
+        if (h->mixed) {
+            PODCG_CK(h, launch_spec(pl.mxaccum, s));
+        } else {
+            PODCG_CK(h, launch_spec(pl.res, s));
+        }
+        rs = read_state(h);
+        if (rs != POD_CG_OK) return rs;
+        if (h->st_host->outer_done) break;
+    }
+    return POD_CG_OK;
+}
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
 {
     return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+void reset_state(pod_cg_t* h, const pod_cg_csr* A, const double* b)
+{
+    *h->pd_host = ProbDesc{A->row_ptr, A->col, A->val, h->val32, b, nullptr, h->n, h->ld};
+    DevState& sh = *h->st_host;
+    std::memset(&sh, 0, sizeof(DevState));
+    sh.k_max = h->cfg.k_max;
+    sh.max_refine = h->cfg.max_refine;
+    sh.pod_w = h->pod_w;
+    sh.w = h->pod_w;
+    sh.mixed = h->mixed ? 1 : 0;
+    sh.rr_stage1 = -1.0;
+}
+
+pod_cg_status finish_solve(pod_cg_t* h, double* out, int w_pod, int launches, pod_cg_stats* stats, int sysid)
+{
+    cudaStream_t s = h->stream;
+    PODCG_CK(h, cudaEventRecord(h->ev[3], s));
+    PODCG_CK(h, cudaMemcpyAsync(out, h->x, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
+    pod_cg_status rs = read_state(h);
+    if (rs != POD_CG_OK) return rs;
+    const DevState& d = *h->st_host;
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->status = d.status;
+        stats->iters = d.iters;
+        stats->refinements = d.restarts;
+        stats->w = d.w;
+        stats->s = h->s_count;
+        stats->chol_failed = d.chol_failed;
+        stats->system_id = sysid;
+        stats->spmv_count = d.iters + w_pod + d.restarts + 1;
+        const int per_pass = h->mixed ? 6 : 3;
+        stats->launches = launches + per_pass * (d.restarts + 1) + 3 * d.iters;
+        stats->stage1_relres = d.bb > 0.0 ? std::sqrt(std::max(d.rr_stage1, 0.0) / d.bb) : 0.0;
+        stats->final_relres = d.bb > 0.0 ? std::sqrt(d.rr_true / d.bb) : 0.0;
+        stats->cond_gram = d.cond;
+        cudaEventElapsedTime(&stats->ms_pod, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&stats->ms_stage1, h->ev[1], h->ev[2]);
+        cudaEventElapsedTime(&stats->ms_stage2, h->ev[2], h->ev[3]);
+    }
+    if (d.status != 0) {
+        static const char* names[] = {"ok", "arg", "not SPD (non-positive diagonal)", "breakdown: (Ap, p) <= 0",
+                                      "iteration/refinement cap reached", "non-finite scalar"};
+        const char* nm = (d.status >= 0 && d.status <= 5) ? names[d.status] : "error";
+        return fail(h, (pod_cg_status)d.status, std::string("solve: ") + nm);
+    }
+    return POD_CG_OK;
 }
 
 }  // namespace
@@ -260,6 +500,7 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->use_tc_gram = 0;
     c->cond_diag = 0;
     c->keep_factors = 0;
+    c->loop_mode = 0;
     return POD_CG_OK;
 }
 
@@ -271,10 +512,11 @@ const char* pod_cg_last_error(const pod_cg_t* h)
 pod_cg_status pod_cg_destroy(pod_cg_t* h)
 {
     if (!h) return POD_CG_OK;
-    for (auto& row : h->graphs)
-        for (auto& g : row) destroy_graph(g);
-    void* bufs[] = {h->S, h->GS, h->grow, h->C, h->sigma2, h->W, h->AW, h->G, h->Rinv, h->x, h->r, h->p,
-                    h->q, h->dinv, h->dinv32, h->partials, h->counters, h->gram_work, h->st, h->pd};
+    for (auto& g : h->graphs) destroy_graph(g);
+    for (auto& g : h->chunks) destroy_graph(g);
+    void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->W, h->AW, h->W32, h->AW32, h->G, h->Rinv,
+                    h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
+                    h->partials, h->counters, h->gram_work, h->st, h->pd, h->kW, h->kAW, h->kG};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->st_host) cudaFreeHost(h->st_host);
@@ -295,19 +537,21 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     else pod_cg_config_default(&c);
     if (c.w_max < 1 || c.w_max > kWMax || c.s_max < 1 || c.s_max > kSMax || !(c.energy >= 0.0 && c.energy <= 1.0) ||
         c.k_max < 0 || c.max_refine < 0 || (c.precision != POD_CG_FP64 && c.precision != POD_CG_MIXED) ||
-        c.keep_factors < 0)
+        c.keep_factors < 0 || c.keep_factors > 4096 || (c.loop_mode != 0 && c.loop_mode != 1) ||
+        !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
         return fail(nullptr, POD_CG_ERR_ARG, "invalid configuration");
     pod_cg_t* h = new (std::nothrow) pod_cg_t();
     if (!h) return fail(nullptr, POD_CG_ERR_OOM, "host allocation failed");
     h->n = n;
     h->ld = ((n + 31) / 32) * 32;
     h->cfg = c;
+    h->mixed = c.precision == POD_CG_MIXED;
     h->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&h->device);
     h->sms = device_sms();
     const size_t ld = (size_t)h->ld;
     cudaError_t e = cudaSuccess;
-#define PODCG_ALLOC(ptr, cnt)                                           \
+#define PODCG_ALLOC(ptr, cnt) \
     if (e == cudaSuccess) e = dalloc(&(ptr), (cnt));
     PODCG_ALLOC(h->S, ld * c.s_max)
     PODCG_ALLOC(h->GS, (size_t)kSMax * kSMax)
@@ -324,10 +568,26 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     PODCG_ALLOC(h->q, ld)
     PODCG_ALLOC(h->dinv, ld)
     PODCG_ALLOC(h->dinv32, ld)
-    PODCG_ALLOC(h->partials, (size_t)h->sms * 8 * (kWMax + 2))
+    PODCG_ALLOC(h->partials, (size_t)(kWMax + 2) * kPartialStride)
     PODCG_ALLOC(h->counters, 16)
     PODCG_ALLOC(h->st, 1)
     PODCG_ALLOC(h->pd, 1)
+    if (h->mixed) {
+        PODCG_ALLOC(h->S32, ld * c.s_max)
+        PODCG_ALLOC(h->W32, ld * c.w_max)
+        PODCG_ALLOC(h->AW32, ld * c.w_max)
+        PODCG_ALLOC(h->r32, ld)
+        PODCG_ALLOC(h->p32, ld)
+        PODCG_ALLOC(h->q32, ld)
+        PODCG_ALLOC(h->d32, ld)
+    }
+    if (c.keep_factors > 0) {
+        PODCG_ALLOC(h->kW, ld * c.w_max * c.keep_factors)
+        PODCG_ALLOC(h->kAW, ld * c.w_max * c.keep_factors)
+        PODCG_ALLOC(h->kG, (size_t)kWMax * (kWMax + 1) * c.keep_factors)
+        h->k_id.assign(c.keep_factors, -1);
+        h->k_w.assign(c.keep_factors, 0);
+    }
 #undef PODCG_ALLOC
     if (e == cudaSuccess) {
         h->gram_work_bytes = std::max(gram_workspace_bytes(n, 1, c.s_max, h->sms),
@@ -342,6 +602,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     if (e == cudaSuccess) e = cudaMemsetAsync(h->S, 0, sizeof(double) * ld * c.s_max, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->GS, 0, sizeof(double) * kSMax * kSMax, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->p, 0, sizeof(double) * ld, h->stream);
+    if (e == cudaSuccess && h->mixed) e = cudaMemsetAsync(h->p32, 0, sizeof(float) * ld, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         pod_cg_status s = cuda_fail(nullptr, "pod_cg_create", e);
@@ -371,6 +632,7 @@ pod_cg_status pod_cg_add_snapshots(pod_cg_t* h, const double* X, int m)
         const int slot = h->s_next;
         double* col = h->S + (size_t)slot * h->ld;
         PODCG_CK(h, cudaMemcpyAsync(col, X + (size_t)c * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+        if (h->mixed) PODCG_CK(h, launch_to_f32(col, h->S32 + (size_t)slot * h->ld, n, h->sms, h->stream));
         h->s_next = (h->s_next + 1) % h->cfg.s_max;
         h->s_count = std::min(h->s_count + 1, h->cfg.s_max);
         // new row of S^T S: s_new^T S (Algorithm 4 step 1, one row at a time)
@@ -387,6 +649,7 @@ pod_cg_status pod_cg_get_basis(pod_cg_t* h, double* W_out, int* w_out)
     if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
     if (w_out) *w_out = h->pod_w;
     if (W_out && h->pod_w > 0) {
+        if (h->mixed) return fail(h, POD_CG_ERR_STATE, "the FP64 basis is not formed in mixed precision");
         PODCG_CK(h, cudaMemcpy2DAsync(W_out, sizeof(double) * h->n, h->W, sizeof(double) * h->ld,
                                       sizeof(double) * h->n, h->pod_w, cudaMemcpyDeviceToDevice, h->stream));
     }
@@ -403,33 +666,37 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     if (!b || !x_out) return fail(h, POD_CG_ERR_ARG, "b and x_out must be non-NULL");
     if (b == x_out) return fail(h, POD_CG_ERR_ARG, "x_out may not alias b");
     if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(h, POD_CG_ERR_ARG, "tol must be finite and >= 0");
-    if (h->cfg.precision != POD_CG_FP64) return fail(h, POD_CG_ERR_ARG, "precision mode not available");
     const int n = h->n;
     cudaStream_t s = h->stream;
+    if (h->mixed && A->nnz > h->val32_cap) {
+        if (h->val32) cudaFree(h->val32);
+        h->val32 = nullptr;
+        h->val32_cap = 0;
+        PODCG_CK(h, cudaMalloc((void**)&h->val32, sizeof(float) * (size_t)std::max<int64_t>(A->nnz, 1)));
+        h->val32_cap = A->nnz;
+    }
 
-    // problem descriptor and fresh device state
-    *h->pd_host = ProbDesc{A->row_ptr, A->col, A->val, nullptr, b, nullptr, n, h->ld};
+    reset_state(h, A, b);
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
-    DevState& sh = *h->st_host;
-    std::memset(&sh, 0, sizeof(DevState));
-    sh.k_max = h->cfg.k_max;
-    sh.max_refine = h->cfg.max_refine;
-    sh.pod_w = h->pod_w;
-    sh.w = h->pod_w;
-    PODCG_CK(h, cudaMemcpyAsync(h->st, &sh, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
     PODCG_CK(h, launch_dinv(h->pd, n, h->dinv, h->dinv32, h->st, h->sms, s));
-
     int launches = 2;   // dinv, stage-one lift
+    if (h->mixed) {
+        PODCG_CK(h, launch_desc_val_to_f32(h->pd, h->val32, A->nnz, h->sms, s));
+        launches += 1;
+    }
+
     // POD of the current snapshots (Algorithm 4)
     if (h->s_count > 0 && h->pod_dirty) {
-        launches += 2;
         PODCG_CK(h, launch_pod_eig(h->GS, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, h->cfg.w_max, h->C,
                                    h->sigma2, h->st, s));
-        PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->W, h->ld, h->sms, s));
-        PODCG_CK(h, cudaMemcpyAsync(&sh.pod_w, &h->st->pod_w, sizeof(int), cudaMemcpyDeviceToHost, s));
-        PODCG_CK(h, cudaStreamSynchronize(s));
-        h->pod_w = sh.pod_w;
+        if (h->mixed) PODCG_CK(h, launch_lift32(n, h->S32, h->ld, h->s_count, h->C, h->st, h->W32, h->ld, h->sms, s));
+        else PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->W, h->ld, h->sms, s));
+        launches += 2;
+        pod_cg_status rs = read_state(h);
+        if (rs != POD_CG_OK) return rs;
+        h->pod_w = h->st_host->pod_w;
         h->pod_dirty = false;
     } else if (h->s_count == 0) {
         h->pod_w = 0;
@@ -439,67 +706,100 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
 
     // stage one (Algorithm 2)
     if (w > 0) {
-        PODCG_CK(h, launch_spmm(A->row_ptr, A->col, A->val, h->W, h->ld, h->AW, h->ld, n, w, h->sms, s));
-        PODCG_CK(h, launch_gram(n, h->W, h->ld, w, h->AW, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
+        if (h->mixed) {
+            PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32, h->ld, h->AW32, h->ld, n, w, h->sms, s));
+            PODCG_CK(h, launch_gram32(n, h->W32, h->ld, w, h->AW32, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
+                                      h->gram_work_bytes, h->sms, s));
+        } else {
+            PODCG_CK(h, launch_spmm(A->row_ptr, A->col, A->val, h->W, h->ld, h->AW, h->ld, n, w, h->sms, s));
+            PODCG_CK(h, launch_gram(n, h->W, h->ld, w, h->AW, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
+                                    h->gram_work_bytes, h->sms, s));
+        }
+        PODCG_CK(h, launch_chol(h->G, kWMax + 1, h->Rinv, h->st, h->cfg.cond_diag, s));
+        launches += 4;
+    }
+    const int wb = wb_bucket(w);
+    if (h->mixed)
+        PODCG_CK(h, launch_stage1_mx(wb, h->pd, n, h->W32, h->x, h->partials, h->counters + 4, h->st, tol, h->sms, s));
+    else
+        PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4, h->st, tol,
+                                  h->sms, s));
+    PODCG_CK(h, cudaEventRecord(h->ev[2], s));
+
+    // stage two
+    const int L = spmv_lanes_for(n > 0 ? double(A->nnz) / n : 1.0);
+    pod_cg_status ls = run_loop(h, wb, L);
+    if (ls != POD_CG_OK) return ls;
+    const int sysid = h->system_counter++;
+    pod_cg_status fs = finish_solve(h, x_out, w, launches, stats, sysid);
+
+    // keep this system's factors for the adjoint
+    if (h->cfg.keep_factors > 0 && !h->mixed && fs == POD_CG_OK) {
+        const int slot = h->k_next;
+        h->k_next = (h->k_next + 1) % h->cfg.keep_factors;
+        const int wu = h->st_host->w;
+        const size_t blk = (size_t)h->ld * h->cfg.w_max;
+        if (wu > 0) {
+            PODCG_CK(h, cudaMemcpyAsync(h->kW + slot * blk, h->W, sizeof(double) * h->ld * wu, cudaMemcpyDeviceToDevice, s));
+            PODCG_CK(h, cudaMemcpyAsync(h->kAW + slot * blk, h->AW, sizeof(double) * h->ld * wu, cudaMemcpyDeviceToDevice, s));
+            PODCG_CK(h, cudaMemcpyAsync(h->kG + (size_t)slot * kWMax * (kWMax + 1), h->G,
+                                        sizeof(double) * kWMax * (kWMax + 1), cudaMemcpyDeviceToDevice, s));
+        }
+        h->k_id[slot] = sysid;
+        h->k_w[slot] = wu;
+        PODCG_CK(h, cudaStreamSynchronize(s));
+    }
+    return fs;
+}
+
+pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr* A, const double* g, double tol,
+                                   double* lambda_out, pod_cg_stats* stats)
+{
+    if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
+    pod_cg_status cs = check_csr(h, A, h->n);
+    if (cs != POD_CG_OK) return cs;
+    if (!g || !lambda_out || g == lambda_out) return fail(h, POD_CG_ERR_ARG, "bad g / lambda_out");
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(h, POD_CG_ERR_ARG, "tol must be finite and >= 0");
+    if (h->mixed) return fail(h, POD_CG_ERR_ARG, "the adjoint solve runs in FP64 mode");
+    int slot = -1;
+    for (int k = 0; k < (int)h->k_id.size(); ++k)
+        if (h->k_id[k] == system_id) slot = k;
+    if (slot < 0) return fail(h, POD_CG_ERR_STATE, "factors of this system were not kept (keep_factors too small?)");
+    const int n = h->n;
+    cudaStream_t s = h->stream;
+    const int w = h->k_w[slot];
+    const size_t blk = (size_t)h->ld * h->cfg.w_max;
+    // restore W_j, A_j W_j and W_j^T A_j W_j of the forward solve (A_j symmetric: same factor)
+    if (w > 0) {
+        PODCG_CK(h, cudaMemcpyAsync(h->W, h->kW + slot * blk, sizeof(double) * h->ld * w, cudaMemcpyDeviceToDevice, s));
+        PODCG_CK(h, cudaMemcpyAsync(h->AW, h->kAW + slot * blk, sizeof(double) * h->ld * w, cudaMemcpyDeviceToDevice, s));
+        PODCG_CK(h, cudaMemcpyAsync(h->G, h->kG + (size_t)slot * kWMax * (kWMax + 1),
+                                    sizeof(double) * kWMax * (kWMax + 1), cudaMemcpyDeviceToDevice, s));
+    }
+    h->pod_w = w;
+    h->pod_dirty = h->s_count > 0;   // the next forward solve recomputes its own basis
+    reset_state(h, A, g);
+    PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+    PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    PODCG_CK(h, cudaEventRecord(h->ev[0], s));
+    PODCG_CK(h, launch_dinv(h->pd, n, h->dinv, h->dinv32, h->st, h->sms, s));
+    PODCG_CK(h, cudaEventRecord(h->ev[1], s));
+    int launches = 2;
+    if (w > 0) {
+        // ghat = W^T g into the right-hand-side column of the saved Gram, then the Cholesky
+        PODCG_CK(h, launch_gram(n, h->W, h->ld, w, nullptr, h->ld, 0, g, h->G + w, kWMax + 1, 0, h->gram_work,
                                 h->gram_work_bytes, h->sms, s));
         PODCG_CK(h, launch_chol(h->G, kWMax + 1, h->Rinv, h->st, h->cfg.cond_diag, s));
-        launches += 4;   // spmm, gram partial + reduce, cholesky
+        launches += 3;
     }
     const int wb = wb_bucket(w);
     PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4, h->st, tol,
                               h->sms, s));
     PODCG_CK(h, cudaEventRecord(h->ev[2], s));
-
-    // stage two: the captured loop
-    const double mean_row = n > 0 ? double(A->nnz) / n : 1.0;
-    const int L = spmv_lanes_for(mean_row);
-    GraphSlot& gs = h->graphs[bucket_index(wb)][0];
-    if (gs.valid && gs.L != L) destroy_graph(gs);
-    if (!gs.valid) {
-        pod_cg_status bs = build_graph_fp64(h, wb, L, gs);
-        if (bs != POD_CG_OK) return bs;
-    }
-    PODCG_CK(h, cudaGraphLaunch(gs.exec, s));
-    PODCG_CK(h, cudaEventRecord(h->ev[3], s));
-    PODCG_CK(h, cudaMemcpyAsync(x_out, h->x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    PODCG_CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    PODCG_CK(h, cudaStreamSynchronize(s));
-
-    const DevState& d = *h->st_host;
-    const int sysid = h->system_counter++;
-    if (stats) {
-        std::memset(stats, 0, sizeof(*stats));
-        stats->status = d.status;
-        stats->iters = d.iters;
-        stats->refinements = d.restarts;
-        stats->w = d.w;
-        stats->s = h->s_count;
-        stats->chol_failed = d.chol_failed;
-        stats->system_id = sysid;
-        stats->spmv_count = d.iters + w + d.restarts + 1;
-        // graph: per outer pass init + first direction + residual; per iteration 3 kernels
-        stats->launches = launches + 3 * (d.restarts + 1) + 3 * d.iters;
-        stats->stage1_relres = d.bb > 0.0 ? std::sqrt(d.rr_stage1 / d.bb) : 0.0;
-        stats->final_relres = d.bb > 0.0 ? std::sqrt(d.rr_true / d.bb) : 0.0;
-        stats->cond_gram = d.cond;
-        cudaEventElapsedTime(&stats->ms_pod, h->ev[0], h->ev[1]);
-        cudaEventElapsedTime(&stats->ms_stage1, h->ev[1], h->ev[2]);
-        cudaEventElapsedTime(&stats->ms_stage2, h->ev[2], h->ev[3]);
-    }
-    if (d.status != 0) {
-        static const char* names[] = {"ok", "arg", "not SPD (non-positive diagonal)", "breakdown: (Ap, p) <= 0",
-                                      "iteration/refinement cap reached", "non-finite scalar"};
-        const char* nm = (d.status >= 0 && d.status <= 5) ? names[d.status] : "error";
-        return fail(h, (pod_cg_status)d.status, std::string("solve: ") + nm);
-    }
-    return POD_CG_OK;
-}
-
-pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr* A, const double* g, double tol,
-                                   double* lambda_out, pod_cg_stats* st)
-{
-    (void)system_id; (void)A; (void)g; (void)tol; (void)lambda_out; (void)st;
-    return fail(h, POD_CG_ERR_STATE, "adjoint factors not kept");
+    const int L = spmv_lanes_for(n > 0 ? double(A->nnz) / n : 1.0);
+    pod_cg_status ls = run_loop(h, wb, L);
+    if (ls != POD_CG_OK) return ls;
+    return finish_solve(h, lambda_out, w, launches, stats, system_id);
 }
 
 pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double* b, int reps, float* ms_out)
@@ -508,67 +808,34 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
     pod_cg_status cs = check_csr(h, A, h->n);
     if (cs != POD_CG_OK) return cs;
     if (!b || !ms_out || reps < 1) return fail(h, POD_CG_ERR_ARG, "bad arguments");
-    const int n = h->n, ld = h->ld;
     cudaStream_t s = h->stream;
-    *h->pd_host = ProbDesc{A->row_ptr, A->col, A->val, nullptr, b, nullptr, n, h->ld};
+    reset_state(h, A, b);
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
+    DevState& t = *h->st_host;
+    t.rho = 1.0;
+    t.alpha = 1e-30;
+    t.beta = 0.5;
+    t.k_max = 1 << 30;
+    t.max_refine = 1 << 30;
+    t.tol2 = 0.0;
+    t.tol2_in = -1.0;
+    t.dir_pending = 1;
     const int w = h->pod_w;
-    const int wb = wb_bucket(w);
-    const int L = spmv_lanes_for(n > 0 ? double(A->nnz) / n : 1.0);
-    const int grid = grid_rows(n, kBlock, h->sms);
-    const int grid_spmv = grid_rows(n, kBlock / L, h->sms);
-    void *k_init_f, *k_upd_f, *k_dir0_f, *k_dir_f;
-    cg_kernels(wb, false, &k_init_f, &k_upd_f, &k_dir0_f, &k_dir_f);
-    void* k_spmv_f = kernel_spmv_cg(L, false);
-    void* k_res_f = kernel_residual(L);
-    DevState tmpl;
-    std::memset(&tmpl, 0, sizeof(tmpl));
-    tmpl.rho = 1.0;
-    tmpl.alpha = 1e-30;
-    tmpl.beta = 0.5;
-    tmpl.w = w;
-    tmpl.pod_w = w;
-    tmpl.k_max = 1 << 30;
-    tmpl.max_refine = 1 << 30;
-    tmpl.tol2 = 0.0;
-    tmpl.tol2_in = -1.0;
-    *h->st_host = tmpl;
-    const double* cW = h->W;
-    const double* cAW = h->AW;
-    const double* cRinv = h->Rinv;
-    const double* cdinv = h->dinv;
-    const double* cr = h->r;
-    const double* cq = h->q;
-    const double* cp = h->p;
-    const double* cx = h->x;
-    const DevState* cst = h->st;
-    const ProbDesc* cpd = h->pd;
-    cudaGraphConditionalHandle h0 = 0;
-    int no_cond = 0, zero = 0;
-    double inner_tol = h->cfg.inner_tol;
-    unsigned int* c2 = h->counters + 2;
-    unsigned int* c3 = h->counters + 3;
-    unsigned int* c1 = h->counters + 1;
-    void* a_spmv[] = {(void*)&cpd, (void*)&cp, (void*)&h->q, (void*)&h->partials, (void*)&c2, (void*)&h->st};
-    void* a_upd[] = {(void*)&n, (void*)&ld, (void*)&h->r, (void*)&cq, (void*)&cdinv, (void*)&cAW, (void*)&cRinv,
-                     (void*)&h->partials, (void*)&c3, (void*)&h->st, (void*)&h0, (void*)&no_cond};
-    void* a_dir[] = {(void*)&n, (void*)&ld, (void*)&h->x, (void*)&h->p, (void*)&cr, (void*)&cdinv, (void*)&cW,
-                     (void*)&cst};
-    void* a_res[] = {(void*)&cpd, (void*)&cx, (void*)&h->r, (void*)&h->partials, (void*)&c1, (void*)&h->st,
-                     (void*)&zero, (void*)&inner_tol, (void*)&h0, (void*)&no_cond};
-    struct K { void* f; int g; void** a; } ks[4] = {{k_spmv_f, grid_spmv, a_spmv}, {k_upd_f, grid, a_upd},
-                                                   {k_dir_f, grid, a_dir}, {k_res_f, grid_spmv, a_res}};
+    const int L = spmv_lanes_for(h->n > 0 ? double(A->nnz) / h->n : 1.0);
+    Plan pl;
+    make_plan(h, wb_bucket(w), L, h->mixed, 0, 0, 0, pl);
+    KSpec* ks[4] = {&pl.spmv, &pl.upd, &pl.dir, &pl.res};
     for (int k = 0; k < 4; ++k) {
         float total = 0.0f;
         for (int rep = 0; rep < reps + 1; ++rep) {
             PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
             PODCG_CK(h, cudaEventRecord(h->ev[0], s));
-            PODCG_CK(h, cudaLaunchKernel(ks[k].f, dim3(ks[k].g), dim3(kBlock), ks[k].a, 0, s));
+            PODCG_CK(h, launch_spec(*ks[k], s));
             PODCG_CK(h, cudaEventRecord(h->ev[1], s));
             PODCG_CK(h, cudaEventSynchronize(h->ev[1]));
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
-            if (rep > 0) total += ms;   // first launch is a warm-up
+            if (rep > 0) total += ms;   // the first launch is a warm-up
         }
         ms_out[k] = total / reps;
     }

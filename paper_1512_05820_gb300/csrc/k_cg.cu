@@ -5,85 +5,104 @@
 // One iteration is three launches:
 //   k_spmv_cg : q = A p, gamma = (q, p), alpha = (r, z)/gamma            (k_sparse.cu)
 //   k_update  : r -= alpha q, z = M^{-1} r, (r, z), ||r||^2, c = (A W)^T z;
-//               last block: beta, mu = R^{-1} R^{-T} c (stage-one factor reused,
-//               Section 4.3), iteration count, exit test -> graph condition
-//   k_dir     : x += alpha p, p = z + beta p - W mu  (z recomputed from r, never stored)
+//               last block: beta, iteration count, exit test -> graph condition
+//   k_dir     : mu = R^{-1} R^{-T} c (every block, from the stage-one factor reused as in
+//               Section 4.3), x += alpha p, p = z + beta p - W mu (z recomputed from r)
 // (A W)^T z equals the paper's W^T A z because A is symmetric.
+//
+// The same kernels run inside a conditional while-graph (the loop stops on the device)
+// or inside a plain graph of several unrolled iterations whose later launches return
+// immediately: k_spmv_cg and k_update skip once `done` is set, and k_dir runs only when
+// the k_update of its iteration did (`dir_pending`). COND = false compiles the variants
+// with no graph-condition call at all, for plain graphs and direct launches.
 #include "common.cuh"
 #include "launch.h"
 
 namespace podcg {
 
-// mu = R^{-1} (R^{-T} c) for c in s_c[0..w) (shared), R^{-1} upper with row stride kWMax.
-__device__ __forceinline__ void apply_rinv(const double* __restrict__ Rinv, const double* s_c, double* s_t,
-                                           int w, double* mu_out)
+// mu = R^{-1} (R^{-T} c) in shared memory: s_R holds R^{-1} (row stride WB), s_c holds c.
+template <int WB>
+__device__ __forceinline__ void block_mu(const double* __restrict__ Rinv, const double* __restrict__ c, int w,
+                                         double* s_R, double* s_c, double* s_t, double* s_mu)
 {
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int i = e / w, j = e % w;
+        s_R[i * WB + j] = Rinv[i * kWMax + j];
+    }
+    for (int a = threadIdx.x; a < w; a += blockDim.x) s_c[a] = c[a];
+    __syncthreads();
     for (int a = threadIdx.x; a < w; a += blockDim.x) {
         double v = 0.0;
-        for (int k = 0; k <= a; ++k) v += Rinv[k * kWMax + a] * s_c[k];
+        for (int k = 0; k <= a; ++k) v += s_R[k * WB + a] * s_c[k];
         s_t[a] = v;
     }
     __syncthreads();
     for (int a = threadIdx.x; a < w; a += blockDim.x) {
         double v = 0.0;
-        for (int k = a; k < w; ++k) v += Rinv[a * kWMax + k] * s_t[k];
-        mu_out[a] = v;
+        for (int k = a; k < w; ++k) v += s_R[a * WB + k] * s_t[k];
+        s_mu[a] = v;
     }
     __syncthreads();
 }
 
-// Start of a CG pass from the residual r: z0 = M^{-1} r, (r, z0), ||r||^2, c = (A W)^T z0,
-// mu0; the residual test on r0 (zero iterations allowed).
-template <int WB, typename T>
+// Start of a CG pass from the residual r: z0 = M^{-1} r, (r, z0), ||r||^2, c = (A W)^T z0;
+// the residual test on r0 (zero iterations allowed). mu0 is formed by k_dir<FIRST>.
+template <int WB, typename T, bool COND>
 __global__ void __launch_bounds__(kBlock) k_init(int n, int ld, const T* __restrict__ r, const T* __restrict__ dinv,
-                                                 const T* __restrict__ AW, const double* __restrict__ Rinv,
-                                                 double* __restrict__ partials, unsigned int* counter, DevState* st,
+                                                 const T* __restrict__ AW, double* __restrict__ partials,
+                                                 unsigned int* counter, DevState* st,
                                                  cudaGraphConditionalHandle h_inner, int use_cond)
 {
     const int w = st->w;
-    double acc[WB + 2];
     T cl[WB > 0 ? WB : 1];
 #pragma unroll
     for (int j = 0; j < WB; ++j) cl[j] = T(0);
     T rho = T(0), rr = T(0);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const T ri = r[i];
-        const T zi = dinv[i] * ri;
-        rho += ri * zi;
-        rr += ri * ri;
+    const bool skip = st->outer_done != 0;   // mixed precision: the outer loop already stopped
+    if (!skip) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const T ri = r[i];
+            const T zi = dinv[i] * ri;
+            rho += ri * zi;
+            rr += ri * ri;
 #pragma unroll
-        for (int j = 0; j < WB; ++j)
-            if (j < w) cl[j] += __ldg(AW + (size_t)j * ld + i) * zi;
+            for (int j = 0; j < WB; ++j)
+                if (j < w) cl[j] += __ldg(AW + (size_t)j * ld + i) * zi;
+        }
     }
+    double acc[WB + 2];
     acc[0] = double(rho);
     acc[1] = double(rr);
 #pragma unroll
     for (int j = 0; j < WB; ++j) acc[2 + j] = double(cl[j]);
     __shared__ double tot[WB + 2];
-    __shared__ double s_t[WB > 0 ? WB : 1];
     if (reduce_to_last_block<WB + 2>(acc, 2 + w, partials, counter, tot)) {
-        apply_rinv(Rinv, tot + 2, s_t, w, st->mu);
+        for (int a = threadIdx.x; a < w; a += blockDim.x) st->c[a] = tot[2 + a];
         if (threadIdx.x == 0) {
             st->rho = tot[0];
             st->rr = tot[1];
             st->alpha = 0.0;
             st->beta = 0.0;
             if (st->status == 0 && !(isfinite(tot[0]) && isfinite(tot[1]))) st->status = 5;
-            const int done = (st->status != 0) || !(tot[1] > st->tol2_in);
+            const int done = skip || (st->status != 0) || !(tot[1] > st->tol2_in);
             st->done = done;
+            st->dir_pending = 0;
             st->inner_iters = 0;
-            if (use_cond) cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+            st->inner_break = 0;
+            if constexpr (COND) {
+                if (use_cond) cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+            }
         }
     }
 }
 
-template <int WB, typename T>
+template <int WB, typename T, bool COND>
 __global__ void __launch_bounds__(kBlock) k_update(int n, int ld, T* __restrict__ r, const T* __restrict__ q,
                                                    const T* __restrict__ dinv, const T* __restrict__ AW,
-                                                   const double* __restrict__ Rinv, double* __restrict__ partials,
-                                                   unsigned int* counter, DevState* st,
-                                                   cudaGraphConditionalHandle h_inner, int use_cond)
+                                                   double* __restrict__ partials, unsigned int* counter,
+                                                   DevState* st, cudaGraphConditionalHandle h_inner, int use_cond)
 {
+    if (st->done) return;   // uniform: only this kernel's last block writes `done`
     const int w = st->w;
     const T alpha = (st->status == 0) ? T(st->alpha) : T(0);
     T cl[WB > 0 ? WB : 1];
@@ -106,9 +125,8 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, int ld, T* __restrict_
 #pragma unroll
     for (int j = 0; j < WB; ++j) acc[2 + j] = double(cl[j]);
     __shared__ double tot[WB + 2];
-    __shared__ double s_t[WB > 0 ? WB : 1];
     if (reduce_to_last_block<WB + 2>(acc, 2 + w, partials, counter, tot)) {
-        apply_rinv(Rinv, tot + 2, s_t, w, st->mu);
+        for (int a = threadIdx.x; a < w; a += blockDim.x) st->c[a] = tot[2 + a];
         if (threadIdx.x == 0) {
             const double rho_new = tot[0];
             st->beta = rho_new / st->rho;
@@ -116,33 +134,47 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, int ld, T* __restrict_
             st->rr = tot[1];
             st->iters += 1;
             st->inner_iters += 1;
-            if (st->status == 0 && !(isfinite(rho_new) && isfinite(tot[1]))) st->status = 5;
-            int done = (st->status != 0) || !(tot[1] > st->tol2_in);
+            if (st->status == 0 && !(isfinite(rho_new) && isfinite(tot[1]))) {
+                if (st->mixed) st->inner_break = 1;
+                else st->status = 5;
+            }
+            int done = (st->status != 0) || st->inner_break || !(tot[1] > st->tol2_in);
             if (!done && st->iters >= st->k_max) {
                 st->status = 4;
                 done = 1;
             }
             st->done = done;
-            if (use_cond) cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+            st->dir_pending = 1;
+            if constexpr (COND) {
+                if (use_cond) cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+            }
         }
     }
 }
 
-// x += alpha p; then (unless the pass has finished) p = z + beta p - W mu with z = M^{-1} r.
-// FIRST: the initial direction p0 = z0 - W mu0 (x untouched).
+// mu = R^{-1} R^{-T} c; x += alpha p; then (unless the pass has finished)
+// p = z + beta p - W mu with z = M^{-1} r. FIRST: p0 = z0 - W mu0, x untouched.
 template <int WB, typename T, bool FIRST>
 __global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x, T* __restrict__ p,
                                                 const T* __restrict__ r, const T* __restrict__ dinv,
-                                                const T* __restrict__ W, const DevState* st)
+                                                const T* __restrict__ W, const double* __restrict__ Rinv,
+                                                const DevState* st)
 {
+    if (!FIRST && !st->dir_pending) return;
+    if (FIRST && st->outer_done) return;
     const int w = st->w;
-    const bool ok = st->status == 0;
+    const bool ok = st->status == 0 && !st->inner_break;
     const T alpha = ok ? T(st->alpha) : T(0);
     const T beta = T(st->beta);
     const bool upd_p = FIRST || (!st->done && ok);
+    __shared__ double s_R[WB > 0 ? WB * WB : 1];
+    __shared__ double s_c[WB > 0 ? WB : 1], s_t[WB > 0 ? WB : 1], s_mud[WB > 0 ? WB : 1];
     __shared__ T s_mu[WB > 0 ? WB : 1];
-    for (int j = threadIdx.x; j < WB; j += blockDim.x) s_mu[j] = (j < w) ? T(st->mu[j]) : T(0);
-    __syncthreads();
+    if (WB > 0 && upd_p) {
+        block_mu<WB>(Rinv, st->c, w, s_R, s_c, s_t, s_mud);
+        for (int j = threadIdx.x; j < WB; j += blockDim.x) s_mu[j] = (j < w) ? T(s_mud[j]) : T(0);
+        __syncthreads();
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const T pi = p[i];
         if (!FIRST) x[i] += alpha * pi;
@@ -159,12 +191,12 @@ __global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x
 
 // ------------------------------------------------------------------ kernel pointers
 
-template <typename T>
+template <typename T, bool COND>
 static void pick(int wb, void** init, void** upd, void** dir0, void** dir)
 {
 #define PODCG_PICK(WW)                                   \
-    *init = (void*)k_init<WW, T>;                        \
-    *upd = (void*)k_update<WW, T>;                       \
+    *init = (void*)k_init<WW, T, COND>;                  \
+    *upd = (void*)k_update<WW, T, COND>;                 \
     *dir0 = (void*)k_dir<WW, T, true>;                   \
     *dir = (void*)k_dir<WW, T, false>;
     if (wb <= 0) { PODCG_PICK(0) }
@@ -176,10 +208,15 @@ static void pick(int wb, void** init, void** upd, void** dir0, void** dir)
 #undef PODCG_PICK
 }
 
-void cg_kernels(int wb, bool fp32, void** init, void** upd, void** dir0, void** dir)
+void cg_kernels(int wb, bool fp32, bool cond, void** init, void** upd, void** dir0, void** dir)
 {
-    if (fp32) pick<float>(wb, init, upd, dir0, dir);
-    else pick<double>(wb, init, upd, dir0, dir);
+    if (fp32) {
+        if (cond) pick<float, true>(wb, init, upd, dir0, dir);
+        else pick<float, false>(wb, init, upd, dir0, dir);
+    } else {
+        if (cond) pick<double, true>(wb, init, upd, dir0, dir);
+        else pick<double, false>(wb, init, upd, dir0, dir);
+    }
 }
 
 int wb_bucket(int w)

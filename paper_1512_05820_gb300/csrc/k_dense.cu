@@ -124,6 +124,12 @@ cudaError_t launch_gram(int n, const double* X, int ldx, int p, const double* Y,
     if ((size_t)splits * tiles * kTile * kTile * sizeof(double) > work_bytes) return cudaErrorInvalidValue;
     dim3 grid(tiles, splits);
     k_gram_partial<<<grid, kBlock, 0, s>>>(n, X, ldx, p, Y, ldy, qy, extra, q, tj, upper_only, rps, work);
+    return launch_gram_reduce(work, splits, tiles, tj, p, q, G, ldg, s);
+}
+
+cudaError_t launch_gram_reduce(const double* work, int splits, int tiles, int tj, int p, int q, double* G, int ldg,
+                               cudaStream_t s)
+{
     const int m = p * q;
     k_gram_reduce<<<(m + 127) / 128, 128, 0, s>>>(work, splits, tiles, tj, p, q, G, ldg);
     return cudaGetLastError();

@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
                                                     T* __restrict__ q, double* __restrict__ partials,
                                                     unsigned int* counter, DevState* st)
 {
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;
+    if (st->done) return;   // uniform: `done` is written by k_init / k_update only
     const int n = pd->n;
     const int32_t* rp = pd->rp;
     const int32_t* col = pd->col;
@@ -82,11 +84,12 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
     if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) {
         const double gamma = tot[0];
         st->gamma = gamma;
-        if (st->status == 0) {
-            if (!isfinite(gamma)) st->status = 5;
-            else if (!(gamma > 0.0)) st->status = 3;
+        const bool bad = !isfinite(gamma) || !(gamma > 0.0);
+        if (bad && st->status == 0) {
+            if (st->mixed) st->inner_break = 1;          // FP32 inner pass ends; FP64 outer goes on
+            else st->status = !isfinite(gamma) ? 5 : 3;
         }
-        st->alpha = (st->status == 0) ? st->rho / gamma : 0.0;
+        st->alpha = (st->status == 0 && !st->inner_break) ? st->rho / gamma : 0.0;
     }
 }
 
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
 //   Mixed mode (mixed = 1): same test; otherwise it is the start of the next refinement
 //     step, whose inner solve must reduce ||r|| by inner_tol.
 // The decision is published to the graph's outer while-loop through `h_outer`.
-template <int L>
+template <int L, bool COND>
 __global__ void __launch_bounds__(kBlock) k_residual(const ProbDesc* __restrict__ pd, const double* __restrict__ x, double* __restrict__ r,
                                                      double* __restrict__ partials, unsigned int* counter,
                                                      DevState* st, int mixed, double inner_tol,
@@ -124,6 +127,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(const ProbDesc* __restrict_
     if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) {
         const double rt = tot[0];
         st->rr_true = rt;
+        if (st->rr_stage1 < 0.0) st->rr_stage1 = rt;
         int stop = 0;
         if (st->status != 0) stop = 1;
         else if (!isfinite(rt)) { st->status = 5; stop = 1; }
@@ -137,7 +141,9 @@ __global__ void __launch_bounds__(kBlock) k_residual(const ProbDesc* __restrict_
             }
         }
         st->outer_done = stop;
-        if (use_cond) cudaGraphSetConditional(h_outer, stop ? 0u : 1u);
+        if constexpr (COND) {
+            if (use_cond) cudaGraphSetConditional(h_outer, stop ? 0u : 1u);
+        }
     }
 }
 
@@ -246,10 +252,11 @@ void* kernel_spmv_cg(int L, bool fp32)
     return f;
 }
 
-void* kernel_residual(int L)
+void* kernel_residual(int L, bool cond)
 {
     void* f = nullptr;
-    PODCG_LANES(L, f = (void*)k_residual<LL>);
+    if (cond) { PODCG_LANES(L, f = (void*)k_residual<LL, true>); }
+    else { PODCG_LANES(L, f = (void*)k_residual<LL, false>); }
     return f;
 }
 

@@ -21,7 +21,7 @@ int wb_bucket(int w);
 cudaError_t launch_spmv_plain(int L, const int32_t* rp, const int32_t* col, const double* val, const double* x,
                               double* y, int n, int sms, cudaStream_t s);
 void* kernel_spmv_cg(int L, bool fp32);
-void* kernel_residual(int L);
+void* kernel_residual(int L, bool cond);
 cudaError_t launch_spmm(const int32_t* rp, const int32_t* col, const double* val, const double* W, int ldw,
                         double* AW, int lda, int n, int w, int sms, cudaStream_t s);
 cudaError_t launch_spmm_f32(const int32_t* rp, const int32_t* col, const float* val, const float* W, int ldw,
@@ -32,7 +32,10 @@ cudaError_t launch_to_f32(const double* a, float* b, size_t m, int sms, cudaStre
 cudaError_t launch_desc_val_to_f32(const ProbDesc* pd, float* v32, int64_t nnz, int sms, cudaStream_t s);
 
 // dense
+void gram_shape(int n, int p, int q, int sms, int* tiles_j, int* tiles, int* splits, int* rows_per_split);
 size_t gram_workspace_bytes(int n, int p, int q, int sms);
+cudaError_t launch_gram_reduce(const double* work, int splits, int tiles, int tj, int p, int q, double* G, int ldg,
+                               cudaStream_t s);
 cudaError_t launch_gram(int n, const double* X, int ldx, int p, const double* Y, int ldy, int qy,
                         const double* extra, double* G, int ldg, int upper_only, double* work,
                         size_t work_bytes, int sms, cudaStream_t s);
@@ -47,6 +50,31 @@ cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, in
 cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
 
 // CG iteration (k_cg.cu): kernel pointers for graph construction
-void cg_kernels(int wb, bool fp32, void** init, void** upd, void** dir0, void** dir);
+void cg_kernels(int wb, bool fp32, bool cond, void** init, void** upd, void** dir0, void** dir);
+
+// mixed precision (k_mixed.cu)
+void mixed_kernels(int wb, void** proj, void** start);
+void* kernel_mx_accum();
+cudaError_t launch_lift32(int n, const float* S, int lds, int s, const double* C, const DevState* st, float* W,
+                          int ldw, int sms, cudaStream_t str);
+cudaError_t launch_stage1_mx(int wb, const ProbDesc* pd, int n, const float* W32, double* x, double* partials,
+                             unsigned int* counter, DevState* st, double tol, int sms, cudaStream_t s);
+cudaError_t launch_gram32(int n, const float* X, int ldx, int p, const float* Y, int ldy, int qy, const double* extra,
+                          double* G, int ldg, int upper_only, double* work, size_t work_bytes, int sms,
+                          cudaStream_t s);
+
+// differentiation (k_adjoint.cu)
+cudaError_t launch_diffusion_assemble(int mx, int my, int mz, const double* theta, const double* extra,
+                                      const int32_t* rp, double* val, int sms, cudaStream_t s);
+cudaError_t launch_theta_grad(int mx, int my, int mz, const double* theta, int nsys, const double* lam,
+                              const double* xs, double* grad, int sms, cudaStream_t s);
+
+// batched persistent solver (k_batch.cu)
+struct BatchSeqDev;
+int batch_max_clusters(int cluster);
+size_t batch_smem_bytes();
+cudaError_t launch_batch(const BatchSeqDev* seqs, const int* order, int nseq, unsigned int* ticket, int cluster,
+                         int grid_clusters, int k_max, int max_refine, double inner_tol, double rank_tol,
+                         cudaStream_t s);
 
 }  // namespace podcg

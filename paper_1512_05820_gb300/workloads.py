@@ -90,17 +90,19 @@ class DiffusionOperator:
 
     def face_conductances(self, k):
         """Interior face conductances per axis: (fx, fy, fz) on the face grids."""
-        K = np.asarray(k, dtype=np.float64).reshape(self.shape3)
+        K = np.asarray(k).reshape(self.shape3)
         fx = _hm(K[:, :, :-1], K[:, :, 1:])
         fy = _hm(K[:, :-1, :], K[:, 1:, :])
         fz = _hm(K[:-1, :, :], K[1:, :, :])
         return fx, fy, fz
 
     def values(self, k, extra_diag=None) -> np.ndarray:
-        K = np.asarray(k, dtype=np.float64).reshape(self.shape3)
+        """CSR values; ``k`` may be complex (complex-step differentiation in tests)."""
+        K = np.asarray(k)
+        K = K.astype(np.complex128 if np.iscomplexobj(K) else np.float64).reshape(self.shape3)
         fx, fy, fz = self.face_conductances(K)
         mz, my, mx = self.shape3
-        diag = np.zeros(self.shape3)
+        diag = np.zeros(self.shape3, dtype=K.dtype)
         diag[:, :, :-1] += fx
         diag[:, :, 1:] += fx
         diag[:, :, 0] += 2.0 * K[:, :, 0]
@@ -118,10 +120,10 @@ class DiffusionOperator:
         if extra_diag is not None:
             d = d + np.asarray(extra_diag, dtype=np.float64)
         n = self.n
-        V = np.zeros((n, 7))
+        V = np.zeros((n, 7), dtype=K.dtype)
 
         def put(slot, arr, sl):
-            tmp = np.zeros(self.shape3)
+            tmp = np.zeros(self.shape3, dtype=K.dtype)
             tmp[sl] = -arr
             V[:, slot] = tmp.ravel()
 
@@ -233,7 +235,7 @@ def _moving3d_gen(seq: Sequence):
 
 def diffusion3d_moving(m: int = 128, p: int = 50, seed: int = 1235, w_max: int = 32,
                        s_max: int = 40, energy: float = 0.9999, tol: float = 1e-8,
-                       period: float | None = None) -> Sequence:
+                       period: float | None = None, coef_sigma: float = 1.0) -> Sequence:
     """3D 7-point diffusion on an m^3 grid; lognormal(0, 1) coefficients perturbed by
     0.5% per system (theta <- theta + log(1 + 0.005 xi), xi ~ N(0, 1) per cell); a
     Gaussian heat source (sigma 4 cells at m = 128, scaled with m) moving on the circle
@@ -242,7 +244,7 @@ def diffusion3d_moving(m: int = 128, p: int = 50, seed: int = 1235, w_max: int =
     Random draws, in order: theta_1 ~ N(0, 1) (n values); then for each j >= 2 one
     xi ~ N(0, 1) draw of n values."""
     op = DiffusionOperator((m, m, m))
-    recipe = {"coef_sigma": 1.0, "perturb": 0.005, "period": float(period or 50),
+    recipe = {"coef_sigma": coef_sigma, "perturb": 0.005, "period": float(period or 50),
               "sigma": max(1.5, 4.0 * m / 128.0)}
     return Sequence("diffusion3d_moving", op, p, tol, s_max, w_max, energy, seed, recipe, _moving3d_gen)
 
@@ -277,6 +279,33 @@ def diffusion3d_theta(m: int = 96, p: int = 20, seed: int = 1238, w_max: int = 3
     recipe = {"theta": th if theta is None else np.asarray(theta, dtype=np.float64), "u": u, "c": c,
               "period": 50.0, "sigma": max(1.5, 4.0 * m / 128.0)}
     return Sequence("diffusion3d_theta", op, p, tol, s_max, w_max, energy, seed, recipe, _theta3d_gen)
+
+
+def batch_sequences(nseq: int = 256, p: int = 8, n_min: int = 2000, n_max: int = 260000, seed: int = 1237,
+                    w_range=(4, 24), s_max: int = 8, energy: float = 0.9999, tol: float = 1e-8) -> list[Sequence]:
+    """Many independent sequences of uneven sizes (the batched workload): n drawn
+    log-uniformly in [n_min, n_max]; with probability 1/2 a 2D five-point sequence on an
+    m x m grid (m = round(sqrt n)) evolving like ``diffusion2d_drift``, else a 3D seven-point
+    sequence on m^3 (m = round(cbrt n)) evolving like ``diffusion3d_moving``; coefficients
+    lognormal(0, 0.5) in both; w_max drawn uniformly in w_range (inclusive).
+
+    Random draws from ``numpy.random.default_rng(seed)``, per sequence in order: log n
+    (uniform), the 2D/3D coin, w_max, and the sequence's own seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nseq):
+        n_t = float(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        is3d = rng.random() >= 0.5
+        w_i = int(rng.integers(w_range[0], w_range[1] + 1))
+        s_i = int(rng.integers(0, 2**31 - 1))
+        if is3d:
+            m = max(3, int(round(n_t ** (1.0 / 3.0))))
+            out.append(diffusion3d_moving(m=m, p=p, seed=s_i, w_max=w_i, s_max=s_max, energy=energy, tol=tol,
+                                          period=p, coef_sigma=0.5))
+        else:
+            m = max(3, int(round(np.sqrt(n_t))))
+            out.append(diffusion2d_drift(m=m, p=p, seed=s_i, w_max=w_i, s_max=s_max, energy=energy, tol=tol))
+    return out
 
 
 def random_spd_csr(n: int, density: float, seed: int, shift: float = 1.0, empty_rows: int = 0) -> CSR:

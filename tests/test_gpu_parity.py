@@ -258,3 +258,87 @@ def test_arg_errors(dev):
     with pytest.raises(PodCGError) as e:
         s.solve(dcsr(wl.DiffusionOperator((2, 5)).csr(np.ones(10)), dev), to_dev(np.ones(10), dev), -1.0)
     assert e.value.status == 1
+
+
+# ------------------------------------------------------------------ loop forms, precision, adjoint
+
+
+def _gpu_sequence(dev, seq, n_systems, **cfg):
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, **cfg)
+    A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+    xs, sts = [], []
+    for j, val, b in seq.systems():
+        if j > n_systems:
+            break
+        x, st = solver.solve(A0.with_values(to_dev(val, dev)), to_dev(b, dev), seq.tol)
+        solver.add_snapshots(x)
+        xs.append(x.clone())
+        sts.append(st)
+    solver.close()
+    return xs, sts
+
+
+def test_loop_modes_bitwise_equal(dev):
+    """The conditional-graph loop and the chunked plain-graph loop run the same kernels
+    with the same launch shapes, so the iterates are identical bit for bit."""
+    seq = wl.diffusion3d_moving(m=18, p=5, s_max=6, w_max=8, period=10)
+    xa, sa = _gpu_sequence(dev, seq, 5, loop_mode=0)
+    xb, sb = _gpu_sequence(dev, seq, 5, loop_mode=1)
+    for a, b, s1, s2 in zip(xa, xb, sa, sb):
+        assert torch.equal(a, b)
+        assert s1["iters"] == s2["iters"] and s1["w"] == s2["w"]
+
+
+@pytest.mark.parametrize("loop_mode", [0, 1])
+def test_sequence_mixed_precision(dev, loop_mode):
+    """FP32 inner CG inside FP64 refinement: the FP64 true residual reaches tol for every
+    system, w matches the oracle's, and the solution is within the accuracy that two
+    solutions of residual <= tol can differ by (reported, bounded loosely here)."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=20, p=10, s_max=10, w_max=16, period=12)
+    orc = Oracle()
+    oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=1, loop_mode=loop_mode)
+    A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+    for j, val, b in seq.systems():
+        A = (seq.row_ptr, seq.col, val)
+        x, st = solver.solve(A0.with_values(to_dev(val, dev)), to_dev(b, dev), seq.tol)
+        xo, info = oseq.solve(A, b, seq.tol)
+        solver.add_snapshots(to_dev(xo, dev))
+        x = x.cpu().numpy()
+        true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
+        assert st["status"] == "ok", st
+        assert true_rel <= seq.tol and st["final_relres"] <= seq.tol
+        assert st["w"] == info["w"]
+        assert a_err(orc, A, x, xo) <= 1e-5
+        assert st["refinements"] >= 1
+
+
+def test_adjoint_reuses_forward_factors(dev, orc):
+    """lambda = A_j^{-1} g with the basis of forward system j (A_j symmetric): same
+    iterate as the oracle's solve with that basis, to the FP64 parity tolerance."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=16, p=6, s_max=6, w_max=8, period=10)
+    oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, keep_factors=3)
+    A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+    g = np.random.default_rng(3).normal(size=seq.n)
+    kept = []
+    for j, val, b in seq.systems():
+        Wo, wo, _ = oseq.basis()
+        x, st = solver.solve(A0.with_values(to_dev(val, dev)), to_dev(b, dev), seq.tol)
+        xo, info = oseq.solve((seq.row_ptr, seq.col, val), b, seq.tol)
+        solver.add_snapshots(to_dev(xo, dev))
+        kept.append((st["system_id"], val, Wo))
+    for sysid, val, Wo in kept[-3:]:
+        A = (seq.row_ptr, seq.col, val)
+        lam, st = solver.solve_adjoint(sysid, A0.with_values(to_dev(val, dev)), to_dev(g, dev), 1e-10)
+        lo, info, _, _ = orc.solve_system(A, g, Wo, 1e-10)
+        assert st["w"] == Wo.shape[1] and abs(st["iters"] - info["iters"]) <= 1
+        assert a_err(orc, A, lam.cpu().numpy(), lo) <= 1e-10
+    # evicted system
+    from paper_1512_05820_gb300.solver import PodCGError
+    with pytest.raises(PodCGError) as e:
+        solver.solve_adjoint(kept[0][0], A0.with_values(to_dev(kept[0][1], dev)), to_dev(g, dev), 1e-8)
+    assert e.value.status == 9
