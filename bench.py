@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sequences measurement")
+    ap.add_argument("--kernel-profile", type=int, default=0, metavar="W",
+                    help="profiling target: one full-size system with W synthetic snapshots, a 5-iteration "
+                         "solve, then each stage-two kernel launched --kernel-reps times (few launches)")
     ap.add_argument("--batch-seqs", type=int, default=256)
     ap.add_argument("--loop-mode", choices=["graph", "chunked"], default="graph",
                     help="graph: conditional CUDA graph; chunked: plain graphs of 16 iterations (profilable)")
@@ -269,11 +272,37 @@ def cpu_baseline(seq, systems):
                       f"{info['iters']} iterations, {dt:.1f} s); systems/s = 1/time"}
 
 
+def kernel_profile(args):
+    """A short, fixed launch sequence for kernel profilers: system 1 of the workload with
+    W seeded random snapshots (so the POD basis has about W columns), a solve capped at 5
+    iterations, then pod_cg_time_kernels. Prints the per-kernel times as one JSON line."""
+    import torch
+    from paper_1512_05820_gb300 import workloads as wl
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=args.grid, p=1)
+    j, val, b = next(iter(seq.systems()))
+    prec = 1 if args.precision == "mixed" else 0
+    solver = PodCG(seq.n, w_max=32, s_max=40, energy=0.9999, precision=prec, k_max=5, max_refine=0,
+                   loop_mode=1)
+    snaps = torch.as_tensor(np.random.default_rng(7).normal(size=(seq.n, args.kernel_profile)), device="cuda")
+    solver.add_snapshots(snaps)
+    A = DeviceCSR.from_numpy(seq.row_ptr, seq.col, val)
+    bt = torch.as_tensor(b, device="cuda")
+    _, st = solver.solve(A, bt, seq.tol, raise_on_error=False)
+    ms = solver.time_kernels(A, bt, reps=args.kernel_reps)
+    print(json.dumps({"kernel_profile": True, "w": st["w"], "precision": args.precision,
+                      "ms": dict(zip(["spmv_cg", "update", "direction", "residual"], ms)),
+                      "tuning": solver.tuning()}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.kernel_profile:
+        return kernel_profile(args)
 
     import torch
     from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
@@ -384,6 +413,7 @@ def main():
     run_sequence(solver, dseq, xs)
     ms_k = solver.time_kernels(dseq.matrix(j_last), dseq.bs[j_last], reps=args.kernel_reps)
     w_meas = solver.last_w
+    out["autotune"] = solver.tuning()
     n, nnz = seq.n, seq.nnz
     # algorithmic bytes per launch (each datum once): FP64 or FP32 vectors/panels
     e = 4 if prec == 1 else 8

@@ -173,6 +173,13 @@ pod_cg_status pod_cg_get_basis(pod_cg_t* h, double* W_out, int* w_out);
  * iteration vectors are overwritten (the next solve resets them). Errors: ERR_ARG, ERR_CUDA. */
 pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double* b, int reps, float* ms_out);
 
+/* Autotuner record (no counterpart in the paper): the CSR SpMV lanes-per-row used by the
+ * last solve (1, 2, ..., 32) and, for systems of at least 65,536 rows, the measured
+ * milliseconds of each candidate on that matrix (index k for 2^k lanes; -1 = not tried,
+ * 0 = not timed). The first solve on a new sparsity pattern times the candidates on the
+ * actual matrix; later solves on the same pattern reuse the choice. lane_ms: host, 6. */
+pod_cg_status pod_cg_tuning(const pod_cg_t* h, int* spmv_lanes, float* lane_ms);
+
 /* ------------------------------------------------------ stateless steps of the path */
 
 /* y = A x (the product of Algorithm 1's gamma = (A p, p)); x, y device length n. */

@@ -29,6 +29,8 @@ struct DevState {
     double rr_true;    // ||b - A x||^2 from the last true-residual product
     double rr_stage1;  // ||b - A x0||^2 after stage one
     double rr_outer;   // mixed precision: ||r||^2 of the current outer residual
+    double rnorm;      // mixed precision: ||r|| of the current outer residual; the FP32
+                       // inner solve works on r/||r|| (no underflow or overflow in FP32)
     double cond;       // cond_2(W^T A W) diagnostic
     double mu[kWMax];  // reduced coordinates of the A-orthogonalisation (Algorithm 1)
     double c[kWMax];   // (A W)^T z of the current iterate; mu = R^{-1} R^{-T} c
@@ -127,6 +129,98 @@ __device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], in
     if (threadIdx.x == 0) *counter = 0u;
     __syncthreads();
     return true;
+}
+
+// Publish block totals s_blk[0..nv) (shared memory, complete before the call) as this
+// block's partials; returns true in the last block to finish, which then holds the grid
+// totals in s_tot[0..nv) (same fixed summation order as reduce_to_last_block).
+__device__ __forceinline__ bool partials_to_last_block(const double* s_blk, int nv, double* __restrict__ partials,
+                                                       unsigned int* counter, double* s_tot)
+{
+    __shared__ bool s_last;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) partials[(size_t)v * kPartialStride + blockIdx.x] = s_blk[v];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int ticket = atomicAdd(counter, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int G = gridDim.x;
+    for (int v = wid; v < nv; v += kWarps) {
+        const double* pv = partials + (size_t)v * kPartialStride;
+        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+        int b = lane;
+        for (; b + 96 < G; b += 128) {
+            t0 += __ldcg(pv + b);
+            t1 += __ldcg(pv + b + 32);
+            t2 += __ldcg(pv + b + 64);
+            t3 += __ldcg(pv + b + 96);
+        }
+        for (; b < G; b += 32) t0 += __ldcg(pv + b);
+        const double t = warp_sum((t0 + t1) + (t2 + t3));
+        if (lane == 0) s_tot[v] = t;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// Column-parallel accumulation of c_j += sum_rows col_j[row] * s_z[row - row0] over one
+// 256-row tile: warp `wid` owns columns j = wid, wid + kWarps, ... (CPW of them), lanes read
+// 32 consecutive rows of a column per access (coalesced 128/256-byte segments).
+template <int CPW, typename T>
+__device__ __forceinline__ void tile_columns(const T* __restrict__ M, int ld, int w, int row0, int n, const T* s_z,
+                                             T (&cacc)[CPW])
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < CPW; ++k) {
+        const int j = wid + kWarps * k;
+        if (j < w) {
+            const T* col = M + (size_t)j * ld + row0;
+            T a = T(0);
+#pragma unroll
+            for (int m = 0; m < kBlock / 32; ++m) {
+                const int rr = lane + 32 * m;
+                if (row0 + rr < n) a += __ldg(col + rr) * s_z[rr];
+            }
+            cacc[k] += a;
+        }
+    }
+}
+
+// Block totals of (two row sums, CPW column sums per warp) into s_blk[0..2+w).
+template <int CPW, typename T>
+__device__ __forceinline__ void block_totals(T v0, T v1, const T (&cacc)[CPW], int w, double* s_blk)
+{
+    __shared__ double s_two[kWarps][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const double a0 = warp_sum(double(v0)), a1 = warp_sum(double(v1));
+    if (lane == 0) {
+        s_two[wid][0] = a0;
+        s_two[wid][1] = a1;
+    }
+#pragma unroll
+    for (int k = 0; k < CPW; ++k) {
+        const int j = wid + kWarps * k;
+        const double t = warp_sum(double(cacc[k]));
+        if (lane == 0 && j < w) s_blk[2 + j] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int k = 0; k < kWarps; ++k) {
+            t0 += s_two[k][0];
+            t1 += s_two[k][1];
+        }
+        s_blk[0] = t0;
+        s_blk[1] = t1;
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }

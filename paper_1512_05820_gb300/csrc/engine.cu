@@ -180,6 +180,11 @@ struct pod_cg_t {
     std::vector<int> k_id, k_w;
     int k_next = 0;
 
+    // SpMV lanes-per-row autotuner: one entry per sparsity pattern seen
+    struct LaneChoice { const int32_t* rp; int n; int64_t nnz; bool mixed; int L; float ms[6]; };
+    std::vector<LaneChoice> lanes;
+    int last_L = 0;
+
     GraphSlot graphs[6];                // conditional graphs [width bucket]
     GraphSlot chunks[6];                // plain chunk graphs [width bucket]
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -226,6 +231,47 @@ pod_cg_status check_csr(pod_cg_t* h, const pod_cg_csr* A, int n)
     if (A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX) return fail(h, POD_CG_ERR_ARG, "nnz out of range");
     if (n > 0 && (!A->row_ptr || !A->col || (A->nnz > 0 && !A->val)))
         return fail(h, POD_CG_ERR_ARG, "CSR arrays must be non-NULL");
+    return POD_CG_OK;
+}
+
+// SpMV lanes per row for this pattern: the mean-row-length heuristic for small systems;
+// otherwise the candidates around it are timed on the actual matrix (plain product in the
+// solve's precision, CUDA events) and the fastest is kept for the pattern.
+pod_cg_status choose_lanes(pod_cg_t* h, const pod_cg_csr* A, int* L_out)
+{
+    for (auto& c : h->lanes)
+        if (c.rp == A->row_ptr && c.n == A->n && c.nnz == A->nnz && c.mixed == h->mixed) {
+            *L_out = c.L;
+            return POD_CG_OK;
+        }
+    const double mean = A->n > 0 ? double(A->nnz) / A->n : 1.0;
+    pod_cg_t::LaneChoice ch{A->row_ptr, A->n, A->nnz, h->mixed, spmv_lanes_for(mean), {0, 0, 0, 0, 0, 0}};
+    if (A->n >= 65536) {
+        const int cands[6] = {1, 2, 4, 8, 16, 32};
+        float best = -1.0f;
+        for (int k = 0; k < 6; ++k) {
+            const int L = cands[k];
+            if (L > 4 * mean + 4 || L * 16 < mean) { ch.ms[k] = -1.0f; continue; }
+            float tot = 0.0f;
+            for (int rep = 0; rep < 4; ++rep) {
+                PODCG_CK(h, cudaEventRecord(h->ev[0], h->stream));
+                if (h->mixed)
+                    PODCG_CK(h, launch_spmv_plain32(L, A->row_ptr, A->col, h->val32, h->p32, h->q32, A->n, h->sms,
+                                                    h->stream));
+                else
+                    PODCG_CK(h, launch_spmv_plain(L, A->row_ptr, A->col, A->val, h->p, h->q, A->n, h->sms, h->stream));
+                PODCG_CK(h, cudaEventRecord(h->ev[1], h->stream));
+                PODCG_CK(h, cudaEventSynchronize(h->ev[1]));
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+                if (rep > 0) tot += ms;
+            }
+            ch.ms[k] = tot / 3.0f;
+            if (best < 0.0f || ch.ms[k] < best) { best = ch.ms[k]; ch.L = L; }
+        }
+    }
+    h->lanes.push_back(ch);
+    *L_out = ch.L;
     return POD_CG_OK;
 }
 
@@ -727,7 +773,10 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     PODCG_CK(h, cudaEventRecord(h->ev[2], s));
 
     // stage two
-    const int L = spmv_lanes_for(n > 0 ? double(A->nnz) / n : 1.0);
+    int L = 1;
+    pod_cg_status lst = choose_lanes(h, A, &L);
+    if (lst != POD_CG_OK) return lst;
+    h->last_L = L;
     pod_cg_status ls = run_loop(h, wb, L);
     if (ls != POD_CG_OK) return ls;
     const int sysid = h->system_counter++;
@@ -796,7 +845,9 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
     PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4, h->st, tol,
                               h->sms, s));
     PODCG_CK(h, cudaEventRecord(h->ev[2], s));
-    const int L = spmv_lanes_for(n > 0 ? double(A->nnz) / n : 1.0);
+    int L = 1;
+    pod_cg_status lst = choose_lanes(h, A, &L);
+    if (lst != POD_CG_OK) return lst;
     pod_cg_status ls = run_loop(h, wb, L);
     if (ls != POD_CG_OK) return ls;
     return finish_solve(h, lambda_out, w, launches, stats, system_id);
@@ -821,7 +872,7 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
     t.tol2_in = -1.0;
     t.dir_pending = 1;
     const int w = h->pod_w;
-    const int L = spmv_lanes_for(h->n > 0 ? double(A->nnz) / h->n : 1.0);
+    const int L = h->last_L > 0 ? h->last_L : spmv_lanes_for(h->n > 0 ? double(A->nnz) / h->n : 1.0);
     Plan pl;
     make_plan(h, wb_bucket(w), L, h->mixed, 0, 0, 0, pl);
     KSpec* ks[4] = {&pl.spmv, &pl.upd, &pl.dir, &pl.res};
@@ -838,6 +889,19 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
             if (rep > 0) total += ms;   // the first launch is a warm-up
         }
         ms_out[k] = total / reps;
+    }
+    return POD_CG_OK;
+}
+
+pod_cg_status pod_cg_tuning(const pod_cg_t* h, int* spmv_lanes, float* lane_ms)
+{
+    if (!h) return POD_CG_ERR_ARG;
+    if (spmv_lanes) *spmv_lanes = h->last_L;
+    if (lane_ms) {
+        for (int k = 0; k < 6; ++k) lane_ms[k] = 0.0f;
+        for (const auto& c : h->lanes)
+            if (c.L == h->last_L)
+                for (int k = 0; k < 6; ++k) lane_ms[k] = c.ms[k];
     }
     return POD_CG_OK;
 }

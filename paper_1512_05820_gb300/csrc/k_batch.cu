@@ -389,7 +389,9 @@ __device__ void solve_sequence(Team& T, BatchSmem& sm, const BatchSeqDev& q, int
             if (!isfinite(rr_true)) { status = 5; break; }
             if (refine >= max_refine) { status = 4; break; }
             ++refine;
-            const double tol2_in = inner_tol * inner_tol * rr_true;
+            // the FP32 inner solve works on r/||r|| (no underflow or overflow in FP32)
+            const double rnorm = sqrt(rr_true), rinv = 1.0 / rnorm;
+            const double tol2_in = inner_tol * inner_tol;
             // projection of the correction onto W: c = W^T r
             {
                 double acc[kBW];
@@ -397,7 +399,7 @@ __device__ void solve_sequence(Team& T, BatchSmem& sm, const BatchSeqDev& q, int
 #pragma unroll
                 for (int c = 0; c < kBW; ++c) cl[c] = 0.0f;
                 for (int i = T.tid; i < n; i += T.nthr) {
-                    const float ri = float(q.r64[i]);
+                    const float ri = float(q.r64[i] * rinv);
                     q.r[i] = ri;
 #pragma unroll
                     for (int c = 0; c < kBW; ++c)
@@ -508,7 +510,7 @@ __device__ void solve_sequence(Team& T, BatchSmem& sm, const BatchSeqDev& q, int
                     q.p32[i] = v;
                 }
             }
-            for (int i = T.tid; i < n; i += T.nthr) x[i] += double(q.d[i]);
+            for (int i = T.tid; i < n; i += T.nthr) x[i] += rnorm * double(q.d[i]);
             if (status != 0) break;
         }
         // statistics of system j

@@ -47,36 +47,43 @@ __device__ __forceinline__ void block_mu(const double* __restrict__ Rinv, const 
 
 // Start of a CG pass from the residual r: z0 = M^{-1} r, (r, z0), ||r||^2, c = (A W)^T z0;
 // the residual test on r0 (zero iterations allowed). mu0 is formed by k_dir<FIRST>.
+// Same column-parallel tiling as k_update.
 template <int WB, typename T, bool COND>
 __global__ void __launch_bounds__(kBlock) k_init(int n, int ld, const T* __restrict__ r, const T* __restrict__ dinv,
                                                  const T* __restrict__ AW, double* __restrict__ partials,
                                                  unsigned int* counter, DevState* st,
                                                  cudaGraphConditionalHandle h_inner, int use_cond)
 {
+    constexpr int CPW = WB > 0 ? (WB + kWarps - 1) / kWarps : 1;
     const int w = st->w;
-    T cl[WB > 0 ? WB : 1];
+    __shared__ T s_z[kBlock];
+    __shared__ double s_blk[WB + 2];
+    T cacc[CPW];
 #pragma unroll
-    for (int j = 0; j < WB; ++j) cl[j] = T(0);
+    for (int k = 0; k < CPW; ++k) cacc[k] = T(0);
     T rho = T(0), rr = T(0);
     const bool skip = st->outer_done != 0;   // mixed precision: the outer loop already stopped
     if (!skip) {
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-            const T ri = r[i];
-            const T zi = dinv[i] * ri;
-            rho += ri * zi;
-            rr += ri * ri;
-#pragma unroll
-            for (int j = 0; j < WB; ++j)
-                if (j < w) cl[j] += __ldg(AW + (size_t)j * ld + i) * zi;
+        for (int row0 = blockIdx.x * kBlock; row0 < n; row0 += gridDim.x * kBlock) {
+            const int i = row0 + threadIdx.x;
+            T zi = T(0);
+            if (i < n) {
+                const T ri = r[i];
+                zi = dinv[i] * ri;
+                rho += ri * zi;
+                rr += ri * ri;
+            }
+            if (WB > 0) {
+                s_z[threadIdx.x] = zi;
+                __syncthreads();
+                tile_columns<CPW, T>(AW, ld, w, row0, n, s_z, cacc);
+                __syncthreads();
+            }
         }
     }
-    double acc[WB + 2];
-    acc[0] = double(rho);
-    acc[1] = double(rr);
-#pragma unroll
-    for (int j = 0; j < WB; ++j) acc[2 + j] = double(cl[j]);
+    block_totals<CPW, T>(rho, rr, cacc, w, s_blk);
     __shared__ double tot[WB + 2];
-    if (reduce_to_last_block<WB + 2>(acc, 2 + w, partials, counter, tot)) {
+    if (partials_to_last_block(s_blk, 2 + w, partials, counter, tot)) {
         for (int a = threadIdx.x; a < w; a += blockDim.x) st->c[a] = tot[2 + a];
         if (threadIdx.x == 0) {
             st->rho = tot[0];
@@ -96,6 +103,10 @@ __global__ void __launch_bounds__(kBlock) k_init(int n, int ld, const T* __restr
     }
 }
 
+// Update pass, column-parallel projection: each 256-row tile computes r, z, (r, z) and
+// ||r||^2 row-wise, stages z in shared memory, then every warp accumulates (A W)^T z for
+// its own columns (j = warp, warp + 8, ...) with coalesced reads of A W. A thread holds at
+// most WB/8 column accumulators, so the kernel stays at high occupancy.
 template <int WB, typename T, bool COND>
 __global__ void __launch_bounds__(kBlock) k_update(int n, int ld, T* __restrict__ r, const T* __restrict__ q,
                                                    const T* __restrict__ dinv, const T* __restrict__ AW,
@@ -103,29 +114,35 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, int ld, T* __restrict_
                                                    DevState* st, cudaGraphConditionalHandle h_inner, int use_cond)
 {
     if (st->done) return;   // uniform: only this kernel's last block writes `done`
+    constexpr int CPW = WB > 0 ? (WB + kWarps - 1) / kWarps : 1;
     const int w = st->w;
     const T alpha = (st->status == 0) ? T(st->alpha) : T(0);
-    T cl[WB > 0 ? WB : 1];
+    __shared__ T s_z[kBlock];
+    __shared__ double s_blk[WB + 2];
+    T cacc[CPW];
 #pragma unroll
-    for (int j = 0; j < WB; ++j) cl[j] = T(0);
+    for (int k = 0; k < CPW; ++k) cacc[k] = T(0);
     T rho = T(0), rr = T(0);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const T ri = r[i] - alpha * q[i];
-        r[i] = ri;
-        const T zi = dinv[i] * ri;
-        rho += ri * zi;
-        rr += ri * ri;
-#pragma unroll
-        for (int j = 0; j < WB; ++j)
-            if (j < w) cl[j] += __ldg(AW + (size_t)j * ld + i) * zi;
+    for (int row0 = blockIdx.x * kBlock; row0 < n; row0 += gridDim.x * kBlock) {
+        const int i = row0 + threadIdx.x;
+        T zi = T(0);
+        if (i < n) {
+            const T ri = r[i] - alpha * q[i];
+            r[i] = ri;
+            zi = dinv[i] * ri;
+            rho += ri * zi;
+            rr += ri * ri;
+        }
+        if (WB > 0) {
+            s_z[threadIdx.x] = zi;
+            __syncthreads();
+            tile_columns<CPW, T>(AW, ld, w, row0, n, s_z, cacc);
+            __syncthreads();
+        }
     }
-    double acc[WB + 2];
-    acc[0] = double(rho);
-    acc[1] = double(rr);
-#pragma unroll
-    for (int j = 0; j < WB; ++j) acc[2 + j] = double(cl[j]);
+    block_totals<CPW, T>(rho, rr, cacc, w, s_blk);
     __shared__ double tot[WB + 2];
-    if (reduce_to_last_block<WB + 2>(acc, 2 + w, partials, counter, tot)) {
+    if (partials_to_last_block(s_blk, 2 + w, partials, counter, tot)) {
         for (int a = threadIdx.x; a < w; a += blockDim.x) st->c[a] = tot[2 + a];
         if (threadIdx.x == 0) {
             const double rho_new = tot[0];
@@ -175,6 +192,9 @@ __global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x
         for (int j = threadIdx.x; j < WB; j += blockDim.x) s_mu[j] = (j < w) ? T(s_mud[j]) : T(0);
         __syncthreads();
     }
+    T mu[WB > 0 ? WB : 1];   // mu in registers: one shared-memory read per block, not per FMA
+#pragma unroll
+    for (int j = 0; j < WB; ++j) mu[j] = s_mu[j];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const T pi = p[i];
         if (!FIRST) x[i] += alpha * pi;
@@ -183,7 +203,7 @@ __global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x
             if (!FIRST) v += beta * pi;
 #pragma unroll
             for (int j = 0; j < WB; ++j)
-                if (j < w) v -= __ldg(W + (size_t)j * ld + i) * s_mu[j];
+                if (j < w) v -= __ldg(W + (size_t)j * ld + i) * mu[j];
             p[i] = v;
         }
     }

@@ -186,13 +186,16 @@ __global__ void __launch_bounds__(kBlock) k_stage1(const ProbDesc* __restrict__ 
     for (int j = threadIdx.x; j < WB; j += blockDim.x) s_what[j] = (j < w) ? st->what[j] : 0.0;
     __syncthreads();
     double rr = 0.0, bb = 0.0;
+    double wh[WB > 0 ? WB : 1];
+#pragma unroll
+    for (int j = 0; j < WB; ++j) wh[j] = (WB > 0) ? s_what[j] : 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double xi = 0.0, ai = 0.0;
 #pragma unroll
         for (int j = 0; j < WB; ++j) {
             if (j < w) {
-                xi += __ldg(W + (size_t)j * ld + i) * s_what[j];
-                ai += __ldg(AW + (size_t)j * ld + i) * s_what[j];
+                xi += __ldg(W + (size_t)j * ld + i) * wh[j];
+                ai += __ldg(AW + (size_t)j * ld + i) * wh[j];
             }
         }
         const double bi = b[i];

@@ -2,13 +2,13 @@
 //
 // Each outer step (graph outer while-loop) is:
 //   k_residual   r64 = b - A x in FP64 and the stop test (k_sparse.cu)
-//   k_mx_proj    r32 = float(r64) and c = W32^T r32: the stage-one projection of the
+//   k_mx_proj    r32 = float(r64/||r64||) and c = W32^T r32: the stage-one projection of the
 //                correction (augmented CG only searches the A-orthogonal complement of
 //                range(W), so the correction's component in range(W) is solved directly
 //                with the stage-one factor, as Algorithm 2 does for x)
 //   k_mx_start   dhat = R^{-1} R^{-T} c, d = W32 dhat, r32 -= AW32 dhat
 //   k_init / inner while { k_spmv_cg, k_update, k_dir } in FP32 on A d = r32
-//   k_mx_accum   x += double(d)
+//   k_mx_accum   x += ||r64|| double(d)
 // All of them return at once after the outer loop decided to stop (outer_done), because
 // the rest of the outer body still runs in that pass.
 //
@@ -49,24 +49,32 @@ __global__ void __launch_bounds__(kBlock) k_mx_proj(int n, int ld, const double*
                                                     DevState* st)
 {
     if (st->outer_done) return;
+    constexpr int CPW = WB > 0 ? (WB + kWarps - 1) / kWarps : 1;
     const int w = st->w;
-    float cl[WB > 0 ? WB : 1];
+    const double inv = st->rnorm > 0.0 ? 1.0 / st->rnorm : 1.0;
+    __shared__ float s_z[kBlock];
+    __shared__ double s_blk[WB + 2];
+    float cacc[CPW];
 #pragma unroll
-    for (int j = 0; j < WB; ++j) cl[j] = 0.0f;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float ri = float(r64[i]);
-        r32[i] = ri;
-#pragma unroll
-        for (int j = 0; j < WB; ++j)
-            if (j < w) cl[j] += __ldg(W32 + (size_t)j * ld + i) * ri;
+    for (int k = 0; k < CPW; ++k) cacc[k] = 0.0f;
+    for (int row0 = blockIdx.x * kBlock; row0 < n; row0 += gridDim.x * kBlock) {
+        const int i = row0 + threadIdx.x;
+        float ri = 0.0f;
+        if (i < n) {
+            ri = float(r64[i] * inv);
+            r32[i] = ri;
+        }
+        if (WB > 0) {
+            s_z[threadIdx.x] = ri;
+            __syncthreads();
+            tile_columns<CPW, float>(W32, ld, w, row0, n, s_z, cacc);
+            __syncthreads();
+        }
     }
-    double acc[WB > 0 ? WB : 1];
-#pragma unroll
-    for (int j = 0; j < WB; ++j) acc[j] = double(cl[j]);
-    if (WB == 0) acc[0] = 0.0;
-    __shared__ double tot[WB > 0 ? WB : 1];
-    if (reduce_to_last_block<(WB > 0 ? WB : 1)>(acc, w, partials, counter, tot)) {
-        for (int a = threadIdx.x; a < w; a += blockDim.x) st->c[a] = tot[a];
+    block_totals<CPW, float>(0.0f, 0.0f, cacc, w, s_blk);
+    __shared__ double tot[WB + 2];
+    if (partials_to_last_block(s_blk, 2 + w, partials, counter, tot)) {
+        for (int a = threadIdx.x; a < w; a += blockDim.x) st->c[a] = tot[2 + a];
     }
 }
 
@@ -86,13 +94,16 @@ __global__ void __launch_bounds__(kBlock) k_mx_start(int n, int ld, float* __res
         for (int j = threadIdx.x; j < WB; j += blockDim.x) s_dh[j] = (j < w) ? float(s_mu[j]) : 0.0f;
         __syncthreads();
     }
+    float dh[WB > 0 ? WB : 1];
+#pragma unroll
+    for (int j = 0; j < WB; ++j) dh[j] = (WB > 0) ? s_dh[j] : 0.0f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float di = 0.0f, ai = 0.0f;
 #pragma unroll
         for (int j = 0; j < WB; ++j) {
             if (j < w) {
-                di += __ldg(W32 + (size_t)j * ld + i) * s_dh[j];
-                ai += __ldg(AW32 + (size_t)j * ld + i) * s_dh[j];
+                di += __ldg(W32 + (size_t)j * ld + i) * dh[j];
+                ai += __ldg(AW32 + (size_t)j * ld + i) * dh[j];
             }
         }
         d32[i] = di;
@@ -104,7 +115,9 @@ __global__ void __launch_bounds__(kBlock) k_mx_accum(int n, double* __restrict__
                                                      const DevState* st)
 {
     if (st->outer_done) return;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] += double(d32[i]);
+    const double scale = st->rnorm > 0.0 ? st->rnorm : 1.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] += scale * double(d32[i]);
 }
 
 // W32[:, j] = sum_k S32[:, k] C[k][j] (C row stride kWMax, FP64 coefficients used in FP32).
@@ -157,11 +170,14 @@ __global__ void __launch_bounds__(kBlock) k_stage1_mx(const ProbDesc* __restrict
     for (int j = threadIdx.x; j < WB; j += blockDim.x) s_what[j] = (j < w) ? float(st->what[j]) : 0.0f;
     __syncthreads();
     double bb = 0.0;
+    float wh[WB > 0 ? WB : 1];
+#pragma unroll
+    for (int j = 0; j < WB; ++j) wh[j] = (WB > 0) ? s_what[j] : 0.0f;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         float xi = 0.0f;
 #pragma unroll
         for (int j = 0; j < WB; ++j)
-            if (j < w) xi += __ldg(W32 + (size_t)j * ld + i) * s_what[j];
+            if (j < w) xi += __ldg(W32 + (size_t)j * ld + i) * wh[j];
         x[i] = double(xi);
         const double bi = b[i];
         bb += bi * bi;

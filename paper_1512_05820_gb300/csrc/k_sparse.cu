@@ -13,7 +13,9 @@
 namespace podcg {
 
 // Row loop shared by the SpMV variants. Returns the group's row sum in lane 0 of the group.
-// Loop bounds are uniform per warp so the group shuffles never diverge.
+// Loop bounds are uniform per warp so the group shuffles never diverge. With one lane per
+// row, rows of up to 8 entries (stencils) issue all index/value loads first and then all
+// gathers, so a row costs two memory round trips instead of one per entry.
 template <int L, typename TV, typename TX>
 __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
                                           const TV* __restrict__ val, const TX* __restrict__ x, int n,
@@ -22,8 +24,24 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const 
     TX s = TX(0);
     if (valid) {
         const int beg = __ldg(rp + row), end = __ldg(rp + row + 1);
-        const int lane = threadIdx.x & (L - 1);
-        for (int k = beg + lane; k < end; k += L) s += TX(__ldg(val + k)) * __ldg(x + __ldg(col + k));
+        if (L == 1 && end - beg <= 8) {
+            const int len = end - beg;
+            int c[8];
+            TV v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                c[t] = (t < len) ? __ldg(col + beg + t) : 0;
+                v[t] = (t < len) ? __ldg(val + beg + t) : TV(0);
+            }
+            TX g[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) g[t] = (t < len) ? __ldg(x + c[t]) : TX(0);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) s += TX(v[t]) * g[t];
+        } else {
+            const int lane = threadIdx.x & (L - 1);
+            for (int k = beg + lane; k < end; k += L) s += TX(__ldg(val + k)) * __ldg(x + __ldg(col + k));
+        }
     }
     if (L > 1) {
 #pragma unroll
@@ -32,11 +50,11 @@ __device__ __forceinline__ void spmv_rows(const int32_t* __restrict__ rp, const 
     out = s;
 }
 
-// y = A x (stateless product).
-template <int L>
+// y = A x (stateless product; also timed by the lanes autotuner in either precision).
+template <int L, typename TV = double, typename TX = double>
 __global__ void __launch_bounds__(kBlock) k_spmv_plain(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                                       const double* __restrict__ val, const double* __restrict__ x,
-                                                       double* __restrict__ y, int n)
+                                                       const TV* __restrict__ val, const TX* __restrict__ x,
+                                                       TX* __restrict__ y, int n)
 {
     const int gpb = kBlock / L;
     const int g = threadIdx.x / L;
@@ -44,8 +62,8 @@ __global__ void __launch_bounds__(kBlock) k_spmv_plain(const int32_t* __restrict
     const int stride = gridDim.x * gpb;
     for (int base = warp_first; base < n; base += stride) {
         const int row = base + (g - (threadIdx.x & ~31) / L);
-        double s;
-        spmv_rows<L>(rp, col, val, x, n, row, row < n, s);
+        TX s;
+        spmv_rows<L, TV, TX>(rp, col, val, x, n, row, row < n, s);
         if ((threadIdx.x & (L - 1)) == 0 && row < n) y[row] = s;
     }
 }
@@ -115,7 +133,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(const ProbDesc* __restrict_
     for (int base = blockIdx.x * gpb + wg0; base < n; base += stride) {
         const int row = base + (g - wg0);
         double s;
-        spmv_rows<L>(pd->rp, pd->col, pd->val, x, n, row, row < n, s);
+        spmv_rows<L, double, double>(pd->rp, pd->col, pd->val, x, n, row, row < n, s);
         if ((threadIdx.x & (L - 1)) == 0 && row < n) {
             const double ri = b[row] - s;
             r[row] = ri;
@@ -137,7 +155,8 @@ __global__ void __launch_bounds__(kBlock) k_residual(const ProbDesc* __restrict_
             st->restarts += 1;
             if (mixed) {
                 st->rr_outer = rt;
-                st->tol2_in = inner_tol * inner_tol * rt;
+                st->rnorm = sqrt(rt);
+                st->tol2_in = inner_tol * inner_tol;   // the inner solve sees r/||r||
             }
         }
         st->outer_done = stop;
@@ -240,7 +259,15 @@ cudaError_t launch_spmv_plain(int L, const int32_t* rp, const int32_t* col, cons
                               double* y, int n, int sms, cudaStream_t s)
 {
     const int grid = grid_rows(n, kBlock / L, sms);
-    PODCG_LANES(L, k_spmv_plain<LL><<<grid, kBlock, 0, s>>>(rp, col, val, x, y, n));
+    PODCG_LANES(L, (k_spmv_plain<LL, double, double><<<grid, kBlock, 0, s>>>(rp, col, val, x, y, n)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_plain32(int L, const int32_t* rp, const int32_t* col, const float* val, const float* x,
+                                float* y, int n, int sms, cudaStream_t s)
+{
+    const int grid = grid_rows(n, kBlock / L, sms);
+    PODCG_LANES(L, (k_spmv_plain<LL, float, float><<<grid, kBlock, 0, s>>>(rp, col, val, x, y, n)));
     return cudaGetLastError();
 }
 

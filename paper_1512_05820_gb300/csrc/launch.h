@@ -20,6 +20,8 @@ int wb_bucket(int w);
 // sparse
 cudaError_t launch_spmv_plain(int L, const int32_t* rp, const int32_t* col, const double* val, const double* x,
                               double* y, int n, int sms, cudaStream_t s);
+cudaError_t launch_spmv_plain32(int L, const int32_t* rp, const int32_t* col, const float* val, const float* x,
+                                float* y, int n, int sms, cudaStream_t s);
 void* kernel_spmv_cg(int L, bool fp32);
 void* kernel_residual(int L, bool cond);
 cudaError_t launch_spmm(const int32_t* rp, const int32_t* col, const double* val, const double* W, int ldw,

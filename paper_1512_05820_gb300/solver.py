@@ -146,6 +146,13 @@ class PodCG:
                self.h)
         return [float(v) for v in ms]
 
+    def tuning(self) -> dict:
+        """SpMV lanes per row chosen for the last solve and the autotuner's timings."""
+        L = ctypes.c_int(0)
+        ms = (ctypes.c_float * 6)()
+        _check(self.L.pod_cg_tuning(self.h, ctypes.byref(L), ms), self.h)
+        return {"spmv_lanes": L.value, "lane_ms": {str(1 << k): ms[k] for k in range(6)}}
+
     @property
     def last_w(self) -> int:
         w = ctypes.c_int(0)
