@@ -96,15 +96,14 @@ __device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], in
         }
     }
     __syncthreads();
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-        double t = 0.0;
-#pragma unroll
-        for (int k = 0; k < kWarps; ++k) t += s_w[k][v];
-        partials[(size_t)v * kPartialStride + blockIdx.x] = t;
-    }
-    __threadfence();
-    __syncthreads();
     if (threadIdx.x == 0) {
+        for (int v = 0; v < nv; ++v) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) t += s_w[k][v];
+            partials[(size_t)v * kPartialStride + blockIdx.x] = t;
+        }
+        __threadfence();
         unsigned int ticket = atomicAdd(counter, 1u);
         s_last = (ticket == gridDim.x - 1);
     }
@@ -138,10 +137,11 @@ __device__ __forceinline__ bool partials_to_last_block(const double* s_blk, int 
                                                        unsigned int* counter, double* s_tot)
 {
     __shared__ bool s_last;
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) partials[(size_t)v * kPartialStride + blockIdx.x] = s_blk[v];
-    __threadfence();
-    __syncthreads();
+    // one thread publishes the block's partials, fences and takes the ticket: the other
+    // threads never wait on a memory fence
     if (threadIdx.x == 0) {
+        for (int v = 0; v < nv; ++v) partials[(size_t)v * kPartialStride + blockIdx.x] = s_blk[v];
+        __threadfence();
         unsigned int ticket = atomicAdd(counter, 1u);
         s_last = (ticket == gridDim.x - 1);
     }

@@ -143,6 +143,8 @@ struct pod_cg_t {
     double* grow = nullptr;     // one Gram row (kSMax)
     double* C = nullptr;        // kSMax x kWMax lift coefficients
     double* sigma2 = nullptr;   // kSMax eigenvalues
+    double* Vprev = nullptr;    // kSMax x kSMax eigenvectors of the last POD (warm start)
+    int vprev_s = 0;            // slots covered by Vprev (0: none)
     int s_count = 0, s_next = 0;
     bool pod_dirty = false;
     int pod_w = 0;
@@ -560,7 +562,7 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     if (!h) return POD_CG_OK;
     for (auto& g : h->graphs) destroy_graph(g);
     for (auto& g : h->chunks) destroy_graph(g);
-    void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->W, h->AW, h->W32, h->AW32, h->G, h->Rinv,
+    void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->G, h->Rinv,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
                     h->partials, h->counters, h->gram_work, h->st, h->pd, h->kW, h->kAW, h->kG};
     for (void* b : bufs)
@@ -604,6 +606,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     PODCG_ALLOC(h->grow, (size_t)kSMax)
     PODCG_ALLOC(h->C, (size_t)kSMax * kWMax)
     PODCG_ALLOC(h->sigma2, (size_t)kSMax)
+    PODCG_ALLOC(h->Vprev, (size_t)kSMax * kSMax)
     PODCG_ALLOC(h->W, ld * c.w_max)
     PODCG_ALLOC(h->AW, ld * c.w_max)
     PODCG_ALLOC(h->G, (size_t)kWMax * (kWMax + 1))
@@ -666,6 +669,7 @@ pod_cg_status pod_cg_clear_snapshots(pod_cg_t* h)
     h->s_next = 0;
     h->pod_dirty = false;
     h->pod_w = 0;
+    h->vprev_s = 0;
     return POD_CG_OK;
 }
 
@@ -736,7 +740,8 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     // POD of the current snapshots (Algorithm 4)
     if (h->s_count > 0 && h->pod_dirty) {
         PODCG_CK(h, launch_pod_eig(h->GS, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, h->cfg.w_max, h->C,
-                                   h->sigma2, h->st, s));
+                                   h->sigma2, h->st, h->Vprev, h->vprev_s, s));
+        h->vprev_s = h->s_count;
         if (h->mixed) PODCG_CK(h, launch_lift32(n, h->S32, h->ld, h->s_count, h->C, h->st, h->W32, h->ld, h->sms, s));
         else PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->W, h->ld, h->sms, s));
         launches += 2;
@@ -960,7 +965,7 @@ pod_cg_status pod_cg_pod(int n, int s, const double* S, double energy, double ra
     if (e == cudaSuccess) e = cudaMalloc((void**)&st, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, sizeof(DevState), str);
     if (e == cudaSuccess) e = launch_gram(n, S, n, s, S, n, s, nullptr, G, kSMax, 0, (double*)work, work_bytes, sms, str);
-    if (e == cudaSuccess) e = launch_pod_eig(G, kSMax, s, energy, rank_tol, w_max, C, sigma2_out, st, str);
+    if (e == cudaSuccess) e = launch_pod_eig(G, kSMax, s, energy, rank_tol, w_max, C, sigma2_out, st, nullptr, 0, str);
     if (e == cudaSuccess) e = launch_lift(n, S, n, s, C, st, W_out, n, sms, str);
     int w = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&w, &st->pod_w, sizeof(int), cudaMemcpyDeviceToHost, str);

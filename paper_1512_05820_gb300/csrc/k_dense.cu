@@ -16,8 +16,10 @@ namespace podcg {
 
 constexpr int kTile = 8;   // Gram output tile edge (8x8 accumulators per thread)
 
-// One split of the rows [r0, r1) for one 8x8 output tile. Y column qy (if ycol_extra)
-// is the extra vector `extra` (the right-hand side b of stage one).
+// One split of the rows [r0, r1) for one TI x 8 output tile (TI = 8, or 1 for a single
+// row such as a new snapshot's Gram row). Y column qy (if `extra`) is the extra vector
+// (the right-hand side b of stage one). Partials are stored 8x8 per tile either way.
+template <int TI>
 __global__ void __launch_bounds__(kBlock) k_gram_partial(int n, const double* __restrict__ X, int ldx, int p,
                                                          const double* __restrict__ Y, int ldy, int qy,
                                                          const double* __restrict__ extra, int q,
@@ -39,7 +41,7 @@ __global__ void __launch_bounds__(kBlock) k_gram_partial(int n, const double* __
         const double* xp[kTile];
         const double* yp[kTile];
 #pragma unroll
-        for (int a = 0; a < kTile; ++a) xp[a] = (a0 + a < p) ? X + (size_t)(a0 + a) * ldx : nullptr;
+        for (int a = 0; a < kTile; ++a) xp[a] = (a < TI && a0 + a < p) ? X + (size_t)(a0 + a) * ldx : nullptr;
 #pragma unroll
         for (int c = 0; c < kTile; ++c) {
             const int cc = c0 + c;
@@ -50,11 +52,11 @@ __global__ void __launch_bounds__(kBlock) k_gram_partial(int n, const double* __
         for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
             double xv[kTile], yv[kTile];
 #pragma unroll
-            for (int a = 0; a < kTile; ++a) xv[a] = xp[a] ? __ldg(xp[a] + i) : 0.0;
+            for (int a = 0; a < TI; ++a) xv[a] = xp[a] ? __ldg(xp[a] + i) : 0.0;
 #pragma unroll
             for (int c = 0; c < kTile; ++c) yv[c] = yp[c] ? __ldg(yp[c] + i) : 0.0;
 #pragma unroll
-            for (int a = 0; a < kTile; ++a)
+            for (int a = 0; a < TI; ++a)
 #pragma unroll
                 for (int c = 0; c < kTile; ++c) acc[a * kTile + c] += xv[a] * yv[c];
         }
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(kBlock) k_gram_partial(int n, const double* __
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int e = 0; e < kTile * kTile; ++e) {
-        const double t = warp_sum(acc[e]);
+        const double t = (e < TI * kTile) ? warp_sum(acc[e]) : 0.0;
         if (lane == 0) s_w[wid][e] = t;
     }
     __syncthreads();
@@ -77,17 +79,21 @@ __global__ void __launch_bounds__(kBlock) k_gram_partial(int n, const double* __
 
 // G[a][c] = sum over splits in split order (deterministic). G row-major p x q with row
 // stride ldg.
+// One warp per output element; lanes take the splits in a fixed interleaved order and a
+// fixed shuffle tree combines them (deterministic).
 __global__ void k_gram_reduce(const double* __restrict__ partials, int splits, int tiles, int tiles_j,
                               int p, int q, double* __restrict__ G, int ldg)
 {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= p * q) return;
+    const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (idx >= p * q) return;   // uniform per warp
     const int a = idx / q, c = idx % q;
     const int tile = (a / kTile) * tiles_j + (c / kTile);
     const int e = (a % kTile) * kTile + (c % kTile);
     double t = 0.0;
-    for (int s = 0; s < splits; ++s) t += partials[((size_t)s * tiles + tile) * (kTile * kTile) + e];
-    G[(size_t)a * ldg + c] = t;
+    for (int s = lane; s < splits; s += 32) t += partials[((size_t)s * tiles + tile) * (kTile * kTile) + e];
+    t = warp_sum(t);
+    if (lane == 0) G[(size_t)a * ldg + c] = t;
 }
 
 void gram_shape(int n, int p, int q, int sms, int* tiles_j, int* tiles, int* splits, int* rows_per_split)
@@ -123,7 +129,8 @@ cudaError_t launch_gram(int n, const double* X, int ldx, int p, const double* Y,
     gram_shape(n, p, q, sms, &tj, &tiles, &splits, &rps);
     if ((size_t)splits * tiles * kTile * kTile * sizeof(double) > work_bytes) return cudaErrorInvalidValue;
     dim3 grid(tiles, splits);
-    k_gram_partial<<<grid, kBlock, 0, s>>>(n, X, ldx, p, Y, ldy, qy, extra, q, tj, upper_only, rps, work);
+    if (p == 1) k_gram_partial<1><<<grid, kBlock, 0, s>>>(n, X, ldx, p, Y, ldy, qy, extra, q, tj, upper_only, rps, work);
+    else k_gram_partial<8><<<grid, kBlock, 0, s>>>(n, X, ldx, p, Y, ldy, qy, extra, q, tj, upper_only, rps, work);
     return launch_gram_reduce(work, splits, tiles, tj, p, q, G, ldg, s);
 }
 
@@ -131,7 +138,7 @@ cudaError_t launch_gram_reduce(const double* work, int splits, int tiles, int tj
                                cudaStream_t s)
 {
     const int m = p * q;
-    k_gram_reduce<<<(m + 127) / 128, 128, 0, s>>>(work, splits, tiles, tj, p, q, G, ldg);
+    k_gram_reduce<<<(m * 32 + 127) / 128, 128, 0, s>>>(work, splits, tiles, tj, p, q, G, ldg);
     return cudaGetLastError();
 }
 
@@ -246,30 +253,45 @@ __device__ int jacobi_parallel(double* A, double* V, int m, int max_sweeps, int*
         const int i = e / kSMax, j = e % kSMax;
         if (j < m) V[e] = (i == j) ? 1.0 : 0.0;
     }
-    double fro = 0.0;
-    // Frobenius norm^2 (one thread; m <= 64)
+    // Frobenius norm^2 and off-diagonal norm^2 by a block reduction (fixed order)
+    auto block_norms = [&](double* total, double* offd) {
+        __shared__ double s_p[2][kBlock / 32];
+        double t = 0.0, o = 0.0;
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = e / m, j = e % m;
+            const double v = A[i * kSMax + j];
+            t += v * v;
+            if (i != j) o += v * v;
+        }
+        t = warp_sum(t);
+        o = warp_sum(o);
+        if ((tid & 31) == 0) {
+            s_p[0][tid >> 5] = t;
+            s_p[1][tid >> 5] = o;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int k = 0; k < nt / 32; ++k) {
+                a += s_p[0][k];
+                b += s_p[1][k];
+            }
+            red[0] = a;
+            red[1] = b;
+        }
+        __syncthreads();
+        *total = red[0];
+        *offd = red[1];
+        __syncthreads();
+    };
+    double fro = 0.0, off0 = 0.0;
     __syncthreads();
-    if (tid == 0) {
-        double t = 0.0;
-        for (int i = 0; i < m; ++i)
-            for (int j = 0; j < m; ++j) t += A[i * kSMax + j] * A[i * kSMax + j];
-        red[0] = t;
-    }
-    __syncthreads();
-    fro = red[0];
+    block_norms(&fro, &off0);
     int sweep = 0;
     const int half = m / 2;
     for (; sweep < max_sweeps; ++sweep) {
-        __syncthreads();
-        if (tid == 0) {
-            double off = 0.0;
-            for (int i = 0; i < m; ++i)
-                for (int j = 0; j < m; ++j)
-                    if (i != j) off += A[i * kSMax + j] * A[i * kSMax + j];
-            red[1] = off;
-        }
-        __syncthreads();
-        const double off = red[1];
+        double tot_unused = 0.0, off = 0.0;
+        block_norms(&tot_unused, &off);
         if (off <= 1e-32 * fro || off == 0.0) break;
         for (int i = tid; i < m; i += nt) pos[i] = i;
         __syncthreads();
@@ -359,6 +381,7 @@ struct SmallSmem {
     double A[kSMax * kSMax];
     double V[kSMax * kSMax];
     double Vs[kSMax * kSMax];
+    double T[kSMax * kSMax];
     double ev[kSMax];
     double cs[kSMax / 2], sn[kSMax / 2];
     double red[4];
@@ -369,21 +392,82 @@ struct SmallSmem {
 // kSMax), numerical rank = #{lambda_i > rank_tol lambda_1}, w = smallest index <= rank with
 // cumulative energy >= energy, capped at w_max; C[k][j] = v_j[k]/sigma_j (row stride kWMax);
 // sigma2[i] = lambda_i. w is written to st->pod_w (and st->w).
+//
+// Warm start: successive snapshot Grams differ in one row and column, so when the
+// eigenvectors of the previous Gram (Vprev, its first prev_s slots) are given, the
+// matrix is first rotated to A' = V0^T G V0 with V0 = blockdiag(Vprev, I), which is
+// nearly diagonal, Jacobi runs on A', and the eigenvectors are mapped back, V = V0 V'.
+// Same eigenpairs (up to rounding) in far fewer sweeps. Vprev receives the new sorted
+// eigenvectors for the next call.
 __global__ void __launch_bounds__(kBlock) k_pod_eig(const double* __restrict__ G, int ldg, int s, double energy,
                                                     double rank_tol, int w_max, double* __restrict__ C,
-                                                    double* __restrict__ sigma2, DevState* st)
+                                                    double* __restrict__ sigma2, DevState* st,
+                                                    double* __restrict__ Vprev, int prev_s)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int m = s + (s & 1);
+    const bool warm = Vprev != nullptr && prev_s > 0 && prev_s <= s;
     for (int e = tid; e < kSMax * kSMax; e += nt) {
         const int i = e / kSMax, j = e % kSMax;
         sm.A[e] = (i < s && j < s) ? G[(size_t)i * ldg + j] : 0.0;
+        if (warm) {
+            double v0 = (i == j) ? 1.0 : 0.0;
+            if (i < prev_s && j < prev_s) v0 = Vprev[e];
+            sm.Vs[e] = (i < s && j < s) ? v0 : 0.0;   // V0
+        }
     }
     __syncthreads();
+    if (warm) {
+        // V = G V0 (in V), then A = V0^T V
+        for (int e = tid; e < s * s; e += nt) {
+            const int i = e / s, j = e % s;
+            double t = 0.0;
+            for (int k = 0; k < s; ++k) t += sm.A[i * kSMax + k] * sm.Vs[k * kSMax + j];
+            sm.V[i * kSMax + j] = t;
+        }
+        __syncthreads();
+        for (int e = tid; e < s * s; e += nt) {
+            const int i = e / s, j = e % s;
+            double t = 0.0;
+            for (int k = 0; k < s; ++k) t += sm.Vs[k * kSMax + i] * sm.V[k * kSMax + j];
+            sm.A[i * kSMax + j] = t;
+        }
+        __syncthreads();
+        // symmetrise the rotated matrix (rounding)
+        for (int e = tid; e < s * s; e += nt) {
+            const int i = e / s, j = e % s;
+            if (i < j) {
+                const double v = 0.5 * (sm.A[i * kSMax + j] + sm.A[j * kSMax + i]);
+                sm.A[i * kSMax + j] = v;
+                sm.A[j * kSMax + i] = v;
+            }
+        }
+        __syncthreads();
+    }
     if (s > 0) jacobi_parallel(sm.A, sm.V, m, 40, sm.pos, sm.cs, sm.sn, sm.pp, sm.qq, sm.red);
+    if (warm) {
+        // V <- V0 V' (V0 in Vs, V' in V, product through T)
+        for (int e = tid; e < s * s; e += nt) {
+            const int i = e / s, j = e % s;
+            double t = 0.0;
+            for (int k = 0; k < s; ++k) t += sm.Vs[i * kSMax + k] * sm.V[k * kSMax + j];
+            sm.T[i * kSMax + j] = t;
+        }
+        __syncthreads();
+        for (int e = tid; e < s * s; e += nt) {
+            const int i = e / s, j = e % s;
+            sm.V[i * kSMax + j] = sm.T[i * kSMax + j];
+        }
+        __syncthreads();
+    }
     sort_eigs(sm.A, sm.V, s, sm.ev, sm.Vs, sm.order);
+    if (Vprev)
+        for (int e = tid; e < kSMax * kSMax; e += nt) {
+            const int i = e / kSMax, j = e % kSMax;
+            Vprev[e] = (i < s && j < s) ? sm.Vs[i * kSMax + j] : 0.0;
+        }
     __shared__ int s_w;
     if (tid == 0) {
         int w = 0;
@@ -418,7 +502,7 @@ __global__ void __launch_bounds__(kBlock) k_pod_eig(const double* __restrict__ G
 size_t pod_eig_smem_bytes() { return sizeof(SmallSmem); }
 
 cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, double rank_tol, int w_max, double* C,
-                           double* sigma2, DevState* st, cudaStream_t str)
+                           double* sigma2, DevState* st, double* Vprev, int prev_s, cudaStream_t str)
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -427,7 +511,7 @@ cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, doubl
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_pod_eig<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, s, energy, rank_tol, w_max, C, sigma2, st);
+    k_pod_eig<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, s, energy, rank_tol, w_max, C, sigma2, st, Vprev, prev_s);
     return cudaGetLastError();
 }
 

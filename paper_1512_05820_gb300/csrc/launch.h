@@ -47,7 +47,7 @@ cudaError_t launch_stage1(int wb, const ProbDesc* pd, int n, const double* W, co
                           double* r, double* partials, unsigned int* counter, DevState* st, double tol, int sms,
                           cudaStream_t s);
 cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, double rank_tol, int w_max, double* C,
-                           double* sigma2, DevState* st, cudaStream_t str);
+                           double* sigma2, DevState* st, double* Vprev, int prev_s, cudaStream_t str);
 cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str);
 cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
 

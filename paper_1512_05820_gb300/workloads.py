@@ -308,6 +308,149 @@ def batch_sequences(nseq: int = 256, p: int = 8, n_min: int = 2000, n_max: int =
     return out
 
 
+def hex8_stiffness(E: float = 1.0, nu: float = 0.3, h: float = 1.0) -> np.ndarray:
+    """24x24 stiffness of a trilinear hexahedron of edge h (linear isotropic elasticity,
+    2x2x2 Gauss quadrature). Local node a = ax + 2 ay + 4 az (ax, ay, az in {0, 1}); dof
+    3a + c for displacement component c."""
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] = lam + 2 * mu
+    D[3, 3] = D[4, 4] = D[5, 5] = mu
+    corners = np.array([[(a >> 0) & 1, (a >> 1) & 1, (a >> 2) & 1] for a in range(8)], float) * 2 - 1
+    g = 1.0 / np.sqrt(3.0)
+    K = np.zeros((24, 24))
+    for gz in (-g, g):
+        for gy in (-g, g):
+            for gx in (-g, g):
+                xi = np.array([gx, gy, gz])
+                dN = np.zeros((8, 3))   # dN/dxi
+                for a in range(8):
+                    ca = corners[a]
+                    f = 1 + ca * xi
+                    dN[a, 0] = ca[0] * f[1] * f[2] / 8
+                    dN[a, 1] = f[0] * ca[1] * f[2] / 8
+                    dN[a, 2] = f[0] * f[1] * ca[2] / 8
+                dNx = dN * (2.0 / h)           # x = h (xi + 1)/2
+                B = np.zeros((6, 24))
+                for a in range(8):
+                    bx, by, bz = dNx[a]
+                    B[0, 3 * a] = bx
+                    B[1, 3 * a + 1] = by
+                    B[2, 3 * a + 2] = bz
+                    B[3, 3 * a] = by
+                    B[3, 3 * a + 1] = bx
+                    B[4, 3 * a + 1] = bz
+                    B[4, 3 * a + 2] = by
+                    B[5, 3 * a] = bz
+                    B[5, 3 * a + 2] = bx
+                K += B.T @ D @ B * (h / 2) ** 3
+    return K
+
+
+class ElasticityOperator:
+    """3D linear elasticity on a block of ex x ey x ez unit trilinear hexahedra, three
+    displacement dofs per node, the nodes of the face x = 0 clamped (their dofs removed).
+    Free node (ix >= 1, iy, iz) has index (ix - 1) + (nx - 1)(iy + ny iz); dof 3 node + c.
+    CSR rows list the up to 27 neighbouring free nodes in increasing node order, each with
+    its three components. ``values(E)`` assembles for per-element Young's moduli."""
+
+    def __init__(self, ex: int, ey: int, ez: int, nu: float = 0.3):
+        self.ex, self.ey, self.ez = ex, ey, ez
+        self.nx, self.ny, self.nz = ex + 1, ey + 1, ez + 1
+        nx, ny, nz = self.nx, self.ny, self.nz
+        self.nfree = (nx - 1) * ny * nz
+        self.n = 3 * self.nfree
+        self.Ke = hex8_stiffness(1.0, nu)
+        iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(1, nx), indexing="ij")
+        self.fix, self.fiy, self.fiz = ix.ravel(), iy.ravel(), iz.ravel()
+        offs = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+        self.offs = offs
+        valid = np.zeros((self.nfree, 27), bool)
+        nbr = np.zeros((self.nfree, 27), np.int64)
+        for s_, (dz, dy, dx) in enumerate(offs):
+            jx, jy, jz = self.fix + dx, self.fiy + dy, self.fiz + dz
+            ok = (jx >= 1) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
+            valid[:, s_] = ok
+            nbr[:, s_] = np.where(ok, (jx - 1) + (nx - 1) * (jy + ny * jz), 0)
+        self.slot_valid = valid
+        mask = np.repeat(np.repeat(valid, 3, axis=1)[:, None, :], 3, axis=1).reshape(self.n, 81)
+        self.mask = mask
+        cols = (3 * np.repeat(nbr, 3, axis=1) + np.tile(np.arange(3), 27)[None, :])
+        cols = np.repeat(cols[:, None, :], 3, axis=1).reshape(self.n, 81)
+        self.col = cols[mask].astype(np.int32)
+        counts = mask.sum(axis=1)
+        self.row_ptr = np.zeros(self.n + 1, dtype=np.int32)
+        np.cumsum(counts, out=self.row_ptr[1:])
+        self.nnz = int(self.row_ptr[-1])
+        ez_, ey_, ex_ = np.meshgrid(np.arange(ez), np.arange(ey), np.arange(ex), indexing="ij")
+        self.eix, self.eiy, self.eiz = ex_.ravel(), ey_.ravel(), ez_.ravel()
+
+    def element_centres(self):
+        return np.stack([self.eix + 0.5, self.eiy + 0.5, self.eiz + 0.5], axis=1)
+
+    def values(self, E) -> np.ndarray:
+        E = np.asarray(E, dtype=np.float64)
+        nx, ny = self.nx, self.ny
+        V = np.zeros((self.nfree, 3, 81))
+        for a in range(8):
+            ax, ay, az = a & 1, (a >> 1) & 1, (a >> 2) & 1
+            nxa, nya, nza = self.eix + ax, self.eiy + ay, self.eiz + az
+            fa = nxa >= 1
+            rows = (nxa - 1) + (nx - 1) * (nya + ny * nza)
+            for b in range(8):
+                bx, by, bz = b & 1, (b >> 1) & 1, (b >> 2) & 1
+                fb = self.eix + bx >= 1
+                ok = fa & fb
+                s_ = 9 * (bz - az + 1) + 3 * (by - ay + 1) + (bx - ax + 1)
+                r_ok, e_ok = rows[ok], E[ok]
+                blk = self.Ke[3 * a:3 * a + 3, 3 * b:3 * b + 3]
+                V[r_ok, :, 3 * s_:3 * s_ + 3] += e_ok[:, None, None] * blk[None, :, :]
+        return V.reshape(self.n, 81)[self.mask]
+
+    def csr(self, E) -> CSR:
+        return CSR(self.n, self.row_ptr, self.col, self.values(E))
+
+    def end_traction(self, phi: float) -> np.ndarray:
+        """Unit traction (0, cos phi, sin phi) on the face x = L, lumped to its nodes with
+        the bilinear face weights (corner 1/4, edge 1/2, interior 1)."""
+        b = np.zeros((self.nfree, 3))
+        on = self.fix == self.nx - 1
+        wy = np.where((self.fiy == 0) | (self.fiy == self.ny - 1), 0.5, 1.0)
+        wz = np.where((self.fiz == 0) | (self.fiz == self.nz - 1), 0.5, 1.0)
+        wgt = np.where(on, wy * wz, 0.0)
+        b[:, 1] = wgt * np.cos(phi)
+        b[:, 2] = wgt * np.sin(phi)
+        return b.ravel()
+
+
+def _elasticity_gen(seq: Sequence):
+    r = seq.recipe
+    op = seq.op
+    rng = np.random.default_rng(seq.seed)
+    E0 = np.exp(rng.normal(0.0, r["e_sigma"], op.ex * op.ey * op.ez))
+    xc = op.element_centres()
+    for j in range(1, seq.p + 1):
+        c = np.array([op.ex * j / (seq.p + 1), op.ey / 2.0, op.ez / 2.0])
+        d = r["damage"] * np.exp(-np.sum((xc - c) ** 2, axis=1) / (2.0 * r["damage_width"] ** 2))
+        val = op.values(E0 * (1.0 - d))
+        b = op.end_traction(2.0 * np.pi * j / seq.p)
+        yield j, val, b
+
+
+def elasticity_cantilever(e: int = 64, p: int = 30, seed: int = 1236, w_max: int = 48, s_max: int = 40,
+                          energy: float = 0.9999, tol: float = 1e-8) -> Sequence:
+    """3D cantilever of e^3 unit trilinear hexahedra, clamped at x = 0, Poisson ratio 0.3;
+    Young's modulus lognormal(0, 0.3) per element scaled by (1 - d_j), d_j = 0.3
+    exp(-|x_e - c_j|^2/(2 8^2)) a damage spot moving along the beam (c_j = (e j/(p+1),
+    e/2, e/2)); load: a unit end traction rotating about the beam axis,
+    phi_j = 2 pi j/p. Draws: E0 ~ lognormal(0, 0.3) (e^3 values)."""
+    op = ElasticityOperator(e, e, e)
+    recipe = {"e_sigma": 0.3, "damage": 0.3, "damage_width": 8.0 * e / 64.0}
+    return Sequence("elasticity_cantilever", op, p, tol, s_max, w_max, energy, seed, recipe, _elasticity_gen)
+
+
 def random_spd_csr(n: int, density: float, seed: int, shift: float = 1.0, empty_rows: int = 0) -> CSR:
     """Random sparse SPD matrix with ragged row lengths (symmetric pattern, strictly
     diagonally dominant): used for edge-case tests (heavy-tailed rows, ``empty_rows``
