@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--kernel-reps", type=int, default=20)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-sequences measurement")
+    ap.add_argument("--diff-check", type=int, default=0, metavar="K",
+                    help="differentiation check on the 96^3, 20-system theta workload: adjoint dL/dtheta "
+                         "against fourth-order central differences at K random cells")
     ap.add_argument("--kernel-profile", type=int, default=0, metavar="W",
                     help="profiling target: one full-size system with W synthetic snapshots, a 5-iteration "
                          "solve, then each stage-two kernel launched --kernel-reps times (few launches)")
@@ -201,7 +204,7 @@ def run_reference(args, rank, world):
 # ----------------------------------------------------------------------------- ours
 
 
-def batch_section(args):
+def batch_section(args, rank=0, world=1):
     """Many independent sequences (256 x 8 systems, n log-uniform in [2k, 260k], 2D/3D mixed,
     w_max in [4, 24]) in one persistent launch under a CUDA graph, cluster size autotuned,
     FP32 inner + FP64 refinement; compared with the single-sequence engine in FP64 on the
@@ -211,7 +214,10 @@ def batch_section(args):
     from paper_1512_05820_gb300.batch import BatchSolver
     from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
     from paper_1512_05820_gb300.solver import PodCG
-    seqs = wl.batch_sequences(nseq=args.batch_seqs)
+    from paper_1512_05820_gb300.dist import combine, shard_by_work
+    all_seqs = wl.batch_sequences(nseq=args.batch_seqs)
+    mine = shard_by_work([float(s.nnz) * s.p * s.n ** (1 / 3) for s in all_seqs], rank, world)
+    seqs = [all_seqs[i] for i in mine]   # independent sequences: each rank solves its share
     systems = [s.all_systems() for s in seqs]
     t0 = time.perf_counter()
     bs = BatchSolver(seqs, systems=systems, cluster=0)
@@ -221,18 +227,22 @@ def batch_section(args):
     for _ in range(max(1, args.steps)):
         stats, ms = bs.solve()
         times.append(ms)
-    ms = statistics.median(times)
-    total = len(stats)
-    ok = sum(1 for s in stats if s["status"] == "ok")
+    ms_local = statistics.median(times)
+    ms, total = combine(ms_local, float(len(stats)))
+    total = int(total)
+    ok = int(combine(0.0, float(sum(1 for s in stats if s["status"] == "ok")))[1])
     info = bs.info()
-    out = {"workload": f"{len(seqs)} sequences x {seqs[0].p} systems, n in [2k, 260k] log-uniform, 2D/3D",
-           "rows_per_layer": int(sum(s.n for s in seqs)), "systems": total, "converged": ok,
+    out = {"workload": f"{len(all_seqs)} sequences x {all_seqs[0].p} systems, n in [2k, 260k] log-uniform, 2D/3D",
+           "rows_per_layer": int(sum(s.n for s in all_seqs)), "systems": total, "converged": ok,
+           "sharding": "independent sequences, no collective" if world > 1 else "single GPU",
            "systems_per_s": total / (ms / 1e3), "ms_per_batch": ms,
            "max_final_relres": max(s["final_relres"] for s in stats),
            "mean_iters": float(np.mean([s["iters"] for s in stats])),
            "cluster": info["cluster"], "workers": info["workers"],
            "autotune_ms": {str(k): v for k, v in info["tune_ms"].items()}, "setup_s": tune_s}
     bs.close()
+    if world > 1:
+        return out
     # single-sequence engine, FP64, same tolerance, first 32 sequences
     sub = seqs[:32]
     t_single, n_single = 0.0, 0
@@ -296,6 +306,53 @@ def kernel_profile(args):
     return 0
 
 
+def diff_check(args):
+    """Loss L = sum_j c^T x_j over the 96^3 sequence A_j(theta) x_j = b_j (20 systems,
+    theta ~ N(0, 0.5^2) per cell): gradient by the adjoint path (forward solves with
+    recycling, adjoint solves reusing each W_j, fused edge-wise kernel) against the
+    fourth-order central difference (h = 1e-3) at K seeded random cells; solves at 1e-12."""
+    import torch
+    from paper_1512_05820_gb300 import workloads as wl
+    from paper_1512_05820_gb300.adjoint import DiffusionProblem, solve_sequence
+    seq = wl.diffusion3d_theta(m=96, p=20)
+    r = seq.recipe
+    shifts = np.stack([0.01 * (j + 1) * r["u"] for j in range(seq.p)])
+    B = torch.as_tensor(np.stack([b for _, _, b in seq.systems()]), device="cuda")
+    c = torch.as_tensor(r["c"], device="cuda")
+    prob = DiffusionProblem.from_operator(seq.op, shifts=shifts, tol=1e-12, w_max=32, s_max=40)
+    th = torch.as_tensor(r["theta"], device="cuda").requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X = solve_sequence(th, B, prob)
+    loss = (X * c).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = th.grad.cpu().numpy()
+
+    def L(theta):
+        with torch.no_grad():
+            Xp = solve_sequence(torch.as_tensor(theta, device="cuda"), B, prob)
+            return float((Xp * c).sum())
+
+    rng = np.random.default_rng(5)
+    cells = rng.choice(seq.n, size=args.diff_check, replace=False)
+    th0 = r["theta"]
+    h = 1e-3
+    errs = []
+    for cc in cells:
+        e = np.zeros(seq.n)
+        e[cc] = h
+        fd = (-L(th0 + 2 * e) + 8 * L(th0 + e) - 8 * L(th0 - e) + L(th0 - 2 * e)) / (12 * h)
+        errs.append(abs(fd - g[cc]) / max(abs(g[cc]), 1e-300))
+    print(json.dumps({"diff_check": True, "workload": "diffusion3d_theta 96^3, 20 systems", "cells": len(cells),
+                      "max_rel_err": float(max(errs)), "median_rel_err": float(np.median(errs)),
+                      "forward_s": t1 - t0, "backward_s": t2 - t1, "loss": float(loss)}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     rank, world, local = dist_env()
@@ -303,6 +360,8 @@ def main():
         return run_reference(args, rank, world)
     if args.kernel_profile:
         return kernel_profile(args)
+    if args.diff_check:
+        return diff_check(args)
 
     import torch
     from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
@@ -345,13 +404,9 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms_total = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    from paper_1512_05820_gb300.dist import combine
+    ms_total, systems_done = combine(e0.elapsed_time(e1), float(seq.p * args.steps))
     ms_step = ms_total / args.steps
-    systems_done = world * seq.p * args.steps
     value = systems_done / (ms_total / 1e3)
     last = all_stats[-1]
     spmv_per_step = sum(s["spmv_count"] for s in last)
@@ -360,6 +415,13 @@ def main():
     launches = sum(s["launches"] + 3 for st in all_stats for s in st)   # + add_snapshots (3 kernels)
     iters = [s["iters"] for s in last]
     ws = [s["w"] for s in last]
+
+    batch_out = None
+    if not args.no_batch:   # every rank takes part (sequences shard across ranks)
+        try:
+            batch_out = batch_section(args, rank, world)
+        except Exception as e:  # reported, not fatal to the headline measurement
+            batch_out = {"error": repr(e)[:300]}
 
     if rank != 0:
         if dist is not None:
@@ -473,12 +535,8 @@ def main():
         out["e2e"] = {"value": world * seq.p / dt, "unit": "systems/s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h}
 
-    if not args.no_batch:
-        try:
-            out["batch"] = batch_section(args)
-        except Exception as e:  # reported, not fatal to the headline measurement
-            out["batch"] = {"error": repr(e)[:300]}
-
+    if batch_out is not None:
+        out["batch"] = batch_out
     out["gpu_launches"] = launches
     out["clocks"] = clocks
     if world == 1 and not args.no_cpu_baseline:
