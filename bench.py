@@ -15,6 +15,7 @@ reference arm of this build) on a bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -149,20 +150,30 @@ class ClockSampler:
                 "reasons": reasons}
 
 
-def traffic_from_profiles(kernel: str):
+KERNEL_SOURCE = {"k_update": "k_cg.cu", "k_dir": "k_cg.cu", "k_init": "k_cg.cu",
+                 "k_spmv_cg": "k_sparse.cu", "k_residual": "k_sparse.cu"}
+
+
+def traffic_from_profiles(kernel: str, precision: str, w: int):
     """Per-launch DRAM bytes of `kernel` from a committed ncu summary (profiles/*.txt lines
-    `traffic_bytes_per_launch <kernel> <bytes> <source-hash>`), or None."""
+    `traffic_bytes_per_launch <kernel> <precision> <w> <bytes> <sha1 prefix of its source>`),
+    or None when there is none for this kernel, precision and w, or when the kernel's source
+    file has changed since the counters were taken."""
     d = os.path.join(ROOT, "profiles")
-    if not os.path.isdir(d):
+    src = KERNEL_SOURCE.get(kernel)
+    if not os.path.isdir(d) or src is None:
         return None
+    with open(os.path.join(ROOT, "paper_1512_05820_gb300", "csrc", src), "rb") as f:
+        digest = hashlib.sha1(f.read()).hexdigest()
     for fn in sorted(os.listdir(d)):
         if not fn.endswith(".txt"):
             continue
         with open(os.path.join(d, fn)) as f:
             for line in f:
                 parts = line.split()
-                if len(parts) >= 3 and parts[0] == "traffic_bytes_per_launch" and parts[1] == kernel:
-                    return float(parts[2])
+                if (len(parts) >= 6 and parts[0] == "traffic_bytes_per_launch" and parts[1] == kernel
+                        and parts[2] == precision and int(parts[3]) == w and digest.startswith(parts[5])):
+                    return float(parts[4])
     return None
 
 
@@ -492,7 +503,7 @@ def main():
     names = {"spmv_cg": "k_spmv_cg", "update": "k_update", "direction": "k_dir", "residual": "k_residual"}
     out["roofline"] = {"bound": "hbm", "kernel": names[dominant], "achieved": achieved, "peak": peak, "unit": "GB/s",
                        "frac": achieved / peak, "peak_source": peak_kind,
-                       "traffic": traffic_from_profiles(names[dominant]),
+                       "traffic": traffic_from_profiles(names[dominant], "mixed" if prec == 1 else "fp64", w_meas),
                        "algorithmic_bytes_per_launch": kbytes[dominant], "w": w_meas,
                        "ms_per_launch": kms[dominant]}
     out["kernels"] = {k: {"ms": kms[k], "GB/s": kbytes[k] / (kms[k] / 1e3) / 1e9,
