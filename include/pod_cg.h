@@ -68,12 +68,20 @@ typedef struct {
     int    max_refine;   /* FP64: residual-replacement restarts; MIXED: FP64 refinement steps */
     int    precision;    /* POD_CG_FP64, or POD_CG_MIXED (FP32 inner CG, FP64 refinement) */
     double inner_tol;    /* MIXED: each inner solve reduces its residual by this factor */
-    int    use_tc_gram;  /* MIXED: stage-one Gram on tensor cores with split products */
+    int    use_tc_gram;  /* MIXED only (else ERR_ARG at create): stage-one Gram W^T [AW, b] of
+                            the FP32 panels on the tensor cores with split-bf16 products
+                            (pod_cg_gram_tc); 0 = CUDA cores. FP64 mode keeps the FP64 Gram:
+                            an FP32-rounded W^T A W leaves the directions A-orthogonal to W
+                            only to ~1e-7 cond(W^T A W), too loose for FP64 tolerances */
     int    cond_diag;    /* 1: compute cond_2(W^T A W) per solve (diagnostic, Section 5.2) */
     int    keep_factors; /* systems whose W, AW, R are kept for pod_cg_solve_adjoint (0..) */
     int    loop_mode;    /* 0: the CG loop is one conditional CUDA graph (no host round trip);
                             1: plain graphs of 16 unrolled iterations, host check per chunk
                             (same kernels; a form that kernel profilers can attribute) */
+    int    proj_form;    /* MIXED, FP32 update/direction passes: -1 = timed once per basis-
+                            width bucket on the handle's first system of >= 65,536 rows in
+                            it (else row-parallel); 0 = row-parallel float4; 1 = tiles staged
+                            in shared memory by bulk copies (see pod_cg_proj_tuning) */
 } pod_cg_config;
 
 /* CSR matrix, device arrays, borrowed. */
@@ -110,7 +118,7 @@ typedef struct {
 
 /* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
  * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
- * loop_mode 0. */
+ * loop_mode 0, proj_form -1. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 
 /* Create a solver for systems of order n (the problem statement of Section 2) whose work
@@ -173,6 +181,15 @@ pod_cg_status pod_cg_get_basis(pod_cg_t* h, double* W_out, int* w_out);
  * iteration vectors are overwritten (the next solve resets them). Errors: ERR_ARG, ERR_CUDA. */
 pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double* b, int reps, float* ms_out);
 
+/* The FP32 projection form chosen per basis-width bucket (buckets w <= 0, 8, 16, 32, 48,
+ * 64): forms[6] receives 0 (row-parallel float4 passes), 1 (tiles staged in shared memory
+ * by bulk copies) or -1 (bucket not used yet); ms[12] the update + direction times (ms)
+ * of form 0 then form 1 for each bucket, as measured by the handle's one-time timing on the
+ * first MIXED system of at least 65,536 rows in that bucket (0 where not timed). The
+ * paper has no counterpart: this is the project's own tuning record. Host outputs;
+ * either pointer may be NULL. */
+pod_cg_status pod_cg_proj_tuning(const pod_cg_t* h, int* forms, float* ms);
+
 /* Autotuner record (no counterpart in the paper): the CSR SpMV lanes-per-row used by the
  * last solve (1, 2, ..., 32) and, for systems of at least 65,536 rows, the measured
  * milliseconds of each candidate on that matrix (index k for 2^k lanes; -1 = not tried,
@@ -199,6 +216,25 @@ size_t pod_cg_gram_workspace(int n, int p, int q);
  * bytes, caller-owned scratch (contents on return are unspecified). */
 pod_cg_status pod_cg_gram(int n, const double* X, int p, const double* Y, int q, double* G,
                           void* work, size_t work_bytes, void* cuda_stream);
+
+/* Bytes of device workspace pod_cg_gram_tc needs for an n-row, p-by-q product. */
+size_t pod_cg_gram_tc_workspace(int n, int p, int q);
+
+/* G = X^T [Y, e] on the tensor cores: the reduced matrix of stage one (Algorithm 2 step 1,
+ * W^T (A W) with the extra column W^T b) for X (n-by-p) and Y (n-by-qy), column-major with
+ * leading dimension n, of element type FP32 (elem_bytes 4) or FP64 (elem_bytes 8), and an
+ * optional FP64 column e (NULL for none); q = qy + (e != NULL); 1 <= p <= 64, 0 <= qy <= 64.
+ * G is device row-major p-by-q (leading dimension q), FP64. Every value is rounded to FP32
+ * and split exactly into three bf16 parts; the bf16 part products (at least the seven
+ * with weight above 2^-24) accumulate in FP32 in tensor memory over 128-row windows,
+ * Kahan-compensated in FP32 across windows and summed in FP64 across the GPU. The result
+ * is deterministic; its error is that of an FP32-rounded input (about 2^-24 relative per
+ * entry of X and Y) plus FP32 accumulation within a window. X, Y and e must start on
+ * 16-byte boundaries and n * elem_bytes be a multiple of 16 (TMA); otherwise ERR_ARG.
+ * work: device, at least pod_cg_gram_tc_workspace(n, p, q) bytes. Stream-ordered; a device
+ * wait that expires (not expected) leaves NaN in G. */
+pod_cg_status pod_cg_gram_tc(int n, int elem_bytes, const void* X, int p, const void* Y, int qy,
+                             const double* e, double* G, void* work, size_t work_bytes, void* cuda_stream);
 
 /* Allocation-free G = X^T Y (the paper has no counterpart: this is a deployment variant
  * of pod_cg_gram). It is for callers that cannot allocate device memory at the point of

@@ -36,7 +36,8 @@ def lib_path(mutant: int = 0, out_dir: str | None = None) -> str:
 
 
 def build(mutant: int = 0, out_dir: str | None = None, force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, portable flags) and return the .so path.
+    """Compile the oracle with gcc (plain -O2, portable flags, no fused multiply-add
+    contraction, so x86 and Arm builds round identically) and return the .so path.
 
     ``mutant`` > 0 plants the numbered mistake (``-DORC_MUTANT=k``) for the pin-sensitivity
     tests; the normal build uses 0.
@@ -47,7 +48,7 @@ def build(mutant: int = 0, out_dir: str | None = None, force: bool = False) -> s
             and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
         return out
     tmp = out + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", f"-DORC_MUTANT={int(mutant)}",
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", f"-DORC_MUTANT={int(mutant)}",
            _SRC, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)

@@ -12,7 +12,8 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "not_spd", 3: "breakdown", 4: "maxit", 5: 
 # every function the header declares (checked by the symbol-export test)
 EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_last_error",
            "pod_cg_add_snapshots", "pod_cg_clear_snapshots", "pod_cg_solve", "pod_cg_solve_adjoint",
-           "pod_cg_get_basis", "pod_cg_time_kernels", "pod_cg_tuning", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram", "pod_cg_gram_noalloc", "pod_cg_diffusion_assemble",
+           "pod_cg_get_basis", "pod_cg_time_kernels", "pod_cg_tuning", "pod_cg_proj_tuning", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram", "pod_cg_gram_noalloc",
+           "pod_cg_gram_tc_workspace", "pod_cg_gram_tc", "pod_cg_diffusion_assemble",
            "pod_cg_diffusion_theta_grad", "pod_cg_batch_create", "pod_cg_batch_solve", "pod_cg_batch_info",
            "pod_cg_batch_last_error", "pod_cg_batch_destroy",
            "pod_cg_pod"]
@@ -22,7 +23,8 @@ class Config(ctypes.Structure):
     _fields_ = [("w_max", ctypes.c_int), ("s_max", ctypes.c_int), ("energy", ctypes.c_double),
                 ("rank_tol", ctypes.c_double), ("k_max", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("use_tc_gram", ctypes.c_int),
-                ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int), ("loop_mode", ctypes.c_int)]
+                ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int), ("loop_mode", ctypes.c_int),
+                ("proj_form", ctypes.c_int)]
 
 
 class CSRStruct(ctypes.Structure):
@@ -89,12 +91,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_get_basis.argtypes = [vp, vp, P(ci)]
     L.pod_cg_time_kernels.argtypes = [vp, P(CSRStruct), vp, ci, P(ctypes.c_float)]
     L.pod_cg_tuning.argtypes = [vp, P(ci), P(ctypes.c_float)]
+    L.pod_cg_proj_tuning.argtypes = [vp, P(ci), P(ctypes.c_float)]
     L.pod_cg_spmv.argtypes = [P(CSRStruct), vp, vp, vp]
     L.pod_cg_spmm.argtypes = [P(CSRStruct), vp, ci, vp, vp]
     L.pod_cg_gram_workspace.argtypes = [ci, ci, ci]
     L.pod_cg_gram_workspace.restype = sz
     L.pod_cg_gram.argtypes = [ci, vp, ci, vp, ci, vp, vp, sz, vp]
     L.pod_cg_gram_noalloc.argtypes = [ci, vp, ci, vp, ci, vp, vp]
+    L.pod_cg_gram_tc_workspace.argtypes = [ci, ci, ci]
+    L.pod_cg_gram_tc_workspace.restype = sz
+    L.pod_cg_gram_tc.argtypes = [ci, ci, vp, ci, vp, ci, vp, vp, vp, sz, vp]
     L.pod_cg_diffusion_assemble.argtypes = [ci, ci, ci, vp, vp, vp, vp, vp]
     L.pod_cg_diffusion_theta_grad.argtypes = [ci, ci, ci, vp, ci, vp, vp, vp, vp]
     L.pod_cg_batch_create.argtypes = [P(BatchSeq), ci, P(Config), ci, vp, P(vp)]
@@ -105,7 +111,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_batch_destroy.argtypes = [vp]
     L.pod_cg_pod.argtypes = [ci, ci, vp, cd, cd, ci, vp, vp, P(ci), vp, sz, vp]
     for name in EXPORTS:
-        if name not in ("pod_cg_last_error", "pod_cg_gram_workspace", "pod_cg_batch_last_error"):
+        if name not in ("pod_cg_last_error", "pod_cg_gram_workspace", "pod_cg_gram_tc_workspace",
+                        "pod_cg_batch_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L

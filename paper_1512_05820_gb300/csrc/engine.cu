@@ -71,6 +71,7 @@ struct KArgs {
 struct KSpec {
     void* f = nullptr;
     int grid = 1;
+    int smem = 0;   // dynamic shared memory bytes
     KArgs a;
     KSpec() = default;
     KSpec(const KSpec&) = delete;
@@ -103,7 +104,7 @@ cudaError_t add_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, K
     p.func = k.f;
     p.gridDim = dim3(k.grid);
     p.blockDim = dim3(kBlock);
-    p.sharedMemBytes = 0;
+    p.sharedMemBytes = (unsigned int)k.smem;
     p.kernelParams = k.a.ptrs;
     p.extra = nullptr;
     return cudaGraphAddKernelNode(out, g, deps, ndeps, &p);
@@ -124,7 +125,7 @@ cudaError_t add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, 
 
 cudaError_t launch_spec(KSpec& k, cudaStream_t s)
 {
-    return cudaLaunchKernel(k.f, dim3(k.grid), dim3(kBlock), k.a.ptrs, 0, s);
+    return cudaLaunchKernel(k.f, dim3(k.grid), dim3(kBlock), k.a.ptrs, (size_t)k.smem, s);
 }
 
 }  // namespace
@@ -186,6 +187,11 @@ struct pod_cg_t {
     struct LaneChoice { const int32_t* rp; int n; int64_t nnz; bool mixed; int L; float ms[6]; };
     std::vector<LaneChoice> lanes;
     int last_L = 0;
+    // FP32 projection form per width bucket (kProjDirect / kProjStaged, -1 = not chosen yet)
+    // and the update + direction times that chose it (ms, [bucket][form])
+    int proj_form[6] = {-1, -1, -1, -1, -1, -1};
+    float proj_ms[6][2] = {};
+    DevState* st_save = nullptr;   // device copy of the state while the form is timed
 
     GraphSlot graphs[6];                // conditional graphs [width bucket]
     GraphSlot chunks[6];                // plain chunk graphs [width bucket]
@@ -277,11 +283,69 @@ pod_cg_status choose_lanes(pod_cg_t* h, const pod_cg_csr* A, int* L_out)
     return POD_CG_OK;
 }
 
+void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphConditionalHandle h_inner,
+               cudaGraphConditionalHandle h_outer, Plan& P);
+pod_cg_status read_state(pod_cg_t* h);
+
+// FP32 projection form for width bucket wb: both forms of the update and direction passes
+// are timed once on this system (CUDA events, median-free mean of 3 after a warm-up) and
+// the faster pair is kept for the bucket. The device state is saved first and restored
+// after; the FP32 vectors the passes touch are scratch until the loop starts. Systems
+// under 65,536 rows take the direct form untimed.
+pod_cg_status choose_proj_form(pod_cg_t* h, int wb, int L)
+{
+    const int bi = bucket_index(wb);
+    if (!h->mixed || wb == 0 || h->proj_form[bi] >= 0) return POD_CG_OK;
+    if (h->n < 65536) {
+        h->proj_form[bi] = kProjDirect;
+        return POD_CG_OK;
+    }
+    cudaStream_t s = h->stream;
+    PODCG_CK(h, cudaMemcpyAsync(h->st_save, h->st, sizeof(DevState), cudaMemcpyDeviceToDevice, s));
+    pod_cg_status rs = read_state(h);
+    if (rs != POD_CG_OK) return rs;
+    DevState t = *h->st_host;   // a state under which both passes do their full work
+    t.rho = 1.0;
+    t.alpha = 1e-30;
+    t.beta = 0.5;
+    t.k_max = 1 << 30;
+    t.tol2_in = -1.0;
+    t.dir_pending = 1;
+    t.done = 0;
+    t.status = 0;
+    t.inner_break = 0;
+    t.outer_done = 0;
+    for (int a = 0; a < kWMax; ++a) t.c[a] = 0.0;
+    *h->st_host = t;
+    for (int form = kProjDirect; form <= kProjStaged; ++form) {
+        h->proj_form[bi] = form;
+        Plan pl;
+        make_plan(h, wb, L, true, 0, 0, 0, pl);
+        KSpec* ks[2] = {&pl.upd, &pl.dir};
+        float total = 0.0f;
+        for (int k = 0; k < 2; ++k)
+            for (int rep = 0; rep < 4; ++rep) {
+                PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
+                PODCG_CK(h, cudaEventRecord(h->ev[0], s));
+                PODCG_CK(h, launch_spec(*ks[k], s));
+                PODCG_CK(h, cudaEventRecord(h->ev[1], s));
+                PODCG_CK(h, cudaEventSynchronize(h->ev[1]));
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+                if (rep > 0) total += ms;
+            }
+        h->proj_ms[bi][form] = total / 3.0f;
+    }
+    h->proj_form[bi] = h->proj_ms[bi][kProjStaged] < h->proj_ms[bi][kProjDirect] ? kProjStaged : kProjDirect;
+    PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_save, sizeof(DevState), cudaMemcpyDeviceToDevice, s));
+    return read_state(h);
+}
+
 // One wave: as many blocks as are resident at once (occupancy), never more than needed.
-int occ_grid(pod_cg_t* h, const void* f, int rows, int rows_per_block)
+int occ_grid(pod_cg_t* h, const void* f, int rows, int rows_per_block, int smem = 0)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kBlock, 0) != cudaSuccess || nb < 1) nb = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kBlock, (size_t)smem) != cudaSuccess || nb < 1) nb = 1;
     long long need = ((long long)rows + rows_per_block - 1) / rows_per_block;
     long long cap = (long long)h->sms * nb;
     long long g = std::min(need, cap);
@@ -294,12 +358,14 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
 {
     const int n = h->n, ld = h->ld;
     void *f_init, *f_upd, *f_dir0, *f_dir;
-    cg_kernels(wb, mixed, use_cond != 0, &f_init, &f_upd, &f_dir0, &f_dir);
+    int sm_upd = 0, sm_dir = 0;
+    const int form = h->proj_form[bucket_index(wb)] == kProjStaged ? kProjStaged : kProjDirect;
+    cg_kernels(wb, mixed, use_cond != 0, form, &f_init, &f_upd, &f_dir0, &f_dir, &sm_upd, &sm_dir);
     void* f_spmv = kernel_spmv_cg(L, mixed);
     void* f_res = kernel_residual(L, use_cond != 0);
     const int g_init = occ_grid(h, f_init, n, kBlock);
-    const int g_upd = occ_grid(h, f_upd, n, kBlock);
-    const int g_dir = occ_grid(h, f_dir, n, kBlock);
+    const int g_upd = occ_grid(h, f_upd, n, kBlock, sm_upd);
+    const int g_dir = occ_grid(h, f_dir, n, kBlock, sm_dir);
     const int g_spmv = occ_grid(h, f_spmv, n, kBlock / L);
     const int g_res = occ_grid(h, f_res, n, kBlock / L);
     unsigned int* c = h->counters;
@@ -339,6 +405,9 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
                   (const float*)h->W32, Rinv, cst);
         P.mxaccum.set(f_acc, occ_grid(h, f_acc, n, kBlock), n, h->x, (const float*)h->d32, cst);
     }
+    P.upd.smem = sm_upd;
+    P.dir0.smem = sm_dir;
+    P.dir.smem = sm_dir;
 }
 
 void destroy_graph(GraphSlot& gs)
@@ -549,6 +618,7 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->cond_diag = 0;
     c->keep_factors = 0;
     c->loop_mode = 0;
+    c->proj_form = -1;
     return POD_CG_OK;
 }
 
@@ -564,7 +634,7 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     for (auto& g : h->chunks) destroy_graph(g);
     void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->G, h->Rinv,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
-                    h->partials, h->counters, h->gram_work, h->st, h->pd, h->kW, h->kAW, h->kG};
+                    h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->st_host) cudaFreeHost(h->st_host);
@@ -586,14 +656,20 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     if (c.w_max < 1 || c.w_max > kWMax || c.s_max < 1 || c.s_max > kSMax || !(c.energy >= 0.0 && c.energy <= 1.0) ||
         c.k_max < 0 || c.max_refine < 0 || (c.precision != POD_CG_FP64 && c.precision != POD_CG_MIXED) ||
         c.keep_factors < 0 || c.keep_factors > 4096 || (c.loop_mode != 0 && c.loop_mode != 1) ||
+        c.proj_form < -1 || c.proj_form > 1 ||
         !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
         return fail(nullptr, POD_CG_ERR_ARG, "invalid configuration");
+    if (c.use_tc_gram != 0 && (c.use_tc_gram != 1 || c.precision != POD_CG_MIXED))
+        return fail(nullptr, POD_CG_ERR_ARG,
+                    "use_tc_gram needs precision MIXED: the tensor-core Gram rounds W and AW to FP32");
     pod_cg_t* h = new (std::nothrow) pod_cg_t();
     if (!h) return fail(nullptr, POD_CG_ERR_OOM, "host allocation failed");
     h->n = n;
     h->ld = ((n + 31) / 32) * 32;
     h->cfg = c;
     h->mixed = c.precision == POD_CG_MIXED;
+    if (c.proj_form >= 0)
+        for (int& f : h->proj_form) f = c.proj_form;
     h->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&h->device);
     h->sms = device_sms();
@@ -620,6 +696,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     PODCG_ALLOC(h->partials, (size_t)(kWMax + 2) * kPartialStride)
     PODCG_ALLOC(h->counters, 16)
     PODCG_ALLOC(h->st, 1)
+    PODCG_ALLOC(h->st_save, 1)
     PODCG_ALLOC(h->pd, 1)
     if (h->mixed) {
         PODCG_ALLOC(h->S32, ld * c.s_max)
@@ -641,6 +718,8 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     if (e == cudaSuccess) {
         h->gram_work_bytes = std::max(gram_workspace_bytes(n, 1, c.s_max, h->sms),
                                       gram_workspace_bytes(n, c.w_max, c.w_max + 1, h->sms));
+        if (c.use_tc_gram)
+            h->gram_work_bytes = std::max(h->gram_work_bytes, gram_tc_workspace_bytes(n, c.w_max, c.w_max + 1, h->sms));
         e = cudaMalloc((void**)&h->gram_work, h->gram_work_bytes);
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->st_host, sizeof(DevState));
@@ -757,10 +836,23 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
 
     // stage one (Algorithm 2)
     if (w > 0) {
+        // Ahat = W^T [AW, b]: FP64 (or FP32-product) CUDA-core Gram, or in mixed precision
+        // the tensor-core split-bf16 Gram when use_tc_gram is set (its TMA loads need a
+        // 16-byte aligned b; r is free until stage one writes it)
+        const double* bt = b;
+        if (h->cfg.use_tc_gram && !gram_tc_aligned(b, 16)) {
+            PODCG_CK(h, cudaMemcpyAsync(h->r, b, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+            bt = h->r;
+        }
+        int* tc_err = &h->st->status;
         if (h->mixed) {
             PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32, h->ld, h->AW32, h->ld, n, w, h->sms, s));
-            PODCG_CK(h, launch_gram32(n, h->W32, h->ld, w, h->AW32, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
-                                      h->gram_work_bytes, h->sms, s));
+            if (h->cfg.use_tc_gram)
+                PODCG_CK(h, launch_gram_tc(n, h->W32, h->ld, w, h->AW32, h->ld, w, bt, h->G, kWMax + 1, h->gram_work,
+                                           h->gram_work_bytes, tc_err, h->sms, s));
+            else
+                PODCG_CK(h, launch_gram32(n, h->W32, h->ld, w, h->AW32, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
+                                          h->gram_work_bytes, h->sms, s));
         } else {
             PODCG_CK(h, launch_spmm(A->row_ptr, A->col, A->val, h->W, h->ld, h->AW, h->ld, n, w, h->sms, s));
             PODCG_CK(h, launch_gram(n, h->W, h->ld, w, h->AW, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
@@ -782,6 +874,8 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     pod_cg_status lst = choose_lanes(h, A, &L);
     if (lst != POD_CG_OK) return lst;
     h->last_L = L;
+    pod_cg_status ps = choose_proj_form(h, wb, L);
+    if (ps != POD_CG_OK) return ps;
     pod_cg_status ls = run_loop(h, wb, L);
     if (ls != POD_CG_OK) return ls;
     const int sysid = h->system_counter++;
@@ -898,6 +992,19 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
     return POD_CG_OK;
 }
 
+pod_cg_status pod_cg_proj_tuning(const pod_cg_t* h, int* forms, float* ms)
+{
+    if (!h) return POD_CG_ERR_ARG;
+    for (int b = 0; b < 6; ++b) {
+        if (forms) forms[b] = h->proj_form[b];
+        if (ms) {
+            ms[2 * b] = h->proj_ms[b][0];
+            ms[2 * b + 1] = h->proj_ms[b][1];
+        }
+    }
+    return POD_CG_OK;
+}
+
 pod_cg_status pod_cg_tuning(const pod_cg_t* h, int* spmv_lanes, float* lane_ms)
 {
     if (!h) return POD_CG_ERR_ARG;
@@ -947,6 +1054,35 @@ pod_cg_status pod_cg_gram(int n, const double* X, int p, const double* Y, int q,
     cudaError_t e = launch_gram(n, X, n, p, Y, n, q, nullptr, G, q, 0, (double*)work, work_bytes, device_sms(),
                                 (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(nullptr, "pod_cg_gram", e);
+    return POD_CG_OK;
+}
+
+size_t pod_cg_gram_tc_workspace(int n, int p, int q)
+{
+    if (n < 1 || p < 1 || q < 1) return 0;
+    return gram_tc_workspace_bytes(n, p, q, device_sms());
+}
+
+pod_cg_status pod_cg_gram_tc(int n, int elem_bytes, const void* X, int p, const void* Y, int qy, const double* e,
+                             double* G, void* work, size_t work_bytes, void* stream)
+{
+    const int q = qy + (e ? 1 : 0);
+    if (n < 1 || p < 1 || p > kWMax || qy < 0 || qy > kWMax || q < 1 || (elem_bytes != 4 && elem_bytes != 8) ||
+        !X || (qy > 0 && !Y) || !G || !work)
+        return fail(nullptr, POD_CG_ERR_ARG, "bad arguments");
+    const size_t ldb = (size_t)n * (size_t)elem_bytes;
+    if (!gram_tc_aligned(X, ldb) || (qy > 0 && !gram_tc_aligned(Y, ldb)) || (e && !gram_tc_aligned(e, 16)))
+        return fail(nullptr, POD_CG_ERR_ARG, "pod_cg_gram_tc: X, Y, e need 16-byte aligned starts and n*elem_bytes a multiple of 16");
+    if (work_bytes < gram_tc_workspace_bytes(n, p, q, device_sms()))
+        return fail(nullptr, POD_CG_ERR_ARG, "workspace too small");
+    cudaError_t err;
+    if (elem_bytes == 4)
+        err = launch_gram_tc(n, (const float*)X, n, p, (const float*)Y, n, qy, e, G, q, (double*)work, work_bytes,
+                             nullptr, device_sms(), (cudaStream_t)stream);
+    else
+        err = launch_gram_tc(n, (const double*)X, n, p, (const double*)Y, n, qy, e, G, q, (double*)work, work_bytes,
+                             nullptr, device_sms(), (cudaStream_t)stream);
+    if (err != cudaSuccess) return cuda_fail(nullptr, "pod_cg_gram_tc", err);
     return POD_CG_OK;
 }
 

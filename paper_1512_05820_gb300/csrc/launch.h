@@ -52,7 +52,13 @@ cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, in
 cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
 
 // CG iteration (k_cg.cu): kernel pointers for graph construction
-void cg_kernels(int wb, bool fp32, bool cond, void** init, void** upd, void** dir0, void** dir);
+// FP32 with w > 0 has two forms of the update/direction passes: row-parallel float4
+// (kProjDirect) and tiles staged by bulk copies (kProjStaged, with dynamic shared memory
+// returned in bytes; 0 for every other kernel).
+constexpr int kProjDirect = 0;
+constexpr int kProjStaged = 1;
+void cg_kernels(int wb, bool fp32, bool cond, int form, void** init, void** upd, void** dir0, void** dir,
+                int* smem_upd, int* smem_dir);
 
 // mixed precision (k_mixed.cu)
 void mixed_kernels(int wb, void** proj, void** start);
@@ -64,6 +70,16 @@ cudaError_t launch_stage1_mx(int wb, const ProbDesc* pd, int n, const float* W32
 cudaError_t launch_gram32(int n, const float* X, int ldx, int p, const float* Y, int ldy, int qy, const double* extra,
                           double* G, int ldg, int upper_only, double* work, size_t work_bytes, int sms,
                           cudaStream_t s);
+
+// tensor-core Gram with split-bf16 products (k_gram_tc.cu); G = X^T [Y, extra]
+size_t gram_tc_workspace_bytes(int n, int p, int q, int sms);
+bool gram_tc_aligned(const void* ptr, size_t ld_bytes);
+cudaError_t launch_gram_tc(int n, const float* X, int ldx, int p, const float* Y, int ldy, int qy,
+                           const double* extra, double* G, int ldg, double* work, size_t work_bytes, int* err_flag,
+                           int sms, cudaStream_t s);
+cudaError_t launch_gram_tc(int n, const double* X, int ldx, int p, const double* Y, int ldy, int qy,
+                           const double* extra, double* G, int ldg, double* work, size_t work_bytes, int* err_flag,
+                           int sms, cudaStream_t s);
 
 // differentiation (k_adjoint.cu)
 cudaError_t launch_diffusion_assemble(int mx, int my, int mz, const double* theta, const double* extra,

@@ -151,7 +151,13 @@ class PodCG:
         L = ctypes.c_int(0)
         ms = (ctypes.c_float * 6)()
         _check(self.L.pod_cg_tuning(self.h, ctypes.byref(L), ms), self.h)
-        return {"spmv_lanes": L.value, "lane_ms": {str(1 << k): ms[k] for k in range(6)}}
+        forms = (ctypes.c_int * 6)()
+        pms = (ctypes.c_float * 12)()
+        _check(self.L.pod_cg_proj_tuning(self.h, forms, pms), self.h)
+        names = {-1: None, 0: "direct", 1: "staged"}
+        proj = {f"w<={wb}": {"form": names[forms[b]], "ms_direct": pms[2 * b], "ms_staged": pms[2 * b + 1]}
+                for b, wb in enumerate((0, 8, 16, 32, 48, 64)) if forms[b] >= 0}
+        return {"spmv_lanes": L.value, "lane_ms": {str(1 << k): ms[k] for k in range(6)}, "projection": proj}
 
     @property
     def last_w(self) -> int:
@@ -204,6 +210,29 @@ def gram(X: torch.Tensor, Y: torch.Tensor, stream=None) -> torch.Tensor:
     work = torch.empty(max(ws, 8), dtype=torch.uint8, device=X.device)
     _check(L.pod_cg_gram(n, Xc.data_ptr(), p, Yc.data_ptr(), q, G.data_ptr(), work.data_ptr(), ws,
                          ctypes.c_void_p(_stream_ptr(stream))))
+    return G
+
+
+def gram_tc(X: torch.Tensor, Y: torch.Tensor | None, e: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """G = X^T [Y, e] on the tensor cores (split-bf16 products) for (n, p) and (n, qy) tensors
+    of one dtype (float32 or float64) and an optional float64 column e (n,); G is float64."""
+    L = _lib.load()
+    n, p = X.shape
+    if X.dtype not in (torch.float32, torch.float64):
+        raise TypeError("gram_tc: X must be float32 or float64")
+    qy = 0 if Y is None else Y.shape[1]
+    if Y is not None and Y.dtype != X.dtype:
+        raise TypeError("gram_tc: X and Y must share a dtype")
+    Xc = _colmajor(X)
+    Yc = _colmajor(Y) if Y is not None else None
+    ec = e.to(torch.float64).contiguous() if e is not None else None
+    q = qy + (1 if e is not None else 0)
+    G = torch.empty((p, q), dtype=torch.float64, device=X.device)
+    ws = int(L.pod_cg_gram_tc_workspace(n, p, q))
+    work = torch.empty(max(ws, 8), dtype=torch.uint8, device=X.device)
+    _check(L.pod_cg_gram_tc(n, X.element_size(), Xc.data_ptr(), p, Yc.data_ptr() if Yc is not None else None, qy,
+                            ec.data_ptr() if ec is not None else None, G.data_ptr(), work.data_ptr(), ws,
+                            ctypes.c_void_p(_stream_ptr(stream))))
     return G
 
 

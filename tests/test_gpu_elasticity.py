@@ -24,8 +24,10 @@ def dev():
 
 
 def test_elasticity_small_fp64(dev):
-    """6^3 elements (n = 882), 5 systems, w <= 8."""
-    run_parity(dev, wl.elasticity_cantilever(e=6, p=5, w_max=8, s_max=8))
+    """6^3 elements (n = 882), 5 systems, w <= 8. A-norm bound 5e-9: on this operator two
+    FP64 CG runs that differ only in summation order already differ by ~1e-9 after the
+    same number of steps (pinned on the CPU in test_oracle_pins)."""
+    run_parity(dev, wl.elasticity_cantilever(e=6, p=5, w_max=8, s_max=8), tol_a=5e-9)
 
 
 @pytest.mark.parametrize("nsnap", [40, 64])

@@ -3,8 +3,13 @@
 Tolerances (FP64 mode): per system ||x - x_orc||_A / ||x_orc||_A <= 1e-10 with the same
 snapshots (the oracle's previous solutions are fed to the GPU handle, so rounding
 differences cannot compound along the sequence), iteration counts within 1 (summation
-order differs), final true residual <= tol. Step-level kernels: element-wise relative
-errors at rounding level of the contraction (bounds stated per test).
+order differs), final true residual <= tol. When the counts differ by one, the exit test
+(Eq. (sequenceInexact)) met its threshold within rounding on one side only; the GPU
+iterate is then compared with the oracle's iterate after the same number of steps (two
+FP64 CG runs that differ only in summation order stop one step apart on the elasticity
+test matrix, and their final iterates differ by one CG step, 7e-10 in the A-norm).
+Step-level kernels: element-wise relative errors at rounding level of the contraction
+(bounds stated per test).
 """
 import numpy as np
 import pytest
@@ -114,16 +119,24 @@ def run_parity(dev, seq, n_systems=None, tol_a=1e-10, **cfg):
             break
         A = (seq.row_ptr, seq.col, val)
         x, st = solver.solve(A0.with_values(to_dev(val, dev)), to_dev(b, dev), seq.tol)
+        W_j = oseq.basis()[0]
         xo, info = oseq.solve(A, b, seq.tol)
         solver.add_snapshots(to_dev(xo, dev))
         x = x.cpu().numpy()
-        err = a_err(orc, A, x, xo)
-        true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
-        out.append((j, st, info, err))
         assert st["status"] == "ok", st
         assert st["w"] == info["w"], (j, st["w"], info["w"])
-        assert err <= tol_a, f"system {j}: A-norm diff {err:.2e}"
         assert abs(st["iters"] - info["iters"]) <= 1, (j, st["iters"], info["iters"])
+        if st["iters"] != info["iters"] and st["refinements"] == 0 and info["refinements"] == 0:
+            # The exit test ||r_k|| <= tol ||b|| landed within rounding of the threshold, so
+            # one side stopped one step later; compare the iterates at the GPU's count.
+            xo_k, info_k, _, _ = orc.solve_system(A, b, W_j, 0.0, kmax=st["iters"], max_refine=0)
+            assert info_k["iters"] == st["iters"]
+            err = a_err(orc, A, x, xo_k)
+        else:
+            err = a_err(orc, A, x, xo)
+        true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
+        out.append((j, st, info, err))
+        assert err <= tol_a, f"system {j}: A-norm diff {err:.2e}"
         assert true_rel <= seq.tol and st["final_relres"] <= seq.tol
         if info["w"] > 0:
             assert abs(st["stage1_relres"] - info["stage1_relres"]) <= 1e-8 * info["stage1_relres"]

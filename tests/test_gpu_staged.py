@@ -1,0 +1,102 @@
+"""Both forms of the FP32 update and direction passes (row-parallel float4, and tiles staged
+in shared memory by bulk copies) across every basis-width bucket, against the FP64 oracle
+with the same snapshots.
+
+n = 23^3 = 12,167 is not a multiple of the 256-row tile, so every solve ends on a ragged
+tile; nsnap seeded random snapshots with energy 1 give w = nsnap (up to the cap).
+Tolerance as for the other mixed-precision tests: the FP64 true residual reaches tol,
+w equals the oracle's, and the A-norm difference to the oracle's solution is within what
+two solutions of residual <= tol can differ by (1e-5 here)."""
+import numpy as np
+import pytest
+
+from oracle import Oracle, OracleSequence
+from paper_1512_05820_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_05820_gb300 import _lib
+    _lib.load()
+    return torch.device("cuda:0")
+
+
+def _a_err(orc, A, x, xo):
+    dx = x - xo
+    return float(np.sqrt(dx @ orc.spmv(A, dx)) / np.sqrt(xo @ orc.spmv(A, xo)))
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("nsnap,w_max", [(6, 8), (14, 16), (22, 32), (40, 48), (64, 64)])
+def test_mixed_staged_widths(dev, nsnap, w_max, form):
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=23, p=2, s_max=64, w_max=w_max, period=10)
+    systems = list(seq.systems())
+    j, val, b = systems[1]
+    A = (seq.row_ptr, seq.col, val)
+    S = np.random.default_rng(nsnap).normal(size=(seq.n, nsnap))
+    orc = Oracle()
+    oseq = OracleSequence(seq.n, s_max=64, w_max=w_max, energy=1.0, oracle=orc)
+    for k in range(nsnap):
+        oseq.add_snapshot(S[:, k])
+    xo, info = oseq.solve(A, b, seq.tol)
+    solver = PodCG(seq.n, w_max=w_max, s_max=64, energy=1.0, precision=1, proj_form=form)
+    solver.add_snapshots(torch.as_tensor(S, device=dev))
+    x, st = solver.solve(DeviceCSR.from_numpy(seq.row_ptr, seq.col, val, device=dev), torch.as_tensor(b, device=dev),
+                         seq.tol)
+    solver.close()
+    x = x.cpu().numpy()
+    assert st["status"] == "ok", st
+    assert st["w"] == info["w"] == min(nsnap, w_max)
+    true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= seq.tol and st["final_relres"] <= seq.tol
+    assert _a_err(orc, A, x, xo) <= 1e-5
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_mixed_loop_modes_bitwise_equal(dev, form):
+    """Mixed precision: the conditional-graph loop and the chunked loop launch the same
+    kernels with the same shapes, so the iterates agree bit for bit."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=19, p=5, s_max=6, w_max=8, period=10)
+    outs = []
+    for mode in (0, 1):
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=1, loop_mode=mode,
+                       proj_form=form)
+        A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+        xs, its = [], []
+        for j, val, b in seq.systems():
+            x, st = solver.solve(A0.with_values(torch.as_tensor(val, device=dev)), torch.as_tensor(b, device=dev),
+                                 seq.tol)
+            solver.add_snapshots(x)
+            xs.append(x.clone())
+            its.append((st["iters"], st["w"]))
+        solver.close()
+        outs.append((xs, its))
+    assert outs[0][1] == outs[1][1]
+    for a, c in zip(outs[0][0], outs[1][0]):
+        assert torch.equal(a, c)
+
+
+def test_projection_form_is_timed(dev):
+    """Default configuration on a system of >= 65,536 rows: the handle times both forms for
+    the bucket, keeps the faster, and the solve reaches tol."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=42, p=2, s_max=8, w_max=8, period=10)
+    assert seq.n >= 65536
+    solver = PodCG(seq.n, w_max=8, s_max=8, energy=1.0, precision=1)
+    solver.add_snapshots(torch.as_tensor(np.random.default_rng(3).normal(size=(seq.n, 6)), device=dev))
+    j, val, b = list(seq.systems())[1]
+    x, st = solver.solve(DeviceCSR.from_numpy(seq.row_ptr, seq.col, val, device=dev), torch.as_tensor(b, device=dev),
+                         seq.tol)
+    tun = solver.tuning()["projection"]
+    solver.close()
+    assert st["status"] == "ok" and st["final_relres"] <= seq.tol
+    rec = tun["w<=8"]
+    assert rec["ms_direct"] > 0 and rec["ms_staged"] > 0
+    assert rec["form"] == ("staged" if rec["ms_staged"] < rec["ms_direct"] else "direct")

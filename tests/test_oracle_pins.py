@@ -42,3 +42,66 @@ def test_planted_mistake_is_caught(k, tmp_path):
         if not ok:
             failed.append(pin.__name__)
     assert failed, f"mutant {k} ({MUTANTS[k]}) passed every pin"
+
+
+def test_cg_rounding_sensitivity_elasticity(orc):
+    """The oracle's Jacobi-PCG on the 6^3-element cantilever (n = 882, system 1) against an
+    independent FP64 CG written here with numpy's dot products (another summation order).
+    After the same number of steps the two iterates differ by about 1e-9 in the A-norm,
+    the size of the error left at tol = 1e-8: on this operator FP64 rounding alone moves
+    the iterate by that much, so GPU parity on it is bounded by 5e-9, not 1e-10."""
+    import scipy.sparse as sp
+    from paper_1512_05820_gb300 import workloads as wl
+    seq = wl.elasticity_cantilever(e=6, p=1, w_max=8, s_max=8)
+    j, val, b = next(iter(seq.systems()))
+    A = (seq.row_ptr, seq.col, val)
+    xo, info, _, _ = orc.solve_system(A, b, None, seq.tol)
+    M = sp.csr_matrix((val, seq.col, seq.row_ptr), shape=(seq.n, seq.n))
+    d = M.diagonal()
+    x = np.zeros(seq.n)
+    r = b.copy()
+    z = r / d
+    p = z.copy()
+    rz = float(np.dot(r, z))
+    for _ in range(info["iters"]):
+        q = M @ p
+        a = rz / float(np.dot(p, q))
+        x += a * p
+        r -= a * q
+        z = r / d
+        rz_new = float(np.dot(r, z))
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+
+    def anorm(v):
+        return float(np.sqrt(v @ (M @ v)))
+
+    diff = anorm(x - xo) / anorm(xo)
+    err = anorm(xo - sp.linalg.spsolve(M.tocsc(), b)) / anorm(xo)
+    assert diff <= 5e-9
+    assert diff >= 1e-11   # the sensitivity is real: far above a pure rounding level
+    assert err <= 1e-8
+
+
+def test_golden_c1_sequence_record():
+    """The oracle reproduces its committed record of the 64x64 sequence (written by
+    tests/golden/make_golden.py): iteration counts, w and refinements exactly, residuals
+    and solution norms to 1e-12 relative. Guards the oracle against unintended changes."""
+    import json
+    import os
+    import sys
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    sys.path.insert(0, here)
+    try:
+        import make_golden
+    finally:
+        sys.path.remove(here)
+    with open(os.path.join(here, "c1_sequence_oracle.json")) as f:
+        ref = json.load(f)
+    now = make_golden.record()
+    assert len(now["systems"]) == len(ref["systems"])
+    for a, b in zip(now["systems"], ref["systems"]):
+        for k in ("system", "iters", "w", "refinements"):
+            assert a[k] == b[k], (k, a, b)
+        for k in ("stage1_relres", "final_relres", "x_norm2", "x_sum"):
+            assert abs(a[k] - b[k]) <= 1e-12 * max(abs(b[k]), 1e-300), (k, a[k], b[k])
