@@ -85,6 +85,7 @@ class Oracle:
         self.lib = lib
         vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
         lib.orc_spmv.argtypes = [ci, vp, vp, vp, vp, vp]
+        lib.orc_theta_grad.argtypes = [ci, ci, ci, vp, ci, vp, vp, vp]
         lib.orc_dot.argtypes = [ci, vp, vp]
         lib.orc_dot.restype = cd
         lib.orc_gram.argtypes = [ci, ci, vp, ci, vp, vp]
@@ -200,6 +201,18 @@ class Oracle:
         k = ctypes.c_int(0)
         st = self.lib.orc_pcg(n, _p(rp), _p(col), _p(val), _p(b), _p(x0), tol_abs, kmax, _p(x), ctypes.byref(k))
         return x, k.value, st
+
+    def theta_grad(self, shape, theta, lam, xs):
+        """dL/dtheta = -sum_j lambda_j^T (dA_j/dtheta) x_j for the diffusion operator on a grid
+        of shape (my, mx) or (mz, my, mx); lam and xs are (nsys, n)."""
+        sh = tuple(shape) if len(shape) == 3 else (1,) + tuple(shape)
+        mz, my, mx = sh
+        lam = np.ascontiguousarray(np.atleast_2d(lam), dtype=np.float64)
+        xs = np.ascontiguousarray(np.atleast_2d(xs), dtype=np.float64)
+        theta = _f64(theta)
+        g = np.empty(mx * my * mz)
+        self.lib.orc_theta_grad(mx, my, mz, _p(theta), lam.shape[0], _p(lam), _p(xs), _p(g))
+        return g
 
     def solve_system(self, A, b, W, tol_rel, kmax=100000, max_refine=5, p_cap=0):
         rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])

@@ -468,3 +468,54 @@ int orc_solve_system(int n, const int* rp, const int* ci, const double* va, cons
     free(what); free(R);
     return st;
 }
+
+/* Gradient of L(theta) = sum_j c^T x_j through A_j(theta) x_j = b_j (the differentiated
+ * sequence): with adjoints lambda_j = A_j^{-1} c (A_j symmetric),
+ *   dL/dtheta_c = - sum_j lambda_j^T (dA_j/dtheta_c) x_j.
+ * A_j(theta) is the cell-centred diffusion operator on an mx x my x mz grid (x fastest;
+ * mz == 1 is the 2D five-point operator with no z faces) with k = exp(theta), interior
+ * face conductance k_f = 2 k_a k_b / (k_a + k_b) and Dirichlet boundary faces of
+ * conductance 2 k_a, plus a theta-independent diagonal shift. A face between cells a and b
+ * adds k_f (v_a - v_b)(u_a - u_b) to v^T A u, a boundary face of cell a adds 2 k_a v_a u_a,
+ * so, differentiating each face term by the chain rule (dk/dtheta = k):
+ *   interior face:  d k_f / d theta_a = k_f k_b / (k_a + k_b)
+ *   boundary face:  d (2 k_a) / d theta_a = 2 k_a.
+ * lam and xs hold nsys vectors of length n back to back; grad (length n) is overwritten.
+ * Written face by face from that definition, one system at a time. */
+void orc_theta_grad(int mx, int my, int mz, const double* theta, int nsys, const double* lam, const double* xs,
+                    double* grad)
+{
+    const int n = mx * my * mz;
+    const int dims = mz > 1 ? 3 : 2;
+    for (int c = 0; c < n; ++c) grad[c] = 0.0;
+    for (int j = 0; j < nsys; ++j) {
+        const double* l = lam + (size_t)j * n;
+        const double* x = xs + (size_t)j * n;
+        for (int iz = 0; iz < mz; ++iz)
+            for (int iy = 0; iy < my; ++iy)
+                for (int ix = 0; ix < mx; ++ix) {
+                    const int a = ix + mx * (iy + my * iz);
+                    const double ka = exp(theta[a]);
+                    /* the six (or four) faces of cell a: -x, +x, -y, +y, -z, +z */
+                    for (int f = 0; f < 2 * dims; ++f) {
+                        int jx = ix, jy = iy, jz = iz;
+                        if (f == 0) jx = ix - 1;
+                        if (f == 1) jx = ix + 1;
+                        if (f == 2) jy = iy - 1;
+                        if (f == 3) jy = iy + 1;
+                        if (f == 4) jz = iz - 1;
+                        if (f == 5) jz = iz + 1;
+                        const int inside = jx >= 0 && jx < mx && jy >= 0 && jy < my && jz >= 0 && jz < mz;
+                        if (inside) {
+                            const int b = jx + mx * (jy + my * jz);
+                            const double kb = exp(theta[b]);
+                            const double kf = 2.0 * ka * kb / (ka + kb);
+                            const double dkf = kf * (MUT(11) ? ka : kb) / (ka + kb);
+                            grad[a] -= dkf * (l[a] - l[b]) * (x[a] - x[b]);
+                        } else {
+                            grad[a] -= 2.0 * ka * l[a] * x[a];
+                        }
+                    }
+                }
+    }
+}

@@ -105,3 +105,24 @@ def test_gradient_vs_central_differences(dev):
         e[cc] = h
         fd = (-L(theta + 2 * e) + 8 * L(theta + e) - 8 * L(theta - e) + L(theta - 2 * e)) / (12 * h)
         assert abs(fd - g_theta[cc]) <= 1e-6 * max(abs(g_theta[cc]), 1e-3 * scale), (cc, fd, g_theta[cc])
+
+
+@pytest.mark.parametrize("shape", [(11, 13, 17), (29, 31), (1, 1), (3, 1, 2)])
+def test_theta_grad_kernel_vs_oracle(dev, orc, shape):
+    """The fused edge-wise dL/dtheta kernel against the oracle's face-by-face formula on the
+    same random theta, lambda, x (3 systems): element-wise to 1e-13 of a bound on the sum of
+    the absolute face terms of a cell."""
+    from paper_1512_05820_gb300.adjoint import DiffusionProblem, theta_grad
+    op = wl.DiffusionOperator(shape)
+    rng = np.random.default_rng(op.n + 3)
+    theta = rng.normal(0, 0.5, op.n)
+    lam = rng.normal(size=(3, op.n))
+    xs = rng.normal(size=(3, op.n))
+    prob = DiffusionProblem.from_operator(op, device=dev)
+    g = theta_grad(prob, torch.as_tensor(theta, device=dev), torch.as_tensor(lam, device=dev),
+                   torch.as_tensor(xs, device=dev)).cpu().numpy()
+    ref = orc.theta_grad(op.shape3, theta, lam, xs)
+    # a bound free of cancellation: each of the <= 6 faces of 3 systems contributes at most
+    # 2 k_max * 2|lam|_max * 2|x|_max in magnitude
+    bound = 1e-13 * (6 * 3 * 8 * np.exp(np.abs(theta)).max() * np.abs(lam).max() * np.abs(xs).max())
+    assert np.max(np.abs(g - ref)) <= bound, np.max(np.abs(g - ref))
