@@ -73,20 +73,96 @@ __device__ __forceinline__ T warp_sum(T v)
 }
 
 // Stride between the partials of two values: partials are stored value-major
-// (partials[v * kPartialStride + block]) so the last block reads them coalesced.
-constexpr int kPartialStride = 4096;   // >= any grid of a reducing kernel
+// (partials[v * kPartialStride + block], then the group partials at G + g).
+constexpr int kPartialStride = 4096;   // >= any grid of a reducing kernel + kRedGroups
+
+// Counters of one reduction site: kRedGroups first-level group tickets, then the top ticket.
+constexpr int kRedGroups = 16;
+constexpr int kCounterStride = 32;
+
+// s_out[v] = sum of partials[v][first + i * step] over i < count, for v < nv: warp wid takes
+// values wid, wid + kWarps, ...; lanes take rows i = lane, lane + 32, ... (fixed order per
+// value: lane strides, then the warp's shuffle tree), with every value's loads in one pass.
+__device__ __forceinline__ void sum_rows(const double* __restrict__ partials, int nv, int first, int step, int count,
+                                         double* s_out)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int kR = (kWMax + 2 + kWarps - 1) / kWarps;
+    double t[kR];
+#pragma unroll
+    for (int k = 0; k < kR; ++k) t[k] = 0.0;
+    for (int i = lane; i < count; i += 32) {
+        const int b = first + i * step;
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            const int v = wid + kWarps * k;
+            if (v < nv) t[k] += __ldcg(partials + (size_t)v * kPartialStride + b);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+        const int v = wid + kWarps * k;
+        if (v < nv) {   // uniform per warp
+            const double a = warp_sum(t[k]);
+            if (lane == 0) s_out[v] = a;
+        }
+    }
+}
+
+// Tail of a deterministic grid reduction, called by every block after thread 0 has published
+// (and fenced) the block's nv partials at partials[v][blockIdx.x]. Two levels, so no block
+// walks all G partials: block b belongs to group b mod NG (NG = min(G, kRedGroups)); the last
+// block of each group to arrive sums its group's partials and publishes them at
+// partials[v][G + g]; the last group to finish sums the NG group partials into s_tot[0..nv)
+// and returns true (every other block returns false). Fixed summation order throughout, so
+// results repeat bit for bit for a given grid. Needs G + kRedGroups <= kPartialStride and
+// counter[0..kRedGroups] zero on entry (each level resets its own counters).
+__device__ __forceinline__ bool grid_tail(double* __restrict__ partials, int nv, unsigned int* counter, double* s_tot)
+{
+    __shared__ int s_role;
+    __shared__ double s_grp[kWMax + 2];
+    const int G = gridDim.x;
+    const int NG = G < kRedGroups ? G : kRedGroups;
+    const int g = blockIdx.x % NG;
+    const int members = (G - g + NG - 1) / NG;
+    if (threadIdx.x == 0) {
+        const unsigned int t = atomicAdd(counter + g, 1u);
+        s_role = (t == (unsigned int)members - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_role == 0) return false;
+    __threadfence();
+    sum_rows(partials, nv, g, NG, members, s_grp);
+    __syncthreads();
+    if ((int)threadIdx.x < nv) {
+        partials[(size_t)threadIdx.x * kPartialStride + G + g] = s_grp[threadIdx.x];
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        counter[g] = 0u;   // every member of the group has taken its ticket
+        const unsigned int t = atomicAdd(counter + kRedGroups, 1u);
+        s_role = (t == (unsigned int)NG - 1) ? 2 : 0;
+    }
+    __syncthreads();
+    if (s_role != 2) return false;
+    __threadfence();
+    sum_rows(partials, nv, G, 1, NG, s_tot);
+    __syncthreads();
+    if (threadIdx.x == 0) counter[kRedGroups] = 0u;
+    return true;
+}
 
 // Block-reduce acc[0..nv) (nv uniform over the grid, nv <= NV), store one partial per
-// block, and return true in the last block to finish, which then holds the grid totals
-// in s_tot[0..nv). Every thread of every block must call this exactly once per launch.
-// `counter` must be 0 on entry; the last block resets it.
+// block, and return true in exactly one block, which then holds the grid totals in
+// s_tot[0..nv) (grid_tail). Every thread of every block must call this exactly once per
+// launch; `counter` points at the site's kCounterStride counters, zero on entry.
 template <int NV>
 __device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], int nv,
                                                      double* __restrict__ partials,
                                                      unsigned int* counter, double* s_tot)
 {
     __shared__ double s_w[kWarps][NV];
-    __shared__ bool s_last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -104,30 +180,8 @@ __device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], in
             partials[(size_t)v * kPartialStride + blockIdx.x] = t;
         }
         __threadfence();
-        unsigned int ticket = atomicAdd(counter, 1u);
-        s_last = (ticket == gridDim.x - 1);
     }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    const int G = gridDim.x;
-    for (int v = wid; v < nv; v += kWarps) {
-        const double* pv = partials + (size_t)v * kPartialStride;
-        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-        int b = lane;
-        for (; b + 96 < G; b += 128) {
-            t0 += __ldcg(pv + b);
-            t1 += __ldcg(pv + b + 32);
-            t2 += __ldcg(pv + b + 64);
-            t3 += __ldcg(pv + b + 96);
-        }
-        for (; b < G; b += 32) t0 += __ldcg(pv + b);
-        double t = warp_sum((t0 + t1) + (t2 + t3));
-        if (lane == 0) s_tot[v] = t;
-    }
-    if (threadIdx.x == 0) *counter = 0u;
-    __syncthreads();
-    return true;
+    return grid_tail(partials, nv, counter, s_tot);
 }
 
 // Publish block totals s_blk[0..nv) (shared memory, complete before the call) as this
@@ -136,37 +190,13 @@ __device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], in
 __device__ __forceinline__ bool partials_to_last_block(const double* s_blk, int nv, double* __restrict__ partials,
                                                        unsigned int* counter, double* s_tot)
 {
-    __shared__ bool s_last;
-    // one thread publishes the block's partials, fences and takes the ticket: the other
-    // threads never wait on a memory fence
+    // one thread publishes the block's partials and fences: the other threads never wait on
+    // a memory fence
     if (threadIdx.x == 0) {
         for (int v = 0; v < nv; ++v) partials[(size_t)v * kPartialStride + blockIdx.x] = s_blk[v];
         __threadfence();
-        unsigned int ticket = atomicAdd(counter, 1u);
-        s_last = (ticket == gridDim.x - 1);
     }
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int G = gridDim.x;
-    for (int v = wid; v < nv; v += kWarps) {
-        const double* pv = partials + (size_t)v * kPartialStride;
-        double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
-        int b = lane;
-        for (; b + 96 < G; b += 128) {
-            t0 += __ldcg(pv + b);
-            t1 += __ldcg(pv + b + 32);
-            t2 += __ldcg(pv + b + 64);
-            t3 += __ldcg(pv + b + 96);
-        }
-        for (; b < G; b += 32) t0 += __ldcg(pv + b);
-        const double t = warp_sum((t0 + t1) + (t2 + t3));
-        if (lane == 0) s_tot[v] = t;
-    }
-    if (threadIdx.x == 0) *counter = 0u;
-    __syncthreads();
-    return true;
+    return grid_tail(partials, nv, counter, s_tot);
 }
 
 // Column-parallel accumulation of c_j += sum_rows col_j[row] * s_z[row - row0] over one

@@ -167,7 +167,7 @@ struct pod_cg_t {
 
     // reductions
     double* partials = nullptr;
-    unsigned int* counters = nullptr;   // 16 counters
+    unsigned int* counters = nullptr;   // 8 reduction sites x kCounterStride
     double* gram_work = nullptr;
     size_t gram_work_bytes = 0;
 
@@ -349,7 +349,7 @@ int occ_grid(pod_cg_t* h, const void* f, int rows, int rows_per_block, int smem 
     long long need = ((long long)rows + rows_per_block - 1) / rows_per_block;
     long long cap = (long long)h->sms * nb;
     long long g = std::min(need, cap);
-    g = std::min<long long>(g, kPartialStride);
+    g = std::min<long long>(g, kPartialStride - kRedGroups);
     return (int)std::max<long long>(g, 1);
 }
 
@@ -374,16 +374,16 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
     const DevState* cst = h->st;
     const double* Rinv = h->Rinv;
     const double inner_tol = h->cfg.inner_tol;
-    P.res.set(f_res, g_res, pd, (const double*)h->x, h->r, h->partials, c + 1, st, (int)mixed, inner_tol, h_outer,
+    P.res.set(f_res, g_res, pd, (const double*)h->x, h->r, h->partials, c + 1 * kCounterStride, st, (int)mixed, inner_tol, h_outer,
               use_cond);
     if (!mixed) {
         P.init.set(f_init, g_init, n, ld, (const double*)h->r, (const double*)h->dinv, (const double*)h->AW,
-                   h->partials, c + 0, st, h_inner, use_cond);
+                   h->partials, c + 0 * kCounterStride, st, h_inner, use_cond);
         P.dir0.set(f_dir0, g_dir, n, ld, h->x, h->p, (const double*)h->r, (const double*)h->dinv,
                    (const double*)h->W, Rinv, cst);
-        P.spmv.set(f_spmv, g_spmv, pd, (const double*)h->p, h->q, h->partials, c + 2, st);
+        P.spmv.set(f_spmv, g_spmv, pd, (const double*)h->p, h->q, h->partials, c + 2 * kCounterStride, st);
         P.upd.set(f_upd, g_upd, n, ld, h->r, (const double*)h->q, (const double*)h->dinv, (const double*)h->AW,
-                  h->partials, c + 3, st, h_inner, use_cond);
+                  h->partials, c + 3 * kCounterStride, st, h_inner, use_cond);
         P.dir.set(f_dir, g_dir, n, ld, h->x, h->p, (const double*)h->r, (const double*)h->dinv,
                   (const double*)h->W, Rinv, cst);
     } else {
@@ -391,16 +391,16 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
         mixed_kernels(wb, &f_proj, &f_start);
         void* f_acc = kernel_mx_accum();
         P.mxproj.set(f_proj, occ_grid(h, f_proj, n, kBlock), n, ld, (const double*)h->r, h->r32,
-                     (const float*)h->W32, h->partials, c + 5, st);
+                     (const float*)h->W32, h->partials, c + 5 * kCounterStride, st);
         P.mxstart.set(f_start, occ_grid(h, f_start, n, kBlock), n, ld, h->d32, h->r32, (const float*)h->W32,
                       (const float*)h->AW32, Rinv, cst);
         P.init.set(f_init, g_init, n, ld, (const float*)h->r32, (const float*)h->dinv32, (const float*)h->AW32,
-                   h->partials, c + 0, st, h_inner, use_cond);
+                   h->partials, c + 0 * kCounterStride, st, h_inner, use_cond);
         P.dir0.set(f_dir0, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
                    (const float*)h->W32, Rinv, cst);
-        P.spmv.set(f_spmv, g_spmv, pd, (const float*)h->p32, h->q32, h->partials, c + 2, st);
+        P.spmv.set(f_spmv, g_spmv, pd, (const float*)h->p32, h->q32, h->partials, c + 2 * kCounterStride, st);
         P.upd.set(f_upd, g_upd, n, ld, h->r32, (const float*)h->q32, (const float*)h->dinv32,
-                  (const float*)h->AW32, h->partials, c + 3, st, h_inner, use_cond);
+                  (const float*)h->AW32, h->partials, c + 3 * kCounterStride, st, h_inner, use_cond);
         P.dir.set(f_dir, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
                   (const float*)h->W32, Rinv, cst);
         P.mxaccum.set(f_acc, occ_grid(h, f_acc, n, kBlock), n, h->x, (const float*)h->d32, cst);
@@ -694,7 +694,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     PODCG_ALLOC(h->dinv, ld)
     PODCG_ALLOC(h->dinv32, ld)
     PODCG_ALLOC(h->partials, (size_t)(kWMax + 2) * kPartialStride)
-    PODCG_ALLOC(h->counters, 16)
+    PODCG_ALLOC(h->counters, (size_t)8 * kCounterStride)
     PODCG_ALLOC(h->st, 1)
     PODCG_ALLOC(h->st_save, 1)
     PODCG_ALLOC(h->pd, 1)
@@ -726,7 +726,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->pd_host, sizeof(ProbDesc));
     for (auto& ev : h->ev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->counters, 0, 16 * sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->counters, 0, (size_t)8 * kCounterStride * sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->S, 0, sizeof(double) * ld * c.s_max, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->GS, 0, sizeof(double) * kSMax * kSMax, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->p, 0, sizeof(double) * ld, h->stream);
@@ -863,9 +863,9 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     }
     const int wb = wb_bucket(w);
     if (h->mixed)
-        PODCG_CK(h, launch_stage1_mx(wb, h->pd, n, h->W32, h->x, h->partials, h->counters + 4, h->st, tol, h->sms, s));
+        PODCG_CK(h, launch_stage1_mx(wb, h->pd, n, h->W32, h->x, h->partials, h->counters + 4 * kCounterStride, h->st, tol, h->sms, s));
     else
-        PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4, h->st, tol,
+        PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4 * kCounterStride, h->st, tol,
                                   h->sms, s));
     PODCG_CK(h, cudaEventRecord(h->ev[2], s));
 
@@ -941,7 +941,7 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
         launches += 3;
     }
     const int wb = wb_bucket(w);
-    PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4, h->st, tol,
+    PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4 * kCounterStride, h->st, tol,
                               h->sms, s));
     PODCG_CK(h, cudaEventRecord(h->ev[2], s));
     int L = 1;

@@ -114,21 +114,28 @@ __device__ __forceinline__ void update_finish(const double* s_blk, int w, double
     if (partials_to_last_block(s_blk, 2 + w, partials, counter, tot)) {
         for (int a = threadIdx.x; a < w; a += blockDim.x) st->c[a] = tot[2 + a];
         if (threadIdx.x == 0) {
+            // read every state field first (independent loads, one round of latency)
+            const double rho_old = st->rho, tol2_in = st->tol2_in;
+            const int iters = st->iters + 1, inner_iters = st->inner_iters + 1, k_max = st->k_max;
+            int status = st->status, inner_break = st->inner_break;
+            const int mixed = st->mixed;
             const double rho_new = tot[0];
-            st->beta = rho_new / st->rho;
-            st->rho = rho_new;
-            st->rr = tot[1];
-            st->iters += 1;
-            st->inner_iters += 1;
-            if (st->status == 0 && !(isfinite(rho_new) && isfinite(tot[1]))) {
-                if (st->mixed) st->inner_break = 1;
-                else st->status = 5;
+            if (status == 0 && !(isfinite(rho_new) && isfinite(tot[1]))) {
+                if (mixed) inner_break = 1;
+                else status = 5;
             }
-            int done = (st->status != 0) || st->inner_break || !(tot[1] > st->tol2_in);
-            if (!done && st->iters >= st->k_max) {
-                st->status = 4;
+            int done = (status != 0) || inner_break || !(tot[1] > tol2_in);
+            if (!done && iters >= k_max) {
+                status = 4;
                 done = 1;
             }
+            st->beta = rho_new / rho_old;
+            st->rho = rho_new;
+            st->rr = tot[1];
+            st->iters = iters;
+            st->inner_iters = inner_iters;
+            st->status = status;
+            st->inner_break = inner_break;
             st->done = done;
             st->dir_pending = 1;
             if constexpr (COND) {

@@ -100,14 +100,20 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
     double acc[1] = {double(dot)};
     __shared__ double tot[1];
     if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) {
+        // read the state fields first (independent loads, one round of latency)
+        int status = st->status, inner_break = st->inner_break;
+        const int mixed = st->mixed;
+        const double rho = st->rho;
         const double gamma = tot[0];
-        st->gamma = gamma;
         const bool bad = !isfinite(gamma) || !(gamma > 0.0);
-        if (bad && st->status == 0) {
-            if (st->mixed) st->inner_break = 1;          // FP32 inner pass ends; FP64 outer goes on
-            else st->status = !isfinite(gamma) ? 5 : 3;
+        if (bad && status == 0) {
+            if (mixed) inner_break = 1;          // FP32 inner pass ends; FP64 outer goes on
+            else status = !isfinite(gamma) ? 5 : 3;
         }
-        st->alpha = (st->status == 0 && !st->inner_break) ? st->rho / gamma : 0.0;
+        st->gamma = gamma;
+        st->status = status;
+        st->inner_break = inner_break;
+        st->alpha = (status == 0 && !inner_break) ? rho / gamma : 0.0;
     }
 }
 
