@@ -61,6 +61,9 @@ def parse_args():
     ap.add_argument("--proj-form", choices=["auto", "direct", "staged"], default="auto",
                     help="FP32 update/direction form: timed per width bucket (auto), row-parallel float4, "
                          "or tiles staged by bulk copies")
+    ap.add_argument("--spmv-lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
+                    help="CSR SpMV lanes per row (0: timed by the handle); profiling commands force the "
+                         "timed choice so the profiled kernels are the ones the bench times")
     ap.add_argument("--batch-seqs", type=int, default=256)
     ap.add_argument("--loop-mode", choices=["graph", "chunked"], default="graph",
                     help="graph: conditional CUDA graph; chunked: plain graphs of 16 iterations (profilable)")
@@ -321,7 +324,8 @@ def kernel_profile(args):
     j, val, b = next(iter(seq.systems()))
     prec = 1 if args.precision == "mixed" else 0
     solver = PodCG(seq.n, w_max=32, s_max=40, energy=0.9999, precision=prec, k_max=5, max_refine=0,
-                   loop_mode=1, proj_form={"auto": -1, "direct": 0, "staged": 1}[args.proj_form])
+                   loop_mode=1, proj_form={"auto": -1, "direct": 0, "staged": 1}[args.proj_form],
+                   spmv_lanes=args.spmv_lanes)
     snaps = torch.as_tensor(np.random.default_rng(7).normal(size=(seq.n, args.kernel_profile)), device="cuda")
     solver.add_snapshots(snaps)
     A = DeviceCSR.from_numpy(seq.row_ptr, seq.col, val)
@@ -527,7 +531,8 @@ def main():
     dseq = DeviceSequence(seq, systems=systems)
     xs = [torch.empty(seq.n, dtype=torch.float64, device="cuda") for _ in range(dseq.p)]
     loop_mode = 0 if args.loop_mode == "graph" else 1
-    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec, loop_mode=loop_mode)
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec, loop_mode=loop_mode,
+                   proj_form={"auto": -1, "direct": 0, "staged": 1}[args.proj_form], spmv_lanes=args.spmv_lanes)
     stream = solver.stream
 
     def barrier():

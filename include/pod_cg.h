@@ -82,6 +82,9 @@ typedef struct {
                             width bucket on the handle's first system of >= 65,536 rows in
                             it (else row-parallel); 0 = row-parallel float4; 1 = tiles staged
                             in shared memory by bulk copies (see pod_cg_proj_tuning) */
+    int    spmv_lanes;   /* CSR SpMV lanes per row: 0 = timed once per sparsity pattern
+                            (systems of >= 65,536 rows; the pattern's heuristic width is kept
+                            unless another is >= 10% faster); 1, 2, 4, 8, 16 or 32 = forced */
 } pod_cg_config;
 
 /* CSR matrix, device arrays, borrowed. */
@@ -118,7 +121,7 @@ typedef struct {
 
 /* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
  * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
- * loop_mode 0, proj_form -1. */
+ * loop_mode 0, proj_form -1, spmv_lanes 0. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 
 /* Create a solver for systems of order n (the problem statement of Section 2) whose work

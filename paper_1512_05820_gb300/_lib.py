@@ -24,7 +24,7 @@ class Config(ctypes.Structure):
                 ("rank_tol", ctypes.c_double), ("k_max", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("use_tc_gram", ctypes.c_int),
                 ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int), ("loop_mode", ctypes.c_int),
-                ("proj_form", ctypes.c_int)]
+                ("proj_form", ctypes.c_int), ("spmv_lanes", ctypes.c_int)]
 
 
 class CSRStruct(ctypes.Structure):

@@ -254,9 +254,13 @@ pod_cg_status choose_lanes(pod_cg_t* h, const pod_cg_csr* A, int* L_out)
         }
     const double mean = A->n > 0 ? double(A->nnz) / A->n : 1.0;
     pod_cg_t::LaneChoice ch{A->row_ptr, A->n, A->nnz, h->mixed, spmv_lanes_for(mean), {0, 0, 0, 0, 0, 0}};
-    if (A->n >= 65536) {
+    if (h->cfg.spmv_lanes > 0) {
+        ch.L = h->cfg.spmv_lanes;
+    } else if (A->n >= 65536) {
         const int cands[6] = {1, 2, 4, 8, 16, 32};
-        float best = -1.0f;
+        const int heur = ch.L;
+        float best = -1.0f, t_heur = -1.0f;
+        int best_L = heur;
         for (int k = 0; k < 6; ++k) {
             const int L = cands[k];
             if (L > 4 * mean + 4 || L * 16 < mean) { ch.ms[k] = -1.0f; continue; }
@@ -275,8 +279,12 @@ pod_cg_status choose_lanes(pod_cg_t* h, const pod_cg_csr* A, int* L_out)
                 if (rep > 0) tot += ms;
             }
             ch.ms[k] = tot / 3.0f;
-            if (best < 0.0f || ch.ms[k] < best) { best = ch.ms[k]; ch.L = L; }
+            if (L == heur) t_heur = ch.ms[k];
+            if (best < 0.0f || ch.ms[k] < best) { best = ch.ms[k]; best_L = L; }
         }
+        // keep the heuristic width unless another is clearly (>= 10%) faster: one noisy
+        // timing must not switch the kernel
+        ch.L = (t_heur > 0.0f && best >= 0.9f * t_heur) ? heur : best_L;
     }
     h->lanes.push_back(ch);
     *L_out = ch.L;
@@ -619,6 +627,7 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->keep_factors = 0;
     c->loop_mode = 0;
     c->proj_form = -1;
+    c->spmv_lanes = 0;
     return POD_CG_OK;
 }
 
@@ -657,6 +666,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
         c.k_max < 0 || c.max_refine < 0 || (c.precision != POD_CG_FP64 && c.precision != POD_CG_MIXED) ||
         c.keep_factors < 0 || c.keep_factors > 4096 || (c.loop_mode != 0 && c.loop_mode != 1) ||
         c.proj_form < -1 || c.proj_form > 1 ||
+        (c.spmv_lanes != 0 && (c.spmv_lanes < 1 || c.spmv_lanes > 32 || (c.spmv_lanes & (c.spmv_lanes - 1)))) ||
         !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
         return fail(nullptr, POD_CG_ERR_ARG, "invalid configuration");
     if (c.use_tc_gram != 0 && (c.use_tc_gram != 1 || c.precision != POD_CG_MIXED))

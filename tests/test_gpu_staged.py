@@ -100,3 +100,21 @@ def test_projection_form_is_timed(dev):
     rec = tun["w<=8"]
     assert rec["ms_direct"] > 0 and rec["ms_staged"] > 0
     assert rec["form"] == ("staged" if rec["ms_staged"] < rec["ms_direct"] else "direct")
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+def test_forced_spmv_lanes(dev, lanes):
+    """A forced CSR SpMV width is used as given (FP64 and mixed) and the solves still reach
+    tol with the oracle's basis width."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=20, p=3, s_max=4, w_max=8, period=10)
+    for prec in (0, 1):
+        solver = PodCG(seq.n, w_max=8, s_max=4, energy=seq.energy, precision=prec, spmv_lanes=lanes)
+        A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+        for j, val, b in seq.systems():
+            x, st = solver.solve(A0.with_values(torch.as_tensor(val, device=dev)), torch.as_tensor(b, device=dev),
+                                 seq.tol)
+            assert st["status"] == "ok" and st["final_relres"] <= seq.tol
+            solver.add_snapshots(x)
+        assert solver.tuning()["spmv_lanes"] == lanes
+        solver.close()
