@@ -58,6 +58,9 @@ def parse_args():
                     help="profiling target: the tensor-core Gram W^T [AW, b] at n = 2,097,152, w = 22 (FP32 "
                          "inputs), launched --kernel-reps times")
     ap.add_argument("--no-gram", action="store_true", help="skip the stage-one Gram measurement")
+    ap.add_argument("--elasticity", type=int, default=0, metavar="K",
+                    help="the 64^3-element cantilever, first K systems: POD-aug (mixed; tensor-core and "
+                         "CUDA-core stage-one Gram) against plain Jacobi CG (mixed), one JSON line")
     ap.add_argument("--proj-form", choices=["auto", "direct", "staged"], default="auto",
                     help="FP32 update/direction form: timed per width bucket (auto), row-parallel float4, "
                          "or tiles staged by bulk copies")
@@ -425,6 +428,50 @@ def gram_section(args):
     return out
 
 
+def elasticity_bench(args):
+    """The 64^3-element cantilever of trilinear hexahedra (n = 811,200, ~78.5 nonzeros per
+    row, w <= 48), its first K systems (seeded, generated on the host): POD-augmented CG in
+    mixed precision with the tensor-core split-bf16 stage-one Gram and with the CUDA-core
+    FP32 Gram, against plain Jacobi CG in mixed precision, each timed over the K systems
+    (CUDA events) after one untimed pass. Prints one JSON line."""
+    import torch
+    from paper_1512_05820_gb300 import workloads as wl
+    from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
+    from paper_1512_05820_gb300.solver import PodCG
+    K = args.elasticity
+    seq = wl.elasticity_cantilever(e=64, p=K)
+    t0 = time.perf_counter()
+    systems = seq.all_systems()
+    gen_s = time.perf_counter() - t0
+    dseq = DeviceSequence(seq, systems=systems)
+    xs = [torch.empty(seq.n, dtype=torch.float64, device="cuda") for _ in range(K)]
+
+    def one(recycle, tc):
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=1, use_tc_gram=tc,
+                       spmv_lanes=args.spmv_lanes)
+        run_sequence(solver, dseq, xs, recycle=recycle)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(solver.stream)
+        st = run_sequence(solver, dseq, xs, recycle=recycle)
+        b.record(solver.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        tun = solver.tuning()
+        solver.close()
+        return {"systems_per_s": K / (ms / 1e3), "ms": ms, "iters": [s["iters"] for s in st],
+                "w": [s["w"] for s in st], "stage1_relres": [s["stage1_relres"] for s in st],
+                "ms_stage1_mean": float(np.mean([s["ms_stage1"] for s in st])),
+                "max_final_relres": max(s["final_relres"] for s in st), "spmv_lanes": tun["spmv_lanes"]}
+
+    out = {"elasticity": True, "workload": f"elasticity_cantilever 64^3 elements, first {K} systems",
+           "n": seq.n, "nnz": seq.nnz, "w_max": seq.w_max, "tol": seq.tol, "generation_s": gen_s,
+           "pod_aug_tc_gram": one(True, 1), "pod_aug_cuda_core_gram": one(True, 0), "plain_cg": one(False, 0)}
+    out["speedup_pod_aug_vs_plain"] = out["pod_aug_tc_gram"]["systems_per_s"] / out["plain_cg"]["systems_per_s"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def gram_profile(args):
     """A short launch sequence for kernel profilers: the tensor-core Gram of the 128^3
     stage-one shape (FP32 W and AW panels, w = 22, plus b), --kernel-reps launches."""
@@ -514,6 +561,8 @@ def main():
         return diff_check(args)
     if args.gram_profile:
         return gram_profile(args)
+    if args.elasticity:
+        return elasticity_bench(args)
 
     import torch
     from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
