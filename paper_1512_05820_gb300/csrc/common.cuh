@@ -80,30 +80,41 @@ constexpr int kPartialStride = 4096;   // >= any grid of a reducing kernel + kRe
 constexpr int kRedGroups = 16;
 constexpr int kCounterStride = 32;
 
-// s_out[v] = sum of partials[v][first + i * step] over i < count, for v < nv: warp wid takes
-// values wid, wid + kWarps, ...; lanes take rows i = lane, lane + 32, ... (fixed order per
-// value: lane strides, then the warp's shuffle tree), with every value's loads in one pass.
+// s_out[v] = sum of partials[v][first + i * step] over i < count, for v < nv <= NV: warp wid
+// takes values wid, wid + kWarps, ...; lanes take rows i = lane, lane + 32, ... with U rows
+// unrolled into independent sums, so up to 32 U rows cost one round of latency (partials
+// written by other SMs a moment earlier take microseconds to read). Fixed order per value:
+// lane strides, the U sums in order, then the warp's shuffle tree.
+template <int NV, int U>
 __device__ __forceinline__ void sum_rows(const double* __restrict__ partials, int nv, int first, int step, int count,
                                          double* s_out)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int kR = (kWMax + 2 + kWarps - 1) / kWarps;
-    double t[kR];
+    constexpr int kR = (NV + kWarps - 1) / kWarps;
+    double t[kR][U];
 #pragma unroll
-    for (int k = 0; k < kR; ++k) t[k] = 0.0;
-    for (int i = lane; i < count; i += 32) {
-        const int b = first + i * step;
+    for (int k = 0; k < kR; ++k)
+#pragma unroll
+        for (int u = 0; u < U; ++u) t[k][u] = 0.0;
+    for (int i0 = lane; i0 < count; i0 += 32 * U) {
 #pragma unroll
         for (int k = 0; k < kR; ++k) {
             const int v = wid + kWarps * k;
-            if (v < nv) t[k] += __ldcg(partials + (size_t)v * kPartialStride + b);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + 32 * u;
+                if (v < nv && i < count) t[k][u] += __ldcg(partials + (size_t)v * kPartialStride + first + i * step);
+            }
         }
     }
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
         const int v = wid + kWarps * k;
         if (v < nv) {   // uniform per warp
-            const double a = warp_sum(t[k]);
+            double a = t[k][0];
+#pragma unroll
+            for (int u = 1; u < U; ++u) a += t[k][u];
+            a = warp_sum(a);
             if (lane == 0) s_out[v] = a;
         }
     }
@@ -117,6 +128,7 @@ __device__ __forceinline__ void sum_rows(const double* __restrict__ partials, in
 // and returns true (every other block returns false). Fixed summation order throughout, so
 // results repeat bit for bit for a given grid. Needs G + kRedGroups <= kPartialStride and
 // counter[0..kRedGroups] zero on entry (each level resets its own counters).
+template <int NV, int U>
 __device__ __forceinline__ bool grid_tail(double* __restrict__ partials, int nv, unsigned int* counter, double* s_tot)
 {
     __shared__ int s_role;
@@ -132,7 +144,7 @@ __device__ __forceinline__ bool grid_tail(double* __restrict__ partials, int nv,
     __syncthreads();
     if (s_role == 0) return false;
     __threadfence();
-    sum_rows(partials, nv, g, NG, members, s_grp);
+    sum_rows<NV, U>(partials, nv, g, NG, members, s_grp);
     __syncthreads();
     if ((int)threadIdx.x < nv) {
         partials[(size_t)threadIdx.x * kPartialStride + G + g] = s_grp[threadIdx.x];
@@ -147,7 +159,7 @@ __device__ __forceinline__ bool grid_tail(double* __restrict__ partials, int nv,
     __syncthreads();
     if (s_role != 2) return false;
     __threadfence();
-    sum_rows(partials, nv, G, 1, NG, s_tot);
+    sum_rows<NV, U>(partials, nv, G, 1, NG, s_tot);
     __syncthreads();
     if (threadIdx.x == 0) counter[kRedGroups] = 0u;
     return true;
@@ -181,7 +193,7 @@ __device__ __forceinline__ bool reduce_to_last_block(const double (&acc)[NV], in
         }
         __threadfence();
     }
-    return grid_tail(partials, nv, counter, s_tot);
+    return grid_tail<NV, 1>(partials, nv, counter, s_tot);
 }
 
 // Publish block totals s_blk[0..nv) (shared memory, complete before the call) as this
@@ -196,7 +208,7 @@ __device__ __forceinline__ bool partials_to_last_block(const double* s_blk, int 
         for (int v = 0; v < nv; ++v) partials[(size_t)v * kPartialStride + blockIdx.x] = s_blk[v];
         __threadfence();
     }
-    return grid_tail(partials, nv, counter, s_tot);
+    return grid_tail<kWMax + 2, 1>(partials, nv, counter, s_tot);
 }
 
 // Column-parallel accumulation of c_j += sum_rows col_j[row] * s_z[row - row0] over one
