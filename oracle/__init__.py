@@ -100,6 +100,11 @@ class Oracle:
         lib.orc_pcg.argtypes = [ci, vp, vp, vp, vp, vp, cd, ci, vp, ctypes.POINTER(ci)]
         lib.orc_solve_system.argtypes = [ci, vp, vp, vp, vp, ci, vp, cd, ci, ci, vp,
                                          ctypes.POINTER(_Info), vp, vp, ci]
+        lib.orc_stage_two.argtypes = [ci, vp, vp, vp, vp, ci, vp, ci, vp, vp, cd, ci,
+                                      ctypes.POINTER(ci), vp, vp, vp, ctypes.POINTER(cd)]
+        lib.orc_solve_system3.argtypes = [ci, vp, vp, vp, vp, ci, vp, ci, cd, cd, ci, ci, ci, vp,
+                                          ctypes.POINTER(_Info), ctypes.POINTER(ci), ctypes.POINTER(cd),
+                                          vp, vp, ci]
 
     # -- Section 2 / basic kernels -------------------------------------------------
     def spmv(self, A, x):
@@ -229,6 +234,49 @@ class Oracle:
                                   kmax, max_refine, _p(x), ctypes.byref(info), _p(P), _p(g), p_cap)
         return x, _info_dict(info), P, g
 
+    # -- Section 4.2 / 4.3 ------------------------------------------------------------------
+    def stage_two(self, A, b, Y, w, R, what, tol_abs, kcap):
+        """Stage two (Section 4.2) on the reduced system Y^T A Y yhat = Y^T b from
+        yhat0 = [what; 0], augmenting with the first w columns of Y (factor R of W^T A W).
+        Returns dict(k2, alpha, V2 (n x k2), T2, rhat_norm, status)."""
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        n = len(rp) - 1
+        b, Y = _f64(b), _f64(Y)
+        y = Y.shape[1]
+        R = np.ascontiguousarray(R if w > 0 else np.zeros((1, 1)), dtype=np.float64)
+        what = _f64(what if w > 0 else np.zeros(1))
+        m = max(kcap, 1)
+        alpha, T2 = np.zeros(m), np.zeros(m)
+        V2 = np.zeros((n, m), order="F")
+        k2, rn = ctypes.c_int(0), ctypes.c_double(0.0)
+        st = self.lib.orc_stage_two(n, _p(rp), _p(col), _p(val), _p(b), y, _p(Y), w, _p(R), _p(what),
+                                    tol_abs, kcap, ctypes.byref(k2), _p(alpha), _p(V2), _p(T2),
+                                    ctypes.byref(rn))
+        k = k2.value
+        return {"k2": k, "alpha": alpha[:k], "V2": np.asfortranarray(V2[:, :k]), "T2": T2[:k],
+                "rhat_norm": rn.value, "status": STATUS.get(st, str(st))}
+
+    def solve_system3(self, A, b, Y, w, tol_rel, tol2_rel, w3_cap=64, kmax=100000, max_refine=5, p_cap=0):
+        """Three-stage solve (Section 4): stage one on the first w columns of Y, stage two
+        over range(Y) to tol2_rel * tol_rel * ||b||, stage three (Algorithm 1) augmented with
+        [W, V2]. info gains k2 and stage2_relres; info["w"] is the stage-three basis size."""
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        n = len(rp) - 1
+        b = _f64(b)
+        Y = _f64(Y if Y is not None else np.zeros((n, 0)))
+        x = np.empty(n)
+        info = _Info()
+        k2, s2 = ctypes.c_int(0), ctypes.c_double(0.0)
+        P = np.zeros((n, p_cap), order="F") if p_cap else None
+        g = np.zeros(p_cap) if p_cap else None
+        self.lib.orc_solve_system3(n, _p(rp), _p(col), _p(val), _p(b), Y.shape[1], _p(Y), w, tol_rel, tol2_rel,
+                                   w3_cap, kmax, max_refine, _p(x), ctypes.byref(info), ctypes.byref(k2),
+                                   ctypes.byref(s2), _p(P), _p(g), p_cap)
+        d = _info_dict(info)
+        d["k2"] = k2.value
+        d["stage2_relres"] = s2.value
+        return x, d, P, g
+
 
 def _info_dict(info: _Info) -> dict:
     return {"status": STATUS.get(info.status, str(info.status)), "iters": info.iters,
@@ -242,12 +290,21 @@ class OracleSequence:
 
     ``solve(A, b, tol)`` solves the next system and records its solution as a snapshot;
     ``add_snapshot(x)`` records an externally supplied solution instead.
+
+    With ``three_stage`` the POD also gives the augmenting basis Y (energy ``energy_y``,
+    at most ``y_max`` modes, never fewer than the stage-one dimension w, so that W is the
+    first w columns of Y: POD bases are nested) and each system runs the three-stage
+    algorithm (Section 4) with stage-two tolerance ``tol_stage2`` times the system's.
     """
 
     def __init__(self, n: int, s_max: int = 40, w_max: int = 32, energy: float = 0.9999,
-                 kmax: int = 100000, max_refine: int = 5, oracle: Oracle | None = None):
+                 kmax: int = 100000, max_refine: int = 5, oracle: Oracle | None = None,
+                 three_stage: bool = False, y_max: int = 40, energy_y: float = 1.0,
+                 tol_stage2: float = 1e-4, w3_cap: int = 64):
         self.n, self.s_max, self.w_max, self.energy = n, s_max, w_max, energy
         self.kmax, self.max_refine = kmax, max_refine
+        self.three_stage, self.y_max, self.energy_y = three_stage, y_max, energy_y
+        self.tol_stage2, self.w3_cap = tol_stage2, w3_cap
         self.orc = oracle or Oracle()
         self.snaps: list[np.ndarray] = []
 
@@ -262,7 +319,28 @@ class OracleSequence:
         S = np.asfortranarray(np.stack(self.snaps, axis=1))
         return self.orc.pod_evd(S, self.energy, self.w_max)
 
+    def basis_y(self):
+        """(Y, w): the augmenting basis and the stage-one dimension (W = Y[:, :w])."""
+        if not self.snaps:
+            return np.zeros((self.n, 0), order="F"), 0
+        S = np.asfortranarray(np.stack(self.snaps, axis=1))
+        _, w, _ = self.orc.pod_evd(S, self.energy, self.w_max)
+        _, y, _ = self.orc.pod_evd(S, self.energy_y, self.y_max)
+        y = max(y, w)
+        # energy 2 is never reached: all modes up to the numerical rank, capped at y
+        Y, y2, _ = self.orc.pod_evd(S, 2.0, y)
+        return Y, min(w, y2)
+
     def solve(self, A, b, tol_rel, record: bool = True):
+        if self.three_stage:
+            Y, w = self.basis_y()
+            x, info, _, _ = self.orc.solve_system3(A, b, Y, w, tol_rel, self.tol_stage2, self.w3_cap,
+                                                   self.kmax, self.max_refine)
+            info["s"] = len(self.snaps)
+            info["y"] = Y.shape[1]
+            if record:
+                self.add_snapshot(x)
+            return x, info
         W, w, sig2 = self.basis()
         x, info, _, _ = self.orc.solve_system(A, b, W, tol_rel, self.kmax, self.max_refine)
         info["s"] = len(self.snaps)

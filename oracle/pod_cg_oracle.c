@@ -469,6 +469,185 @@ int orc_solve_system(int n, const int* rp, const int* ci, const double* va, cons
     return st;
 }
 
+/* ------------------------------------- stage two (Section 4.2) and stage three (Section 4.3) */
+
+/* Reduced product qhat = Y^T (A (Y phat)) (Section 4.2): Y^T A Y is never formed; the
+ * product costs one matrix-vector product and two passes over Y. v receives Y phat and
+ * Av receives A v (length n each). */
+static void orc_reduced_product(int n, const int* rp, const int* ci, const double* va, int y,
+                                const double* Y, const double* phat, double* v, double* Av, double* qhat)
+{
+    for (int i = 0; i < n; ++i) v[i] = 0.0;
+    for (int l = 0; l < y; ++l)
+        for (int i = 0; i < n; ++i) v[i] += Y[(size_t)l * n + i] * phat[l];
+    orc_spmv(n, rp, ci, va, v, Av);
+    for (int l = 0; l < y; ++l) qhat[l] = orc_dot(n, Y + (size_t)l * n, Av);
+}
+
+/* Stage two (Section 4.2): Algorithm 1 applied to the reduced system
+ *     (Y^T A Y) yhat = Y^T b                    (xbar = 0)
+ * from yhat0 = Phi what with augmenting basis Phi = [I_w; 0] (the stage-one basis in
+ * augmenting-subspace coordinates: W = Y Phi is the first w columns of Y), preconditioner
+ * M = I and absolute tolerance tol_abs on ||rhat||, for at most kcap iterations. The
+ * augmentation solves Phi^T (Y^T A Y) Phi mu = Phi^T (Y^T A Y) zhat reuse the stage-one
+ * factor (Phi^T Y^T A Y Phi = W^T A W = R^T R); their right-hand sides are formed
+ * literally, with one more reduced product. rhat0 is tested before the loop.
+ * Outputs: *k2 iterations; alpha[k] the step lengths (the coordinates of the increment in
+ * the stage-two basis); V2 (n x k2 column-major, may be NULL) the lifted directions
+ * Y phat_k, i.e. the stage-two basis V2 = Y Phi2; T2[k] = (Y^T A Y phat_k, phat_k), the
+ * diagonal of V2^T A V2; *rhat_norm the final ||rhat||. A non-positive or non-finite
+ * (Y^T A Y phat, phat) ends stage two with the directions accepted so far. */
+int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const double* b,
+                  int y, const double* Y, int w, const double* R, const double* what,
+                  double tol_abs, int kcap, int* k2, double* alpha, double* V2, double* T2,
+                  double* rhat_norm)
+{
+    size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    size_t yb = sizeof(double) * (size_t)(y > 0 ? y : 1);
+    double* v = (double*)malloc(nb);
+    double* Av = (double*)malloc(nb);
+    double* xh = (double*)calloc(1, yb);
+    double* rh = (double*)malloc(yb);
+    double* zh = (double*)malloc(yb);
+    double* ph = (double*)malloc(yb);
+    double* qh = (double*)malloc(yb);
+    double* th = (double*)malloc(yb);
+    double* mu = (double*)malloc(sizeof(double) * (size_t)(w > 0 ? w : 1));
+    int k = 0, status = ORC_OK;
+
+    for (int l = 0; l < y; ++l) xh[l] = (l < w) ? what[l] : 0.0;          /* step 1 */
+    orc_reduced_product(n, rp, ci, va, y, Y, xh, v, Av, qh);             /* step 2 */
+    for (int l = 0; l < y; ++l)
+        rh[l] = orc_dot(n, Y + (size_t)l * n, b) - (MUT(14) ? 0.0 : qh[l]);
+    for (int l = 0; l < y; ++l) zh[l] = rh[l];                            /* step 3, M = I */
+    if (w > 0) {                                                          /* step 4 */
+        orc_reduced_product(n, rp, ci, va, y, Y, zh, v, Av, th);
+        orc_chol_solve(w, R, th, mu);
+    }
+    for (int l = 0; l < y; ++l) ph[l] = zh[l] - ((l < w) ? mu[l] : 0.0);  /* step 5 */
+    double rz = 0.0, rr = 0.0;
+    for (int l = 0; l < y; ++l) { rz += rh[l] * zh[l]; rr += rh[l] * rh[l]; }
+    double rnorm = sqrt(rr);
+    while (rnorm > tol_abs && k < kcap) {
+        orc_reduced_product(n, rp, ci, va, y, Y, ph, v, Av, qh);
+        double gamma = 0.0;
+        for (int l = 0; l < y; ++l) gamma += qh[l] * ph[l];
+        if (!isfinite(gamma) || !(gamma > 0.0)) { status = ORC_BREAKDOWN; break; }
+        double a = rz / gamma;
+        alpha[k] = a;
+        T2[k] = gamma;
+        if (V2) memcpy(V2 + (size_t)k * n, v, nb);
+        for (int l = 0; l < y; ++l) xh[l] += a * ph[l];
+        for (int l = 0; l < y; ++l) rh[l] -= a * qh[l];
+        for (int l = 0; l < y; ++l) zh[l] = rh[l];
+        double rz_new = 0.0;
+        rr = 0.0;
+        for (int l = 0; l < y; ++l) { rz_new += rh[l] * zh[l]; rr += rh[l] * rh[l]; }
+        double beta = rz_new / rz;
+        if (w > 0) {
+            orc_reduced_product(n, rp, ci, va, y, Y, zh, v, Av, th);
+            orc_chol_solve(w, R, th, mu);
+        }
+        for (int l = 0; l < y; ++l)
+            ph[l] = zh[l] + beta * ph[l] - ((l < w && !MUT(12)) ? mu[l] : 0.0);
+        rz = rz_new;
+        rnorm = sqrt(rr);
+        ++k;
+    }
+    *k2 = k;
+    *rhat_norm = rnorm;
+    free(mu); free(th); free(qh); free(ph); free(zh); free(rh); free(xh); free(Av); free(v);
+    return status;
+}
+
+/* One system by the three-stage algorithm (Section 4; the overall algorithm with the stage-
+ * three option of Section 4.3, whose augmenting basis is [W, V2]):
+ *   stage one   Algorithm 2 on W = the first w columns of Y (R, what); if W^T A W is not
+ *               numerically SPD the stage-one basis is dropped (w = 0);
+ *   stage two   Section 4.2 over range(Y) to tol_abs2 = tol2_rel * tol_rel * ||b||: V2, alpha,
+ *               T2, with at most min(y - w, w3_cap - w) iterations (the reduced system's
+ *               dimension less the stage-one directions it deflates; w3_cap bounds the
+ *               stage-three basis dimension w + k2);
+ *   stage three Algorithm 1 on A x = b with augmenting basis [W, V2], initial coordinates
+ *               [what; alpha] and the Cholesky factor blockdiag(R, sqrt(T2)) of
+ *               [W, V2]^T A [W, V2], known from stages one and two (Section 4.3).
+ * info as orc_solve_system (info->w = w + k2, the stage-three basis dimension); *k2_out the
+ * stage-two iterations; *s2_relres = ||b - A x_2||/||b|| at x_2 = W what + V2 alpha.
+ * P_out/gamma_out/p_cap: stage-three directions as orc_aug_pcg. */
+int orc_solve_system3(int n, const int* rp, const int* ci, const double* va, const double* b,
+                      int y, const double* Y, int w, double tol_rel, double tol2_rel, int w3_cap,
+                      int kmax, int max_refine, double* x, orc_info* info, int* k2_out,
+                      double* s2_relres, double* P_out, double* gamma_out, int p_cap)
+{
+    memset(info, 0, sizeof(*info));
+    if (w > y) w = y;
+    double bnorm = sqrt(orc_dot(n, b, b));
+    double tol_abs = tol_rel * bnorm;
+    int cap = (y < w3_cap ? y : w3_cap);   /* room for w + k2 columns */
+    if (cap < w) cap = w;
+    int wt = cap;
+    double* R = (double*)calloc((size_t)(w > 0 ? w * w : 1), sizeof(double));
+    double* what = (double*)calloc((size_t)(wt > 0 ? wt : 1), sizeof(double));
+    double* B = (double*)malloc(sizeof(double) * (size_t)n * (size_t)(wt > 0 ? wt : 1));
+    double* R3 = (double*)calloc((size_t)(wt > 0 ? wt * wt : 1), sizeof(double));
+    double* T2 = (double*)malloc(sizeof(double) * (size_t)(wt > 0 ? wt : 1));
+    double* vv = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int wu = w;
+    if (w > 0 && orc_stage_one(n, rp, ci, va, b, w, Y, R, what) != ORC_OK) {   /* stage one */
+        info->chol_failed = 1;
+        wu = 0;
+        for (int a = 0; a < w; ++a) what[a] = 0.0;
+    }
+    {   /* stage-one residual */
+        for (int i = 0; i < n; ++i) vv[i] = 0.0;
+        for (int a = 0; a < wu; ++a)
+            for (int i = 0; i < n; ++i) vv[i] += Y[(size_t)a * n + i] * what[a];
+        double* q = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        orc_spmv(n, rp, ci, va, vv, q);
+        double rr = 0.0;
+        for (int i = 0; i < n; ++i) rr += (b[i] - q[i]) * (b[i] - q[i]);
+        info->stage1_relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+        free(q);
+    }
+    int k2 = 0;                                                            /* stage two */
+    double rhat = 0.0;
+    orc_stage_two(n, rp, ci, va, b, y, Y, wu, R, what, tol2_rel * tol_abs, cap - wu, &k2,
+                  what + wu, B + (size_t)wu * n, T2, &rhat);
+    /* stage-three basis [W, V2] and factor blockdiag(R, sqrt(T2)) */
+    memcpy(B, Y, sizeof(double) * (size_t)n * (size_t)wu);
+    int w3 = wu + k2;
+    for (int a = 0; a < wu; ++a)
+        for (int c = 0; c < wu; ++c) R3[a * w3 + c] = R[a * wu + c];
+    for (int k = 0; k < k2; ++k) R3[(wu + k) * w3 + wu + k] = MUT(13) ? T2[k] : sqrt(T2[k]);
+    {   /* stage-two residual */
+        for (int i = 0; i < n; ++i) vv[i] = 0.0;
+        for (int a = 0; a < w3; ++a)
+            for (int i = 0; i < n; ++i) vv[i] += B[(size_t)a * n + i] * what[a];
+        double* q = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        orc_spmv(n, rp, ci, va, vv, q);
+        double rr = 0.0;
+        for (int i = 0; i < n; ++i) rr += (b[i] - q[i]) * (b[i] - q[i]);
+        *s2_relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+        free(q);
+    }
+    int chol = info->chol_failed;
+    double s1 = info->stage1_relres;
+    int st = orc_aug_pcg(n, rp, ci, va, b, w3, B, R3, what, tol_abs, kmax, max_refine, x, info,  /* stage three */
+                         P_out, gamma_out, p_cap);
+    info->chol_failed = chol; info->stage1_relres = s1; info->w = w3;
+    {
+        double* q = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        orc_spmv(n, rp, ci, va, x, q);
+        double rr = 0.0;
+        for (int i = 0; i < n; ++i) rr += (b[i] - q[i]) * (b[i] - q[i]);
+        info->final_relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+        free(q);
+    }
+    *k2_out = k2;
+    free(vv); free(T2); free(R3); free(B); free(what); free(R);
+    return st;
+}
+
 /* Gradient of L(theta) = sum_j c^T x_j through A_j(theta) x_j = b_j (the differentiated
  * sequence): with adjoints lambda_j = A_j^{-1} c (A_j symmetric),
  *   dL/dtheta_c = - sum_j lambda_j^T (dA_j/dtheta_c) x_j.

@@ -298,7 +298,107 @@ def pin_theta_grad_complex_step(orc):
     return e <= 1e-13, f"theta gradient vs complex step: {e:.1e}"
 
 
+def _three_stage_problem(n_side=10, y=10, w=3, seed=3):
+    """A small diffusion system and an orthonormal augmenting basis Y of y vectors near the
+    solution; the stage-one basis is its first w columns."""
+    A = small_diffusion(n_side, seed=seed)
+    D = A.todense()
+    rng = np.random.default_rng(seed + 4)
+    xs = rng.normal(size=A.n)
+    b = D @ xs
+    Y = orth_basis(np.stack([xs + 0.5 * rng.normal(size=A.n) for _ in range(y)]))
+    return A, D, b, Y, w
+
+
+def pin_stage_two_optimality(orc):
+    """After k stage-two iterations (Section 4.2) the iterate W what + V2 alpha minimises the
+    A-norm error over range(W) + Y K_k(H, rhat0): the Krylov space of the reduced operator
+    Ahat = Y^T A Y deflated by the stage-one coordinates Phi = [I_w; 0],
+    H = Ahat - Ahat Phi (Phi^T Ahat Phi)^{-1} Phi^T Ahat, from rhat0 = Y^T (b - A W what).
+    The reference is a dense Galerkin solve on that space, built from explicit powers of
+    the dense reduced matrix."""
+    A, D, b, Y, w = _three_stage_problem()
+    W = np.asfortranarray(Y[:, :w])
+    what, R, st = orc.stage_one(A.arrays(), b, W)
+    Ah = Y.T @ D @ Y
+    Phi = np.eye(Y.shape[1])[:, :w]
+    H = Ah - Ah @ Phi @ np.linalg.solve(Phi.T @ Ah @ Phi, Phi.T @ Ah)
+    r0 = Y.T @ (b - D @ (W @ what))
+    worst = 0.0
+    for k in (1, 2, 3, 4):
+        out = orc.stage_two(A.arrays(), b, Y, w, R, what, 0.0, k)
+        x2 = W @ what + out["V2"] @ out["alpha"]
+        K = [r0]
+        for _ in range(k - 1):
+            K.append(H @ K[-1])
+        Q, _ = np.linalg.qr(np.concatenate([W, Y @ np.stack(K, axis=1)], axis=1))
+        xg = Q @ np.linalg.solve(Q.T @ D @ Q, Q.T @ b)
+        worst = max(worst, a_norm(D, x2 - xg) / a_norm(D, xg))
+        if out["k2"] != k:
+            return False, f"stage two stopped at {out['k2']} < {k}"
+    return st == 0 and worst < 1e-11, f"stage-two optimality err {worst:.1e}"
+
+
+def pin_stage_two_full(orc):
+    """With no tolerance and y - w iterations stage two solves the reduced system exactly
+    (augmented CG on a y-dimensional SPD system with w directions deflated): the result is
+    the Galerkin solution over range(Y), Y (Y^T A Y)^{-1} Y^T b (dense LAPACK solve). Its
+    basis satisfies Section 4.2's properties V2^T A W = 0 and V2^T A V2 = diag(T2)."""
+    A, D, b, Y, w = _three_stage_problem(seed=9)
+    W = np.asfortranarray(Y[:, :w])
+    what, R, st = orc.stage_one(A.arrays(), b, W)
+    y = Y.shape[1]
+    out = orc.stage_two(A.arrays(), b, Y, w, R, what, 0.0, y - w)
+    V2 = out["V2"]
+    x2 = W @ what + V2 @ out["alpha"]
+    xg = Y @ np.linalg.solve(Y.T @ D @ Y, Y.T @ b)
+    e = a_norm(D, x2 - xg) / a_norm(D, xg)
+    AV = D @ V2
+    va = np.sqrt(np.einsum("ij,ij->j", V2, AV))
+    wa = np.sqrt(np.einsum("ij,ij->j", W, D @ W))
+    e1 = np.max(np.abs(W.T @ AV) / np.outer(wa, va))
+    C = V2.T @ AV
+    e2 = np.max(np.abs(C - np.diag(out["T2"])) / np.outer(va, va))
+    ok = out["k2"] == y - w and e < 1e-11 and e1 < 1e-12 and e2 < 1e-11
+    return ok, f"stage two full: Galerkin err {e:.1e}, V2^T A W {e1:.1e}, V2^T A V2 - T2 {e2:.1e}, k2={out['k2']}"
+
+
+def pin_three_stage_optimality(orc):
+    """Stage three (Section 4.3) started from the stage-two solution with augmenting basis
+    [W, V2] and the block-diagonal factor blockdiag(R, sqrt(T2)): after k iterations the
+    iterate is the A-orthogonal projection onto range(W) + range(V2) + range(P) (dense
+    Galerkin on the explicit basis); at tol 1e-14 it agrees with the dense direct solve."""
+    A, D, b, Y, w = _three_stage_problem(n_side=12, y=8, w=3, seed=11)
+    tol, tol2 = 1e-4, 1e-2
+    x, info, P, g = orc.solve_system3(A.arrays(), b, Y, w, tol, tol2, 64, p_cap=400)
+    W = np.asfortranarray(Y[:, :w])
+    what, R, _ = orc.stage_one(A.arrays(), b, W)
+    out = orc.stage_two(A.arrays(), b, Y, w, R, what, tol2 * tol * np.linalg.norm(b), Y.shape[1] - w)
+    k = info["iters"]
+    B = np.concatenate([W, out["V2"], P[:, :k]], axis=1)
+    xg = B @ np.linalg.solve(B.T @ D @ B, B.T @ b)
+    e = a_norm(D, x - xg) / a_norm(D, xg)
+    x2, info2, _, _ = orc.solve_system3(A.arrays(), b, Y, w, 1e-14, tol2, 64)
+    xs = np.linalg.solve(D, b)
+    e2 = a_norm(D, x2 - xs) / a_norm(D, xs)
+    ok = (info["k2"] == out["k2"] and info["k2"] >= 1 and k >= 3 and info["refinements"] == 0
+          and e < 1e-9 and info2["status"] == "ok" and e2 < 1e-12)
+    return ok, (f"three-stage optimality err {e:.1e} (k2={info['k2']}, k={k}), "
+                f"dense agreement {e2:.1e} ({info2['status']})")
+
+
+def pin_three_stage_collapse(orc):
+    """With Y = W (no room for stage two) the three-stage solve is the two-stage solve:
+    Algorithm 3 with an empty stage-two basis. Bitwise equal solutions."""
+    A, D, b, W = _aug_problem(seed=7)
+    x1, i1, _, _ = orc.solve_system(A.arrays(), b, W, 1e-9)
+    x3, i3, _, _ = orc.solve_system3(A.arrays(), b, W, W.shape[1], 1e-9, 1e-3, 64)
+    ok = np.array_equal(x1, x3) and i3["k2"] == 0 and i1["iters"] == i3["iters"]
+    return ok, f"collapse: bitwise {np.array_equal(x1, x3)}, k2={i3['k2']}, iters {i1['iters']}/{i3['iters']}"
+
+
 ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
-            pin_finite_termination, pin_theta_grad_complex_step]
+            pin_finite_termination, pin_theta_grad_complex_step, pin_stage_two_optimality,
+            pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse]

@@ -28,6 +28,9 @@ MUTANTS = {
     9: "wrong sign in the eigenvector rotation",
     10: "SpMV drops the first entry of each row",
     11: "interior-face derivative uses its own cell's coefficient instead of the neighbour's",
+    12: "stage two drops the stage-one deflation term from the direction update",
+    13: "stage-three factor takes T2 instead of its square root",
+    14: "stage-two initial residual omits the stage-one solution's product",
 }
 
 
