@@ -5,7 +5,7 @@ Workload (default): the 128^3 seven-point variable-coefficient diffusion sequenc
 systems (lognormal(0, 1) coefficients perturbed 0.5% per system, moving heat source),
 POD of the last 40 solutions truncated at 99.99% energy to w <= 32, Jacobi
 preconditioner, relative residual 1e-8. One step = solving the whole sequence on the GPU
-(POD + stage one + stage two for each system, snapshots recorded as it goes), inputs
+(POD + stage one + stage three for each system, snapshots recorded as it goes), inputs
 resident in HBM. A_j values (117 MB each) and the basis blocks (~1 GB) exceed the 129 MB
 L2, so no L2 flush is needed between steps.
 
@@ -53,7 +53,7 @@ def parse_args():
                          "against fourth-order central differences at K random cells")
     ap.add_argument("--kernel-profile", type=int, default=0, metavar="W",
                     help="profiling target: one full-size system with W synthetic snapshots, a 5-iteration "
-                         "solve, then each stage-two kernel launched --kernel-reps times (few launches)")
+                         "solve, then each stage-three kernel launched --kernel-reps times (few launches)")
     ap.add_argument("--gram-profile", action="store_true",
                     help="profiling target: the tensor-core Gram W^T [AW, b] at n = 2,097,152, w = 22 (FP32 "
                          "inputs), launched --kernel-reps times")
@@ -67,6 +67,10 @@ def parse_args():
     ap.add_argument("--spmv-lanes", type=int, default=0, choices=[0, 1, 2, 4, 8, 16, 32],
                     help="CSR SpMV lanes per row (0: timed by the handle); profiling commands force the "
                          "timed choice so the profiled kernels are the ones the bench times")
+    ap.add_argument("--three-stage", action="store_true",
+                    help="the three-stage algorithm (Section 4) against the two-stage form on the same "
+                         "sequence (the --grid/--systems diffusion sequence, or the cantilever with "
+                         "--elasticity K), each timed over the sequence after one untimed pass; one JSON line")
     ap.add_argument("--batch-seqs", type=int, default=256)
     ap.add_argument("--loop-mode", choices=["graph", "chunked"], default="graph",
                     help="graph: conditional CUDA graph; chunked: plain graphs of 16 iterations (profilable)")
@@ -472,6 +476,65 @@ def elasticity_bench(args):
     return 0
 
 
+def three_stage_bench(args):
+    """Three-stage solves (stage one on the dominant POD modes, stage two over all retained
+    modes, stage three augmented with [W, V2]) against the two-stage form (stage one on the
+    POD basis at energy 0.9999, then stage three), same sequence, same precision and
+    tolerance. Each variant is timed over the whole sequence (CUDA events) after one
+    untimed pass. Prints one JSON line."""
+    import torch
+    from paper_1512_05820_gb300 import workloads as wl
+    from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
+    from paper_1512_05820_gb300.solver import PodCG
+    if args.elasticity:
+        seq = wl.elasticity_cantilever(e=64, p=args.elasticity)
+        name = f"elasticity_cantilever 64^3 elements, first {args.elasticity} systems"
+    else:
+        seq = workload(args)
+        name = f"diffusion3d_moving {args.grid}^3 7-point, {seq.p} systems"
+    prec = 1 if args.precision == "mixed" else 0
+    dseq = DeviceSequence(seq, systems=seq.all_systems())
+    xs = [torch.empty(seq.n, dtype=torch.float64, device="cuda") for _ in range(dseq.p)]
+
+    def one(**cfg):
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, precision=prec, spmv_lanes=args.spmv_lanes,
+                       use_tc_gram=1 if prec == 1 else 0, **cfg)
+        run_sequence(solver, dseq, xs)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(solver.stream)
+        st = run_sequence(solver, dseq, xs)
+        b.record(solver.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        solver.close()
+        return {"config": {k: v for k, v in cfg.items()}, "systems_per_s": dseq.p / (ms / 1e3), "ms": ms,
+                "mean_iters_stage3": float(np.mean([s["iters"] for s in st])),
+                "mean_stage2_iters": float(np.mean([s["stage2_iters"] for s in st])),
+                "mean_w_stage3": float(np.mean([s["w"] for s in st])),
+                "mean_y": float(np.mean([s["y"] for s in st])),
+                "ms_stage1_mean": float(np.mean([s["ms_stage1"] for s in st])),
+                "ms_stage2_mean": float(np.mean([s["ms_stage2"] for s in st])),
+                "ms_stage3_mean": float(np.mean([s["ms_stage3"] for s in st])),
+                "spmv_total": int(sum(s["spmv_count"] for s in st)),
+                "max_final_relres": max(s["final_relres"] for s in st)}
+
+    out = {"three_stage": True, "workload": name, "n": seq.n, "nnz": seq.nnz, "tol": seq.tol,
+           "precision": args.precision, "s_max": seq.s_max,
+           "two_stage": one(energy=seq.energy),
+           "three_stage_e099_all_modes": one(energy=0.99, three_stage=1, y_max=seq.s_max, energy_y=0.99999999,
+                                             tol_stage2=1e-4),
+           "three_stage_e0999_all_modes": one(energy=0.999, three_stage=1, y_max=seq.s_max, energy_y=0.99999999,
+                                              tol_stage2=1e-4),
+           "three_stage_e09999_all_modes": one(energy=seq.energy, three_stage=1, y_max=seq.s_max,
+                                               energy_y=0.99999999, tol_stage2=1e-4)}
+    base = out["two_stage"]["systems_per_s"]
+    out["speedup_vs_two_stage"] = {k: v["systems_per_s"] / base for k, v in out.items()
+                                   if isinstance(v, dict) and k.startswith("three_stage_")}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def gram_profile(args):
     """A short launch sequence for kernel profilers: the tensor-core Gram of the 128^3
     stage-one shape (FP32 W and AW panels, w = 22, plus b), --kernel-reps launches."""
@@ -561,6 +624,8 @@ def main():
         return diff_check(args)
     if args.gram_profile:
         return gram_profile(args)
+    if args.three_stage:
+        return three_stage_bench(args)
     if args.elasticity:
         return elasticity_bench(args)
 
@@ -641,6 +706,7 @@ def main():
                        "ms_pod_mean": float(np.mean([s["ms_pod"] for s in last])),
                        "ms_stage1_mean": float(np.mean([s["ms_stage1"] for s in last])),
                        "ms_stage2_mean": float(np.mean([s["ms_stage2"] for s in last])),
+                       "ms_stage3_mean": float(np.mean([s["ms_stage3"] for s in last])),
                        "spmv_per_step": spmv_per_step}}
 
     # one timed pass each: POD-aug in the other precision, plain Jacobi CG (no recycling)
@@ -672,7 +738,7 @@ def main():
         out["speedup_vs_plain_cg_same_precision"] = value / world / same["systems_per_s"]
         out["speedup_vs_fp64_pod_aug"] = (value / world / out["pod_aug_fp64"]["systems_per_s"]) if prec == 1 else 1.0
 
-    # per-kernel device times of one stage-two iteration (CUDA events, launching stream)
+    # per-kernel device times of one stage-three iteration (CUDA events, launching stream)
     j_last = dseq.p - 1
     run_sequence(solver, dseq, xs)
     ms_k = solver.time_kernels(dseq.matrix(j_last), dseq.bs[j_last], reps=args.kernel_reps)

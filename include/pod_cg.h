@@ -5,15 +5,21 @@
  * POD-augmented conjugate-gradient method". A sequence of sparse SPD systems
  * A_j x_j = b_j (Section 2, Eq. (sequence)) is solved to inexact tolerances
  * ||b_j - A_j x_j||_2 <= tol ||b_j||_2 (Eq. (sequenceInexact), with a relative tolerance).
- * For system j the library
+ * For system j the library, with the stages numbered as in Section 4,
  *   1. computes a POD basis W_j of the retained snapshots (previous solutions) with the
  *      eigenvalue route of Algorithm 4 (identity metric, unit weights): Gram S^T S,
  *      symmetric eigensolve, energy truncation, lift W = S V Sigma^{-1};
  *   2. stage one (Section 4.1, Algorithm 2): AW = A_j W, Ahat = W^T AW, Cholesky
  *      Ahat = R^T R, Ahat what = W^T b, x0 = W what, r0 = b - AW what;
- *   3. stage two (the paper's stage 3, Section 4.3, Algorithm 1 with Y = W): Jacobi-
- *      preconditioned CG whose directions are A_j-orthogonalised against W through
- *      mu = R^{-1} R^{-T} (AW)^T z and p = z + beta p - W mu.
+ *   3. (three_stage = 1 only) stage two (Section 4.2): the POD also gives a larger
+ *      augmenting basis Y whose first w columns are W; Algorithm 1 runs on the reduced
+ *      system Y^T A Y yhat = Y^T b through products Y^T (A (Y p)) (Y^T A Y is never
+ *      formed), augmented with the stage-one coordinates, reusing R and unpreconditioned,
+ *      to tol_stage2 * tol * ||b||; its k2 directions V2 = Y Phi2 extend the basis to
+ *      [W, V2] with the block-diagonal factor blockdiag(R, sqrt(T2)), T2 = diag(V2^T A V2);
+ *   4. stage three (Section 4.3, Algorithm 1 with basis [W, V2], V2 empty without stage
+ *      two): Jacobi-preconditioned CG whose directions are A_j-orthogonalised against the
+ *      basis through mu = R^{-1} R^{-T} (AW)^T z and p = z + beta p - W mu.
  * Every step runs in hand-written CUDA kernels; this header is the only interface.
  *
  * Conventions for every entry point:
@@ -70,7 +76,9 @@ typedef struct {
     double inner_tol;    /* MIXED: each inner solve reduces its residual by this factor */
     int    use_tc_gram;  /* MIXED only (else ERR_ARG at create): stage-one Gram W^T [AW, b] of
                             the FP32 panels on the tensor cores with split-bf16 products
-                            (pod_cg_gram_tc); 0 = CUDA cores. FP64 mode keeps the FP64 Gram:
+                            (pod_cg_gram_tc); 0 = CUDA cores. Solves that run stage two keep
+                            the CUDA-core Gram (its reduced residual cancels). FP64 mode keeps
+                            the FP64 Gram:
                             an FP32-rounded W^T A W leaves the directions A-orthogonal to W
                             only to ~1e-7 cond(W^T A W), too loose for FP64 tolerances */
     int    cond_diag;    /* 1: compute cond_2(W^T A W) per solve (diagnostic, Section 5.2) */
@@ -85,6 +93,18 @@ typedef struct {
     int    spmv_lanes;   /* CSR SpMV lanes per row: 0 = timed once per sparsity pattern
                             (systems of >= 65,536 rows; the pattern's heuristic width is kept
                             unless another is >= 10% faster); 1, 2, 4, 8, 16 or 32 = forced */
+    int    three_stage;  /* 1: the three-stage algorithm of Section 4 (stage two over the
+                            augmenting basis Y before stage three); 0: stages one and three */
+    int    y_max;        /* three_stage: cap on the augmenting-basis dimension y (1..s_max); y
+                            is chosen by the POD energy criterion energy_y (Algorithm 4 step
+                            3), capped at y_max, then raised to w when smaller (so y can reach
+                            w_max), so that W is the first w columns of Y */
+    double energy_y;     /* three_stage: POD energy criterion for Y (>= energy in practice) */
+    double tol_stage2;   /* three_stage: stage two stops when ||Y^T (b - A x)||_2 <=
+                            tol_stage2 * tol * ||b||_2, or after min(y, 64) - w iterations
+                            (the reduced system is then solved exactly in exact arithmetic).
+                            Stage two runs in FP64 in both precisions (MIXED converts its
+                            directions to FP32 for stage three) */
 } pod_cg_config;
 
 /* CSR matrix, device arrays, borrowed. */
@@ -97,31 +117,36 @@ typedef struct {
 } pod_cg_csr;
 
 /* Per-solve statistics (host). The paper's measures (Section 5.1): matrix-vector
- * products, preconditioner applications (= stage-two iterations) and wall time. */
+ * products, preconditioner applications (= stage-three iterations) and wall time. */
 typedef struct {
     int    status;          /* pod_cg_status of the solve */
-    int    iters;           /* stage-two CG iterations (all restarts / inner solves) */
+    int    iters;           /* stage-three CG iterations (all restarts / inner solves) */
     int    refinements;     /* FP64: residual-replacement restarts; MIXED: outer steps */
     int    w;               /* POD basis dimension used (0 = plain PCG) */
     int    s;               /* snapshots available */
     int    chol_failed;     /* 1 if W^T A W was not numerically SPD (basis dropped) */
     int    system_id;       /* id of this solve for pod_cg_solve_adjoint */
-    int    spmv_count;      /* sparse products: iters + w (stage one) + true-residual products */
+    int    spmv_count;      /* sparse products: iters + w (stage one) + stage2_iters +
+                               true-residual products */
     int    launches;        /* kernels launched by this solve (graph-internal ones included) */
+    int    y;               /* augmenting-basis dimension when stage two ran, else 0 */
+    int    stage2_iters;    /* stage-two iterations k2 (stage three's basis is w + k2 wide) */
     int    pad_;
     double stage1_relres;   /* ||b - A x0||/||b|| after stage one */
     double final_relres;    /* ||b - A x||/||b|| at exit, from an FP64 product */
     double cond_gram;       /* cond_2(W^T A W) when cond_diag = 1, else 0 */
     float  ms_pod;          /* device time of the POD update (eigensolve + lift) */
-    float  ms_stage1;       /* device time of stage one */
-    float  ms_stage2;       /* device time of the CG iteration */
+    float  ms_stage1;       /* device time of stage one (A W, Gram, Cholesky) */
+    float  ms_stage2;       /* device time of stage two and the start x0, r0 of stage three */
+    float  ms_stage3;       /* device time of the stage-three CG iteration */
 } pod_cg_stats;
 
 /* ------------------------------------------------------------------ handle lifecycle */
 
 /* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
  * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
- * loop_mode 0, proj_form -1, spmv_lanes 0. */
+ * loop_mode 0, proj_form -1, spmv_lanes 0, three_stage 0, y_max 40, energy_y 0.99999999,
+ * tol_stage2 1e-4. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 
 /* Create a solver for systems of order n (the problem statement of Section 2) whose work
@@ -151,7 +176,8 @@ pod_cg_status pod_cg_clear_snapshots(pod_cg_t* h);
 
 /* Solve A x = b to ||b - A x||_2 <= tol ||b||_2 (Eq. (sequenceInexact)) with the
  * POD-augmented method: POD of the current snapshots (Algorithm 4), stage one
- * (Algorithm 2) and augmented PCG (Algorithm 1, Y = W), then a true-residual check in
+ * (Algorithm 2), stage two when three_stage is set (Section 4.2), and augmented PCG
+ * (stage three, Algorithm 1 with basis [W, V2]), then a true-residual check in
  * FP64 with residual replacement (FP64 mode) or FP64 iterative refinement around FP32
  * inner solves (MIXED). A: device CSR of order n; b, x_out: device, length n (x_out is
  * written, caller-owned; it may not alias b). st: host, may be NULL.
@@ -161,8 +187,9 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
                            double* x_out, pod_cg_stats* st);
 
 /* Adjoint solve for a loss L(x_j): lambda = A_j^{-1} g (A_j symmetric, so A_j^{-T} = A_j^{-1}),
- * by the same POD-augmented method reusing the basis W_j, A_j W_j and the stage-one factor
- * R_j saved by the forward solve whose stats reported `system_id` (requires
+ * by the same POD-augmented method reusing the stage-one basis W_j, A_j W_j and the factor
+ * R_j saved by the forward solve whose stats reported `system_id` (three-stage handles keep
+ * the stage-one basis only; the adjoint runs stages one and three) (requires
  * keep_factors > 0 and that the system is among the last keep_factors solves).
  * A: the same matrix as that forward solve. g, lambda_out: device, length n.
  * Errors: as pod_cg_solve, plus ERR_STATE when the factors were not kept. */
@@ -174,8 +201,14 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
  * w_max columns) and its dimension (host out). */
 pod_cg_status pod_cg_get_basis(pod_cg_t* h, double* W_out, int* w_out);
 
+/* Copy stage three's augmenting basis [W, V2] of the last solve and its product
+ * A [W, V2] (device outs, n-by-w3 column-major, room for 64 columns; either may be NULL)
+ * and w3 = w + k2 (host out, may be NULL). FP64 handles only (ERR_STATE in MIXED, where
+ * the basis is held in FP32). */
+pod_cg_status pod_cg_get_stage3_basis(pod_cg_t* h, double* B_out, double* AB_out, int* w3_out);
+
 /* Measurement support (no counterpart in the paper): time, with CUDA events on the
- * handle's stream, `reps` separate launches of each kernel of one stage-two iteration
+ * handle's stream, `reps` separate launches of each kernel of one stage-three iteration
  * (Algorithm 1's loop body) with the launch shapes the solve uses: [0] the CG product
  * q = A p with (A p, p), [1] the update r -= alpha q, z = M^{-1} r, (r, z), ||r||^2,
  * c = (A W)^T z, [2] the direction x += alpha p, p = z + beta p - W mu, [3] the FP64 true

@@ -104,7 +104,7 @@ class Oracle:
                                       ctypes.POINTER(ci), vp, vp, vp, ctypes.POINTER(cd)]
         lib.orc_solve_system3.argtypes = [ci, vp, vp, vp, vp, ci, vp, ci, cd, cd, ci, ci, ci, vp,
                                           ctypes.POINTER(_Info), ctypes.POINTER(ci), ctypes.POINTER(cd),
-                                          vp, vp, ci]
+                                          vp, vp, ci, cd]
 
     # -- Section 2 / basic kernels -------------------------------------------------
     def spmv(self, A, x):
@@ -256,10 +256,12 @@ class Oracle:
         return {"k2": k, "alpha": alpha[:k], "V2": np.asfortranarray(V2[:, :k]), "T2": T2[:k],
                 "rhat_norm": rn.value, "status": STATUS.get(st, str(st))}
 
-    def solve_system3(self, A, b, Y, w, tol_rel, tol2_rel, w3_cap=64, kmax=100000, max_refine=5, p_cap=0):
+    def solve_system3(self, A, b, Y, w, tol_rel, tol2_rel, w3_cap=64, kmax=100000, max_refine=5, p_cap=0,
+                      tol3_rel=-1.0):
         """Three-stage solve (Section 4): stage one on the first w columns of Y, stage two
         over range(Y) to tol2_rel * tol_rel * ||b||, stage three (Algorithm 1) augmented with
-        [W, V2]. info gains k2 and stage2_relres; info["w"] is the stage-three basis size."""
+        [W, V2] to tol_rel (or tol3_rel when >= 0). info gains k2 and stage2_relres;
+        info["w"] is the stage-three basis size."""
         rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
         n = len(rp) - 1
         b = _f64(b)
@@ -271,7 +273,7 @@ class Oracle:
         g = np.zeros(p_cap) if p_cap else None
         self.lib.orc_solve_system3(n, _p(rp), _p(col), _p(val), _p(b), Y.shape[1], _p(Y), w, tol_rel, tol2_rel,
                                    w3_cap, kmax, max_refine, _p(x), ctypes.byref(info), ctypes.byref(k2),
-                                   ctypes.byref(s2), _p(P), _p(g), p_cap)
+                                   ctypes.byref(s2), _p(P), _p(g), p_cap, float(tol3_rel))
         d = _info_dict(info)
         d["k2"] = k2.value
         d["stage2_relres"] = s2.value

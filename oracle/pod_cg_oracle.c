@@ -496,7 +496,14 @@ static void orc_reduced_product(int n, const int* rp, const int* ci, const doubl
  * the stage-two basis); V2 (n x k2 column-major, may be NULL) the lifted directions
  * Y phat_k, i.e. the stage-two basis V2 = Y Phi2; T2[k] = (Y^T A Y phat_k, phat_k), the
  * diagonal of V2^T A V2; *rhat_norm the final ||rhat||. A non-positive or non-finite
- * (Y^T A Y phat, phat) ends stage two with the directions accepted so far. */
+ * (Y^T A Y phat, phat) ends stage two with the directions accepted so far.
+ * Reading (not in Algorithm 1): every new direction is re-A-orthogonalised against the
+ * directions taken so far, phat -= sum_i (qhat_i^T phat / T2[i]) phat_i with the stored
+ * reduced products qhat_i = Y^T A Y phat_i (classical Gram-Schmidt, one pass, in the order
+ * i = 0..k). In exact arithmetic the correction is zero; in floating point CG directions
+ * lose their mutual A-orthogonality once the reduced residual has fallen far (cond(Y^T A Y)
+ * is large for an identity-metric POD basis), and stage three uses V2 as an explicit basis
+ * whose factor blockdiag(R, sqrt(T2)) assumes that orthogonality. */
 int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const double* b,
                   int y, const double* Y, int w, const double* R, const double* what,
                   double tol_abs, int kcap, int* k2, double* alpha, double* V2, double* T2,
@@ -513,6 +520,9 @@ int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const d
     double* qh = (double*)malloc(yb);
     double* th = (double*)malloc(yb);
     double* mu = (double*)malloc(sizeof(double) * (size_t)(w > 0 ? w : 1));
+    double* Ph = (double*)malloc(yb * (size_t)(kcap > 0 ? kcap : 1));   /* directions taken */
+    double* Qh = (double*)malloc(yb * (size_t)(kcap > 0 ? kcap : 1));   /* their reduced products */
+    double* cf = (double*)malloc(sizeof(double) * (size_t)(kcap > 0 ? kcap : 1));
     int k = 0, status = ORC_OK;
 
     for (int l = 0; l < y; ++l) xh[l] = (l < w) ? what[l] : 0.0;          /* step 1 */
@@ -536,6 +546,8 @@ int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const d
         double a = rz / gamma;
         alpha[k] = a;
         T2[k] = gamma;
+        memcpy(Ph + (size_t)k * y, ph, yb);
+        memcpy(Qh + (size_t)k * y, qh, yb);
         if (V2) memcpy(V2 + (size_t)k * n, v, nb);
         for (int l = 0; l < y; ++l) xh[l] += a * ph[l];
         for (int l = 0; l < y; ++l) rh[l] -= a * qh[l];
@@ -550,12 +562,23 @@ int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const d
         }
         for (int l = 0; l < y; ++l)
             ph[l] = zh[l] + beta * ph[l] - ((l < w && !MUT(12)) ? mu[l] : 0.0);
+        for (int i = 0; i <= k && !MUT(15); ++i) {          /* re-A-orthogonalisation */
+            double c = 0.0;
+            for (int l = 0; l < y; ++l) c += Qh[(size_t)i * y + l] * ph[l];
+            cf[i] = c / T2[i];
+        }
+        for (int l = 0; l < y && !MUT(15); ++l) {
+            double t = 0.0;
+            for (int i = 0; i <= k; ++i) t += cf[i] * Ph[(size_t)i * y + l];
+            ph[l] -= t;
+        }
         rz = rz_new;
         rnorm = sqrt(rr);
         ++k;
     }
     *k2 = k;
     *rhat_norm = rnorm;
+    free(cf); free(Qh); free(Ph);
     free(mu); free(th); free(qh); free(ph); free(zh); free(rh); free(xh); free(Av); free(v);
     return status;
 }
@@ -573,16 +596,19 @@ int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const d
  *               [W, V2]^T A [W, V2], known from stages one and two (Section 4.3).
  * info as orc_solve_system (info->w = w + k2, the stage-three basis dimension); *k2_out the
  * stage-two iterations; *s2_relres = ||b - A x_2||/||b|| at x_2 = W what + V2 alpha.
- * P_out/gamma_out/p_cap: stage-three directions as orc_aug_pcg. */
+ * P_out/gamma_out/p_cap: stage-three directions as orc_aug_pcg. tol3_rel >= 0 replaces
+ * tol_rel in stage three's own test only (stage two keeps tol2_rel * tol_rel * ||b||), so a
+ * run can be replayed to a given stage-three iteration count with tol3_rel = 0. */
 int orc_solve_system3(int n, const int* rp, const int* ci, const double* va, const double* b,
                       int y, const double* Y, int w, double tol_rel, double tol2_rel, int w3_cap,
                       int kmax, int max_refine, double* x, orc_info* info, int* k2_out,
-                      double* s2_relres, double* P_out, double* gamma_out, int p_cap)
+                      double* s2_relres, double* P_out, double* gamma_out, int p_cap, double tol3_rel)
 {
     memset(info, 0, sizeof(*info));
     if (w > y) w = y;
     double bnorm = sqrt(orc_dot(n, b, b));
     double tol_abs = tol_rel * bnorm;
+    double tol3_abs = (tol3_rel >= 0.0 ? tol3_rel : tol_rel) * bnorm;
     int cap = (y < w3_cap ? y : w3_cap);   /* room for w + k2 columns */
     if (cap < w) cap = w;
     int wt = cap;
@@ -632,7 +658,7 @@ int orc_solve_system3(int n, const int* rp, const int* ci, const double* va, con
     }
     int chol = info->chol_failed;
     double s1 = info->stage1_relres;
-    int st = orc_aug_pcg(n, rp, ci, va, b, w3, B, R3, what, tol_abs, kmax, max_refine, x, info,  /* stage three */
+    int st = orc_aug_pcg(n, rp, ci, va, b, w3, B, R3, what, tol3_abs, kmax, max_refine, x, info,  /* stage three */
                          P_out, gamma_out, p_cap);
     info->chol_failed = chol; info->stage1_relres = s1; info->w = w3;
     {

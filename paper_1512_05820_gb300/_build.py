@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libpodcg.so")
 
-SOURCES = ["k_sparse.cu", "k_dense.cu", "k_cg.cu", "k_mixed.cu", "k_adjoint.cu", "k_batch.cu", "engine.cu", "noalloc.cu", "k_gram_tc.cu"]
+SOURCES = ["k_sparse.cu", "k_dense.cu", "k_cg.cu", "k_mixed.cu", "k_adjoint.cu", "k_batch.cu", "engine.cu", "noalloc.cu",
+           "k_gram_tc.cu", "k_stage2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                 "-I", INCLUDE, "-I", CSRC]

@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "not_spd", 3: "breakdown", 4: "maxit", 5: 
 # every function the header declares (checked by the symbol-export test)
 EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_last_error",
            "pod_cg_add_snapshots", "pod_cg_clear_snapshots", "pod_cg_solve", "pod_cg_solve_adjoint",
-           "pod_cg_get_basis", "pod_cg_time_kernels", "pod_cg_tuning", "pod_cg_proj_tuning", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram", "pod_cg_gram_noalloc",
+           "pod_cg_get_basis", "pod_cg_get_stage3_basis", "pod_cg_time_kernels", "pod_cg_tuning", "pod_cg_proj_tuning", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram", "pod_cg_gram_noalloc",
            "pod_cg_gram_tc_workspace", "pod_cg_gram_tc", "pod_cg_diffusion_assemble",
            "pod_cg_diffusion_theta_grad", "pod_cg_batch_create", "pod_cg_batch_solve", "pod_cg_batch_info",
            "pod_cg_batch_last_error", "pod_cg_batch_destroy",
@@ -24,7 +24,8 @@ class Config(ctypes.Structure):
                 ("rank_tol", ctypes.c_double), ("k_max", ctypes.c_int), ("max_refine", ctypes.c_int),
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("use_tc_gram", ctypes.c_int),
                 ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int), ("loop_mode", ctypes.c_int),
-                ("proj_form", ctypes.c_int), ("spmv_lanes", ctypes.c_int)]
+                ("proj_form", ctypes.c_int), ("spmv_lanes", ctypes.c_int), ("three_stage", ctypes.c_int),
+                ("y_max", ctypes.c_int), ("energy_y", ctypes.c_double), ("tol_stage2", ctypes.c_double)]
 
 
 class CSRStruct(ctypes.Structure):
@@ -48,10 +49,11 @@ class Stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("w", ctypes.c_int), ("s", ctypes.c_int), ("chol_failed", ctypes.c_int),
                 ("system_id", ctypes.c_int), ("spmv_count", ctypes.c_int),
-                ("launches", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("launches", ctypes.c_int), ("y", ctypes.c_int), ("stage2_iters", ctypes.c_int),
+                ("pad_", ctypes.c_int),
                 ("stage1_relres", ctypes.c_double), ("final_relres", ctypes.c_double),
                 ("cond_gram", ctypes.c_double), ("ms_pod", ctypes.c_float), ("ms_stage1", ctypes.c_float),
-                ("ms_stage2", ctypes.c_float)]
+                ("ms_stage2", ctypes.c_float), ("ms_stage3", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}
@@ -89,6 +91,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_solve.argtypes = [vp, P(CSRStruct), vp, cd, vp, P(Stats)]
     L.pod_cg_solve_adjoint.argtypes = [vp, ci, P(CSRStruct), vp, cd, vp, P(Stats)]
     L.pod_cg_get_basis.argtypes = [vp, vp, P(ci)]
+    L.pod_cg_get_stage3_basis.argtypes = [vp, vp, vp, P(ci)]
     L.pod_cg_time_kernels.argtypes = [vp, P(CSRStruct), vp, ci, P(ctypes.c_float)]
     L.pod_cg_tuning.argtypes = [vp, P(ci), P(ctypes.c_float)]
     L.pod_cg_proj_tuning.argtypes = [vp, P(ci), P(ctypes.c_float)]

@@ -49,6 +49,18 @@ struct DevState {
     int dir_pending;   // the direction kernel of this iteration has work (chunked loops)
     int mixed;         // FP32 inner loop: a breakdown ends the inner pass instead of the solve
     int inner_break;   // set by an FP32 inner breakdown (mixed mode)
+    // stage two of the three-stage algorithm (Section 4.2)
+    int pod_y;         // augmenting-basis dimension y chosen by the POD (0: no stage two)
+    int w1;            // stage-one dimension after its Cholesky; stage two's basis starts here
+    int k2;            // stage-two iterations so far
+    int k2_cap;        // at most min(y, basis capacity) - w1 of them
+    int s2_done;       // stage two finished
+    int s2_break;      // it ended on a non-positive or non-finite (Y^T A Y p, p)
+    double tol_rel;    // the solve's relative tolerance (host-written)
+    double rho2;       // (rhat, rhat)
+    double tol2_s2;    // squared absolute stage-two tolerance
+    double rh[kSMax];  // reduced residual
+    double ph[kSMax];  // reduced direction
 };
 
 // Borrowed problem pointers of the current solve, read by the kernels of a captured

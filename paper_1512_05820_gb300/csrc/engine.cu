@@ -4,10 +4,14 @@
 // 32), its Gram S^T S (kept up to date one row per added snapshot), the POD basis W, A W,
 // the stage-one Gram and R^{-1}, the CG vectors, reduction scratch and the captured graphs.
 //
-// pod_cg_solve enqueues, on the handle's stream:
+// pod_cg_solve enqueues, on the handle's stream (stages numbered as in Section 4):
 //   POD (when the snapshots changed): Jacobi eigensolve of S^T S, truncation, lift W = S C
-//   stage one: A W, W^T [A W, b], Cholesky + R^{-1} + what, x0 = W what, r0 = b - A W what
-//   the stage-two loop, either
+//     (three-stage mode: lift the augmenting basis Y = S C and copy W = its first w columns)
+//   stage one: A W, W^T [A W, b] (three-stage: Y^T [A W, b]), Cholesky + R^{-1} + what
+//   stage two (three-stage mode only, k_stage2.cu): reduced augmented CG over range(Y),
+//     appending its directions V2 and A V2 to the basis buffers
+//   x0 = [W, V2] [what; alpha], r0 = b - [A W, A V2] [what; alpha]
+//   the stage-three loop (Algorithm 1 with basis [W, V2]), either
 //     loop_mode 0: one graph launch with two nested conditional while-nodes
 //        FP64 : outer (residual replacement) { init; first direction;
 //                 inner { q = A p; update; direction }; true residual }
@@ -91,10 +95,15 @@ struct Plan {
     KSpec init, dir0, spmv, upd, dir, res, mxproj, mxstart, mxaccum;
 };
 
+struct Stage2Plan {
+    KSpec bb, init, lift, apply;
+};
+
 struct GraphSlot {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int L = 0;
+    int yb = 0;   // stage-two graphs: the y bucket they were built for
     bool valid = false;
 };
 
@@ -151,10 +160,18 @@ struct pod_cg_t {
     int pod_w = 0;
 
     // basis and stage one
-    double* W = nullptr;        // ld x w_max
-    double* AW = nullptr;       // ld x w_max
+    double* W = nullptr;        // ld x wcap: W, then (three-stage) the stage-two basis V2
+    double* AW = nullptr;       // ld x wcap: A W, then A V2
     float* W32 = nullptr;       // mixed
     float* AW32 = nullptr;      // mixed
+    int wcap = 0;               // columns of the basis buffers: w_max, or kWMax in three-stage mode
+    double* Y = nullptr;        // three-stage: augmenting basis, ld x max(y_max, w_max)
+    float* Y32 = nullptr;       // three-stage, mixed: its FP32 copy (stage-one panels)
+    double* s2_hist = nullptr;  // three-stage: stage-two reduced directions, products, gammas
+    int pod_y = 0;              // augmenting-basis dimension of the current POD
+    int pod_y_used = 0;         // last solve: y when stage two ran, else 0
+    int k2 = 0, k2_launch = 0;  // last solve: stage-two iterations, their loop bodies run
+    bool w_clobbered = false;   // stage two wrote over W's columns (stage-one Cholesky failed)
     double* G = nullptr;        // kWMax x (kWMax + 1) row-major
     double* Rinv = nullptr;     // kWMax x kWMax
 
@@ -195,7 +212,9 @@ struct pod_cg_t {
 
     GraphSlot graphs[6];                // conditional graphs [width bucket]
     GraphSlot chunks[6];                // plain chunk graphs [width bucket]
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    GraphSlot s2graph;                  // stage-two conditional graph
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // solve timeline
+    cudaEvent_t tev[2] = {nullptr, nullptr};                              // autotuner timing
     int system_counter = 0;
 };
 
@@ -266,16 +285,16 @@ pod_cg_status choose_lanes(pod_cg_t* h, const pod_cg_csr* A, int* L_out)
             if (L > 4 * mean + 4 || L * 16 < mean) { ch.ms[k] = -1.0f; continue; }
             float tot = 0.0f;
             for (int rep = 0; rep < 4; ++rep) {
-                PODCG_CK(h, cudaEventRecord(h->ev[0], h->stream));
+                PODCG_CK(h, cudaEventRecord(h->tev[0], h->stream));
                 if (h->mixed)
                     PODCG_CK(h, launch_spmv_plain32(L, A->row_ptr, A->col, h->val32, h->p32, h->q32, A->n, h->sms,
                                                     h->stream));
                 else
                     PODCG_CK(h, launch_spmv_plain(L, A->row_ptr, A->col, A->val, h->p, h->q, A->n, h->sms, h->stream));
-                PODCG_CK(h, cudaEventRecord(h->ev[1], h->stream));
-                PODCG_CK(h, cudaEventSynchronize(h->ev[1]));
+                PODCG_CK(h, cudaEventRecord(h->tev[1], h->stream));
+                PODCG_CK(h, cudaEventSynchronize(h->tev[1]));
                 float ms = 0.0f;
-                cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+                cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]);
                 if (rep > 0) tot += ms;
             }
             ch.ms[k] = tot / 3.0f;
@@ -334,12 +353,12 @@ pod_cg_status choose_proj_form(pod_cg_t* h, int wb, int L)
         for (int k = 0; k < 2; ++k)
             for (int rep = 0; rep < 4; ++rep) {
                 PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
-                PODCG_CK(h, cudaEventRecord(h->ev[0], s));
+                PODCG_CK(h, cudaEventRecord(h->tev[0], s));
                 PODCG_CK(h, launch_spec(*ks[k], s));
-                PODCG_CK(h, cudaEventRecord(h->ev[1], s));
-                PODCG_CK(h, cudaEventSynchronize(h->ev[1]));
+                PODCG_CK(h, cudaEventRecord(h->tev[1], s));
+                PODCG_CK(h, cudaEventSynchronize(h->tev[1]));
                 float ms = 0.0f;
-                cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]);
+                cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]);
                 if (rep > 0) total += ms;
             }
         h->proj_ms[bi][form] = total / 3.0f;
@@ -425,7 +444,7 @@ void destroy_graph(GraphSlot& gs)
     gs = GraphSlot();
 }
 
-// The whole stage-two loop as one graph with two nested conditional while-nodes.
+// The whole stage-three loop as one graph with two nested conditional while-nodes.
 pod_cg_status build_conditional(pod_cg_t* h, int wb, int L, GraphSlot& gs)
 {
     cudaGraph_t P = nullptr, O = nullptr, I = nullptr;
@@ -489,6 +508,83 @@ pod_cg_status build_chunk(pod_cg_t* h, int wb, int L, GraphSlot& gs)
     return POD_CG_OK;
 }
 
+int s2_bucket(int y) { return y <= 8 ? 8 : y <= 16 ? 16 : y <= 32 ? 32 : y <= 48 ? 48 : 64; }
+
+// Stage two (Section 4.2; kernels in k_stage2.cu): ||b||^2, the reduced residual and first
+// direction, then lift / apply iterations while the reduced residual is above
+// tol_stage2 * tol * ||b|| and fewer than min(y, wcap) - w1 iterations ran. FP64 products
+// in both precisions: with FP32 products the reduced iteration's directions lose their
+// mutual A-orthogonality at about eps_32 cond(Y^T A Y), which the block-diagonal stage-three
+// factor cannot absorb (MIXED solves then stalled in stage three); MIXED converts the
+// directions to FP32 afterwards.
+void make_s2_plan(pod_cg_t* h, int L, bool cond, cudaGraphConditionalHandle hl, Stage2Plan& P)
+{
+    void *f_bb, *f_init, *f_lift, *f_apply;
+    stage2_kernels(h->pod_y, L, cond, &f_bb, &f_init, &f_lift, &f_apply);
+    const int n = h->n, ld = h->ld;
+    unsigned int* c = h->counters;
+    const ProbDesc* pd = h->pd;
+    P.bb.set(f_bb, occ_grid(h, f_bb, n, kBlock), pd, h->partials, c + 6 * kCounterStride, h->st);
+    P.init.set(f_init, 1, (const double*)h->G, kWMax + 1, (const double*)h->Rinv, h->st, h->wcap,
+               h->cfg.tol_stage2, hl);
+    P.lift.set(f_lift, occ_grid(h, f_lift, n, kBlock), n, ld, (const double*)h->Y, h->W, (const DevState*)h->st);
+    P.apply.set(f_apply, occ_grid(h, f_apply, n, kBlock), pd, ld, (const double*)h->Y, (const double*)h->W,
+                h->AW, h->partials, c + 7 * kCounterStride, h->st, h->Rinv, (const double*)h->G, kWMax + 1, h->s2_hist,
+                hl);
+}
+
+pod_cg_status build_s2_graph(pod_cg_t* h, int L, GraphSlot& gs)
+{
+    cudaGraph_t P = nullptr, B = nullptr;
+    PODCG_CK(h, cudaGraphCreate(&P, 0));
+    cudaGraphConditionalHandle hl;
+    PODCG_CK(h, cudaGraphConditionalHandleCreate(&hl, P, 0, 0));
+    Stage2Plan pl;
+    make_s2_plan(h, L, true, hl, pl);
+    cudaGraphNode_t a, b, c, d, e;
+    PODCG_CK(h, add_node(P, nullptr, 0, pl.bb, &a));
+    PODCG_CK(h, add_node(P, &a, 1, pl.init, &b));
+    PODCG_CK(h, add_while(P, &b, 1, hl, &c, &B));
+    PODCG_CK(h, add_node(B, nullptr, 0, pl.lift, &d));
+    PODCG_CK(h, add_node(B, &d, 1, pl.apply, &e));
+    cudaGraphExec_t exec = nullptr;
+    PODCG_CK(h, cudaGraphInstantiate(&exec, P, 0));
+    gs.graph = P;
+    gs.exec = exec;
+    gs.L = L;
+    gs.yb = s2_bucket(h->pod_y);
+    gs.valid = true;
+    return POD_CG_OK;
+}
+
+pod_cg_status read_state(pod_cg_t* h);
+
+pod_cg_status run_stage2(pod_cg_t* h, int L)
+{
+    cudaStream_t s = h->stream;
+    if (h->cfg.loop_mode == 0) {
+        GraphSlot& gs = h->s2graph;
+        if (gs.valid && (gs.L != L || gs.yb != s2_bucket(h->pod_y))) destroy_graph(gs);
+        if (!gs.valid) {
+            pod_cg_status bs = build_s2_graph(h, L, gs);
+            if (bs != POD_CG_OK) return bs;
+        }
+        PODCG_CK(h, cudaGraphLaunch(gs.exec, s));
+        return read_state(h);
+    }
+    Stage2Plan pl;
+    make_s2_plan(h, L, false, 0, pl);
+    PODCG_CK(h, launch_spec(pl.bb, s));
+    PODCG_CK(h, launch_spec(pl.init, s));
+    pod_cg_status rs = read_state(h);
+    for (int it = 0; rs == POD_CG_OK && !h->st_host->s2_done && it <= kWMax; ++it) {
+        PODCG_CK(h, launch_spec(pl.lift, s));
+        PODCG_CK(h, launch_spec(pl.apply, s));
+        rs = read_state(h);
+    }
+    return rs;
+}
+
 pod_cg_status read_state(pod_cg_t* h)
 {
     PODCG_CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
@@ -496,7 +592,7 @@ pod_cg_status read_state(pod_cg_t* h)
     return POD_CG_OK;
 }
 
-// Stage two: run the loop in the configured form.
+// Stage three: run the loop in the configured form.
 pod_cg_status run_loop(pod_cg_t* h, int wb, int L)
 {
     const int bi = bucket_index(wb);
@@ -553,7 +649,7 @@ cudaError_t dalloc(T** p, size_t count)
     return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
 }
 
-void reset_state(pod_cg_t* h, const pod_cg_csr* A, const double* b)
+void reset_state(pod_cg_t* h, const pod_cg_csr* A, const double* b, double tol)
 {
     *h->pd_host = ProbDesc{A->row_ptr, A->col, A->val, h->val32, b, nullptr, h->n, h->ld};
     DevState& sh = *h->st_host;
@@ -564,12 +660,16 @@ void reset_state(pod_cg_t* h, const pod_cg_csr* A, const double* b)
     sh.w = h->pod_w;
     sh.mixed = h->mixed ? 1 : 0;
     sh.rr_stage1 = -1.0;
+    sh.pod_y = h->pod_y;
+    sh.w1 = h->pod_w;
+    sh.s2_done = 1;
+    sh.tol_rel = tol;
 }
 
 pod_cg_status finish_solve(pod_cg_t* h, double* out, int w_pod, int launches, pod_cg_stats* stats, int sysid)
 {
     cudaStream_t s = h->stream;
-    PODCG_CK(h, cudaEventRecord(h->ev[3], s));
+    PODCG_CK(h, cudaEventRecord(h->ev[4], s));
     PODCG_CK(h, cudaMemcpyAsync(out, h->x, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, s));
     pod_cg_status rs = read_state(h);
     if (rs != POD_CG_OK) return rs;
@@ -583,15 +683,18 @@ pod_cg_status finish_solve(pod_cg_t* h, double* out, int w_pod, int launches, po
         stats->s = h->s_count;
         stats->chol_failed = d.chol_failed;
         stats->system_id = sysid;
-        stats->spmv_count = d.iters + w_pod + d.restarts + 1;
+        stats->spmv_count = d.iters + w_pod + d.restarts + 1 + h->k2;
         const int per_pass = h->mixed ? 6 : 3;
         stats->launches = launches + per_pass * (d.restarts + 1) + 3 * d.iters;
+        stats->y = h->pod_y_used;
+        stats->stage2_iters = h->k2;
         stats->stage1_relres = d.bb > 0.0 ? std::sqrt(std::max(d.rr_stage1, 0.0) / d.bb) : 0.0;
         stats->final_relres = d.bb > 0.0 ? std::sqrt(d.rr_true / d.bb) : 0.0;
         stats->cond_gram = d.cond;
         cudaEventElapsedTime(&stats->ms_pod, h->ev[0], h->ev[1]);
         cudaEventElapsedTime(&stats->ms_stage1, h->ev[1], h->ev[2]);
         cudaEventElapsedTime(&stats->ms_stage2, h->ev[2], h->ev[3]);
+        cudaEventElapsedTime(&stats->ms_stage3, h->ev[3], h->ev[4]);
     }
     if (d.status != 0) {
         static const char* names[] = {"ok", "arg", "not SPD (non-positive diagonal)", "breakdown: (Ap, p) <= 0",
@@ -628,6 +731,10 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->loop_mode = 0;
     c->proj_form = -1;
     c->spmv_lanes = 0;
+    c->three_stage = 0;
+    c->y_max = 40;
+    c->energy_y = 0.99999999;
+    c->tol_stage2 = 1e-4;
     return POD_CG_OK;
 }
 
@@ -641,7 +748,10 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     if (!h) return POD_CG_OK;
     for (auto& g : h->graphs) destroy_graph(g);
     for (auto& g : h->chunks) destroy_graph(g);
-    void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->G, h->Rinv,
+    destroy_graph(h->s2graph);
+    void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->Y, h->Y32,
+                    h->s2_hist,
+                    h->G, h->Rinv,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
                     h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
     for (void* b : bufs)
@@ -649,6 +759,8 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     if (h->st_host) cudaFreeHost(h->st_host);
     if (h->pd_host) cudaFreeHost(h->pd_host);
     for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto& e : h->tev)
         if (e) cudaEventDestroy(e);
     delete h;
     return POD_CG_OK;
@@ -669,6 +781,12 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
         (c.spmv_lanes != 0 && (c.spmv_lanes < 1 || c.spmv_lanes > 32 || (c.spmv_lanes & (c.spmv_lanes - 1)))) ||
         !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
         return fail(nullptr, POD_CG_ERR_ARG, "invalid configuration");
+    if (c.three_stage != 0 && (c.three_stage != 1 || c.y_max < 1 || c.y_max > c.s_max ||
+                               !(c.energy_y >= 0.0 && c.energy_y <= 1.0) ||
+                               !(c.tol_stage2 >= 0.0 && std::isfinite(c.tol_stage2))))
+        return fail(nullptr, POD_CG_ERR_ARG,
+                    "invalid three-stage configuration (three_stage 0/1, 1 <= y_max <= s_max, energy_y in [0, 1], "
+                    "tol_stage2 >= 0)");
     if (c.use_tc_gram != 0 && (c.use_tc_gram != 1 || c.precision != POD_CG_MIXED))
         return fail(nullptr, POD_CG_ERR_ARG,
                     "use_tc_gram needs precision MIXED: the tensor-core Gram rounds W and AW to FP32");
@@ -678,6 +796,8 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     h->ld = ((n + 31) / 32) * 32;
     h->cfg = c;
     h->mixed = c.precision == POD_CG_MIXED;
+    // three-stage mode appends up to y - w stage-two directions after W: room for kWMax
+    h->wcap = c.three_stage ? kWMax : c.w_max;
     if (c.proj_form >= 0)
         for (int& f : h->proj_form) f = c.proj_form;
     h->stream = (cudaStream_t)cuda_stream;
@@ -693,8 +813,13 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     PODCG_ALLOC(h->C, (size_t)kSMax * kWMax)
     PODCG_ALLOC(h->sigma2, (size_t)kSMax)
     PODCG_ALLOC(h->Vprev, (size_t)kSMax * kSMax)
-    PODCG_ALLOC(h->W, ld * c.w_max)
-    PODCG_ALLOC(h->AW, ld * c.w_max)
+    // stage two runs in FP64 in both precisions: its directions go to the FP64 W/AW buffers
+    PODCG_ALLOC(h->W, ld * h->wcap)
+    PODCG_ALLOC(h->AW, ld * h->wcap)
+    // Y holds y <= max(y_max, w_max) columns (y is raised to w when the energy rule gives less)
+    const size_t ycols = (size_t)std::max(c.y_max, c.w_max);
+    if (c.three_stage) PODCG_ALLOC(h->Y, ld * ycols)
+    if (c.three_stage) PODCG_ALLOC(h->s2_hist, (size_t)2 * kWMax * kSMax + kWMax)
     PODCG_ALLOC(h->G, (size_t)kWMax * (kWMax + 1))
     PODCG_ALLOC(h->Rinv, (size_t)kWMax * kWMax)
     PODCG_ALLOC(h->x, ld)
@@ -710,8 +835,9 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     PODCG_ALLOC(h->pd, 1)
     if (h->mixed) {
         PODCG_ALLOC(h->S32, ld * c.s_max)
-        PODCG_ALLOC(h->W32, ld * c.w_max)
-        PODCG_ALLOC(h->AW32, ld * c.w_max)
+        PODCG_ALLOC(h->W32, ld * h->wcap)
+        PODCG_ALLOC(h->AW32, ld * h->wcap)
+        if (c.three_stage) PODCG_ALLOC(h->Y32, ld * ycols)
         PODCG_ALLOC(h->r32, ld)
         PODCG_ALLOC(h->p32, ld)
         PODCG_ALLOC(h->q32, ld)
@@ -728,13 +854,19 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     if (e == cudaSuccess) {
         h->gram_work_bytes = std::max(gram_workspace_bytes(n, 1, c.s_max, h->sms),
                                       gram_workspace_bytes(n, c.w_max, c.w_max + 1, h->sms));
+        const int gp = c.three_stage ? std::max(c.w_max, c.y_max) : c.w_max;
+        h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, gp, c.w_max + 1, h->sms));
+        if (c.three_stage && h->mixed)   // the re-formed stage-three Gram, up to kWMax columns
+            h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, kWMax, kWMax + 1, h->sms));
         if (c.use_tc_gram)
-            h->gram_work_bytes = std::max(h->gram_work_bytes, gram_tc_workspace_bytes(n, c.w_max, c.w_max + 1, h->sms));
+            h->gram_work_bytes = std::max(h->gram_work_bytes, gram_tc_workspace_bytes(n, gp, c.w_max + 1, h->sms));
         e = cudaMalloc((void**)&h->gram_work, h->gram_work_bytes);
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->st_host, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->pd_host, sizeof(ProbDesc));
     for (auto& ev : h->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    for (auto& ev : h->tev)
         if (e == cudaSuccess) e = cudaEventCreate(&ev);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->counters, 0, (size_t)8 * kCounterStride * sizeof(unsigned int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->S, 0, sizeof(double) * ld * c.s_max, h->stream);
@@ -796,6 +928,24 @@ pod_cg_status pod_cg_get_basis(pod_cg_t* h, double* W_out, int* w_out)
     return POD_CG_OK;
 }
 
+pod_cg_status pod_cg_get_stage3_basis(pod_cg_t* h, double* B_out, double* AB_out, int* w3_out)
+{
+    if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
+    const int w3 = h->st_host ? h->st_host->w : 0;
+    if (w3_out) *w3_out = w3;
+    if ((B_out || AB_out) && w3 > 0) {
+        if (h->mixed) return fail(h, POD_CG_ERR_STATE, "the FP64 basis is not formed in mixed precision");
+        if (B_out)
+            PODCG_CK(h, cudaMemcpy2DAsync(B_out, sizeof(double) * h->n, h->W, sizeof(double) * h->ld,
+                                          sizeof(double) * h->n, w3, cudaMemcpyDeviceToDevice, h->stream));
+        if (AB_out)
+            PODCG_CK(h, cudaMemcpy2DAsync(AB_out, sizeof(double) * h->n, h->AW, sizeof(double) * h->ld,
+                                          sizeof(double) * h->n, w3, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    PODCG_CK(h, cudaStreamSynchronize(h->stream));
+    return POD_CG_OK;
+}
+
 pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, double tol, double* x_out,
                            pod_cg_stats* stats)
 {
@@ -815,7 +965,7 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         h->val32_cap = A->nnz;
     }
 
-    reset_state(h, A, b);
+    reset_state(h, A, b, tol);
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
@@ -826,64 +976,147 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         launches += 1;
     }
 
-    // POD of the current snapshots (Algorithm 4)
+    // SpMV lanes for this pattern (timed once per pattern, with the autotuner's own events)
+    int L = 1;
+    pod_cg_status lst = choose_lanes(h, A, &L);
+    if (lst != POD_CG_OK) return lst;
+    h->last_L = L;
+
+    // POD of the current snapshots (Algorithm 4); in three-stage mode also the augmenting
+    // basis Y, whose first w columns are W (nested POD bases)
+    const bool three = h->cfg.three_stage != 0;
     if (h->s_count > 0 && h->pod_dirty) {
         PODCG_CK(h, launch_pod_eig(h->GS, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, h->cfg.w_max, h->C,
-                                   h->sigma2, h->st, h->Vprev, h->vprev_s, s));
+                                   h->sigma2, h->st, h->Vprev, h->vprev_s, s, h->cfg.energy_y,
+                                   three ? h->cfg.y_max : 0));
         h->vprev_s = h->s_count;
-        if (h->mixed) PODCG_CK(h, launch_lift32(n, h->S32, h->ld, h->s_count, h->C, h->st, h->W32, h->ld, h->sms, s));
-        else PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->W, h->ld, h->sms, s));
+        if (three) {
+            PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->Y, h->ld, h->sms, s, 1));
+        } else {
+            if (h->mixed) PODCG_CK(h, launch_lift32(n, h->S32, h->ld, h->s_count, h->C, h->st, h->W32, h->ld, h->sms, s));
+            else PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->W, h->ld, h->sms, s));
+        }
         launches += 2;
         pod_cg_status rs = read_state(h);
         if (rs != POD_CG_OK) return rs;
         h->pod_w = h->st_host->pod_w;
+        h->pod_y = three ? h->st_host->pod_y : 0;
         h->pod_dirty = false;
+        h->w_clobbered = three;   // W is copied out of Y below
+        if (three && h->mixed && h->pod_y > 0) {
+            PODCG_CK(h, launch_to_f32(h->Y, h->Y32, (size_t)h->ld * h->pod_y, h->sms, s));
+            launches += 1;
+        }
     } else if (h->s_count == 0) {
         h->pod_w = 0;
+        h->pod_y = 0;
     }
     const int w = h->pod_w;
+    if (three && w > 0 && h->w_clobbered) {
+        PODCG_CK(h, cudaMemcpy2DAsync(h->W, sizeof(double) * h->ld, h->Y, sizeof(double) * h->ld,
+                                      sizeof(double) * n, w, cudaMemcpyDeviceToDevice, s));
+        if (h->mixed)
+            PODCG_CK(h, cudaMemcpy2DAsync(h->W32, sizeof(float) * h->ld, h->Y32, sizeof(float) * h->ld,
+                                          sizeof(float) * n, w, cudaMemcpyDeviceToDevice, s));
+        h->w_clobbered = false;
+    }
+    const int y = three ? h->pod_y : 0;
     PODCG_CK(h, cudaEventRecord(h->ev[1], s));
 
     // stage one (Algorithm 2)
     if (w > 0) {
         // Ahat = W^T [AW, b]: FP64 (or FP32-product) CUDA-core Gram, or in mixed precision
         // the tensor-core split-bf16 Gram when use_tc_gram is set (its TMA loads need a
-        // 16-byte aligned b; r is free until stage one writes it)
+        // 16-byte aligned b; r is free until stage one writes it). In three-stage mode the
+        // Gram is Y^T [AW, b]: its first w rows are W^T [AW, b], the rest feed stage two,
+        // and it stays on the CUDA cores: stage two's reduced residual Y^T b - Y^T A W what
+        // cancels, and the split-bf16 products' error (2^-16 of sum |y| |A w| per entry)
+        // left its deflation terms too loose for the block-diagonal stage-three factor.
         const double* bt = b;
         if (h->cfg.use_tc_gram && !gram_tc_aligned(b, 16)) {
             PODCG_CK(h, cudaMemcpyAsync(h->r, b, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
             bt = h->r;
         }
         int* tc_err = &h->st->status;
+        const int p = y > w ? y : w;
+        const int upper = y > w ? 0 : 1;
         if (h->mixed) {
+            const float* X32 = y > w ? h->Y32 : h->W32;
             PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32, h->ld, h->AW32, h->ld, n, w, h->sms, s));
-            if (h->cfg.use_tc_gram)
-                PODCG_CK(h, launch_gram_tc(n, h->W32, h->ld, w, h->AW32, h->ld, w, bt, h->G, kWMax + 1, h->gram_work,
+            if (h->cfg.use_tc_gram && y <= w)
+                PODCG_CK(h, launch_gram_tc(n, X32, h->ld, p, h->AW32, h->ld, w, bt, h->G, kWMax + 1, h->gram_work,
                                            h->gram_work_bytes, tc_err, h->sms, s));
             else
-                PODCG_CK(h, launch_gram32(n, h->W32, h->ld, w, h->AW32, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
+                PODCG_CK(h, launch_gram32(n, X32, h->ld, p, h->AW32, h->ld, w, b, h->G, kWMax + 1, upper, h->gram_work,
                                           h->gram_work_bytes, h->sms, s));
         } else {
+            const double* X = y > w ? h->Y : h->W;
             PODCG_CK(h, launch_spmm(A->row_ptr, A->col, A->val, h->W, h->ld, h->AW, h->ld, n, w, h->sms, s));
-            PODCG_CK(h, launch_gram(n, h->W, h->ld, w, h->AW, h->ld, w, b, h->G, kWMax + 1, 1, h->gram_work,
+            PODCG_CK(h, launch_gram(n, X, h->ld, p, h->AW, h->ld, w, b, h->G, kWMax + 1, upper, h->gram_work,
                                     h->gram_work_bytes, h->sms, s));
         }
         PODCG_CK(h, launch_chol(h->G, kWMax + 1, h->Rinv, h->st, h->cfg.cond_diag, s));
         launches += 4;
+    } else if (y > 0) {
+        // no stage-one basis (cannot happen with y >= w unless the POD is empty): stage two
+        // needs Y^T b alone, with w = 0
+        if (h->mixed)
+            PODCG_CK(h, launch_gram32(n, h->Y32, h->ld, y, nullptr, h->ld, 0, b, h->G, kWMax + 1, 0, h->gram_work,
+                                      h->gram_work_bytes, h->sms, s));
+        else
+            PODCG_CK(h, launch_gram(n, h->Y, h->ld, y, nullptr, h->ld, 0, b, h->G, kWMax + 1, 0, h->gram_work,
+                                    h->gram_work_bytes, h->sms, s));
+        launches += 2;
     }
-    const int wb = wb_bucket(w);
+    PODCG_CK(h, cudaEventRecord(h->ev[2], s));
+
+    // stage two (Section 4.2): iterative solve over range(Y), directions appended to the basis
+    h->k2 = 0;
+    h->pod_y_used = 0;
+    int w3 = w;
+    if (y > 0) {
+        pod_cg_status s2 = run_stage2(h, L);
+        if (s2 != POD_CG_OK) return s2;
+        const DevState& d = *h->st_host;
+        if (d.status != 0) return fail(h, (pod_cg_status)d.status, "stage two: device error status");
+        h->k2 = d.k2;
+        h->pod_y_used = y;
+        h->k2_launch = d.k2 + d.s2_break;
+        w3 = d.w;
+        if (d.w1 < w) h->w_clobbered = true;   // stage-one basis dropped: V2 starts at column 0
+        launches += 2 + 2 * h->k2_launch;
+        if (h->mixed && h->k2 > 0) {
+            // MIXED: stage three iterates on the FP32 basis [W32, V2_32], whose A-products
+            // come from the FP32 SpMM as A W32's do, and it re-forms that basis' Gram and
+            // Cholesky factor instead of taking blockdiag(R, sqrt(T2)): rounded to FP32, and
+            // multiplied by the FP32 matrix with its cancellation on smooth vectors, [W, V2]
+            // is A-orthogonal only to FP32 accuracy times that cancellation, and the FP32 inner
+            // CG needs a factor consistent with the basis it projects with (as stage one's W32
+            // gets one). The factor solve also replaces [what; alpha] by the Galerkin
+            // coordinates over range([W, V2]), which the stage-two solution equals in exact
+            // arithmetic.
+            const size_t off = (size_t)d.w1 * h->ld, cnt = (size_t)h->k2 * h->ld;
+            PODCG_CK(h, launch_to_f32(h->W + off, h->W32 + off, cnt, h->sms, s));
+            PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32 + off, h->ld, h->AW32 + off, h->ld, n,
+                                        h->k2, h->sms, s));
+            PODCG_CK(h, launch_gram32(n, h->W32, h->ld, w3, h->AW32, h->ld, w3, b, h->G, kWMax + 1, 1, h->gram_work,
+                                      h->gram_work_bytes, h->sms, s));
+            PODCG_CK(h, launch_chol(h->G, kWMax + 1, h->Rinv, h->st, h->cfg.cond_diag, s, w3));
+            pod_cg_status rs3 = read_state(h);
+            if (rs3 != POD_CG_OK) return rs3;
+            w3 = h->st_host->w;   // 0 if the re-formed Gram was not numerically SPD
+            launches += 5;
+        }
+    }
+    const int wb = wb_bucket(w3);
     if (h->mixed)
         PODCG_CK(h, launch_stage1_mx(wb, h->pd, n, h->W32, h->x, h->partials, h->counters + 4 * kCounterStride, h->st, tol, h->sms, s));
     else
         PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4 * kCounterStride, h->st, tol,
                                   h->sms, s));
-    PODCG_CK(h, cudaEventRecord(h->ev[2], s));
+    PODCG_CK(h, cudaEventRecord(h->ev[3], s));
 
-    // stage two
-    int L = 1;
-    pod_cg_status lst = choose_lanes(h, A, &L);
-    if (lst != POD_CG_OK) return lst;
-    h->last_L = L;
+    // stage three (Algorithm 1 with basis [W, V2])
     pod_cg_status ps = choose_proj_form(h, wb, L);
     if (ps != POD_CG_OK) return ps;
     pod_cg_status ls = run_loop(h, wb, L);
@@ -895,7 +1128,8 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     if (h->cfg.keep_factors > 0 && !h->mixed && fs == POD_CG_OK) {
         const int slot = h->k_next;
         h->k_next = (h->k_next + 1) % h->cfg.keep_factors;
-        const int wu = h->st_host->w;
+        // the stage-one basis (three-stage mode: without the stage-two directions)
+        const int wu = h->pod_y_used > 0 ? h->st_host->w1 : h->st_host->w;
         const size_t blk = (size_t)h->ld * h->cfg.w_max;
         if (wu > 0) {
             PODCG_CK(h, cudaMemcpyAsync(h->kW + slot * blk, h->W, sizeof(double) * h->ld * wu, cudaMemcpyDeviceToDevice, s));
@@ -936,7 +1170,8 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
     }
     h->pod_w = w;
     h->pod_dirty = h->s_count > 0;   // the next forward solve recomputes its own basis
-    reset_state(h, A, g);
+    h->w_clobbered = true;
+    reset_state(h, A, g, tol);
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
@@ -951,9 +1186,12 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
         launches += 3;
     }
     const int wb = wb_bucket(w);
+    PODCG_CK(h, cudaEventRecord(h->ev[2], s));
+    h->k2 = 0;
+    h->pod_y_used = 0;
     PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4 * kCounterStride, h->st, tol,
                               h->sms, s));
-    PODCG_CK(h, cudaEventRecord(h->ev[2], s));
+    PODCG_CK(h, cudaEventRecord(h->ev[3], s));
     int L = 1;
     pod_cg_status lst = choose_lanes(h, A, &L);
     if (lst != POD_CG_OK) return lst;
@@ -969,7 +1207,7 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
     if (cs != POD_CG_OK) return cs;
     if (!b || !ms_out || reps < 1) return fail(h, POD_CG_ERR_ARG, "bad arguments");
     cudaStream_t s = h->stream;
-    reset_state(h, A, b);
+    reset_state(h, A, b, 0.0);
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     DevState& t = *h->st_host;
     t.rho = 1.0;

@@ -142,14 +142,15 @@ cudaError_t launch_gram_reduce(const double* work, int splits, int tiles, int tj
     return cudaGetLastError();
 }
 
-// W[:, j] = sum_k S[:, k] C[k][j], k < s, j < w. C row-major s x w (row stride kWMax).
+// W[:, j] = sum_k S[:, k] C[k][j], k < s, j < w (w = st->pod_w, or st->pod_y when cols_y:
+// the augmenting basis Y). C row-major s x w (row stride kWMax).
 template <int SB>
 __global__ void __launch_bounds__(kBlock) k_lift(int n, const double* __restrict__ S, int lds, int s,
                                                  const double* __restrict__ C, const DevState* st,
-                                                 double* __restrict__ W, int ldw)
+                                                 double* __restrict__ W, int ldw, int cols_y)
 {
     __shared__ double sC[SB * kWMax];
-    const int w = st->pod_w;
+    const int w = cols_y ? st->pod_y : st->pod_w;
     for (int e = threadIdx.x; e < s * kWMax; e += blockDim.x) sC[e] = C[e];
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -167,14 +168,14 @@ __global__ void __launch_bounds__(kBlock) k_lift(int n, const double* __restrict
 }
 
 cudaError_t launch_lift(int n, const double* S, int lds, int s, const double* C, const DevState* st,
-                        double* W, int ldw, int sms, cudaStream_t str)
+                        double* W, int ldw, int sms, cudaStream_t str, int cols_y)
 {
     const int grid = grid_rows(n, kBlock, sms);
-    if (s <= 8) k_lift<8><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
-    else if (s <= 16) k_lift<16><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
-    else if (s <= 32) k_lift<32><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
-    else if (s <= 48) k_lift<48><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
-    else k_lift<64><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
+    if (s <= 8) k_lift<8><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
+    else if (s <= 16) k_lift<16><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
+    else if (s <= 32) k_lift<32><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
+    else if (s <= 48) k_lift<48><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
+    else k_lift<64><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
     return cudaGetLastError();
 }
 
@@ -391,7 +392,10 @@ struct SmallSmem {
 // POD of the snapshot Gram (Algorithm 4 steps 2-3): eigen-decompose G (s x s, row stride
 // kSMax), numerical rank = #{lambda_i > rank_tol lambda_1}, w = smallest index <= rank with
 // cumulative energy >= energy, capped at w_max; C[k][j] = v_j[k]/sigma_j (row stride kWMax);
-// sigma2[i] = lambda_i. w is written to st->pod_w (and st->w).
+// sigma2[i] = lambda_i. w is written to st->pod_w (and st->w). With y_max > 0 (three-stage
+// mode) the augmenting-basis dimension y is chosen the same way with energy_y, capped at
+// y_max and raised to w (POD bases are nested, so W is then the first w columns of Y), and
+// written to st->pod_y; C then has max(w, y) columns.
 //
 // Warm start: successive snapshot Grams differ in one row and column, so when the
 // eigenvectors of the previous Gram (Vprev, its first prev_s slots) are given, the
@@ -402,7 +406,8 @@ struct SmallSmem {
 __global__ void __launch_bounds__(kBlock) k_pod_eig(const double* __restrict__ G, int ldg, int s, double energy,
                                                     double rank_tol, int w_max, double* __restrict__ C,
                                                     double* __restrict__ sigma2, DevState* st,
-                                                    double* __restrict__ Vprev, int prev_s)
+                                                    double* __restrict__ Vprev, int prev_s, double energy_y,
+                                                    int y_max)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
@@ -470,7 +475,7 @@ __global__ void __launch_bounds__(kBlock) k_pod_eig(const double* __restrict__ G
         }
     __shared__ int s_w;
     if (tid == 0) {
-        int w = 0;
+        int w = 0, y = 0;
         if (s > 0 && sm.ev[0] > 0.0) {
             const double lam1 = sm.ev[0];
             int rank = 0;
@@ -479,30 +484,39 @@ __global__ void __launch_bounds__(kBlock) k_pod_eig(const double* __restrict__ G
             double total = 0.0;
             for (int i = 0; i < s; ++i) total += fmax(sm.ev[i], 0.0);
             w = rank;
+            y = rank;
             double cum = 0.0;
-            for (int i = 0; i < rank; ++i) {
+            bool got_w = false, got_y = false;
+            for (int i = 0; i < rank && !(got_w && got_y); ++i) {
                 cum += sm.ev[i];
-                if (cum / total >= energy) { w = i + 1; break; }
+                if (!got_w && cum / total >= energy) { w = i + 1; got_w = true; }
+                if (!got_y && cum / total >= energy_y) { y = i + 1; got_y = true; }
             }
             if (w > w_max) w = w_max;
+            // the augmenting basis (three-stage mode) holds the stage-one basis: y >= w
+            if (y > y_max) y = y_max;
+            if (y_max > 0 && y < w) y = w;
+            if (y_max <= 0) y = 0;
         }
-        s_w = w;
+        s_w = y > w ? y : w;
         st->pod_w = w;
         st->w = w;
+        st->pod_y = y;
     }
     __syncthreads();
-    const int w = s_w;
+    const int nc = s_w;   // columns of C: max(w, y)
     for (int i = tid; i < s; i += nt) sigma2[i] = sm.ev[i];
     for (int e = tid; e < s * kWMax; e += nt) {
         const int k = e / kWMax, j = e % kWMax;
-        C[e] = (j < w) ? sm.Vs[k * kSMax + j] / sqrt(sm.ev[j]) : 0.0;
+        C[e] = (j < nc) ? sm.Vs[k * kSMax + j] / sqrt(sm.ev[j]) : 0.0;
     }
 }
 
 size_t pod_eig_smem_bytes() { return sizeof(SmallSmem); }
 
 cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, double rank_tol, int w_max, double* C,
-                           double* sigma2, DevState* st, double* Vprev, int prev_s, cudaStream_t str)
+                           double* sigma2, DevState* st, double* Vprev, int prev_s, cudaStream_t str,
+                           double energy_y, int y_max)
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -511,24 +525,26 @@ cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, doubl
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_pod_eig<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, s, energy, rank_tol, w_max, C, sigma2, st, Vprev, prev_s);
+    k_pod_eig<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, s, energy, rank_tol, w_max, C, sigma2, st, Vprev, prev_s,
+                                                     energy_y, y_max);
     return cudaGetLastError();
 }
 
 // Stage one, small part (Algorithm 2 step 2): upper Cholesky R^T R of Ahat = G[:, :w]
-// (row-major, row stride ldg, upper triangle read), then R^{-1} (stored upper, row stride
-// kWMax) and what = R^{-1} R^{-T} bhat with bhat = G[:, w]. A non-positive pivot marks the
+// (row-major, row stride ldg, upper triangle read; w = w_dim, or st->pod_w when w_dim < 0),
+// then R^{-1} (stored upper, row stride kWMax) and what = R^{-1} R^{-T} bhat with
+// bhat = G[:, w]. A non-positive pivot marks the
 // basis unusable: chol_failed = 1 and w = 0 (plain PCG for this system). Optionally the
 // condition number of Ahat by the Jacobi eigensolver.
 __global__ void __launch_bounds__(kBlock) k_chol(const double* __restrict__ G, int ldg, double* __restrict__ Rinv,
-                                                 DevState* st, int want_cond)
+                                                 DevState* st, int want_cond, int w_dim)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
     double* R = sm.A;     // working copy, row stride kSMax
     double* X = sm.Vs;    // R^{-1}, row stride kSMax
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int w = st->pod_w;
+    const int w = w_dim >= 0 ? w_dim : st->pod_w;
     __shared__ int s_fail;
     if (tid == 0) s_fail = 0;
     for (int e = tid; e < kSMax * kSMax; e += nt) {
@@ -614,7 +630,8 @@ __global__ void __launch_bounds__(kBlock) k_chol(const double* __restrict__ G, i
     }
 }
 
-cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str)
+cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str,
+                        int w_dim)
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -623,7 +640,7 @@ cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, in
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_chol<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, Rinv, st, want_cond);
+    k_chol<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, Rinv, st, want_cond, w_dim);
     return cudaGetLastError();
 }
 

@@ -120,14 +120,15 @@ __global__ void __launch_bounds__(kBlock) k_mx_accum(int n, double* __restrict__
         x[i] += scale * double(d32[i]);
 }
 
-// W32[:, j] = sum_k S32[:, k] C[k][j] (C row stride kWMax, FP64 coefficients used in FP32).
+// W32[:, j] = sum_k S32[:, k] C[k][j] (C row stride kWMax, FP64 coefficients used in FP32),
+// j < st->pod_w, or j < st->pod_y when cols_y (the augmenting basis Y).
 template <int SB>
 __global__ void __launch_bounds__(kBlock) k_lift32(int n, const float* __restrict__ S, int lds, int s,
                                                    const double* __restrict__ C, const DevState* st,
-                                                   float* __restrict__ W, int ldw)
+                                                   float* __restrict__ W, int ldw, int cols_y)
 {
     __shared__ float sC[SB * kWMax];
-    const int w = st->pod_w;
+    const int w = cols_y ? st->pod_y : st->pod_w;
     for (int e = threadIdx.x; e < s * kWMax; e += blockDim.x) sC[e] = float(C[e]);
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -145,14 +146,14 @@ __global__ void __launch_bounds__(kBlock) k_lift32(int n, const float* __restric
 }
 
 cudaError_t launch_lift32(int n, const float* S, int lds, int s, const double* C, const DevState* st, float* W,
-                          int ldw, int sms, cudaStream_t str)
+                          int ldw, int sms, cudaStream_t str, int cols_y)
 {
     const int grid = grid_rows(n, kBlock, sms);
-    if (s <= 8) k_lift32<8><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
-    else if (s <= 16) k_lift32<16><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
-    else if (s <= 32) k_lift32<32><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
-    else if (s <= 48) k_lift32<48><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
-    else k_lift32<64><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw);
+    if (s <= 8) k_lift32<8><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
+    else if (s <= 16) k_lift32<16><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
+    else if (s <= 32) k_lift32<32><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
+    else if (s <= 48) k_lift32<48><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
+    else k_lift32<64><<<grid, kBlock, 0, str>>>(n, S, lds, s, C, st, W, ldw, cols_y);
     return cudaGetLastError();
 }
 

@@ -42,13 +42,15 @@ cudaError_t launch_gram(int n, const double* X, int ldx, int p, const double* Y,
                         const double* extra, double* G, int ldg, int upper_only, double* work,
                         size_t work_bytes, int sms, cudaStream_t s);
 cudaError_t launch_lift(int n, const double* S, int lds, int s, const double* C, const DevState* st,
-                        double* W, int ldw, int sms, cudaStream_t str);
+                        double* W, int ldw, int sms, cudaStream_t str, int cols_y = 0);
 cudaError_t launch_stage1(int wb, const ProbDesc* pd, int n, const double* W, const double* AW, double* x,
                           double* r, double* partials, unsigned int* counter, DevState* st, double tol, int sms,
                           cudaStream_t s);
 cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, double rank_tol, int w_max, double* C,
-                           double* sigma2, DevState* st, double* Vprev, int prev_s, cudaStream_t str);
-cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str);
+                           double* sigma2, DevState* st, double* Vprev, int prev_s, cudaStream_t str,
+                           double energy_y = 1.0, int y_max = 0);
+cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str,
+                        int w_dim = -1);
 cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
 
 // CG iteration (k_cg.cu): kernel pointers for graph construction
@@ -60,11 +62,15 @@ constexpr int kProjStaged = 1;
 void cg_kernels(int wb, bool fp32, bool cond, int form, void** init, void** upd, void** dir0, void** dir,
                 int* smem_upd, int* smem_dir);
 
+// stage two of the three-stage algorithm (k_stage2.cu, FP64): kernel pointers for graph
+// construction, y = the augmenting-basis dimension (selects the width bucket), L = SpMV lanes
+void stage2_kernels(int y, int L, bool cond, void** bb, void** init, void** lift, void** apply);
+
 // mixed precision (k_mixed.cu)
 void mixed_kernels(int wb, void** proj, void** start);
 void* kernel_mx_accum();
 cudaError_t launch_lift32(int n, const float* S, int lds, int s, const double* C, const DevState* st, float* W,
-                          int ldw, int sms, cudaStream_t str);
+                          int ldw, int sms, cudaStream_t str, int cols_y = 0);
 cudaError_t launch_stage1_mx(int wb, const ProbDesc* pd, int n, const float* W32, double* x, double* partials,
                              unsigned int* counter, DevState* st, double tol, int sms, cudaStream_t s);
 cudaError_t launch_gram32(int n, const float* X, int ldx, int p, const float* Y, int ldy, int qy, const double* extra,

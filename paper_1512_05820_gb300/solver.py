@@ -138,7 +138,7 @@ class PodCG:
         return lam_out, st.as_dict()
 
     def time_kernels(self, A: DeviceCSR, b: torch.Tensor, reps: int = 20) -> list[float]:
-        """Mean ms per launch of the stage-two kernels [spmv_cg, update, direction, residual]
+        """Mean ms per launch of the stage-three kernels [spmv_cg, update, direction, residual]
         (CUDA events on the handle's stream), on the basis of the last solve."""
         ms = (ctypes.c_float * 4)()
         A_s = A.struct()
@@ -171,6 +171,15 @@ class PodCG:
         buf = torch.empty((self.cfg.w_max, self.n), dtype=torch.float64, device="cuda")
         _check(self.L.pod_cg_get_basis(self.h, buf.data_ptr(), ctypes.byref(w)), self.h)
         return buf[: w.value].t()
+
+    def stage3_basis(self) -> tuple[torch.Tensor, torch.Tensor]:
+        """Stage three's augmenting basis [W, V2] of the last solve and A [W, V2], as (n, w3)
+        tensors (FP64 handles)."""
+        w3 = ctypes.c_int(0)
+        B = torch.empty((64, self.n), dtype=torch.float64, device="cuda")
+        AB = torch.empty((64, self.n), dtype=torch.float64, device="cuda")
+        _check(self.L.pod_cg_get_stage3_basis(self.h, B.data_ptr(), AB.data_ptr(), ctypes.byref(w3)), self.h)
+        return B[: w3.value].t(), AB[: w3.value].t()
 
 
 # ------------------------------------------------------------------ stateless steps

@@ -397,8 +397,39 @@ def pin_three_stage_collapse(orc):
     return ok, f"collapse: bitwise {np.array_equal(x1, x3)}, k2={i3['k2']}, iters {i1['iters']}/{i3['iters']}"
 
 
+def pin_stage_two_reorthogonalised(orc):
+    """An ill-conditioned reduced system (cond(Y^T A Y) ~ 1e5: Y holds the 20 lowest and 20
+    highest eigenvectors of a 24x24 diffusion operator with coefficients exp(N(0, 2^2)),
+    perturbed) run to y - w stage-two iterations: the stage-two basis stays A-orthogonal
+    (V2^T A V2 diagonal to 1e-10 in the A-normalised columns) and the result is the
+    Galerkin solution over range(Y) (dense LAPACK solve) to 1e-10. Without the stage-two
+    re-A-orthogonalisation the directions lose orthogonality completely here."""
+    rng = np.random.default_rng(3)
+    op = DiffusionOperator((24, 24))
+    A = op.csr(np.exp(rng.normal(0, 2.0, op.n)))
+    D = A.todense()
+    _, V = np.linalg.eigh(D)
+    b = D @ rng.normal(size=A.n)
+    idx = np.concatenate([np.arange(20), np.arange(A.n - 20, A.n)])
+    Y = orth_basis((V[:, idx] + 1e-3 * rng.normal(size=(A.n, 40))).T)
+    w = 3
+    W = np.asfortranarray(Y[:, :w])
+    what, R, _ = orc.stage_one(A.arrays(), b, W)
+    out = orc.stage_two(A.arrays(), b, Y, w, R, what, 0.0, 40 - w)
+    V2 = out["V2"]
+    C = V2.T @ D @ V2
+    na = np.sqrt(np.diag(C))
+    Cn = C / np.outer(na, na)
+    off = float(np.max(np.abs(Cn - np.diag(np.diag(Cn)))))
+    x2 = W @ what + V2 @ out["alpha"]
+    xg = Y @ np.linalg.solve(Y.T @ D @ Y, Y.T @ b)
+    e = a_norm(D, x2 - xg) / a_norm(D, xg)
+    return off < 1e-10 and e < 1e-10, f"ill-conditioned stage two: V2 A-orthogonality {off:.1e}, Galerkin err {e:.1e}"
+
+
 ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
             pin_finite_termination, pin_theta_grad_complex_step, pin_stage_two_optimality,
-            pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse]
+            pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse,
+            pin_stage_two_reorthogonalised]

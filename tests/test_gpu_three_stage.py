@@ -1,0 +1,181 @@
+"""Three-stage solves (Section 4: stage two over the augmenting basis Y, then stage three
+augmented with [W, V2]) on the GPU against the FP64 oracle, through the C ABI.
+
+FP64 tolerances: the GPU handle gets the oracle's previous solutions as snapshots, so both
+sides build the same bases up to rounding; per system w, y and the stage-two count k2
+equal the oracle's, stage-three iterations agree within 1 (summation order), and
+||x - x_orc||_A / ||x_orc||_A <= 1e-10 (with the same equal-step rule as the two-stage
+parity tests when the stage-three counts differ by one); the final true residual is <= tol.
+The stage-three basis the GPU builds satisfies Section 4.2's properties V2^T A W = 0 and
+V2^T A V2 = diag(T2) to rounding (relative to the A-norms of the columns).
+MIXED: the FP64 true residual reaches tol for every system, and the solution is within
+1e-5 (A-norm, relative) of the FP64 oracle's three-stage solution, the same bound as the
+two-stage mixed test; stage two runs in FP64 there too and takes the oracle's k2.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, OracleSequence
+from paper_1512_05820_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_05820_gb300 import _lib
+    _lib.load()
+    return torch.device("cuda:0")
+
+
+def to_dev(a, dev):
+    return torch.as_tensor(np.ascontiguousarray(a), device=dev)
+
+
+def a_err(orc, A, x, xo):
+    dx = x - xo
+    num = dx @ orc.spmv(A, dx)
+    den = xo @ orc.spmv(A, xo)
+    return float(np.sqrt(max(num, 0.0) / den))
+
+
+def run_three_stage(dev, seq, cfg, n_systems=None, tol_a=1e-10, check_basis=False, mixed=False):
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    orc = Oracle()
+    oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc,
+                          three_stage=True, y_max=cfg["y_max"], energy_y=cfg["energy_y"],
+                          tol_stage2=cfg["tol_stage2"])
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, three_stage=1,
+                   precision=1 if mixed else 0, **cfg)
+    A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+    out = []
+    for j, val, b in seq.systems():
+        if n_systems and j > n_systems:
+            break
+        A = (seq.row_ptr, seq.col, val)
+        Y, w1 = oseq.basis_y()
+        x, st = solver.solve(A0.with_values(to_dev(val, dev)), to_dev(b, dev), seq.tol)
+        xo, info = oseq.solve(A, b, seq.tol)
+        solver.add_snapshots(to_dev(xo, dev))
+        x = x.cpu().numpy()
+        true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
+        assert st["status"] == "ok", st
+        assert true_rel <= seq.tol and st["final_relres"] <= seq.tol
+        assert st["y"] == info["y"] or (st["stage2_iters"] == 0 and info["k2"] == 0)
+        assert st["stage2_iters"] == info["k2"], (j, st["stage2_iters"], info["k2"])
+        assert st["w"] == info["w"], (j, st["w"], info["w"])
+        if mixed:
+            assert a_err(orc, A, x, xo) <= 1e-5
+            out.append((j, st, info))
+            continue
+        assert abs(st["iters"] - info["iters"]) <= 1, (j, st["iters"], info["iters"])
+        if st["iters"] != info["iters"] and st["refinements"] == 0 and info["refinements"] == 0:
+            # the stage-three exit test met its threshold within rounding on one side only:
+            # compare with the oracle's iterate after the GPU's number of stage-three steps
+            xo_k, info_k, _, _ = orc.solve_system3(A, b, Y, w1, seq.tol, cfg["tol_stage2"], kmax=st["iters"],
+                                                   max_refine=0, tol3_rel=0.0)
+            assert info_k["iters"] == st["iters"] and info_k["k2"] == info["k2"]
+            err = a_err(orc, A, x, xo_k)
+        else:
+            err = a_err(orc, A, x, xo)
+        assert err <= tol_a, f"system {j}: A-norm diff {err:.2e}"
+        if check_basis and st["stage2_iters"] > 0:
+            B, AB = solver.stage3_basis()
+            B, AB = B.cpu().numpy(), AB.cpu().numpy()
+            w3 = st["w"]
+            assert B.shape[1] == w3
+            wk = w3 - st["stage2_iters"]
+            Av = np.stack([orc.spmv(A, B[:, k]) for k in range(w3)], axis=1)
+            assert np.max(np.abs(AB - Av)) <= 1e-12 * np.max(np.abs(Av))
+            na = np.sqrt(np.einsum("ij,ij->j", B, Av))
+            C = (B.T @ Av) / np.outer(na, na)
+            if wk > 0:
+                assert np.max(np.abs(C[:wk, wk:])) <= 1e-8, np.max(np.abs(C[:wk, wk:]))
+            V = C[wk:, wk:]
+            assert np.max(np.abs(V - np.diag(np.diag(V)))) <= 1e-8
+        out.append((j, st, info))
+    solver.close()
+    return out
+
+
+CFG = dict(y_max=12, energy_y=1 - 1e-10, tol_stage2=0.0)
+
+
+def test_three_stage_3d_full_stage_two(dev):
+    """20^3 moving-source sequence, window 12, stage-one energy 0.99 (w small), Y = all POD
+    modes: stage two runs to min(y, 64) - w iterations (tol_stage2 = 0), then stage three."""
+    seq = wl.diffusion3d_moving(m=20, p=10, s_max=12, w_max=16, period=12)
+    seq.energy = 0.99
+    out = run_three_stage(dev, seq, CFG, check_basis=True)
+    assert max(st["stage2_iters"] for _, st, _ in out) >= 3
+
+
+def test_three_stage_2d_ragged_tolerance_stop(dev):
+    """A 37x37 grid (n = 1369, not a multiple of the block): stage two stopped by its
+    tolerance (tol_stage2 = 1e-1) before the cap."""
+    seq = wl.diffusion2d_drift(m=37, p=8, w_max=16)
+    seq.energy = 0.99
+    cfg = dict(y_max=10, energy_y=1 - 1e-10, tol_stage2=1e-1)
+    run_three_stage(dev, seq, cfg)
+
+
+def test_three_stage_loop_modes_bitwise(dev):
+    """The conditional-graph stage-two loop and the host-driven one launch the same kernels
+    in the same order: bitwise equal solutions."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=16, p=6, s_max=6, w_max=8, period=10)
+    xs = {}
+    for mode in (0, 1):
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=0.99, three_stage=1, loop_mode=mode,
+                       **dict(CFG, y_max=seq.s_max))
+        A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+        res = []
+        for j, val, b in seq.systems():
+            x, st = solver.solve(A0.with_values(to_dev(val, dev)), to_dev(b, dev), seq.tol)
+            solver.add_snapshots(x)
+            res.append((x.clone(), st["stage2_iters"], st["iters"]))
+        xs[mode] = res
+        solver.close()
+    for (a, k2a, ia), (b, k2b, ib) in zip(xs[0], xs[1]):
+        assert torch.equal(a, b) and k2a == k2b and ia == ib
+
+
+def test_three_stage_collapse_is_two_stage(dev):
+    """y_max = 1 gives y = w (the augmenting basis is the stage-one basis): no stage-two
+    iteration, and the solve is the two-stage solve bit for bit."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=16, p=5, s_max=6, w_max=8, period=10)
+    runs = []
+    for three in (0, 1):
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, three_stage=three, y_max=1)
+        A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+        res = []
+        for j, val, b in seq.systems():
+            x, st = solver.solve(A0.with_values(to_dev(val, dev)), to_dev(b, dev), seq.tol)
+            solver.add_snapshots(x)
+            res.append((x.clone(), st))
+        runs.append(res)
+        solver.close()
+    for (a, sa), (b, sb) in zip(runs[0], runs[1]):
+        assert sb["stage2_iters"] == 0 and sa["w"] == sb["w"]
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("loop_mode", [0, 1])
+def test_three_stage_mixed_precision(dev, loop_mode):
+    """FP32 stage two and FP32 stage-three inner CG inside FP64 refinement."""
+    seq = wl.diffusion3d_moving(m=20, p=8, s_max=10, w_max=16, period=12)
+    seq.energy = 0.99
+    run_three_stage(dev, seq, dict(CFG, y_max=seq.s_max, loop_mode=loop_mode), mixed=True)
+
+
+def test_three_stage_config_errors(dev):
+    from paper_1512_05820_gb300.solver import PodCG, PodCGError
+    for bad in (dict(three_stage=1, y_max=0), dict(three_stage=1, y_max=41), dict(three_stage=1, energy_y=1.5),
+                dict(three_stage=1, tol_stage2=-1.0), dict(three_stage=2)):
+        with pytest.raises(PodCGError) as e:
+            PodCG(100, **bad)
+        assert e.value.status == 1

@@ -31,6 +31,7 @@ MUTANTS = {
     12: "stage two drops the stage-one deflation term from the direction update",
     13: "stage-three factor takes T2 instead of its square root",
     14: "stage-two initial residual omits the stage-one solution's product",
+    15: "stage two skips the re-A-orthogonalisation of its directions",
 }
 
 
