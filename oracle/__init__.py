@@ -105,6 +105,8 @@ class Oracle:
         lib.orc_solve_system3.argtypes = [ci, vp, vp, vp, vp, ci, vp, ci, cd, cd, ci, ci, ci, vp,
                                           ctypes.POINTER(_Info), ctypes.POINTER(ci), ctypes.POINTER(cd),
                                           vp, vp, ci, cd]
+        lib.orc_solve_system3_it.argtypes = [ci, vp, vp, vp, vp, ci, vp, ci, cd, cd, cd, ci, ci, vp,
+                                             ctypes.POINTER(_Info), ctypes.POINTER(ci), ctypes.POINTER(ci)]
 
     # -- Section 2 / basic kernels -------------------------------------------------
     def spmv(self, A, x):
@@ -279,6 +281,26 @@ class Oracle:
         d["stage2_relres"] = s2.value
         return x, d, P, g
 
+    def solve_system3_it(self, A, b, Y, w, tol_rel, tol2_rel, tol_in, kmax=100000, max_refine=5):
+        """Three-stage solve with the stage-three option of Section 4.3.1: stage three
+        augments with the entire Y, each augmentation solve an inner reduced solve to
+        tol_in * ||Y^T A z||. info gains k2 (stage-two iterations) and inner (inner reduced
+        iterations, summed)."""
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        n = len(rp) - 1
+        b = _f64(b)
+        Y = _f64(Y if Y is not None else np.zeros((n, 0)))
+        x = np.empty(n)
+        info = _Info()
+        k2, inner = ctypes.c_int(0), ctypes.c_int(0)
+        self.lib.orc_solve_system3_it(n, _p(rp), _p(col), _p(val), _p(b), Y.shape[1], _p(Y), w, tol_rel, tol2_rel,
+                                      tol_in, kmax, max_refine, _p(x), ctypes.byref(info), ctypes.byref(k2),
+                                      ctypes.byref(inner))
+        d = _info_dict(info)
+        d["k2"] = k2.value
+        d["inner"] = inner.value
+        return x, d
+
 
 def _info_dict(info: _Info) -> dict:
     return {"status": STATUS.get(info.status, str(info.status)), "iters": info.iters,
@@ -296,17 +318,21 @@ class OracleSequence:
     With ``three_stage`` the POD also gives the augmenting basis Y (energy ``energy_y``,
     at most ``y_max`` modes, never fewer than the stage-one dimension w, so that W is the
     first w columns of Y: POD bases are nested) and each system runs the three-stage
-    algorithm (Section 4) with stage-two tolerance ``tol_stage2`` times the system's.
+    algorithm (Section 4) with stage-two tolerance ``tol_stage2`` times the system's;
+    ``stage3_full`` selects the stage-three option of Section 4.3.1 (augmenting with all of
+    Y, inner reduced solves to ``tol_inner``).
     """
 
     def __init__(self, n: int, s_max: int = 40, w_max: int = 32, energy: float = 0.9999,
                  kmax: int = 100000, max_refine: int = 5, oracle: Oracle | None = None,
                  three_stage: bool = False, y_max: int = 40, energy_y: float = 1.0,
-                 tol_stage2: float = 1e-4, w3_cap: int = 64):
+                 tol_stage2: float = 1e-4, w3_cap: int = 64, stage3_full: bool = False,
+                 tol_inner: float = 1e-12):
         self.n, self.s_max, self.w_max, self.energy = n, s_max, w_max, energy
         self.kmax, self.max_refine = kmax, max_refine
         self.three_stage, self.y_max, self.energy_y = three_stage, y_max, energy_y
         self.tol_stage2, self.w3_cap = tol_stage2, w3_cap
+        self.stage3_full, self.tol_inner = stage3_full, tol_inner
         self.orc = oracle or Oracle()
         self.snaps: list[np.ndarray] = []
 
@@ -336,8 +362,12 @@ class OracleSequence:
     def solve(self, A, b, tol_rel, record: bool = True):
         if self.three_stage:
             Y, w = self.basis_y()
-            x, info, _, _ = self.orc.solve_system3(A, b, Y, w, tol_rel, self.tol_stage2, self.w3_cap,
-                                                   self.kmax, self.max_refine)
+            if self.stage3_full:
+                x, info = self.orc.solve_system3_it(A, b, Y, w, tol_rel, self.tol_stage2, self.tol_inner,
+                                                    self.kmax, self.max_refine)
+            else:
+                x, info, _, _ = self.orc.solve_system3(A, b, Y, w, tol_rel, self.tol_stage2, self.w3_cap,
+                                                       self.kmax, self.max_refine)
             info["s"] = len(self.snaps)
             info["y"] = Y.shape[1]
             if record:

@@ -504,10 +504,10 @@ static void orc_reduced_product(int n, const int* rp, const int* ci, const doubl
  * lose their mutual A-orthogonality once the reduced residual has fallen far (cond(Y^T A Y)
  * is large for an identity-metric POD basis), and stage three uses V2 as an explicit basis
  * whose factor blockdiag(R, sqrt(T2)) assumes that orthogonality. */
-int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const double* b,
-                  int y, const double* Y, int w, const double* R, const double* what,
-                  double tol_abs, int kcap, int* k2, double* alpha, double* V2, double* T2,
-                  double* rhat_norm)
+static int orc_stage_two_hist(int n, const int* rp, const int* ci, const double* va, const double* b,
+                              int y, const double* Y, int w, const double* R, const double* what,
+                              double tol_abs, int kcap, int* k2, double* alpha, double* V2, double* T2,
+                              double* rhat_norm, double* Ph_out, double* Qh_out)
 {
     size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1);
     size_t yb = sizeof(double) * (size_t)(y > 0 ? y : 1);
@@ -578,9 +578,20 @@ int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const d
     }
     *k2 = k;
     *rhat_norm = rnorm;
+    if (Ph_out) memcpy(Ph_out, Ph, yb * (size_t)k);
+    if (Qh_out) memcpy(Qh_out, Qh, yb * (size_t)k);
     free(cf); free(Qh); free(Ph);
     free(mu); free(th); free(qh); free(ph); free(zh); free(rh); free(xh); free(Av); free(v);
     return status;
+}
+
+int orc_stage_two(int n, const int* rp, const int* ci, const double* va, const double* b,
+                  int y, const double* Y, int w, const double* R, const double* what,
+                  double tol_abs, int kcap, int* k2, double* alpha, double* V2, double* T2,
+                  double* rhat_norm)
+{
+    return orc_stage_two_hist(n, rp, ci, va, b, y, Y, w, R, what, tol_abs, kcap, k2, alpha, V2, T2, rhat_norm,
+                              NULL, NULL);
 }
 
 /* One system by the three-stage algorithm (Section 4; the overall algorithm with the stage-
@@ -672,6 +683,256 @@ int orc_solve_system3(int n, const int* rp, const int* ci, const double* va, con
     *k2_out = k2;
     free(vv); free(T2); free(R3); free(B); free(what); free(R);
     return st;
+}
+
+/* ----------------------------------- stage three over the entire augmenting basis (4.3.1) */
+
+/* Inner reduced solve of the "it" stage three (Section 4.3.1): Algorithm 1 on
+ *     (Y^T A Y) mu = chat
+ * with augmenting basis Psi = [Phi, psi_0 .. psi_{m-1}] (the stage-one coordinates Phi and
+ * the reduced directions stored so far by stage two and by earlier inner solves; their
+ * factor is blockdiag(R, sqrt(g_i)) by construction), preconditioner M = I and absolute
+ * tolerance tol_abs on ||rhat||. Reading: the solve starts from the Galerkin solution over
+ * range(Psi), mu0 = Phi R^{-1} R^{-T} Phi^T chat + sum_i psi_i (psi_i^T chat) / g_i; from
+ * mu0 = 0, as printed, Psi^T rhat would keep the value Psi^T chat (every direction is
+ * A-orthogonal to Psi) and the residual could not fall below it. The directions it takes are
+ * appended to Psi (psi, their reduced products qpsi and g; at most m_cap in total) and each
+ * new direction is re-A-orthogonalised against all stored ones, as in stage two. The
+ * augmentation right-hand side Phi^T (Y^T A Y) zhat is formed literally, with a reduced
+ * product. mu (length y) receives the solution; returns the iterations taken. */
+static int orc_inner_solve(int n, const int* rp, const int* ci, const double* va, int y, const double* Y,
+                           int w, const double* R, double* psi, double* qpsi, double* g, int* m, int m_cap,
+                           const double* chat, double tol_abs, double* mu)
+{
+    size_t yb = sizeof(double) * (size_t)(y > 0 ? y : 1);
+    double* v = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* Av = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double* rh = (double*)malloc(yb);
+    double* ph = (double*)malloc(yb);
+    double* qh = (double*)malloc(yb);
+    double* th = (double*)malloc(yb);
+    double* nu = (double*)malloc(sizeof(double) * (size_t)(w > 0 ? w : 1));
+    double* cf = (double*)malloc(sizeof(double) * (size_t)(m_cap > 0 ? m_cap : 1));
+    int k = 0;
+    /* Galerkin start over range(Psi) */
+    for (int l = 0; l < y; ++l) mu[l] = 0.0;
+    if (w > 0 && !MUT(16)) {
+        orc_chol_solve(w, R, chat, nu);
+        for (int a = 0; a < w; ++a) mu[a] += nu[a];
+    }
+    for (int i = 0; i < *m && !MUT(16); ++i) {
+        double c = 0.0;
+        for (int l = 0; l < y; ++l) c += psi[(size_t)i * y + l] * chat[l];
+        c /= g[i];
+        for (int l = 0; l < y; ++l) mu[l] += c * psi[(size_t)i * y + l];
+    }
+    orc_reduced_product(n, rp, ci, va, y, Y, mu, v, Av, qh);      /* rhat0 = chat - Ahat mu0 */
+    for (int l = 0; l < y; ++l) rh[l] = chat[l] - qh[l];
+    if (w > 0) {                                                   /* zhat = rhat (M = I); aug */
+        orc_reduced_product(n, rp, ci, va, y, Y, rh, v, Av, th);
+        orc_chol_solve(w, R, th, nu);
+    }
+    for (int l = 0; l < y; ++l) ph[l] = rh[l] - ((l < w) ? nu[l] : 0.0);
+    for (int i = 0; i < *m; ++i) {
+        double c = 0.0;
+        for (int l = 0; l < y; ++l) c += qpsi[(size_t)i * y + l] * ph[l];
+        cf[i] = c / g[i];
+    }
+    for (int l = 0; l < y; ++l) {
+        double t = 0.0;
+        for (int i = 0; i < *m; ++i) t += cf[i] * psi[(size_t)i * y + l];
+        ph[l] -= t;
+    }
+    double rz = 0.0;
+    for (int l = 0; l < y; ++l) rz += rh[l] * rh[l];
+    double rnorm = sqrt(rz);
+    while (rnorm > tol_abs && *m < m_cap) {
+        orc_reduced_product(n, rp, ci, va, y, Y, ph, v, Av, qh);
+        double gamma = 0.0;
+        for (int l = 0; l < y; ++l) gamma += qh[l] * ph[l];
+        if (!isfinite(gamma) || !(gamma > 0.0)) break;
+        memcpy(psi + (size_t)(*m) * y, ph, yb);
+        memcpy(qpsi + (size_t)(*m) * y, qh, yb);
+        g[*m] = gamma;
+        *m += 1;
+        double a = rz / gamma;
+        for (int l = 0; l < y; ++l) mu[l] += a * ph[l];
+        for (int l = 0; l < y; ++l) rh[l] -= a * qh[l];
+        double rz_new = 0.0;
+        for (int l = 0; l < y; ++l) rz_new += rh[l] * rh[l];
+        double beta = rz_new / rz;
+        if (w > 0) {
+            orc_reduced_product(n, rp, ci, va, y, Y, rh, v, Av, th);
+            orc_chol_solve(w, R, th, nu);
+        }
+        for (int l = 0; l < y; ++l) ph[l] = rh[l] + beta * ph[l] - ((l < w) ? nu[l] : 0.0);
+        for (int i = 0; i < *m; ++i) {
+            double c = 0.0;
+            for (int l = 0; l < y; ++l) c += qpsi[(size_t)i * y + l] * ph[l];
+            cf[i] = c / g[i];
+        }
+        for (int l = 0; l < y; ++l) {
+            double t = 0.0;
+            for (int i = 0; i < *m; ++i) t += cf[i] * psi[(size_t)i * y + l];
+            ph[l] -= t;
+        }
+        rz = rz_new;
+        rnorm = sqrt(rz);
+        ++k;
+    }
+    free(cf); free(nu); free(th); free(qh); free(ph); free(rh); free(Av); free(v);
+    return k;
+}
+
+/* One system by the three-stage algorithm with the stage-three option of Section 4.3.1
+ * (orthogonalisation against the entire augmenting subspace, the "it" variant):
+ *   stage one   Algorithm 2 on W = the first w columns of Y (R, what);
+ *   stage two   Section 4.2 to tol2_rel * tol_rel * ||b|| (as orc_solve_system3), keeping
+ *               its reduced directions, products and T2;
+ *   stage three Algorithm 1 on A x = b with augmenting basis Y, initial coordinates the
+ *               stage-two solution [what; 0] + Phi2 alpha, Jacobi preconditioner, tol_rel;
+ *               each augmentation solve (Y^T A Y) mu = Y^T (A z) is the inner reduced solve
+ *               above, to tol_in * ||Y^T A z||, its directions accumulating over the
+ *               iterations (at most y - w directions in all, so the inner work of a whole
+ *               solve is bounded by y - w reduced products). Reading: tol_in is relative to
+ *               the inner right-hand side and must be tight (the callers use 1e-12); the
+ *               paper's 1e-2 eps_j (absolute) presumes a well-conditioned Y^T A Y, and with an
+ *               identity-metric Y inexact projections made stage three diverge (relative
+ *               1e-8 still did on a 20-mode basis; 1e-10 converged).
+ *               The augmentation solve is skipped once the exit test is met (its direction
+ *               would not be used).
+ * info as orc_solve_system (info->w = y); *k2_out the stage-two iterations; *inner_out the
+ * inner reduced iterations summed over the solve. */
+int orc_solve_system3_it(int n, const int* rp, const int* ci, const double* va, const double* b,
+                         int y, const double* Y, int w, double tol_rel, double tol2_rel, double tol_in,
+                         int kmax, int max_refine, double* x, orc_info* info, int* k2_out, int* inner_out)
+{
+    memset(info, 0, sizeof(*info));
+    if (w > y) w = y;
+    size_t nb = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    size_t yb = sizeof(double) * (size_t)(y > 0 ? y : 1);
+    int cap = y > 0 ? y : 1;
+    double bnorm = sqrt(orc_dot(n, b, b));
+    double tol_abs = tol_rel * bnorm;
+    double* R = (double*)calloc((size_t)(w > 0 ? w * w : 1), sizeof(double));
+    double* what = (double*)calloc((size_t)cap, sizeof(double));
+    double* psi = (double*)malloc(yb * (size_t)cap);
+    double* qpsi = (double*)malloc(yb * (size_t)cap);
+    double* g = (double*)malloc(sizeof(double) * (size_t)cap);
+    double* alpha2 = (double*)malloc(sizeof(double) * (size_t)cap);
+    double* xh = (double*)malloc(yb);
+    double* chat = (double*)malloc(yb);
+    double* mu = (double*)malloc(yb);
+    double* r = (double*)malloc(nb);
+    double* z = (double*)malloc(nb);
+    double* p = (double*)malloc(nb);
+    double* q = (double*)malloc(nb);
+    double* u = (double*)malloc(nb);
+    double* dinv = (double*)malloc(nb);
+    int wu = w, status = ORC_OK, iters = 0, refinements = 0, inner = 0;
+    if (w > 0 && orc_stage_one(n, rp, ci, va, b, w, Y, R, what) != ORC_OK) {   /* stage one */
+        info->chol_failed = 1;
+        wu = 0;
+        for (int a = 0; a < w; ++a) what[a] = 0.0;
+    }
+    int k2 = 0, m = 0, m_cap = y - wu;
+    double rhat = 0.0;
+    orc_stage_two_hist(n, rp, ci, va, b, y, Y, wu, R, what, tol2_rel * tol_abs, m_cap, &k2, alpha2,   /* stage two */
+                       NULL, g, &rhat, psi, qpsi);
+    m = k2;
+    for (int l = 0; l < y; ++l) xh[l] = (l < wu) ? what[l] : 0.0;   /* stage-two solution, reduced */
+    for (int k = 0; k < k2; ++k)
+        for (int l = 0; l < y; ++l) xh[l] += alpha2[k] * psi[(size_t)k * y + l];
+    for (int i = 0; i < n; ++i) {                                   /* M = diag(A) */
+        double d = 0.0;
+        for (int kk = rp[i]; kk < rp[i + 1]; ++kk)
+            if (ci[kk] == i) d += va[kk];
+        if (!(d > 0.0)) { status = ORC_NOT_SPD; goto done; }
+        dinv[i] = 1.0 / d;
+    }
+    for (int i = 0; i < n; ++i) {                                   /* x0 = Y xhat0 */
+        double t = 0.0;
+        for (int l = 0; l < y; ++l) t += Y[(size_t)l * n + i] * xh[l];
+        x[i] = t;
+    }
+    orc_spmv(n, rp, ci, va, x, q);                                  /* r0 = b - A x0 */
+    for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    {
+        double rr = 0.0;
+        for (int i = 0; i < n; ++i) rr += r[i] * r[i];
+        info->stage1_relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;   /* after stages one and two */
+    }
+    for (;;) {   /* one pass of Algorithm 1 from the current (true) residual */
+        for (int i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+        orc_spmv(n, rp, ci, va, z, u);                              /* Y^T A z; inner solve */
+        for (int l = 0; l < y; ++l) chat[l] = orc_dot(n, Y + (size_t)l * n, u);
+        {
+            double cn = 0.0;
+            for (int l = 0; l < y; ++l) cn += chat[l] * chat[l];
+            inner += orc_inner_solve(n, rp, ci, va, y, Y, wu, R, psi, qpsi, g, &m, m_cap, chat, tol_in * sqrt(cn), mu);
+        }
+        for (int i = 0; i < n; ++i) {                               /* p0 = z0 - Y mu0 */
+            double t = 0.0;
+            for (int l = 0; l < y; ++l) t += Y[(size_t)l * n + i] * mu[l];
+            p[i] = z[i] - t;
+        }
+        double rz = orc_dot(n, r, z);
+        double rnorm = sqrt(orc_dot(n, r, r));
+        if (!isfinite(rnorm)) { status = ORC_NONFINITE; break; }
+        while (rnorm > tol_abs) {
+            if (iters >= kmax) { status = ORC_MAXIT; break; }
+            orc_spmv(n, rp, ci, va, p, q);
+            double gamma = orc_dot(n, q, p);
+            if (!isfinite(gamma)) { status = ORC_NONFINITE; break; }
+            if (!(gamma > 0.0)) { status = ORC_BREAKDOWN; break; }
+            double a = rz / gamma;
+            for (int i = 0; i < n; ++i) x[i] += a * p[i];
+            for (int i = 0; i < n; ++i) r[i] -= a * q[i];
+            for (int i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
+            double rz_new = orc_dot(n, r, z);
+            double beta = rz_new / rz;
+            rnorm = sqrt(orc_dot(n, r, r));
+            ++iters;
+            if (!isfinite(rnorm)) { status = ORC_NONFINITE; break; }
+            if (rnorm <= tol_abs) break;   /* the augmentation solve is only needed for a next step */
+            orc_spmv(n, rp, ci, va, z, u);
+            for (int l = 0; l < y; ++l) chat[l] = orc_dot(n, Y + (size_t)l * n, u);
+            {
+                double cn = 0.0;
+                for (int l = 0; l < y; ++l) cn += chat[l] * chat[l];
+                inner += orc_inner_solve(n, rp, ci, va, y, Y, wu, R, psi, qpsi, g, &m, m_cap, chat,
+                                         tol_in * sqrt(cn), mu);
+            }
+            for (int i = 0; i < n; ++i) {
+                double t = 0.0;
+                for (int l = 0; l < y; ++l) t += Y[(size_t)l * n + i] * mu[l];
+                p[i] = z[i] + beta * p[i] - t;
+            }
+            rz = rz_new;
+        }
+        if (status != ORC_OK) break;
+        orc_spmv(n, rp, ci, va, x, q);                              /* true residual */
+        for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
+        if (sqrt(orc_dot(n, r, r)) <= tol_abs) break;
+        if (refinements >= max_refine) { status = ORC_MAXIT; break; }
+        ++refinements;                                              /* residual replacement */
+    }
+done:
+    info->status = status;
+    info->iters = iters;
+    info->refinements = refinements;
+    info->w = y;
+    {
+        orc_spmv(n, rp, ci, va, x, q);
+        double rr = 0.0;
+        for (int i = 0; i < n; ++i) rr += (b[i] - q[i]) * (b[i] - q[i]);
+        info->final_relres = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+    }
+    *k2_out = k2;
+    *inner_out = inner;
+    free(dinv); free(u); free(q); free(p); free(z); free(r); free(mu); free(chat); free(xh);
+    free(alpha2); free(g); free(qpsi); free(psi); free(what); free(R);
+    return status;
 }
 
 /* Gradient of L(theta) = sum_j c^T x_j through A_j(theta) x_j = b_j (the differentiated

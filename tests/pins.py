@@ -427,9 +427,31 @@ def pin_stage_two_reorthogonalised(orc):
     return off < 1e-10 and e < 1e-10, f"ill-conditioned stage two: V2 A-orthogonality {off:.1e}, Galerkin err {e:.1e}"
 
 
+def pin_stage3_full_matches_direct(orc):
+    """The stage-three option of Section 4.3.1 with exact inner solves (tol_in = 0) and an
+    exact stage two (tol2 = 0) is Algorithm 1 augmented with all of Y and exact reduced
+    solves, i.e. the two-stage solve with stage-one basis W = Y (dense Cholesky of
+    Y^T A Y): same iterations (within 1) and solutions within 1e-11 in the A-norm. With a
+    wider Y (y = 20) stage two stops on its tolerance before exhausting the reduced space,
+    the inner solves take the remaining reduced directions, and the solve agrees with a
+    dense solve at tol 1e-13."""
+    A, D, b, Y, w = _three_stage_problem(n_side=12, y=8, w=3, seed=13)
+    x1, i1, _, _ = orc.solve_system(A.arrays(), b, Y, 1e-10)
+    x2, i2 = orc.solve_system3_it(A.arrays(), b, Y, w, 1e-10, 0.0, 0.0)
+    e = a_norm(D, x1 - x2) / a_norm(D, x1)
+    A3, D3, b3, Y3, w3 = _three_stage_problem(n_side=14, y=20, w=3, seed=13)
+    x3, i3 = orc.solve_system3_it(A3.arrays(), b3, Y3, w3, 1e-13, 1e-2, 1e-12)
+    xs = np.linalg.solve(D3, b3)
+    e3 = a_norm(D3, x3 - xs) / a_norm(D3, xs)
+    ok = (i2["status"] == "ok" and abs(i1["iters"] - i2["iters"]) <= 1 and e < 1e-11
+          and i3["status"] == "ok" and e3 < 1e-11 and i3["k2"] < 20 - 3 and i3["inner"] >= 1)
+    return ok, (f"it stage three vs W = Y: err {e:.1e}, iters {i1['iters']}/{i2['iters']}; inner-driven run: "
+                f"dense agreement {e3:.1e}, k2 {i3['k2']}, inner {i3['inner']}")
+
+
 ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
             pin_finite_termination, pin_theta_grad_complex_step, pin_stage_two_optimality,
             pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse,
-            pin_stage_two_reorthogonalised]
+            pin_stage_two_reorthogonalised, pin_stage3_full_matches_direct]

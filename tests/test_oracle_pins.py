@@ -32,6 +32,7 @@ MUTANTS = {
     13: "stage-three factor takes T2 instead of its square root",
     14: "stage-two initial residual omits the stage-one solution's product",
     15: "stage two skips the re-A-orthogonalisation of its directions",
+    16: "inner reduced solves start from zero instead of the Galerkin solution over the stored basis",
 }
 
 
