@@ -19,7 +19,9 @@
  *      [W, V2] with the block-diagonal factor blockdiag(R, sqrt(T2)), T2 = diag(V2^T A V2);
  *   4. stage three (Section 4.3, Algorithm 1 with basis [W, V2], V2 empty without stage
  *      two): Jacobi-preconditioned CG whose directions are A_j-orthogonalised against the
- *      basis through mu = R^{-1} R^{-T} (AW)^T z and p = z + beta p - W mu.
+ *      basis through mu = R^{-1} R^{-T} (AW)^T z and p = z + beta p - W mu; or
+ *      (three_stage = 2, Section 4.3.1) against all of Y, mu from an inner reduced solve
+ *      of Y^T A Y mu = Y^T A z that reuses the reduced directions stored so far.
  * Every step runs in hand-written CUDA kernels; this header is the only interface.
  *
  * Conventions for every entry point:
@@ -94,7 +96,10 @@ typedef struct {
                             (systems of >= 65,536 rows; the pattern's heuristic width is kept
                             unless another is >= 10% faster); 1, 2, 4, 8, 16 or 32 = forced */
     int    three_stage;  /* 1: the three-stage algorithm of Section 4 (stage two over the
-                            augmenting basis Y before stage three); 0: stages one and three */
+                            augmenting basis Y before stage three, which augments with
+                            [W, V2]); 2: the same with stage three augmenting with all of Y,
+                            its reduced solves done iteratively (Section 4.3.1; FP64 only,
+                            else ERR_ARG); 0: stages one and three */
     int    y_max;        /* three_stage: cap on the augmenting-basis dimension y (1..s_max); y
                             is chosen by the POD energy criterion energy_y (Algorithm 4 step
                             3), capped at y_max, then raised to w when smaller (so y can reach
@@ -105,6 +110,11 @@ typedef struct {
                             (the reduced system is then solved exactly in exact arithmetic).
                             Stage two runs in FP64 in both precisions (MIXED converts its
                             directions to FP32 for stage three) */
+    double tol_inner;    /* three_stage = 2: each inner reduced solve stops when its residual
+                            is <= tol_inner * ||Y^T A z||_2 (default 1e-12: inexact
+                            projections onto range(Y) stall stage three when Y^T A Y is ill-
+                            conditioned; the inner directions accumulate, so the inner work
+                            of a whole solve is at most y - w reduced products) */
 } pod_cg_config;
 
 /* CSR matrix, device arrays, borrowed. */
@@ -131,7 +141,7 @@ typedef struct {
     int    launches;        /* kernels launched by this solve (graph-internal ones included) */
     int    y;               /* augmenting-basis dimension when stage two ran, else 0 */
     int    stage2_iters;    /* stage-two iterations k2 (stage three's basis is w + k2 wide) */
-    int    pad_;
+    int    inner_iters;     /* three_stage = 2: inner reduced iterations, summed */
     double stage1_relres;   /* ||b - A x0||/||b|| after stage one */
     double final_relres;    /* ||b - A x||/||b|| at exit, from an FP64 product */
     double cond_gram;       /* cond_2(W^T A W) when cond_diag = 1, else 0 */
@@ -146,7 +156,7 @@ typedef struct {
 /* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
  * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
  * loop_mode 0, proj_form -1, spmv_lanes 0, three_stage 0, y_max 40, energy_y 0.99999999,
- * tol_stage2 1e-4. */
+ * tol_stage2 1e-4, tol_inner 1e-12. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 
 /* Create a solver for systems of order n (the problem statement of Section 2) whose work

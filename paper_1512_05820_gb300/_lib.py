@@ -25,7 +25,8 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("use_tc_gram", ctypes.c_int),
                 ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int), ("loop_mode", ctypes.c_int),
                 ("proj_form", ctypes.c_int), ("spmv_lanes", ctypes.c_int), ("three_stage", ctypes.c_int),
-                ("y_max", ctypes.c_int), ("energy_y", ctypes.c_double), ("tol_stage2", ctypes.c_double)]
+                ("y_max", ctypes.c_int), ("energy_y", ctypes.c_double), ("tol_stage2", ctypes.c_double),
+                ("tol_inner", ctypes.c_double)]
 
 
 class CSRStruct(ctypes.Structure):
@@ -50,7 +51,7 @@ class Stats(ctypes.Structure):
                 ("w", ctypes.c_int), ("s", ctypes.c_int), ("chol_failed", ctypes.c_int),
                 ("system_id", ctypes.c_int), ("spmv_count", ctypes.c_int),
                 ("launches", ctypes.c_int), ("y", ctypes.c_int), ("stage2_iters", ctypes.c_int),
-                ("pad_", ctypes.c_int),
+                ("inner_iters", ctypes.c_int),
                 ("stage1_relres", ctypes.c_double), ("final_relres", ctypes.c_double),
                 ("cond_gram", ctypes.c_double), ("ms_pod", ctypes.c_float), ("ms_stage1", ctypes.c_float),
                 ("ms_stage2", ctypes.c_float), ("ms_stage3", ctypes.c_float)]

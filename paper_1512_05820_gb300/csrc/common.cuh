@@ -52,15 +52,18 @@ struct DevState {
     // stage two of the three-stage algorithm (Section 4.2)
     int pod_y;         // augmenting-basis dimension y chosen by the POD (0: no stage two)
     int w1;            // stage-one dimension after its Cholesky; stage two's basis starts here
-    int k2;            // stage-two iterations so far
-    int k2_cap;        // at most min(y, basis capacity) - w1 of them
-    int s2_done;       // stage two finished
+    int k2;            // iterations of the current reduced solve (stage two, or an inner solve)
+    int m_dirs;        // reduced directions stored so far (stage two's, then inner solves')
+    int m_cap;         // at most min(y, basis capacity) - w1 of them
+    int inner_total;   // inner reduced iterations of the whole-Y stage three
+    int s2_done;       // the current reduced solve finished
     int s2_break;      // it ended on a non-positive or non-finite (Y^T A Y p, p)
     double tol_rel;    // the solve's relative tolerance (host-written)
     double rho2;       // (rhat, rhat)
     double tol2_s2;    // squared absolute stage-two tolerance
     double rh[kSMax];  // reduced residual
     double ph[kSMax];  // reduced direction
+    double xh[kSMax];  // solution of the current inner reduced solve (whole-Y stage three)
 };
 
 // Borrowed problem pointers of the current solve, read by the kernels of a captured

@@ -168,10 +168,12 @@ struct pod_cg_t {
     double* Y = nullptr;        // three-stage: augmenting basis, ld x max(y_max, w_max)
     float* Y32 = nullptr;       // three-stage, mixed: its FP32 copy (stage-one panels)
     double* s2_hist = nullptr;  // three-stage: stage-two reduced directions, products, gammas
+    double* s2tmp = nullptr;    // whole-Y stage three: the inner solves' lifted v and A v
     int pod_y = 0;              // augmenting-basis dimension of the current POD
     int pod_y_used = 0;         // last solve: y when stage two ran, else 0
     int k2 = 0, k2_launch = 0;  // last solve: stage-two iterations, their loop bodies run
     bool w_clobbered = false;   // stage two wrote over W's columns (stage-one Cholesky failed)
+    bool it_mode = false;       // last solve ran stage three over the whole Y
     double* G = nullptr;        // kWMax x (kWMax + 1) row-major
     double* Rinv = nullptr;     // kWMax x kWMax
 
@@ -517,7 +519,7 @@ int s2_bucket(int y) { return y <= 8 ? 8 : y <= 16 ? 16 : y <= 32 ? 32 : y <= 48
 // mutual A-orthogonality at about eps_32 cond(Y^T A Y), which the block-diagonal stage-three
 // factor cannot absorb (MIXED solves then stalled in stage three); MIXED converts the
 // directions to FP32 afterwards.
-void make_s2_plan(pod_cg_t* h, int L, bool cond, cudaGraphConditionalHandle hl, Stage2Plan& P)
+void make_s2_plan(pod_cg_t* h, int L, bool cond, cudaGraphConditionalHandle hl, Stage2Plan& P, int inner = 0)
 {
     void *f_bb, *f_init, *f_lift, *f_apply;
     stage2_kernels(h->pod_y, L, cond, &f_bb, &f_init, &f_lift, &f_apply);
@@ -527,9 +529,12 @@ void make_s2_plan(pod_cg_t* h, int L, bool cond, cudaGraphConditionalHandle hl, 
     P.bb.set(f_bb, occ_grid(h, f_bb, n, kBlock), pd, h->partials, c + 6 * kCounterStride, h->st);
     P.init.set(f_init, 1, (const double*)h->G, kWMax + 1, (const double*)h->Rinv, h->st, h->wcap,
                h->cfg.tol_stage2, hl);
-    P.lift.set(f_lift, occ_grid(h, f_lift, n, kBlock), n, ld, (const double*)h->Y, h->W, (const DevState*)h->st);
-    P.apply.set(f_apply, occ_grid(h, f_apply, n, kBlock), pd, ld, (const double*)h->Y, (const double*)h->W,
-                h->AW, h->partials, c + 7 * kCounterStride, h->st, h->Rinv, (const double*)h->G, kWMax + 1, h->s2_hist,
+    // inner solves of the whole-Y stage three lift into scratch vectors (v, then u)
+    double* Bv = inner ? h->s2tmp : h->W;
+    double* Bu = inner ? h->s2tmp + h->ld : h->AW;
+    P.lift.set(f_lift, occ_grid(h, f_lift, n, kBlock), n, ld, (const double*)h->Y, Bv, (const DevState*)h->st, inner);
+    P.apply.set(f_apply, occ_grid(h, f_apply, n, kBlock), pd, ld, (const double*)h->Y, (const double*)Bv, Bu,
+                h->partials, c + 7 * kCounterStride, h->st, h->Rinv, (const double*)h->G, kWMax + 1, h->s2_hist, inner,
                 hl);
 }
 
@@ -589,6 +594,73 @@ pod_cg_status read_state(pod_cg_t* h)
 {
     PODCG_CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
     PODCG_CK(h, cudaStreamSynchronize(h->stream));
+    return POD_CG_OK;
+}
+
+// Stage three over the entire augmenting basis (three_stage = 2, Section 4.3.1; FP64):
+// Algorithm 1 with the plain Jacobi-PCG product and update kernels, the augmentation step
+// k_it_az, inner reduced iterations (k_s2_lift / k_s2_apply, inner = 1) and k_it_dir, driven
+// from the host with one state read per iteration and one per inner reduced iteration (the
+// inner iterations of a whole solve are at most y - w: the reduced directions accumulate).
+// Passes of residual replacement as in the other loops.
+pod_cg_status run_loop_it(pod_cg_t* h, int L, int* launches)
+{
+    cudaStream_t s = h->stream;
+    const int n = h->n, ld = h->ld;
+    Plan pl;
+    make_plan(h, 0, L, false, 0, 0, 0, pl);   // no basis in the product / update kernels
+    void *f_az, *f_dir0, *f_dir, *f_begin;
+    it_kernels(h->pod_y, L, &f_az, &f_dir0, &f_dir, &f_begin);
+    KSpec az, dir0, dir, begin;
+    az.set(f_az, occ_grid(h, f_az, n, kBlock), (const ProbDesc*)h->pd, ld, (const double*)h->dinv, (const double*)h->r,
+           (const double*)h->Y, h->partials, h->counters + 6 * kCounterStride, h->st, (const double*)h->Rinv,
+           (const double*)h->G, kWMax + 1, (const double*)h->s2_hist, h->cfg.tol_inner);
+    dir0.set(f_dir0, occ_grid(h, f_dir0, n, kBlock), n, ld, h->x, h->p, (const double*)h->r, (const double*)h->dinv,
+             (const double*)h->Y, (const DevState*)h->st);
+    dir.set(f_dir, occ_grid(h, f_dir, n, kBlock), n, ld, h->x, h->p, (const double*)h->r, (const double*)h->dinv,
+            (const double*)h->Y, (const DevState*)h->st);
+    begin.set(f_begin, 1, h->st);
+    Stage2Plan s2;
+    make_s2_plan(h, L, false, 0, s2, 1);
+    PODCG_CK(h, launch_spec(begin, s));
+    int nl = 1;
+    auto inner_loop = [&]() -> pod_cg_status {
+        for (int it = 0; !h->st_host->s2_done && it <= kWMax; ++it) {
+            PODCG_CK(h, launch_spec(s2.lift, s));
+            PODCG_CK(h, launch_spec(s2.apply, s));
+            nl += 2;
+            pod_cg_status rs = read_state(h);
+            if (rs != POD_CG_OK) return rs;
+        }
+        return POD_CG_OK;
+    };
+    for (int pass = 0; pass <= h->cfg.max_refine + 1; ++pass) {
+        PODCG_CK(h, launch_spec(pl.init, s));
+        PODCG_CK(h, launch_spec(az, s));
+        pod_cg_status rs = read_state(h);
+        if (rs != POD_CG_OK) return rs;
+        rs = inner_loop();
+        if (rs != POD_CG_OK) return rs;
+        PODCG_CK(h, launch_spec(dir0, s));
+        nl += 3;
+        for (long long it = 0; !h->st_host->done && it <= (long long)h->cfg.k_max + 1; ++it) {
+            PODCG_CK(h, launch_spec(pl.spmv, s));
+            PODCG_CK(h, launch_spec(pl.upd, s));
+            PODCG_CK(h, launch_spec(az, s));
+            rs = read_state(h);
+            if (rs != POD_CG_OK) return rs;
+            rs = inner_loop();
+            if (rs != POD_CG_OK) return rs;
+            PODCG_CK(h, launch_spec(dir, s));
+            nl += 4;
+        }
+        PODCG_CK(h, launch_spec(pl.res, s));
+        nl += 1;
+        rs = read_state(h);
+        if (rs != POD_CG_OK) return rs;
+        if (h->st_host->outer_done) break;
+    }
+    *launches += nl;
     return POD_CG_OK;
 }
 
@@ -688,6 +760,11 @@ pod_cg_status finish_solve(pod_cg_t* h, double* out, int w_pod, int launches, po
         stats->launches = launches + per_pass * (d.restarts + 1) + 3 * d.iters;
         stats->y = h->pod_y_used;
         stats->stage2_iters = h->k2;
+        if (h->it_mode) {
+            stats->w = h->pod_y_used;   // stage three augments with all of Y
+            stats->inner_iters = d.inner_total;
+            stats->spmv_count += d.inner_total + d.iters + d.restarts + 1;   // A z per iteration and pass
+        }
         stats->stage1_relres = d.bb > 0.0 ? std::sqrt(std::max(d.rr_stage1, 0.0) / d.bb) : 0.0;
         stats->final_relres = d.bb > 0.0 ? std::sqrt(d.rr_true / d.bb) : 0.0;
         stats->cond_gram = d.cond;
@@ -735,6 +812,7 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->y_max = 40;
     c->energy_y = 0.99999999;
     c->tol_stage2 = 1e-4;
+    c->tol_inner = 1e-12;
     return POD_CG_OK;
 }
 
@@ -750,7 +828,7 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     for (auto& g : h->chunks) destroy_graph(g);
     destroy_graph(h->s2graph);
     void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->Y, h->Y32,
-                    h->s2_hist,
+                    h->s2_hist, h->s2tmp,
                     h->G, h->Rinv,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
                     h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
@@ -781,12 +859,15 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
         (c.spmv_lanes != 0 && (c.spmv_lanes < 1 || c.spmv_lanes > 32 || (c.spmv_lanes & (c.spmv_lanes - 1)))) ||
         !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
         return fail(nullptr, POD_CG_ERR_ARG, "invalid configuration");
-    if (c.three_stage != 0 && (c.three_stage != 1 || c.y_max < 1 || c.y_max > c.s_max ||
+    if (c.three_stage != 0 && (c.three_stage < 0 || c.three_stage > 2 || c.y_max < 1 || c.y_max > c.s_max ||
                                !(c.energy_y >= 0.0 && c.energy_y <= 1.0) ||
-                               !(c.tol_stage2 >= 0.0 && std::isfinite(c.tol_stage2))))
+                               !(c.tol_stage2 >= 0.0 && std::isfinite(c.tol_stage2)) ||
+                               !(c.tol_inner >= 0.0 && c.tol_inner < 1.0)))
         return fail(nullptr, POD_CG_ERR_ARG,
-                    "invalid three-stage configuration (three_stage 0/1, 1 <= y_max <= s_max, energy_y in [0, 1], "
-                    "tol_stage2 >= 0)");
+                    "invalid three-stage configuration (three_stage 0/1/2, 1 <= y_max <= s_max, energy_y in [0, 1], "
+                    "tol_stage2 >= 0, 0 <= tol_inner < 1)");
+    if (c.three_stage == 2 && c.precision != POD_CG_FP64)
+        return fail(nullptr, POD_CG_ERR_ARG, "three_stage = 2 (stage three over the whole Y) runs in FP64 only");
     if (c.use_tc_gram != 0 && (c.use_tc_gram != 1 || c.precision != POD_CG_MIXED))
         return fail(nullptr, POD_CG_ERR_ARG,
                     "use_tc_gram needs precision MIXED: the tensor-core Gram rounds W and AW to FP32");
@@ -820,6 +901,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     const size_t ycols = (size_t)std::max(c.y_max, c.w_max);
     if (c.three_stage) PODCG_ALLOC(h->Y, ld * ycols)
     if (c.three_stage) PODCG_ALLOC(h->s2_hist, (size_t)2 * kWMax * kSMax + kWMax)
+    if (c.three_stage == 2) PODCG_ALLOC(h->s2tmp, ld * 2)
     PODCG_ALLOC(h->G, (size_t)kWMax * (kWMax + 1))
     PODCG_ALLOC(h->Rinv, (size_t)kWMax * kWMax)
     PODCG_ALLOC(h->x, ld)
@@ -1116,7 +1198,14 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
                                   h->sms, s));
     PODCG_CK(h, cudaEventRecord(h->ev[3], s));
 
-    // stage three (Algorithm 1 with basis [W, V2])
+    // stage three (Algorithm 1 with basis [W, V2], or with all of Y: three_stage = 2)
+    h->it_mode = h->cfg.three_stage == 2 && y > 0;
+    if (h->it_mode) {
+        pod_cg_status its = run_loop_it(h, L, &launches);
+        if (its != POD_CG_OK) return its;
+        const int sysid = h->system_counter++;
+        return finish_solve(h, x_out, w, launches, stats, sysid);
+    }
     pod_cg_status ps = choose_proj_form(h, wb, L);
     if (ps != POD_CG_OK) return ps;
     pod_cg_status ls = run_loop(h, wb, L);
@@ -1189,6 +1278,7 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
     PODCG_CK(h, cudaEventRecord(h->ev[2], s));
     h->k2 = 0;
     h->pod_y_used = 0;
+    h->it_mode = false;
     PODCG_CK(h, launch_stage1(wb, h->pd, n, h->W, h->AW, h->x, h->r, h->partials, h->counters + 4 * kCounterStride, h->st, tol,
                               h->sms, s));
     PODCG_CK(h, cudaEventRecord(h->ev[3], s));

@@ -65,6 +65,10 @@ void cg_kernels(int wb, bool fp32, bool cond, int form, void** init, void** upd,
 // stage two of the three-stage algorithm (k_stage2.cu, FP64): kernel pointers for graph
 // construction, y = the augmenting-basis dimension (selects the width bucket), L = SpMV lanes
 void stage2_kernels(int y, int L, bool cond, void** bb, void** init, void** lift, void** apply);
+// stage three over the entire augmenting basis (k_stage2.cu, FP64): the augmentation step
+// A z -> Y^T A z with the inner solve's start, the first and later direction updates with Y,
+// and the switch of the update kernels to no basis
+void it_kernels(int y, int L, void** az, void** dir0, void** dir, void** begin);
 
 // mixed precision (k_mixed.cu)
 void mixed_kernels(int wb, void** proj, void** start);

@@ -35,6 +35,11 @@ def to_dev(a, dev):
     return torch.as_tensor(np.ascontiguousarray(a), device=dev)
 
 
+def dcsr_dev(A, dev):
+    from paper_1512_05820_gb300.solver import DeviceCSR
+    return DeviceCSR.from_numpy(A.row_ptr, A.col, A.val, device=dev)
+
+
 def a_err(orc, A, x, xo):
     dx = x - xo
     num = dx @ orc.spmv(A, dx)
@@ -175,7 +180,48 @@ def test_three_stage_mixed_precision(dev, loop_mode):
 def test_three_stage_config_errors(dev):
     from paper_1512_05820_gb300.solver import PodCG, PodCGError
     for bad in (dict(three_stage=1, y_max=0), dict(three_stage=1, y_max=41), dict(three_stage=1, energy_y=1.5),
-                dict(three_stage=1, tol_stage2=-1.0), dict(three_stage=2)):
+                dict(three_stage=1, tol_stage2=-1.0), dict(three_stage=3),
+                dict(three_stage=2, tol_inner=1.0)):
         with pytest.raises(PodCGError) as e:
             PodCG(100, **bad)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("seed", [13, 14, 15])
+def test_stage3_full_y_vs_oracle(dev, seed):
+    """Stage three over the entire augmenting basis (three_stage = 2, Section 4.3.1), FP64,
+    on a 14x14 diffusion system with 20 snapshots Y diag(0.7^i) (Y orthonormal, near the
+    solution): w = 7 at energy 0.99, y = 20; stage two stops on its tolerance (1e-2 of the
+    system's) before exhausting the reduced space and the inner reduced solves take the
+    remaining directions. Against the oracle: same k2, stage-three iterations within 1,
+    inner reduced iterations within 1, and the 1e-10 A-norm bound at equal counts."""
+    import pins
+    from paper_1512_05820_gb300.solver import PodCG
+    A, D, b, Y, _ = pins._three_stage_problem(n_side=14, y=20, w=3, seed=seed)
+    sig = 0.7 ** np.arange(20)
+    cfg = dict(w_max=8, s_max=20, energy=0.99, y_max=20, energy_y=1 - 1e-14, tol_stage2=1e-2, tol_inner=1e-12)
+    orc = Oracle()
+    oseq = OracleSequence(A.n, oracle=orc, three_stage=True, stage3_full=True, **cfg)
+    solver = PodCG(A.n, three_stage=2, **cfg)
+    for i in range(20):
+        oseq.add_snapshot(Y[:, i] * sig[i])
+    solver.add_snapshots(to_dev(np.asfortranarray(Y * sig), dev))
+    x, st = solver.solve(dcsr_dev(A, dev), to_dev(b, dev), 1e-10)
+    xo, info = oseq.solve(A.arrays(), b, 1e-10)
+    x = x.cpu().numpy()
+    assert st["status"] == "ok" and info["status"] == "ok", (st, info)
+    assert st["y"] == 20 and st["w"] == 20
+    assert st["stage2_iters"] == info["k2"], (st["stage2_iters"], info["k2"])
+    assert abs(st["iters"] - info["iters"]) <= 1, (st["iters"], info["iters"])
+    assert abs(st["inner_iters"] - info["inner"]) <= 1, (st["inner_iters"], info["inner"])
+    assert info["inner"] >= 1
+    assert st["final_relres"] <= 1e-10
+    if st["iters"] == info["iters"]:
+        assert a_err(orc, A.arrays(), x, xo) <= 1e-10
+
+
+def test_stage3_full_y_needs_fp64(dev):
+    from paper_1512_05820_gb300.solver import PodCG, PodCGError
+    with pytest.raises(PodCGError) as e:
+        PodCG(100, three_stage=2, precision=1)
+    assert e.value.status == 1
