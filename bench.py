@@ -71,6 +71,10 @@ def parse_args():
                     help="the three-stage algorithm (Section 4) against the two-stage form on the same "
                          "sequence (the --grid/--systems diffusion sequence, or the cantilever with "
                          "--elasticity K), each timed over the sequence after one untimed pass; one JSON line")
+    ap.add_argument("--stage2-profile", type=int, default=0, metavar="Y",
+                    help="profiling target: system 1 of the workload with Y seeded random snapshots, FP64, "
+                         "stage two run to its cap (y - w reduced iterations, host-driven launches), then 5 "
+                         "iterations of stage three with [W, V2] and 5 with the whole Y; one JSON line")
     ap.add_argument("--batch-seqs", type=int, default=256)
     ap.add_argument("--loop-mode", choices=["graph", "chunked"], default="graph",
                     help="graph: conditional CUDA graph; chunked: plain graphs of 16 iterations (profilable)")
@@ -342,6 +346,35 @@ def kernel_profile(args):
     print(json.dumps({"kernel_profile": True, "w": st["w"], "precision": args.precision,
                       "ms": dict(zip(["spmv_cg", "update", "direction", "residual"], ms)),
                       "tuning": solver.tuning()}), flush=True)
+    return 0
+
+
+def stage2_profile(args):
+    """A short launch sequence for kernel profilers of stage two (Section 4.2) and of the
+    whole-Y stage three (Section 4.3.1): system 1 of the workload, Y seeded random
+    snapshots (flat POD spectrum: y = Y, w from energy 0.5), FP64, stage-two tolerance 0 so
+    it takes all y - w reduced iterations, stage three capped at 5 iterations, plain
+    launches (loop_mode 1). Prints the solve statistics as one JSON line."""
+    import torch
+    from paper_1512_05820_gb300 import workloads as wl
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=args.grid, p=1)
+    j, val, b = next(iter(seq.systems()))
+    A = DeviceCSR.from_numpy(seq.row_ptr, seq.col, val)
+    bt = torch.as_tensor(b, device="cuda")
+    snaps = torch.as_tensor(np.random.default_rng(7).normal(size=(seq.n, args.stage2_profile)), device="cuda")
+    out = {"stage2_profile": True, "n": seq.n, "nnz": seq.nnz, "snapshots": args.stage2_profile}
+    for mode in (1, 2):
+        solver = PodCG(seq.n, w_max=32, s_max=40, energy=0.5, precision=0, k_max=5, max_refine=0, loop_mode=1,
+                       three_stage=mode, y_max=min(40, args.stage2_profile), energy_y=1.0 - 1e-12, tol_stage2=0.0,
+                       spmv_lanes=args.spmv_lanes)
+        solver.add_snapshots(snaps)
+        _, st = solver.solve(A, bt, seq.tol, raise_on_error=False)
+        torch.cuda.synchronize()
+        out[f"three_stage_{mode}"] = {k: st[k] for k in ("status", "y", "w", "stage2_iters", "iters", "inner_iters",
+                                                         "ms_stage1", "ms_stage2", "ms_stage3")}
+        solver.close()
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -632,6 +665,8 @@ def main():
         return diff_check(args)
     if args.gram_profile:
         return gram_profile(args)
+    if args.stage2_profile:
+        return stage2_profile(args)
     if args.three_stage:
         return three_stage_bench(args)
     if args.elasticity:
