@@ -75,6 +75,8 @@ def parse_args():
                     help="profiling target: system 1 of the workload with Y seeded random snapshots, FP64, "
                          "stage two run to its cap (y - w reduced iterations, host-driven launches), then 5 "
                          "iterations of stage three with [W, V2] and 5 with the whole Y; one JSON line")
+    ap.add_argument("--bsr", type=int, default=-1, choices=[-1, 0, 1],
+                    help="CG product in 3x3 block form: -1 when the pattern allows (default), 0 never, 1 required")
     ap.add_argument("--batch-seqs", type=int, default=256)
     ap.add_argument("--loop-mode", choices=["graph", "chunked"], default="graph",
                     help="graph: conditional CUDA graph; chunked: plain graphs of 16 iterations (profilable)")
@@ -325,25 +327,27 @@ def cpu_baseline(seq, systems):
 
 
 def kernel_profile(args):
-    """A short, fixed launch sequence for kernel profilers: system 1 of the workload with
-    W seeded random snapshots (so the POD basis has about W columns), a solve capped at 5
-    iterations, then pod_cg_time_kernels. Prints the per-kernel times as one JSON line."""
+    """A short, fixed launch sequence for kernel profilers: system 1 of the workload (the
+    64^3 cantilever with --elasticity) with W seeded random snapshots (so the POD basis
+    has about W columns), a solve capped at 5 iterations, then pod_cg_time_kernels.
+    Prints the per-kernel times as one JSON line."""
     import torch
     from paper_1512_05820_gb300 import workloads as wl
     from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
-    seq = wl.diffusion3d_moving(m=args.grid, p=1)
+    seq = wl.elasticity_cantilever(e=64, p=1) if args.elasticity else wl.diffusion3d_moving(m=args.grid, p=1)
     j, val, b = next(iter(seq.systems()))
     prec = 1 if args.precision == "mixed" else 0
-    solver = PodCG(seq.n, w_max=32, s_max=40, energy=0.9999, precision=prec, k_max=5, max_refine=0,
+    solver = PodCG(seq.n, w_max=48, s_max=64, energy=0.9999, precision=prec, k_max=5, max_refine=0,
                    loop_mode=1, proj_form={"auto": -1, "direct": 0, "staged": 1}[args.proj_form],
-                   spmv_lanes=args.spmv_lanes)
+                   spmv_lanes=args.spmv_lanes, bsr=args.bsr)
     snaps = torch.as_tensor(np.random.default_rng(7).normal(size=(seq.n, args.kernel_profile)), device="cuda")
     solver.add_snapshots(snaps)
     A = DeviceCSR.from_numpy(seq.row_ptr, seq.col, val)
     bt = torch.as_tensor(b, device="cuda")
     _, st = solver.solve(A, bt, seq.tol, raise_on_error=False)
     ms = solver.time_kernels(A, bt, reps=args.kernel_reps)
-    print(json.dumps({"kernel_profile": True, "w": st["w"], "precision": args.precision,
+    print(json.dumps({"kernel_profile": True, "workload": "elasticity 64^3" if args.elasticity else f"diffusion {args.grid}^3",
+                      "n": seq.n, "nnz": seq.nnz, "bsr": args.bsr, "w": st["w"], "precision": args.precision,
                       "ms": dict(zip(["spmv_cg", "update", "direction", "residual"], ms)),
                       "tuning": solver.tuning()}), flush=True)
     return 0
@@ -470,7 +474,8 @@ def elasticity_bench(args):
     row, w <= 48), its first K systems (seeded, generated on the host): POD-augmented CG in
     mixed precision with the tensor-core split-bf16 stage-one Gram and with the CUDA-core
     FP32 Gram, against plain Jacobi CG in mixed precision, each timed over the K systems
-    (CUDA events) after one untimed pass. Prints one JSON line."""
+    (CUDA events) after one untimed pass; the CG product in 3x3 block form (the default
+    for this pattern) and, for comparison, in CSR. Prints one JSON line."""
     import torch
     from paper_1512_05820_gb300 import workloads as wl
     from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
@@ -483,9 +488,9 @@ def elasticity_bench(args):
     dseq = DeviceSequence(seq, systems=systems)
     xs = [torch.empty(seq.n, dtype=torch.float64, device="cuda") for _ in range(K)]
 
-    def one(recycle, tc):
+    def one(recycle, tc, bsr=-1):
         solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=1, use_tc_gram=tc,
-                       spmv_lanes=args.spmv_lanes)
+                       spmv_lanes=args.spmv_lanes, bsr=bsr)
         run_sequence(solver, dseq, xs, recycle=recycle)
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -503,8 +508,12 @@ def elasticity_bench(args):
 
     out = {"elasticity": True, "workload": f"elasticity_cantilever 64^3 elements, first {K} systems",
            "n": seq.n, "nnz": seq.nnz, "w_max": seq.w_max, "tol": seq.tol, "generation_s": gen_s,
-           "pod_aug_tc_gram": one(True, 1), "pod_aug_cuda_core_gram": one(True, 0), "plain_cg": one(False, 0)}
+           "pod_aug_tc_gram": one(True, 1), "pod_aug_cuda_core_gram": one(True, 0), "plain_cg": one(False, 0),
+           "pod_aug_tc_gram_csr": one(True, 1, 0), "plain_cg_csr": one(False, 0, 0)}
     out["speedup_pod_aug_vs_plain"] = out["pod_aug_tc_gram"]["systems_per_s"] / out["plain_cg"]["systems_per_s"]
+    out["speedup_bsr_vs_csr_pod_aug"] = (out["pod_aug_tc_gram"]["systems_per_s"] /
+                                         out["pod_aug_tc_gram_csr"]["systems_per_s"])
+    out["speedup_bsr_vs_csr_plain"] = out["plain_cg"]["systems_per_s"] / out["plain_cg_csr"]["systems_per_s"]
     print(json.dumps(out), flush=True)
     return 0
 

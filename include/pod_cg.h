@@ -115,6 +115,11 @@ typedef struct {
                             projections onto range(Y) stall stage three when Y^T A Y is ill-
                             conditioned; the inner directions accumulate, so the inner work
                             of a whole solve is at most y - w reduced products) */
+    int    bsr;          /* CG product in 3x3 block-sparse form (one column index per 9 values)
+                            when the CSR pattern is made of full 3x3 blocks (three unknowns
+                            per node, columns in aligned triplets, n % 3 == 0): -1 = when the
+                            pattern allows (checked once per pattern), 0 = never, 1 = required
+                            (ERR_ARG at solve time when the pattern does not allow it) */
 } pod_cg_config;
 
 /* CSR matrix, device arrays, borrowed. */
@@ -156,7 +161,7 @@ typedef struct {
 /* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
  * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
  * loop_mode 0, proj_form -1, spmv_lanes 0, three_stage 0, y_max 40, energy_y 0.99999999,
- * tol_stage2 1e-4, tol_inner 1e-12. */
+ * tol_stage2 1e-4, tol_inner 1e-12, bsr -1. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 
 /* Create a solver for systems of order n (the problem statement of Section 2) whose work

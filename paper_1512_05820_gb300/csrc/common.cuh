@@ -77,7 +77,33 @@ struct ProbDesc {
     double* x;
     int n;
     int ld;            // leading dimension of the n-by-k blocks (W, AW, S)
+    // 3x3 block form of the same matrix (k_bsr.cu), when its pattern has one
+    const int32_t* brp;   // block-row pointers, nb + 1
+    const int32_t* bcol;  // block-column indices, nnzb
+    const double* bval;   // values by block entry: entry (r, c) of block t at bval[(3r + c) nnzb + t]
+    const float* bval32;  // the same in FP32 (mixed precision)
+    int nb;               // block rows (n / 3)
+    int nnzb;             // blocks (nnz / 9)
 };
+
+// The scalar step after the CG product (Algorithm 1): gamma = (A p, p) given, the last
+// block records it, flags a breakdown when it is not positive (an FP32 inner pass ends
+// instead of the solve in mixed precision) and forms alpha = (r, z)/gamma. Thread 0 only.
+__device__ __forceinline__ void cg_product_finish(DevState* st, double gamma)
+{
+    int status = st->status, inner_break = st->inner_break;
+    const int mixed = st->mixed;
+    const double rho = st->rho;
+    const bool bad = !isfinite(gamma) || !(gamma > 0.0);
+    if (bad && status == 0) {
+        if (mixed) inner_break = 1;
+        else status = !isfinite(gamma) ? 5 : 3;
+    }
+    st->gamma = gamma;
+    st->status = status;
+    st->inner_break = inner_break;
+    st->alpha = (status == 0 && !inner_break) ? rho / gamma : 0.0;
+}
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)

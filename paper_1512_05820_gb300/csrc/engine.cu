@@ -104,6 +104,7 @@ struct GraphSlot {
     cudaGraphExec_t exec = nullptr;
     int L = 0;
     int yb = 0;   // stage-two graphs: the y bucket they were built for
+    bool bsr = false;   // built with the 3x3 block product
     bool valid = false;
 };
 
@@ -174,6 +175,20 @@ struct pod_cg_t {
     int k2 = 0, k2_launch = 0;  // last solve: stage-two iterations, their loop bodies run
     bool w_clobbered = false;   // stage two wrote over W's columns (stage-one Cholesky failed)
     bool it_mode = false;       // last solve ran stage three over the whole Y
+
+    // 3x3 block form of the CG product (k_bsr.cu): pattern cache and buffers
+    const int32_t* bsr_key = nullptr;   // row_ptr of the pattern checked last
+    int bsr_key_n = 0;
+    int64_t bsr_key_nnz = -1;
+    bool bsr_ok = false;                // that pattern is made of full 3x3 blocks
+    bool use_bsr = false;               // the current solve uses the block form
+    int bsr_L = 8;
+    bool bsr_timed = false;             // lanes per block row timed for the current pattern
+    int32_t *brp = nullptr, *bcol = nullptr;
+    double* bval = nullptr;
+    float* bval32 = nullptr;
+    int64_t bsr_cap = 0;                // blocks the value buffers hold
+    int* bsr_flag = nullptr;
     double* G = nullptr;        // kWMax x (kWMax + 1) row-major
     double* Rinv = nullptr;     // kWMax x kWMax
 
@@ -390,12 +405,13 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
     int sm_upd = 0, sm_dir = 0;
     const int form = h->proj_form[bucket_index(wb)] == kProjStaged ? kProjStaged : kProjDirect;
     cg_kernels(wb, mixed, use_cond != 0, form, &f_init, &f_upd, &f_dir0, &f_dir, &sm_upd, &sm_dir);
-    void* f_spmv = kernel_spmv_cg(L, mixed);
+    // the CG product: CSR, or the 3x3 block form when the pattern has one (k_bsr.cu)
+    void* f_spmv = h->use_bsr ? kernel_bsr_spmv_cg(h->bsr_L, mixed) : kernel_spmv_cg(L, mixed);
     void* f_res = kernel_residual(L, use_cond != 0);
     const int g_init = occ_grid(h, f_init, n, kBlock);
     const int g_upd = occ_grid(h, f_upd, n, kBlock, sm_upd);
     const int g_dir = occ_grid(h, f_dir, n, kBlock, sm_dir);
-    const int g_spmv = occ_grid(h, f_spmv, n, kBlock / L);
+    const int g_spmv = h->use_bsr ? occ_grid(h, f_spmv, n / 3, kBlock / h->bsr_L) : occ_grid(h, f_spmv, n, kBlock / L);
     const int g_res = occ_grid(h, f_res, n, kBlock / L);
     unsigned int* c = h->counters;
     const ProbDesc* pd = h->pd;
@@ -481,6 +497,7 @@ pod_cg_status build_conditional(pod_cg_t* h, int wb, int L, GraphSlot& gs)
     gs.graph = P;
     gs.exec = exec;
     gs.L = L;
+    gs.bsr = h->use_bsr;
     gs.valid = true;
     return POD_CG_OK;
 }
@@ -506,7 +523,116 @@ pod_cg_status build_chunk(pod_cg_t* h, int wb, int L, GraphSlot& gs)
     gs.graph = P;
     gs.exec = exec;
     gs.L = L;
+    gs.bsr = h->use_bsr;
     gs.valid = true;
+    return POD_CG_OK;
+}
+
+// The 3x3 block form of A for the CG product: the pattern is checked and converted once
+// per pattern (block-row pointers and columns), the values of every system are gathered.
+// bsr = -1 uses it when the pattern allows, 1 requires it (ERR_ARG otherwise), 0 never.
+pod_cg_status setup_bsr(pod_cg_t* h, const pod_cg_csr* A)
+{
+    h->use_bsr = false;
+    if (h->cfg.bsr == 0) return POD_CG_OK;
+    cudaStream_t s = h->stream;
+    const int n = A->n;
+    if (h->bsr_key != A->row_ptr || h->bsr_key_n != n || h->bsr_key_nnz != A->nnz) {
+        h->bsr_key = A->row_ptr;
+        h->bsr_key_n = n;
+        h->bsr_key_nnz = A->nnz;
+        h->bsr_ok = false;
+        if (n % 3 == 0 && A->nnz % 9 == 0 && A->nnz > 0) {
+            if (!h->bsr_flag) PODCG_CK(h, cudaMalloc((void**)&h->bsr_flag, sizeof(int)));
+            PODCG_CK(h, cudaMemsetAsync(h->bsr_flag, 0, sizeof(int), s));
+            PODCG_CK(h, launch_bsr_check(A->row_ptr, A->col, n, h->bsr_flag, h->sms, s));
+            int bad = 1;
+            PODCG_CK(h, cudaMemcpyAsync(&bad, h->bsr_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+            PODCG_CK(h, cudaStreamSynchronize(s));
+            if (!bad) {
+                const int64_t nnzb = A->nnz / 9;
+                const int nb = n / 3;
+                if (nnzb > h->bsr_cap) {
+                    cudaFree(h->bcol);
+                    cudaFree(h->bval);
+                    cudaFree(h->bval32);
+                    h->bcol = nullptr;
+                    h->bval = nullptr;
+                    h->bval32 = nullptr;
+                    h->bsr_cap = 0;
+                    PODCG_CK(h, cudaMalloc((void**)&h->bcol, sizeof(int32_t) * nnzb));
+                    PODCG_CK(h, cudaMalloc((void**)&h->bval, sizeof(double) * 9 * nnzb));
+                    if (h->mixed) PODCG_CK(h, cudaMalloc((void**)&h->bval32, sizeof(float) * 9 * nnzb));
+                    h->bsr_cap = nnzb;
+                }
+                cudaFree(h->brp);
+                h->brp = nullptr;
+                PODCG_CK(h, cudaMalloc((void**)&h->brp, sizeof(int32_t) * (nb + 1)));
+                PODCG_CK(h, launch_bsr_pattern(A->row_ptr, A->col, nb, h->brp, h->bcol, h->sms, s));
+                h->bsr_L = bsr_lanes_for(double(nnzb) / std::max(nb, 1));
+                h->bsr_timed = false;
+                h->bsr_ok = true;
+            }
+        }
+    }
+    if (!h->bsr_ok) {
+        if (h->cfg.bsr == 1) return fail(h, POD_CG_ERR_ARG, "bsr = 1 but the CSR pattern is not made of full 3x3 blocks");
+        return POD_CG_OK;
+    }
+    const int64_t nnzb = A->nnz / 9;
+    PODCG_CK(h, launch_bsr_values(A->row_ptr, A->val, n, (int)nnzb, h->bval, h->mixed ? h->bval32 : nullptr, h->sms, s));
+    h->use_bsr = true;
+    h->pd_host->brp = h->brp;
+    h->pd_host->bcol = h->bcol;
+    h->pd_host->bval = h->bval;
+    h->pd_host->bval32 = h->bval32;
+    h->pd_host->nb = n / 3;
+    h->pd_host->nnzb = (int)nnzb;
+    return POD_CG_OK;
+}
+
+// Lanes per block row of the block CG product, timed once per pattern on the actual
+// matrix for systems of >= 65,536 rows (CUDA events, a scratch state, the handle's p and q
+// as input and output); the heuristic width is kept unless another is >= 10% faster.
+// Needs the problem descriptor with the block arrays on the device.
+pod_cg_status choose_bsr_lanes(pod_cg_t* h)
+{
+    if (!h->use_bsr || h->bsr_timed) return POD_CG_OK;
+    h->bsr_timed = true;
+    if (h->n < 65536) return POD_CG_OK;
+    cudaStream_t s = h->stream;
+    const int cands[4] = {4, 8, 16, 32};
+    const int heur = h->bsr_L;
+    float t_heur = -1.0f, best = -1.0f;
+    int best_L = heur;
+    for (int L : cands) {
+        void* f = kernel_bsr_spmv_cg(L, h->mixed);
+        KSpec k;
+        if (h->mixed)
+            k.set(f, occ_grid(h, f, h->n / 3, kBlock / L), (const ProbDesc*)h->pd, (const float*)h->p32, h->q32,
+                  h->partials, h->counters + 2 * kCounterStride, h->st_save);
+        else
+            k.set(f, occ_grid(h, f, h->n / 3, kBlock / L), (const ProbDesc*)h->pd, (const double*)h->p, h->q,
+                  h->partials, h->counters + 2 * kCounterStride, h->st_save);
+        PODCG_CK(h, cudaMemsetAsync(h->st_save, 0, sizeof(DevState), s));
+        float tot = 0.0f;
+        for (int rep = 0; rep < 4; ++rep) {
+            PODCG_CK(h, cudaEventRecord(h->tev[0], s));
+            PODCG_CK(h, launch_spec(k, s));
+            PODCG_CK(h, cudaEventRecord(h->tev[1], s));
+            PODCG_CK(h, cudaEventSynchronize(h->tev[1]));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]);
+            if (rep > 0) tot += ms;
+        }
+        tot /= 3.0f;
+        if (L == heur) t_heur = tot;
+        if (best < 0.0f || tot < best) {
+            best = tot;
+            best_L = L;
+        }
+    }
+    if (t_heur < 0.0f || best < 0.9f * t_heur) h->bsr_L = best_L;
     return POD_CG_OK;
 }
 
@@ -557,6 +683,7 @@ pod_cg_status build_s2_graph(pod_cg_t* h, int L, GraphSlot& gs)
     gs.graph = P;
     gs.exec = exec;
     gs.L = L;
+    gs.bsr = h->use_bsr;
     gs.yb = s2_bucket(h->pod_y);
     gs.valid = true;
     return POD_CG_OK;
@@ -671,7 +798,7 @@ pod_cg_status run_loop(pod_cg_t* h, int wb, int L)
     cudaStream_t s = h->stream;
     if (h->cfg.loop_mode == 0) {
         GraphSlot& gs = h->graphs[bi];
-        if (gs.valid && gs.L != L) destroy_graph(gs);
+        if (gs.valid && (gs.L != L || gs.bsr != h->use_bsr)) destroy_graph(gs);
         if (!gs.valid) {
             pod_cg_status bs = build_conditional(h, wb, L, gs);
             if (bs != POD_CG_OK) return bs;
@@ -680,7 +807,7 @@ pod_cg_status run_loop(pod_cg_t* h, int wb, int L)
         return POD_CG_OK;
     }
     GraphSlot& gs = h->chunks[bi];
-    if (gs.valid && gs.L != L) destroy_graph(gs);
+    if (gs.valid && (gs.L != L || gs.bsr != h->use_bsr)) destroy_graph(gs);
     if (!gs.valid) {
         pod_cg_status bs = build_chunk(h, wb, L, gs);
         if (bs != POD_CG_OK) return bs;
@@ -813,6 +940,7 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->energy_y = 0.99999999;
     c->tol_stage2 = 1e-4;
     c->tol_inner = 1e-12;
+    c->bsr = -1;
     return POD_CG_OK;
 }
 
@@ -828,7 +956,7 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     for (auto& g : h->chunks) destroy_graph(g);
     destroy_graph(h->s2graph);
     void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->Y, h->Y32,
-                    h->s2_hist, h->s2tmp,
+                    h->s2_hist, h->s2tmp, h->brp, h->bcol, h->bval, h->bval32, h->bsr_flag,
                     h->G, h->Rinv,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
                     h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
@@ -866,6 +994,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
         return fail(nullptr, POD_CG_ERR_ARG,
                     "invalid three-stage configuration (three_stage 0/1/2, 1 <= y_max <= s_max, energy_y in [0, 1], "
                     "tol_stage2 >= 0, 0 <= tol_inner < 1)");
+    if (c.bsr < -1 || c.bsr > 1) return fail(nullptr, POD_CG_ERR_ARG, "bsr must be -1 (auto), 0 or 1");
     if (c.three_stage == 2 && c.precision != POD_CG_FP64)
         return fail(nullptr, POD_CG_ERR_ARG, "three_stage = 2 (stage three over the whole Y) runs in FP64 only");
     if (c.use_tc_gram != 0 && (c.use_tc_gram != 1 || c.precision != POD_CG_MIXED))
@@ -1048,6 +1177,8 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     }
 
     reset_state(h, A, b, tol);
+    pod_cg_status bst = setup_bsr(h, A);
+    if (bst != POD_CG_OK) return bst;
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
@@ -1063,6 +1194,8 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     pod_cg_status lst = choose_lanes(h, A, &L);
     if (lst != POD_CG_OK) return lst;
     h->last_L = L;
+    pod_cg_status blst = choose_bsr_lanes(h);
+    if (blst != POD_CG_OK) return blst;
 
     // POD of the current snapshots (Algorithm 4); in three-stage mode also the augmenting
     // basis Y, whose first w columns are W (nested POD bases)
@@ -1261,6 +1394,8 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
     h->pod_dirty = h->s_count > 0;   // the next forward solve recomputes its own basis
     h->w_clobbered = true;
     reset_state(h, A, g, tol);
+    pod_cg_status bst = setup_bsr(h, A);
+    if (bst != POD_CG_OK) return bst;
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
@@ -1298,6 +1433,8 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
     if (!b || !ms_out || reps < 1) return fail(h, POD_CG_ERR_ARG, "bad arguments");
     cudaStream_t s = h->stream;
     reset_state(h, A, b, 0.0);
+    pod_cg_status bst = setup_bsr(h, A);
+    if (bst != POD_CG_OK) return bst;
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     DevState& t = *h->st_host;
     t.rho = 1.0;

@@ -33,6 +33,15 @@ cudaError_t launch_dinv(const ProbDesc* pd, int n, double* dinv, float* dinv32, 
 cudaError_t launch_to_f32(const double* a, float* b, size_t m, int sms, cudaStream_t s);
 cudaError_t launch_desc_val_to_f32(const ProbDesc* pd, float* v32, int64_t nnz, int sms, cudaStream_t s);
 
+// 3x3 block-sparse form of the CG product (k_bsr.cu)
+cudaError_t launch_bsr_check(const int32_t* rp, const int32_t* col, int n, int* bad, int sms, cudaStream_t s);
+cudaError_t launch_bsr_pattern(const int32_t* rp, const int32_t* col, int nb, int32_t* brp, int32_t* bcol, int sms,
+                               cudaStream_t s);
+cudaError_t launch_bsr_values(const int32_t* rp, const double* val, int n, int nnzb, double* bval, float* bval32,
+                              int sms, cudaStream_t s);
+int bsr_lanes_for(double blocks_per_row);
+void* kernel_bsr_spmv_cg(int L, bool fp32);
+
 // dense
 void gram_shape(int n, int p, int q, int sms, int* tiles_j, int* tiles, int* splits, int* rows_per_split);
 size_t gram_workspace_bytes(int n, int p, int q, int sms);

@@ -23,11 +23,13 @@ def dev():
     return torch.device("cuda:0")
 
 
-def test_elasticity_small_fp64(dev):
-    """6^3 elements (n = 882), 5 systems, w <= 8. A-norm bound 5e-9: on this operator two
-    FP64 CG runs that differ only in summation order already differ by ~1e-9 after the
-    same number of steps (pinned on the CPU in test_oracle_pins)."""
-    run_parity(dev, wl.elasticity_cantilever(e=6, p=5, w_max=8, s_max=8), tol_a=5e-9)
+@pytest.mark.parametrize("bsr", [0, 1])
+def test_elasticity_small_fp64(dev, bsr):
+    """6^3 elements (n = 882), 5 systems, w <= 8, CG product in CSR (bsr = 0) or 3x3 block
+    form (bsr = 1). A-norm bound 5e-9: on this operator two FP64 CG runs that differ only
+    in summation order already differ by ~1e-9 after the same number of steps (pinned on
+    the CPU in test_oracle_pins)."""
+    run_parity(dev, wl.elasticity_cantilever(e=6, p=5, w_max=8, s_max=8), tol_a=5e-9, bsr=bsr)
 
 
 @pytest.mark.parametrize("nsnap", [40, 64])
@@ -54,13 +56,14 @@ def test_elasticity_wide_basis_fp64(dev, nsnap):
     assert a_err(orc, A, x.cpu().numpy(), xo) <= 1e-10
 
 
-def test_elasticity_small_mixed(dev):
+@pytest.mark.parametrize("bsr", [0, 1])
+def test_elasticity_small_mixed(dev, bsr):
     from oracle import OracleSequence
     from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
     seq = wl.elasticity_cantilever(e=6, p=5, w_max=8, s_max=8)
     orc = Oracle()
     oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
-    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=1)
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=1, bsr=bsr)
     A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
     for j, val, b in seq.systems():
         A = (seq.row_ptr, seq.col, val)
