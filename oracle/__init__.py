@@ -94,6 +94,8 @@ class Oracle:
         lib.orc_chol_solve.argtypes = [ci, vp, vp, vp]
         lib.orc_jacobi_eig.argtypes = [ci, vp, vp, vp, ci]
         lib.orc_pod_evd.argtypes = [ci, ci, vp, cd, ci, cd, vp, vp]
+        lib.orc_jacobi_svd.argtypes = [ci, ci, vp, vp, vp, ci]
+        lib.orc_pod_svd.argtypes = [ci, ci, vp, ci, vp, cd, ci, cd, vp, vp]
         lib.orc_stage_one.argtypes = [ci, vp, vp, vp, vp, ci, vp, vp, vp]
         lib.orc_aug_pcg.argtypes = [ci, vp, vp, vp, vp, ci, vp, vp, vp, cd, ci, ci, vp,
                                     ctypes.POINTER(_Info), vp, vp, ci]
@@ -167,6 +169,26 @@ class Oracle:
         W = np.zeros((n, max(w_max, 1)), order="F")
         sig2 = np.empty(max(s, 1))
         w = self.lib.orc_pod_evd(n, s, _p(S), energy, w_max, rank_tol, _p(W), _p(sig2))
+        return np.asfortranarray(W[:, :w]), w, sig2[:s]
+
+    # -- Algorithm 5 ----------------------------------------------------------------------
+    def jacobi_svd(self, B, max_sweeps: int = 60):
+        B = _f64(B)
+        q, s = B.shape
+        sig = np.empty(s)
+        V = np.empty((s, s))
+        sweeps = self.lib.orc_jacobi_svd(q, s, _p(B), _p(sig), _p(V), max_sweeps)
+        return sig, V, sweeps
+
+    def pod_svd(self, S, C, energy: float, w_max: int, rank_tol: float = 1e-13):
+        """POD with the output pseudometric C^T C (Algorithm 5); C is (q, n)."""
+        S = _f64(S)
+        n, s = S.shape
+        C = np.ascontiguousarray(C, dtype=np.float64)
+        q = C.shape[0]
+        W = np.zeros((n, max(w_max, 1)), order="F")
+        sig2 = np.empty(max(s, 1))
+        w = self.lib.orc_pod_svd(n, s, _p(S), q, _p(C), energy, w_max, rank_tol, _p(W), _p(sig2))
         return np.asfortranarray(W[:, :w]), w, sig2[:s]
 
     # -- Algorithm 2 ----------------------------------------------------------------------
@@ -320,19 +342,21 @@ class OracleSequence:
     first w columns of Y: POD bases are nested) and each system runs the three-stage
     algorithm (Section 4) with stage-two tolerance ``tol_stage2`` times the system's;
     ``stage3_full`` selects the stage-three option of Section 4.3.1 (augmenting with all of
-    Y, inner reduced solves to ``tol_inner``).
+    Y, inner reduced solves to ``tol_inner``). With ``C`` (q output functionals, (q, n))
+    the POD uses the output-oriented metric C^T C (Algorithm 5).
     """
 
     def __init__(self, n: int, s_max: int = 40, w_max: int = 32, energy: float = 0.9999,
                  kmax: int = 100000, max_refine: int = 5, oracle: Oracle | None = None,
                  three_stage: bool = False, y_max: int = 40, energy_y: float = 1.0,
                  tol_stage2: float = 1e-4, w3_cap: int = 64, stage3_full: bool = False,
-                 tol_inner: float = 1e-12):
+                 tol_inner: float = 1e-12, C=None):
         self.n, self.s_max, self.w_max, self.energy = n, s_max, w_max, energy
         self.kmax, self.max_refine = kmax, max_refine
         self.three_stage, self.y_max, self.energy_y = three_stage, y_max, energy_y
         self.tol_stage2, self.w3_cap = tol_stage2, w3_cap
         self.stage3_full, self.tol_inner = stage3_full, tol_inner
+        self.C = None if C is None else np.ascontiguousarray(C, dtype=np.float64)
         self.orc = oracle or Oracle()
         self.snaps: list[np.ndarray] = []
 
@@ -345,18 +369,23 @@ class OracleSequence:
         if not self.snaps:
             return np.zeros((self.n, 0), order="F"), 0, np.zeros(0)
         S = np.asfortranarray(np.stack(self.snaps, axis=1))
-        return self.orc.pod_evd(S, self.energy, self.w_max)
+        return self._pod(S, self.energy, self.w_max)
+
+    def _pod(self, S, energy, w_max):
+        if self.C is not None:   # output-oriented metric C^T C (Algorithm 5)
+            return self.orc.pod_svd(S, self.C, energy, w_max)
+        return self.orc.pod_evd(S, energy, w_max)
 
     def basis_y(self):
         """(Y, w): the augmenting basis and the stage-one dimension (W = Y[:, :w])."""
         if not self.snaps:
             return np.zeros((self.n, 0), order="F"), 0
         S = np.asfortranarray(np.stack(self.snaps, axis=1))
-        _, w, _ = self.orc.pod_evd(S, self.energy, self.w_max)
-        _, y, _ = self.orc.pod_evd(S, self.energy_y, self.y_max)
+        _, w, _ = self._pod(S, self.energy, self.w_max)
+        _, y, _ = self._pod(S, self.energy_y, self.y_max)
         y = max(y, w)
         # energy 2 is never reached: all modes up to the numerical rank, capped at y
-        Y, y2, _ = self.orc.pod_evd(S, 2.0, y)
+        Y, y2, _ = self._pod(S, 2.0, y)
         return Y, min(w, y2)
 
     def solve(self, A, b, tol_rel, record: bool = True):

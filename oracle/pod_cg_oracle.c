@@ -232,6 +232,126 @@ int orc_pod_evd(int n, int s, const double* S, double energy, int w_max, double 
     return w;
 }
 
+/* ------------------------------------------- POD with the output metric (Algorithm 5) */
+
+/* Thin SVD of a q x s matrix B (column-major, column j at j*q) by one-sided Jacobi
+ * rotations (Hestenes' method; Golub & Van Loan §8.6): pairs of columns are rotated until
+ * every pair is orthogonal; the singular values are then the column norms, and V (s x s,
+ * row-major) accumulates the rotations. sigma (length s) decreasing, each column of V
+ * signed with its largest-magnitude entry positive. Returns the sweeps used. */
+int orc_jacobi_svd(int q, int s, const double* B, double* sigma, double* V, int max_sweeps)
+{
+    double* X = (double*)malloc(sizeof(double) * (size_t)q * s + 8);
+    double* U = (double*)malloc(sizeof(double) * (size_t)s * s + 8);
+    memcpy(X, B, sizeof(double) * (size_t)q * s);
+    for (int i = 0; i < s; ++i)
+        for (int j = 0; j < s; ++j) U[i * s + j] = (i == j) ? 1.0 : 0.0;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < s - 1; ++p) {
+            for (int r = p + 1; r < s; ++r) {
+                double alpha = 0.0, beta = 0.0, gamma = 0.0;
+                for (int k = 0; k < q; ++k) {
+                    double xp = X[(size_t)p * q + k], xr = X[(size_t)r * q + k];
+                    alpha += xp * xp;
+                    beta += xr * xr;
+                    gamma += xp * xr;
+                }
+                if (gamma == 0.0 || fabs(gamma) <= 1e-15 * sqrt(alpha * beta)) continue;
+                rotated = 1;
+                /* the rotation that diagonalises [[alpha, gamma], [gamma, beta]] */
+                double zeta = (beta - alpha) / (2.0 * gamma);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+                for (int k = 0; k < q; ++k) {
+                    double xp = X[(size_t)p * q + k], xr = X[(size_t)r * q + k];
+                    X[(size_t)p * q + k] = c * xp - sn * xr;
+                    X[(size_t)r * q + k] = sn * xp + (MUT(17) ? -c : c) * xr;
+                }
+                for (int k = 0; k < s; ++k) {
+                    double up = U[k * s + p], ur = U[k * s + r];
+                    U[k * s + p] = c * up - sn * ur;
+                    U[k * s + r] = sn * up + c * ur;
+                }
+            }
+        }
+        if (!rotated) break;
+    }
+    double* nrm = (double*)malloc(sizeof(double) * (size_t)(s > 0 ? s : 1));
+    for (int j = 0; j < s; ++j) {
+        double a = 0.0;
+        for (int k = 0; k < q; ++k) a += X[(size_t)j * q + k] * X[(size_t)j * q + k];
+        nrm[j] = sqrt(a);
+    }
+    int* order = (int*)malloc(sizeof(int) * (s > 0 ? s : 1));
+    for (int i = 0; i < s; ++i) order[i] = i;
+    for (int i = 0; i < s; ++i) {
+        int best = i;
+        for (int j = i + 1; j < s; ++j)
+            if (nrm[order[j]] > nrm[order[best]]) best = j;
+        int tmp = order[i]; order[i] = order[best]; order[best] = tmp;
+    }
+    for (int i = 0; i < s; ++i) {
+        int src = order[i];
+        sigma[i] = nrm[src];
+        int arg = 0;
+        for (int k = 1; k < s; ++k)
+            if (fabs(U[k * s + src]) > fabs(U[arg * s + src])) arg = k;
+        double sg = U[arg * s + src] < 0.0 ? -1.0 : 1.0;
+        for (int k = 0; k < s; ++k) V[k * s + i] = sg * U[k * s + src];
+    }
+    free(order); free(nrm); free(U); free(X);
+    return sweep;
+}
+
+/* POD with the pseudometric C^T C (Appendix, Algorithm 5; the output-oriented metric of
+ * Section 3.3) and unit weights, for q output functionals (C row-major q x n):
+ *   step 1  Sbar = C S                                   (q x s)
+ *   step 2  thin SVD Sbar = U Sigma V^T                  (one-sided Jacobi, decreasing)
+ *   step 3  w = min{ i <= rank(Sbar) : sum_{k<=i} sigma_k^2 / sum_l sigma_l^2 >= energy },
+ *           capped at w_max; rank = #{sigma_i^2 > rank_tol sigma_1^2} (as Algorithm 4's)
+ *   step 4  W = S [v_1/sigma_1 ... v_w/sigma_w]          (C^T C-orthonormal: (CW)^T CW = I)
+ * S column-major n x s; W_out room for w_max columns; sigma2_out (length s) receives the
+ * sigma_i^2. Returns w. */
+int orc_pod_svd(int n, int s, const double* S, int q, const double* C, double energy, int w_max,
+                double rank_tol, double* W_out, double* sigma2_out)
+{
+    if (s <= 0) return 0;
+    double* Sb = (double*)malloc(sizeof(double) * (size_t)q * s + 8);
+    double* V = (double*)malloc(sizeof(double) * (size_t)s * s + 8);
+    double* sig = (double*)malloc(sizeof(double) * (size_t)s + 8);
+    for (int j = 0; j < s; ++j)                                   /* step 1 */
+        for (int k = 0; k < q; ++k) Sb[(size_t)j * q + k] = orc_dot(n, C + (size_t)k * n, S + (size_t)j * n);
+    orc_jacobi_svd(q, s, Sb, sig, V, 60);                         /* step 2 */
+    for (int i = 0; i < s; ++i) sigma2_out[i] = sig[i] * sig[i];
+    double lam1 = sigma2_out[0];
+    int rank = 0;
+    if (lam1 > 0.0)
+        for (int i = 0; i < s; ++i)
+            if (sigma2_out[i] > rank_tol * lam1) rank = i + 1;
+    double total = 0.0;
+    for (int i = 0; i < s; ++i) total += sigma2_out[i];
+    int w = rank;                                                 /* step 3 */
+    double cum = 0.0;
+    for (int i = 0; i < rank; ++i) {
+        cum += sigma2_out[i];
+        if (cum / total >= energy) { w = i + 1; break; }
+    }
+    if (w > w_max) w = w_max;
+    for (int j = 0; j < w; ++j) {                                 /* step 4 */
+        double inv_sigma = MUT(18) ? 1.0 : 1.0 / sig[j];
+        double* wj = W_out + (size_t)j * n;
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < s; ++k) acc += S[(size_t)k * n + i] * V[k * s + j];
+            wj[i] = acc * inv_sigma;
+        }
+    }
+    free(sig); free(V); free(Sb);
+    return w;
+}
+
 /* ------------------------------------------------------------- stage one (Algorithm 2) */
 
 /* Direct reduced solve (Section 4.1, Algorithm 2) with initial guess xbar = 0:

@@ -449,9 +449,52 @@ def pin_stage3_full_matches_direct(orc):
                 f"dense agreement {e3:.1e}, k2 {i3['k2']}, inner {i3['inner']}")
 
 
+def pin_jacobi_svd_numpy(orc):
+    """One-sided Jacobi SVD against LAPACK (numpy.linalg.svd) for a tall and a wide matrix
+    (the wide one has s - q zero singular values), and V orthogonal."""
+    rng = np.random.default_rng(21)
+    worst = 0.0
+    for q, s in ((9, 5), (3, 6)):
+        B = rng.normal(size=(q, s)) * np.exp(rng.normal(size=s))
+        sig, V, _ = orc.jacobi_svd(np.asfortranarray(B))
+        ref = np.zeros(s)
+        r = np.linalg.svd(B, compute_uv=False)
+        ref[:len(r)] = r
+        worst = max(worst, float(np.max(np.abs(sig - ref)) / ref[0]),
+                    float(np.max(np.abs(V.T @ V - np.eye(s)))))
+    return worst < 1e-13, f"Jacobi SVD vs LAPACK / orthogonality {worst:.1e}"
+
+
+def pin_pod_output_metric(orc):
+    """POD with the metric C^T C (Algorithm 5; q = 12 random U[0,1] functionals): sigma^2
+    equal the squared singular values of C S (LAPACK); W is C^T C-orthonormal; the
+    Eckart-Young identity in the C-seminorm, sum_i ||C s_i - CW (CW)^T C s_i||^2 =
+    sum_{k>w} sigma_k^2; and with C = I the basis and spectrum are the identity-metric
+    POD's (Algorithm 4), an independent route."""
+    S, _ = _snapshots(n=300, s=8, seed=4)
+    rng = np.random.default_rng(5)
+    C = rng.uniform(0.0, 1.0, size=(12, 300))
+    W, w, sig2 = orc.pod_svd(S, C, 0.999, 8)
+    ref = np.linalg.svd(C @ S, compute_uv=False) ** 2
+    e1 = float(np.max(np.abs(sig2[:len(ref)] - ref)) / ref[0])
+    CW = C @ W
+    e2 = float(np.max(np.abs(CW.T @ CW - np.eye(w))))
+    CS = C @ S
+    resid = CS - CW @ (CW.T @ CS)
+    e3 = abs(float(np.sum(resid ** 2)) - float(np.sum(sig2[w:]))) / float(np.sum(sig2))
+    We, we, sig2e = orc.pod_evd(S, 0.999, 8)
+    Wi, wi, sig2i = orc.pod_svd(S, np.eye(300), 0.999, 8)
+    e4 = float(np.max(np.abs(sig2i - sig2e)) / sig2e[0])
+    cos = np.linalg.svd(Wi.T @ We, compute_uv=False) if wi == we else np.zeros(1)
+    ok = 0 < w < 8 and e1 < 1e-12 and e2 < 1e-10 and e3 < 1e-12 and wi == we and e4 < 1e-12 and cos.min() > 1 - 1e-10
+    return ok, (f"output POD: sigma^2 vs LAPACK {e1:.1e}, C-orthonormality {e2:.1e}, Eckart-Young {e3:.1e}, "
+                f"C = I vs Algorithm 4: w {wi}/{we}, sigma^2 {e4:.1e}, cos {cos.min():.12f}")
+
+
 ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
             pin_finite_termination, pin_theta_grad_complex_step, pin_stage_two_optimality,
             pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse,
-            pin_stage_two_reorthogonalised, pin_stage3_full_matches_direct]
+            pin_stage_two_reorthogonalised, pin_stage3_full_matches_direct, pin_jacobi_svd_numpy,
+            pin_pod_output_metric]

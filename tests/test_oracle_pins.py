@@ -33,6 +33,8 @@ MUTANTS = {
     14: "stage-two initial residual omits the stage-one solution's product",
     15: "stage two skips the re-A-orthogonalisation of its directions",
     16: "inner reduced solves start from zero instead of the Galerkin solution over the stored basis",
+    17: "one-sided Jacobi SVD rotates the second column with the wrong sign",
+    18: "output-metric POD lift without 1/sigma",
 }
 
 
