@@ -75,6 +75,9 @@ def parse_args():
                     help="profiling target: system 1 of the workload with Y seeded random snapshots, FP64, "
                          "stage two run to its cap (y - w reduced iterations, host-driven launches), then 5 "
                          "iterations of stage three with [W, V2] and 5 with the whole Y; one JSON line")
+    ap.add_argument("--output-pod", type=int, default=0, metavar="Q",
+                    help="output-oriented POD (metric C^T C, Q random U[0,1] functionals) against the identity "
+                         "metric on the --grid/--systems diffusion sequence; one JSON line")
     ap.add_argument("--bsr", type=int, default=-1, choices=[-1, 0, 1],
                     help="CG product in 3x3 block form: -1 when the pattern allows (default), 0 never, 1 required")
     ap.add_argument("--batch-seqs", type=int, default=256)
@@ -518,6 +521,64 @@ def elasticity_bench(args):
     return 0
 
 
+def output_pod_bench(args):
+    """The output-oriented POD of Section 3.3 (metric C^T C with Q functionals of U[0,1]
+    entries, as in the paper's output experiment) against the identity metric, same
+    sequence, precision and tolerance, each timed over the sequence (CUDA events) after one
+    untimed pass. Also reports the relative output error ||C (x0 - x)|| / ||C x|| of the
+    stage-one iterate x0 (the part the POD metric shapes) for the last system. Prints one
+    JSON line."""
+    import torch
+    from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
+    from paper_1512_05820_gb300.solver import PodCG
+    seq = workload(args)
+    prec = 1 if args.precision == "mixed" else 0
+    dseq = DeviceSequence(seq, systems=seq.all_systems())
+    xs = [torch.empty(seq.n, dtype=torch.float64, device="cuda") for _ in range(dseq.p)]
+    gen = torch.Generator(device="cuda").manual_seed(17)
+    C = torch.rand((args.output_pod, seq.n), generator=gen, device="cuda", dtype=torch.float64)
+
+    def one(output):
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec,
+                       spmv_lanes=args.spmv_lanes)
+        if output:
+            solver.set_output_functionals(C)
+        run_sequence(solver, dseq, xs)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(solver.stream)
+        st = run_sequence(solver, dseq, xs)
+        b.record(solver.stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        # stage-one iterate of the last system: a solve capped at 0 iterations
+        j = dseq.p - 1
+        probe = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=0, k_max=0,
+                      max_refine=0)
+        if output:
+            probe.set_output_functionals(C)
+        for k in range(max(0, j - seq.s_max), j):
+            probe.add_snapshots(xs[k])
+        x0, _ = probe.solve(dseq.matrix(j), dseq.bs[j], seq.tol, raise_on_error=False)
+        out_err = float(torch.linalg.norm(C @ (x0 - xs[j])) / torch.linalg.norm(C @ xs[j]))
+        probe.close()
+        solver.close()
+        return {"systems_per_s": dseq.p / (ms / 1e3), "ms": ms,
+                "mean_iters": float(np.mean([s["iters"] for s in st])),
+                "mean_w": float(np.mean([s["w"] for s in st])),
+                "ms_pod_mean": float(np.mean([s["ms_pod"] for s in st])),
+                "last_stage1_relres": st[-1]["stage1_relres"],
+                "last_stage1_output_relerr": out_err,
+                "max_final_relres": max(s["final_relres"] for s in st)}
+
+    out = {"output_pod": True, "workload": f"diffusion3d_moving {args.grid}^3 7-point, {seq.p} systems",
+           "q": args.output_pod, "precision": args.precision, "tol": seq.tol,
+           "identity_metric": one(False), "output_metric": one(True)}
+    out["speedup_output_vs_identity"] = out["output_metric"]["systems_per_s"] / out["identity_metric"]["systems_per_s"]
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def three_stage_bench(args):
     """Three-stage solves (stage one on the dominant POD modes, stage two over all retained
     modes, stage three augmented with [W, V2]) against the two-stage form (stage one on the
@@ -678,6 +739,8 @@ def main():
         return stage2_profile(args)
     if args.three_stage:
         return three_stage_bench(args)
+    if args.output_pod:
+        return output_pod_bench(args)
     if args.elasticity:
         return elasticity_bench(args)
 

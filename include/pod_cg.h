@@ -186,6 +186,14 @@ const char* pod_cg_last_error(const pod_cg_t* h);
  * rows (Algorithm 4 step 1). Errors: ERR_ARG. */
 pod_cg_status pod_cg_add_snapshots(pod_cg_t* h, const double* X, int m);
 
+/* Output-oriented POD (Section 3.3, metric C^T C; Algorithm 5's POD): set q output
+ * functionals (C: device, q-by-n row-major, copied; 1 <= q <= 128) whose values C x the
+ * basis should capture. Later PODs then use the Gram (C S)^T (C S) of the snapshots'
+ * output images instead of S^T S (the library keeps C s for each held snapshot, one
+ * product of C per added snapshot), so W = S V Sigma^{-1} is C^T C-orthonormal. q = 0
+ * returns to the identity metric. Errors: ERR_ARG, ERR_CUDA. */
+pod_cg_status pod_cg_set_output_functionals(pod_cg_t* h, const double* C, int q);
+
 /* Forget all snapshots (the next solve is plain Jacobi PCG). */
 pod_cg_status pod_cg_clear_snapshots(pod_cg_t* h);
 

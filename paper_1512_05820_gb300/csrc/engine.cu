@@ -39,6 +39,7 @@ using namespace podcg;
 namespace {
 
 thread_local std::string g_last_error;
+constexpr int kQMax = 128;   // output functionals of the output-oriented POD metric
 constexpr int kChunk = 16;   // iterations per plain graph in loop_mode 1
 
 int device_sms()
@@ -175,6 +176,14 @@ struct pod_cg_t {
     int k2 = 0, k2_launch = 0;  // last solve: stage-two iterations, their loop bodies run
     bool w_clobbered = false;   // stage two wrote over W's columns (stage-one Cholesky failed)
     bool it_mode = false;       // last solve ran stage three over the whole Y
+
+    // output-oriented POD metric C^T C (Section 3.3): the q functionals and C s per slot
+    int out_q = 0;
+    double* Cout = nullptr;      // q x n row-major (functional i at Cout + i n)
+    double* CSv = nullptr;       // C s_k for slot k at CSv + k * kQMax
+    double* GSC = nullptr;       // kSMax x kSMax Gram (C S)^T (C S), slot order
+    double* out_work = nullptr;  // workspace of the products C s
+    size_t out_work_bytes = 0;
 
     // 3x3 block form of the CG product (k_bsr.cu): pattern cache and buffers
     const int32_t* bsr_key = nullptr;   // row_ptr of the pattern checked last
@@ -956,7 +965,8 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     for (auto& g : h->chunks) destroy_graph(g);
     destroy_graph(h->s2graph);
     void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->Y, h->Y32,
-                    h->s2_hist, h->s2tmp, h->brp, h->bcol, h->bval, h->bval32, h->bsr_flag,
+                    h->s2_hist, h->s2tmp, h->brp, h->bcol, h->bval, h->bval32, h->bsr_flag, h->Cout, h->CSv,
+                    h->GSC, h->out_work,
                     h->G, h->Rinv,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
                     h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
@@ -1121,8 +1131,45 @@ pod_cg_status pod_cg_add_snapshots(pod_cg_t* h, const double* X, int m)
         PODCG_CK(h, launch_gram(n, col, h->ld, 1, h->S, h->ld, h->s_count, nullptr, h->grow, kSMax, 0, h->gram_work,
                                 h->gram_work_bytes, h->sms, h->stream));
         PODCG_CK(h, launch_gram_scatter(h->grow, h->s_count, slot, h->GS, kSMax, h->stream));
+        if (h->out_q > 0)   // C s_new for the output-oriented metric
+            PODCG_CK(h, launch_gram(n, col, h->ld, 1, h->Cout, n, h->out_q, nullptr, h->CSv + (size_t)slot * kQMax,
+                                    kQMax, 0, h->out_work, h->out_work_bytes, h->sms, h->stream));
     }
     if (m > 0) h->pod_dirty = true;
+    return POD_CG_OK;
+}
+
+pod_cg_status pod_cg_set_output_functionals(pod_cg_t* h, const double* C, int q)
+{
+    if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
+    if (q < 0 || q > kQMax || (q > 0 && !C)) return fail(h, POD_CG_ERR_ARG, "q must be 0..128 and C non-NULL");
+    cudaStream_t s = h->stream;
+    const int n = h->n;
+    if (q > 0) {
+        if (!h->Cout) {
+            PODCG_CK(h, cudaMalloc((void**)&h->Cout, sizeof(double) * (size_t)kQMax * n));
+            PODCG_CK(h, cudaMalloc((void**)&h->CSv, sizeof(double) * (size_t)kQMax * kSMax));
+            PODCG_CK(h, cudaMalloc((void**)&h->GSC, sizeof(double) * (size_t)kSMax * kSMax));
+        }
+        // the product's split count depends on q: size the workspace for this q
+        const size_t wb = gram_workspace_bytes(n, 1, q, h->sms);
+        if (wb > h->out_work_bytes) {
+            cudaFree(h->out_work);
+            h->out_work = nullptr;
+            h->out_work_bytes = 0;
+            PODCG_CK(h, cudaMalloc((void**)&h->out_work, wb));
+            h->out_work_bytes = wb;
+        }
+        PODCG_CK(h, cudaMemcpyAsync(h->Cout, C, sizeof(double) * (size_t)q * n, cudaMemcpyDeviceToDevice, s));
+        // images of the snapshots already held
+        for (int k = 0; k < h->s_count; ++k)
+            PODCG_CK(h, launch_gram(n, h->S + (size_t)k * h->ld, h->ld, 1, h->Cout, n, q, nullptr,
+                                    h->CSv + (size_t)k * kQMax, kQMax, 0, h->out_work, h->out_work_bytes, h->sms, s));
+    }
+    h->out_q = q;
+    h->pod_dirty = h->s_count > 0;
+    h->vprev_s = 0;   // the previous eigenvectors belong to the other metric
+    PODCG_CK(h, cudaStreamSynchronize(s));
     return POD_CG_OK;
 }
 
@@ -1201,7 +1248,13 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     // basis Y, whose first w columns are W (nested POD bases)
     const bool three = h->cfg.three_stage != 0;
     if (h->s_count > 0 && h->pod_dirty) {
-        PODCG_CK(h, launch_pod_eig(h->GS, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, h->cfg.w_max, h->C,
+        const double* Gpod = h->GS;
+        if (h->out_q > 0) {   // metric C^T C: the Gram of the snapshots' output images
+            PODCG_CK(h, launch_cs_gram(h->CSv, kQMax, h->s_count, h->out_q, h->GSC, kSMax, s));
+            Gpod = h->GSC;
+            launches += 1;
+        }
+        PODCG_CK(h, launch_pod_eig(Gpod, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, h->cfg.w_max, h->C,
                                    h->sigma2, h->st, h->Vprev, h->vprev_s, s, h->cfg.energy_y,
                                    three ? h->cfg.y_max : 0));
         h->vprev_s = h->s_count;

@@ -644,6 +644,26 @@ cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, in
     return cudaGetLastError();
 }
 
+// Gram of the output-functional images of the snapshots (the output-oriented metric C^T C
+// of Section 3.3): G[k][l] = sum_i cs[k][i] cs[l][i] for slots k, l < s, with cs[k] = C s_k
+// (q values at cs + k * ldc). One thread per entry (s <= 64, q <= 128), fixed order.
+__global__ void k_cs_gram(const double* __restrict__ cs, int ldc, int s, int q, double* __restrict__ G, int ldg)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < s * s; e += gridDim.x * blockDim.x) {
+        const int k = e / s, l = e % s;
+        double v = 0.0;
+        for (int i = 0; i < q; ++i) v += cs[(size_t)k * ldc + i] * cs[(size_t)l * ldc + i];
+        G[(size_t)k * ldg + l] = v;
+    }
+}
+
+cudaError_t launch_cs_gram(const double* cs, int ldc, int s, int q, double* G, int ldg, cudaStream_t str)
+{
+    k_cs_gram<<<(s * s + kBlock - 1) / kBlock > 0 ? (s * s + kBlock - 1) / kBlock : 1, kBlock, 0, str>>>(cs, ldc, s, q,
+                                                                                                         G, ldg);
+    return cudaGetLastError();
+}
+
 // Scatter one new row of the snapshot Gram: G[q][k] = G[k][q] = row[k], k < s.
 __global__ void k_gram_scatter(const double* __restrict__ row, int s, int q, double* __restrict__ G, int ldg)
 {

@@ -61,6 +61,7 @@ cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, doubl
 cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str,
                         int w_dim = -1);
 cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
+cudaError_t launch_cs_gram(const double* cs, int ldc, int s, int q, double* G, int ldg, cudaStream_t str);
 
 // CG iteration (k_cg.cu): kernel pointers for graph construction
 // FP32 with w > 0 has two forms of the update/direction passes: row-parallel float4

@@ -111,6 +111,17 @@ class PodCG:
     def clear_snapshots(self):
         _check(self.L.pod_cg_clear_snapshots(self.h), self.h)
 
+    def set_output_functionals(self, C: torch.Tensor | None):
+        """Output-oriented POD metric C^T C: C is (q, n) float64 on the device (None: back to
+        the identity metric)."""
+        if C is None:
+            _check(self.L.pod_cg_set_output_functionals(self.h, None, 0), self.h)
+            return
+        assert C.dtype == torch.float64 and C.is_cuda and C.shape[1] == self.n
+        C = C.contiguous()
+        self._C = C   # the copy into the handle is stream-ordered
+        _check(self.L.pod_cg_set_output_functionals(self.h, C.data_ptr(), C.shape[0]), self.h)
+
     def solve(self, A: DeviceCSR, b: torch.Tensor, tol: float, x_out: torch.Tensor | None = None,
               raise_on_error: bool = True):
         """Solve A x = b to ||b - A x|| <= tol ||b||. Returns (x, stats dict)."""
