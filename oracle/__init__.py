@@ -95,6 +95,7 @@ class Oracle:
         lib.orc_jacobi_eig.argtypes = [ci, vp, vp, vp, ci]
         lib.orc_pod_evd.argtypes = [ci, ci, vp, cd, ci, cd, vp, vp]
         lib.orc_jacobi_svd.argtypes = [ci, ci, vp, vp, vp, ci]
+        lib.orc_pod_evd_metric.argtypes = [ci, ci, vp, vp, vp, vp, cd, ci, cd, vp, vp]
         lib.orc_pod_svd.argtypes = [ci, ci, vp, ci, vp, cd, ci, cd, vp, vp]
         lib.orc_stage_one.argtypes = [ci, vp, vp, vp, vp, ci, vp, vp, vp]
         lib.orc_aug_pcg.argtypes = [ci, vp, vp, vp, vp, ci, vp, vp, vp, cd, ci, ci, vp,
@@ -169,6 +170,17 @@ class Oracle:
         W = np.zeros((n, max(w_max, 1)), order="F")
         sig2 = np.empty(max(s, 1))
         w = self.lib.orc_pod_evd(n, s, _p(S), energy, w_max, rank_tol, _p(W), _p(sig2))
+        return np.asfortranarray(W[:, :w]), w, sig2[:s]
+
+    def pod_evd_metric(self, S, A, energy: float, w_max: int, rank_tol: float = 1e-13):
+        """POD with the metric A (Algorithm 4 with Theta = A): W^T A W = I."""
+        S = _f64(S)
+        n, s = S.shape
+        rp, col, val = _i32(A[0]), _i32(A[1]), _f64(A[2])
+        W = np.zeros((n, max(w_max, 1)), order="F")
+        sig2 = np.empty(max(s, 1))
+        w = self.lib.orc_pod_evd_metric(n, s, _p(S), _p(rp), _p(col), _p(val), energy, w_max, rank_tol, _p(W),
+                                        _p(sig2))
         return np.asfortranarray(W[:, :w]), w, sig2[:s]
 
     # -- Algorithm 5 ----------------------------------------------------------------------
@@ -343,20 +355,23 @@ class OracleSequence:
     algorithm (Section 4) with stage-two tolerance ``tol_stage2`` times the system's;
     ``stage3_full`` selects the stage-three option of Section 4.3.1 (augmenting with all of
     Y, inner reduced solves to ``tol_inner``). With ``C`` (q output functionals, (q, n))
-    the POD uses the output-oriented metric C^T C (Algorithm 5).
+    the POD uses the output-oriented metric C^T C (Algorithm 5); with ``metric_a`` it uses
+    the metric A of the system being solved (Algorithm 4 with Theta = A).
     """
 
     def __init__(self, n: int, s_max: int = 40, w_max: int = 32, energy: float = 0.9999,
                  kmax: int = 100000, max_refine: int = 5, oracle: Oracle | None = None,
                  three_stage: bool = False, y_max: int = 40, energy_y: float = 1.0,
                  tol_stage2: float = 1e-4, w3_cap: int = 64, stage3_full: bool = False,
-                 tol_inner: float = 1e-12, C=None):
+                 tol_inner: float = 1e-12, C=None, metric_a: bool = False):
         self.n, self.s_max, self.w_max, self.energy = n, s_max, w_max, energy
         self.kmax, self.max_refine = kmax, max_refine
         self.three_stage, self.y_max, self.energy_y = three_stage, y_max, energy_y
         self.tol_stage2, self.w3_cap = tol_stage2, w3_cap
         self.stage3_full, self.tol_inner = stage3_full, tol_inner
         self.C = None if C is None else np.ascontiguousarray(C, dtype=np.float64)
+        self.metric_a = metric_a
+        self._A = None   # the current system's matrix (metric A)
         self.orc = oracle or Oracle()
         self.snaps: list[np.ndarray] = []
 
@@ -374,6 +389,8 @@ class OracleSequence:
     def _pod(self, S, energy, w_max):
         if self.C is not None:   # output-oriented metric C^T C (Algorithm 5)
             return self.orc.pod_svd(S, self.C, energy, w_max)
+        if self.metric_a:        # metric A of the system being solved
+            return self.orc.pod_evd_metric(S, self._A, energy, w_max)
         return self.orc.pod_evd(S, energy, w_max)
 
     def basis_y(self):
@@ -389,6 +406,7 @@ class OracleSequence:
         return Y, min(w, y2)
 
     def solve(self, A, b, tol_rel, record: bool = True):
+        self._A = A
         if self.three_stage:
             Y, w = self.basis_y()
             if self.stage3_full:

@@ -232,6 +232,53 @@ int orc_pod_evd(int n, int s, const double* S, double energy, int w_max, double 
     return w;
 }
 
+/* POD with the metric Theta = A (Algorithm 4 with a metric; Section 3.3's A-norm metric,
+ * under which POD minimises a bound on the A-norm error of the next solution): step 1
+ * forms Kbar = S^T (A S) with the matrix-vector products A s_k, steps 2-4 as
+ * orc_pod_evd. The basis is A-orthonormal: W^T A W = I. */
+int orc_pod_evd_metric(int n, int s, const double* S, const int* rp, const int* ci, const double* va,
+                       double energy, int w_max, double rank_tol, double* W_out, double* sigma2_out)
+{
+    if (s <= 0) return 0;
+    double* AS = (double*)malloc(sizeof(double) * (size_t)n * s + 8);
+    double* K = (double*)malloc(sizeof(double) * (size_t)s * s);
+    double* V = (double*)malloc(sizeof(double) * (size_t)s * s);
+    orc_spmm(n, rp, ci, va, s, S, AS);                           /* step 1 */
+    orc_gram(n, s, S, s, AS, K);
+    for (int a = 0; a < s; ++a)                                   /* symmetric part */
+        for (int c = a + 1; c < s; ++c) {
+            double m = 0.5 * (K[a * s + c] + K[c * s + a]);
+            K[a * s + c] = m;
+            K[c * s + a] = MUT(19) ? -m : m;
+        }
+    orc_jacobi_eig(s, K, sigma2_out, V, 60);                     /* step 2 */
+    double lam1 = sigma2_out[0];
+    int rank = 0;
+    if (lam1 > 0.0)
+        for (int i = 0; i < s; ++i)
+            if (sigma2_out[i] > rank_tol * lam1) rank = i + 1;
+    double total = 0.0;
+    for (int i = 0; i < s; ++i) total += fmax(sigma2_out[i], 0.0);
+    int w = rank;                                                /* step 3 */
+    double cum = 0.0;
+    for (int i = 0; i < rank; ++i) {
+        cum += sigma2_out[i];
+        if (cum / total >= energy) { w = i + 1; break; }
+    }
+    if (w > w_max) w = w_max;
+    for (int j = 0; j < w; ++j) {                                /* step 4 */
+        double inv_sigma = 1.0 / sqrt(sigma2_out[j]);
+        double* wj = W_out + (size_t)j * n;
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int k = 0; k < s; ++k) acc += S[(size_t)k * n + i] * V[k * s + j];
+            wj[i] = acc * inv_sigma;
+        }
+    }
+    free(V); free(K); free(AS);
+    return w;
+}
+
 /* ------------------------------------------- POD with the output metric (Algorithm 5) */
 
 /* Thin SVD of a q x s matrix B (column-major, column j at j*q) by one-sided Jacobi

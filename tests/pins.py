@@ -491,10 +491,34 @@ def pin_pod_output_metric(orc):
                 f"C = I vs Algorithm 4: w {wi}/{we}, sigma^2 {e4:.1e}, cos {cos.min():.12f}")
 
 
+def pin_pod_a_metric(orc):
+    """POD with the metric A (Algorithm 4 with Theta = A): eigenvalues equal LAPACK's of
+    S^T A S; W^T A W = I; the Eckart-Young identity in the A-norm,
+    sum_i ||s_i - W W^T A s_i||_A^2 = sum_{k>w} lambda_k; and A = I reproduces the
+    identity-metric POD."""
+    S, _ = _snapshots(n=300, s=8, seed=6)
+    A = small_diffusion(10, seed=2)
+    n = A.n
+    S = np.asfortranarray(S[:n])
+    D = A.todense()
+    W, w, lam = orc.pod_evd_metric(S, A.arrays(), 0.999, 8)
+    ref = np.sort(np.linalg.eigvalsh(S.T @ D @ S))[::-1]
+    e1 = float(np.max(np.abs(lam - ref)) / ref[0])
+    e2 = float(np.max(np.abs(W.T @ D @ W - np.eye(w))))
+    R = S - W @ (W.T @ (D @ S))
+    e3 = abs(float(np.einsum("ij,ij->", R, D @ R)) - float(np.sum(lam[w:]))) / float(np.sum(lam))
+    I = dense_to_csr(np.eye(n))
+    Wi, wi, lami = orc.pod_evd_metric(S, I.arrays(), 0.999, 8)
+    We, we, lame = orc.pod_evd(S, 0.999, 8)
+    e4 = float(np.max(np.abs(lami - lame)) / lame[0])
+    ok = 0 < w < 8 and e1 < 1e-12 and e2 < 1e-10 and e3 < 1e-10 and wi == we and e4 < 1e-13
+    return ok, f"A-metric POD: lambda vs LAPACK {e1:.1e}, A-orthonormality {e2:.1e}, Eckart-Young {e3:.1e}, A = I {e4:.1e}"
+
+
 ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
             pin_finite_termination, pin_theta_grad_complex_step, pin_stage_two_optimality,
             pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse,
             pin_stage_two_reorthogonalised, pin_stage3_full_matches_direct, pin_jacobi_svd_numpy,
-            pin_pod_output_metric]
+            pin_pod_output_metric, pin_pod_a_metric]

@@ -35,6 +35,7 @@ MUTANTS = {
     16: "inner reduced solves start from zero instead of the Galerkin solution over the stored basis",
     17: "one-sided Jacobi SVD rotates the second column with the wrong sign",
     18: "output-metric POD lift without 1/sigma",
+    19: "A-metric POD Gram symmetrised with a sign error",
 }
 
 
