@@ -522,15 +522,16 @@ def elasticity_bench(args):
 
 
 def output_pod_bench(args):
-    """The output-oriented POD of Section 3.3 (metric C^T C with Q functionals of U[0,1]
-    entries, as in the paper's output experiment) against the identity metric, same
-    sequence, precision and tolerance, each timed over the sequence (CUDA events) after one
-    untimed pass. Also reports the relative output error ||C (x0 - x)|| / ||C x|| of the
+    """The POD metrics of Section 3.3 on one sequence: the identity metric, the output-
+    oriented metric C^T C (Q functionals of U[0,1] entries, as in the paper's output
+    experiment) and the metric A of each system (also with the three-stage algorithm, whose
+    stage two then sees Y^T A Y = I); same precision and tolerance, each timed over the
+    sequence (CUDA events) after one untimed pass. Also reports the relative output error ||C (x0 - x)|| / ||C x|| of the
     stage-one iterate x0 (the part the POD metric shapes) for the last system. Prints one
     JSON line."""
     import torch
     from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
-    from paper_1512_05820_gb300.solver import PodCG
+    from paper_1512_05820_gb300.solver import PodCG, PodCGError
     seq = workload(args)
     prec = 1 if args.precision == "mixed" else 0
     dseq = DeviceSequence(seq, systems=seq.all_systems())
@@ -538,9 +539,15 @@ def output_pod_bench(args):
     gen = torch.Generator(device="cuda").manual_seed(17)
     C = torch.rand((args.output_pod, seq.n), generator=gen, device="cuda", dtype=torch.float64)
 
-    def one(output):
-        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=prec,
-                       spmv_lanes=args.spmv_lanes)
+    def one(output, **cfg):
+        try:
+            return one_(output, **cfg)
+        except PodCGError as e:   # reported in the line, not fatal to the other variants
+            return {"config": dict(cfg), "error": str(e)[:200]}
+
+    def one_(output, **cfg):
+        cfg.setdefault("energy", seq.energy)
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, precision=prec, spmv_lanes=args.spmv_lanes, **cfg)
         if output:
             solver.set_output_functionals(C)
         run_sequence(solver, dseq, xs)
@@ -553,8 +560,8 @@ def output_pod_bench(args):
         ms = a.elapsed_time(b)
         # stage-one iterate of the last system: a solve capped at 0 iterations
         j = dseq.p - 1
-        probe = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=0, k_max=0,
-                      max_refine=0)
+        probe = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=cfg["energy"], precision=0, k_max=0,
+                      max_refine=0, pod_metric=cfg.get("pod_metric", 0))
         if output:
             probe.set_output_functionals(C)
         for k in range(max(0, j - seq.s_max), j):
@@ -566,6 +573,7 @@ def output_pod_bench(args):
         return {"systems_per_s": dseq.p / (ms / 1e3), "ms": ms,
                 "mean_iters": float(np.mean([s["iters"] for s in st])),
                 "mean_w": float(np.mean([s["w"] for s in st])),
+                "mean_stage2_iters": float(np.mean([s["stage2_iters"] for s in st])),
                 "ms_pod_mean": float(np.mean([s["ms_pod"] for s in st])),
                 "last_stage1_relres": st[-1]["stage1_relres"],
                 "last_stage1_output_relerr": out_err,
@@ -573,8 +581,13 @@ def output_pod_bench(args):
 
     out = {"output_pod": True, "workload": f"diffusion3d_moving {args.grid}^3 7-point, {seq.p} systems",
            "q": args.output_pod, "precision": args.precision, "tol": seq.tol,
-           "identity_metric": one(False), "output_metric": one(True)}
-    out["speedup_output_vs_identity"] = out["output_metric"]["systems_per_s"] / out["identity_metric"]["systems_per_s"]
+           "identity_metric": one(False), "output_metric": one(True), "a_metric": one(False, pod_metric=1),
+           "a_metric_three_stage_e099": one(False, pod_metric=1, energy=0.99, three_stage=1, y_max=seq.s_max,
+                                            energy_y=0.99999999, tol_stage2=1e-4)}
+    base = out["identity_metric"].get("systems_per_s")
+    out["speedup_vs_identity"] = {k: out[k]["systems_per_s"] / base
+                                  for k in ("output_metric", "a_metric", "a_metric_three_stage_e099")
+                                  if base and "systems_per_s" in out[k]}
     print(json.dumps(out), flush=True)
     return 0
 

@@ -120,6 +120,11 @@ typedef struct {
                             per node, columns in aligned triplets, n % 3 == 0): -1 = when the
                             pattern allows (checked once per pattern), 0 = never, 1 = required
                             (ERR_ARG at solve time when the pattern does not allow it) */
+    int    pod_metric;   /* POD metric (Section 3.3): 0 = identity (S^T S); 1 = the matrix A of
+                            the system being solved (S^T A S from one SpMM of the snapshots
+                            per solve: W is A-orthonormal, the metric under which POD bounds
+                            the A-norm error). Output functionals (pod_cg_set_output_
+                            functionals) need 0. */
 } pod_cg_config;
 
 /* CSR matrix, device arrays, borrowed. */
@@ -161,7 +166,7 @@ typedef struct {
 /* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
  * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
  * loop_mode 0, proj_form -1, spmv_lanes 0, three_stage 0, y_max 40, energy_y 0.99999999,
- * tol_stage2 1e-4, tol_inner 1e-12, bsr -1. */
+ * tol_stage2 1e-4, tol_inner 1e-12, bsr -1, pod_metric 0. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 
 /* Create a solver for systems of order n (the problem statement of Section 2) whose work
@@ -191,7 +196,7 @@ pod_cg_status pod_cg_add_snapshots(pod_cg_t* h, const double* X, int m);
  * basis should capture. Later PODs then use the Gram (C S)^T (C S) of the snapshots'
  * output images instead of S^T S (the library keeps C s for each held snapshot, one
  * product of C per added snapshot), so W = S V Sigma^{-1} is C^T C-orthonormal. q = 0
- * returns to the identity metric. Errors: ERR_ARG, ERR_CUDA. */
+ * returns to the identity metric. Errors: ERR_ARG, ERR_STATE (pod_metric = 1), ERR_CUDA. */
 pod_cg_status pod_cg_set_output_functionals(pod_cg_t* h, const double* C, int q);
 
 /* Forget all snapshots (the next solve is plain Jacobi PCG). */

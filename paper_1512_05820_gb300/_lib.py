@@ -26,7 +26,7 @@ class Config(ctypes.Structure):
                 ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int), ("loop_mode", ctypes.c_int),
                 ("proj_form", ctypes.c_int), ("spmv_lanes", ctypes.c_int), ("three_stage", ctypes.c_int),
                 ("y_max", ctypes.c_int), ("energy_y", ctypes.c_double), ("tol_stage2", ctypes.c_double),
-                ("tol_inner", ctypes.c_double), ("bsr", ctypes.c_int)]
+                ("tol_inner", ctypes.c_double), ("bsr", ctypes.c_int), ("pod_metric", ctypes.c_int)]
 
 
 class CSRStruct(ctypes.Structure):

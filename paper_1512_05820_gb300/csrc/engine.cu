@@ -184,6 +184,9 @@ struct pod_cg_t {
     double* GSC = nullptr;       // kSMax x kSMax Gram (C S)^T (C S), slot order
     double* out_work = nullptr;  // workspace of the products C s
     size_t out_work_bytes = 0;
+    // POD metric A (pod_metric = 1): A S and S^T A S of the system being solved
+    double* AS = nullptr;        // ld x s_max
+    double* GA = nullptr;        // kSMax x kSMax
 
     // 3x3 block form of the CG product (k_bsr.cu): pattern cache and buffers
     const int32_t* bsr_key = nullptr;   // row_ptr of the pattern checked last
@@ -950,6 +953,7 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->tol_stage2 = 1e-4;
     c->tol_inner = 1e-12;
     c->bsr = -1;
+    c->pod_metric = 0;
     return POD_CG_OK;
 }
 
@@ -966,7 +970,7 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     destroy_graph(h->s2graph);
     void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->Y, h->Y32,
                     h->s2_hist, h->s2tmp, h->brp, h->bcol, h->bval, h->bval32, h->bsr_flag, h->Cout, h->CSv,
-                    h->GSC, h->out_work,
+                    h->GSC, h->out_work, h->AS, h->GA,
                     h->G, h->Rinv,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
                     h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
@@ -1005,6 +1009,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
                     "invalid three-stage configuration (three_stage 0/1/2, 1 <= y_max <= s_max, energy_y in [0, 1], "
                     "tol_stage2 >= 0, 0 <= tol_inner < 1)");
     if (c.bsr < -1 || c.bsr > 1) return fail(nullptr, POD_CG_ERR_ARG, "bsr must be -1 (auto), 0 or 1");
+    if (c.pod_metric < 0 || c.pod_metric > 1) return fail(nullptr, POD_CG_ERR_ARG, "pod_metric must be 0 or 1");
     if (c.three_stage == 2 && c.precision != POD_CG_FP64)
         return fail(nullptr, POD_CG_ERR_ARG, "three_stage = 2 (stage three over the whole Y) runs in FP64 only");
     if (c.use_tc_gram != 0 && (c.use_tc_gram != 1 || c.precision != POD_CG_MIXED))
@@ -1041,6 +1046,10 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     if (c.three_stage) PODCG_ALLOC(h->Y, ld * ycols)
     if (c.three_stage) PODCG_ALLOC(h->s2_hist, (size_t)2 * kWMax * kSMax + kWMax)
     if (c.three_stage == 2) PODCG_ALLOC(h->s2tmp, ld * 2)
+    if (c.pod_metric == 1) {
+        PODCG_ALLOC(h->AS, ld * c.s_max)
+        PODCG_ALLOC(h->GA, (size_t)kSMax * kSMax)
+    }
     PODCG_ALLOC(h->G, (size_t)kWMax * (kWMax + 1))
     PODCG_ALLOC(h->Rinv, (size_t)kWMax * kWMax)
     PODCG_ALLOC(h->x, ld)
@@ -1073,12 +1082,20 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     }
 #undef PODCG_ALLOC
     if (e == cudaSuccess) {
-        h->gram_work_bytes = std::max(gram_workspace_bytes(n, 1, c.s_max, h->sms),
-                                      gram_workspace_bytes(n, c.w_max, c.w_max + 1, h->sms));
+        // the split count of a Gram depends on its shape, and smaller shapes can need more
+        // workspace: take the maximum over the shapes each use can take
+        for (int k = 1; k <= c.s_max; ++k) {
+            h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, 1, k, h->sms));
+            if (c.pod_metric == 1)
+                h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, k, k, h->sms));
+        }
+        for (int k = 1; k <= std::max(c.w_max, c.three_stage ? c.y_max : 0); ++k)
+            for (int j = 1; j <= c.w_max + 1; ++j)
+                h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, k, j, h->sms));
         const int gp = c.three_stage ? std::max(c.w_max, c.y_max) : c.w_max;
-        h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, gp, c.w_max + 1, h->sms));
         if (c.three_stage && h->mixed)   // the re-formed stage-three Gram, up to kWMax columns
-            h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, kWMax, kWMax + 1, h->sms));
+            for (int k = 1; k <= kWMax; ++k)
+                h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, k, k + 1, h->sms));
         if (c.use_tc_gram)
             h->gram_work_bytes = std::max(h->gram_work_bytes, gram_tc_workspace_bytes(n, gp, c.w_max + 1, h->sms));
         e = cudaMalloc((void**)&h->gram_work, h->gram_work_bytes);
@@ -1143,6 +1160,8 @@ pod_cg_status pod_cg_set_output_functionals(pod_cg_t* h, const double* C, int q)
 {
     if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
     if (q < 0 || q > kQMax || (q > 0 && !C)) return fail(h, POD_CG_ERR_ARG, "q must be 0..128 and C non-NULL");
+    if (q > 0 && h->cfg.pod_metric == 1)
+        return fail(h, POD_CG_ERR_STATE, "the handle's POD uses the metric A (pod_metric = 1)");
     cudaStream_t s = h->stream;
     const int n = h->n;
     if (q > 0) {
@@ -1247,12 +1266,20 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     // POD of the current snapshots (Algorithm 4); in three-stage mode also the augmenting
     // basis Y, whose first w columns are W (nested POD bases)
     const bool three = h->cfg.three_stage != 0;
+    if (h->cfg.pod_metric == 1 && h->s_count > 0) h->pod_dirty = true;   // the metric is this system's A
     if (h->s_count > 0 && h->pod_dirty) {
         const double* Gpod = h->GS;
         if (h->out_q > 0) {   // metric C^T C: the Gram of the snapshots' output images
             PODCG_CK(h, launch_cs_gram(h->CSv, kQMax, h->s_count, h->out_q, h->GSC, kSMax, s));
             Gpod = h->GSC;
             launches += 1;
+        } else if (h->cfg.pod_metric == 1) {   // metric A: S^T (A S), symmetrised
+            PODCG_CK(h, launch_spmm(A->row_ptr, A->col, A->val, h->S, h->ld, h->AS, h->ld, n, h->s_count, h->sms, s));
+            PODCG_CK(h, launch_gram(n, h->S, h->ld, h->s_count, h->AS, h->ld, h->s_count, nullptr, h->GA, kSMax, 0,
+                                    h->gram_work, h->gram_work_bytes, h->sms, s));
+            PODCG_CK(h, launch_symmetrize(h->GA, kSMax, h->s_count, s));
+            Gpod = h->GA;
+            launches += 4;
         }
         PODCG_CK(h, launch_pod_eig(Gpod, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, h->cfg.w_max, h->C,
                                    h->sigma2, h->st, h->Vprev, h->vprev_s, s, h->cfg.energy_y,
@@ -1354,8 +1381,9 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         if (d.w1 < w) h->w_clobbered = true;   // stage-one basis dropped: V2 starts at column 0
         launches += 2 + 2 * h->k2_launch;
         if (h->mixed && h->k2 > 0) {
-            // MIXED: stage three iterates on the FP32 basis [W32, V2_32], whose A-products
-            // come from the FP32 SpMM as A W32's do, and it re-forms that basis' Gram and
+            // MIXED: stage three iterates on the FP32 basis [W32, V2_32] (V2's columns scaled
+            // to unit A-norm), whose A-products come from the FP32 SpMM as A W32's do, and it
+            // re-forms that basis' Gram and
             // Cholesky factor instead of taking blockdiag(R, sqrt(T2)): rounded to FP32, and
             // multiplied by the FP32 matrix with its cancellation on smooth vectors, [W, V2]
             // is A-orthogonal only to FP32 accuracy times that cancellation, and the FP32 inner
@@ -1363,16 +1391,19 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
             // gets one). The factor solve also replaces [what; alpha] by the Galerkin
             // coordinates over range([W, V2]), which the stage-two solution equals in exact
             // arithmetic.
-            const size_t off = (size_t)d.w1 * h->ld, cnt = (size_t)h->k2 * h->ld;
-            PODCG_CK(h, launch_to_f32(h->W + off, h->W32 + off, cnt, h->sms, s));
+            const size_t off = (size_t)d.w1 * h->ld;
+            PODCG_CK(h, launch_s2_to_f32(n, h->ld, h->W, h->W32, d.w1, h->k2, h->Rinv, h->sms, s));
             PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32 + off, h->ld, h->AW32 + off, h->ld, n,
                                         h->k2, h->sms, s));
             PODCG_CK(h, launch_gram32(n, h->W32, h->ld, w3, h->AW32, h->ld, w3, b, h->G, kWMax + 1, 1, h->gram_work,
                                       h->gram_work_bytes, h->sms, s));
-            PODCG_CK(h, launch_chol(h->G, kWMax + 1, h->Rinv, h->st, h->cfg.cond_diag, s, w3));
+            // a non-positive pivot keeps the leading columns: stage two's last directions,
+            // taken after its residual had fallen to rounding level, are the ones that turn
+            // dependent once rounded to FP32
+            PODCG_CK(h, launch_chol(h->G, kWMax + 1, h->Rinv, h->st, h->cfg.cond_diag, s, w3, 1));
             pod_cg_status rs3 = read_state(h);
             if (rs3 != POD_CG_OK) return rs3;
-            w3 = h->st_host->w;   // 0 if the re-formed Gram was not numerically SPD
+            w3 = h->st_host->w;
             launches += 5;
         }
     }

@@ -533,11 +533,12 @@ cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, doubl
 // Stage one, small part (Algorithm 2 step 2): upper Cholesky R^T R of Ahat = G[:, :w]
 // (row-major, row stride ldg, upper triangle read; w = w_dim, or st->pod_w when w_dim < 0),
 // then R^{-1} (stored upper, row stride kWMax) and what = R^{-1} R^{-T} bhat with
-// bhat = G[:, w]. A non-positive pivot marks the
+// bhat = G[:, w]. With truncate, a non-positive pivot k keeps the leading k columns (whose
+// factor is complete) instead of dropping the basis. A non-positive pivot marks the
 // basis unusable: chol_failed = 1 and w = 0 (plain PCG for this system). Optionally the
 // condition number of Ahat by the Jacobi eigensolver.
 __global__ void __launch_bounds__(kBlock) k_chol(const double* __restrict__ G, int ldg, double* __restrict__ Rinv,
-                                                 DevState* st, int want_cond, int w_dim)
+                                                 DevState* st, int want_cond, int w_dim, int truncate)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
@@ -545,8 +546,11 @@ __global__ void __launch_bounds__(kBlock) k_chol(const double* __restrict__ G, i
     double* X = sm.Vs;    // R^{-1}, row stride kSMax
     const int tid = threadIdx.x, nt = blockDim.x;
     const int w = w_dim >= 0 ? w_dim : st->pod_w;
-    __shared__ int s_fail;
-    if (tid == 0) s_fail = 0;
+    __shared__ int s_fail, s_kfail;
+    if (tid == 0) {
+        s_fail = 0;
+        s_kfail = 0;
+    }
     for (int e = tid; e < kSMax * kSMax; e += nt) {
         const int i = e / kSMax, j = e % kSMax;
         R[e] = (i < w && j < w && j >= i) ? G[(size_t)i * ldg + j] : 0.0;
@@ -558,7 +562,10 @@ __global__ void __launch_bounds__(kBlock) k_chol(const double* __restrict__ G, i
         __shared__ double s_piv;
         if (tid == 0) {
             const double d = R[k * kSMax + k];
-            if (!(d > 0.0) || !isfinite(d)) s_fail = 1;
+            if (!(d > 0.0) || !isfinite(d)) {
+                s_fail = 1;
+                s_kfail = k;
+            }
             s_piv = (d > 0.0) ? sqrt(d) : 1.0;
             R[k * kSMax + k] = s_piv;
         }
@@ -574,7 +581,7 @@ __global__ void __launch_bounds__(kBlock) k_chol(const double* __restrict__ G, i
         __syncthreads();
     }
     __syncthreads();
-    const int wu = s_fail ? 0 : w;
+    const int wu = s_fail ? (truncate ? s_kfail : 0) : w;
     // R^{-1}: column j by back substitution (one thread per column)
     for (int j = tid; j < wu; j += nt) {
         for (int i = j; i >= 0; --i) {
@@ -631,7 +638,7 @@ __global__ void __launch_bounds__(kBlock) k_chol(const double* __restrict__ G, i
 }
 
 cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str,
-                        int w_dim)
+                        int w_dim, int truncate)
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -640,7 +647,7 @@ cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, in
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_chol<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, Rinv, st, want_cond, w_dim);
+    k_chol<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, Rinv, st, want_cond, w_dim, truncate);
     return cudaGetLastError();
 }
 
@@ -661,6 +668,25 @@ cudaError_t launch_cs_gram(const double* cs, int ldc, int s, int q, double* G, i
 {
     k_cs_gram<<<(s * s + kBlock - 1) / kBlock > 0 ? (s * s + kBlock - 1) / kBlock : 1, kBlock, 0, str>>>(cs, ldc, s, q,
                                                                                                          G, ldg);
+    return cudaGetLastError();
+}
+
+// Symmetric part of an s x s matrix in place: G[k][l] = G[l][k] = (G[k][l] + G[l][k]) / 2.
+__global__ void k_symmetrize(double* __restrict__ G, int ldg, int s)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < s * s; e += gridDim.x * blockDim.x) {
+        const int k = e / s, l = e % s;
+        if (k < l) {
+            const double m = 0.5 * (G[(size_t)k * ldg + l] + G[(size_t)l * ldg + k]);
+            G[(size_t)k * ldg + l] = m;
+            G[(size_t)l * ldg + k] = m;
+        }
+    }
+}
+
+cudaError_t launch_symmetrize(double* G, int ldg, int s, cudaStream_t str)
+{
+    k_symmetrize<<<(s * s + kBlock - 1) / kBlock > 0 ? (s * s + kBlock - 1) / kBlock : 1, kBlock, 0, str>>>(G, ldg, s);
     return cudaGetLastError();
 }
 

@@ -466,6 +466,30 @@ __global__ void __launch_bounds__(kBlock) k_it_dir(int n, int ld, double* __rest
 __global__ void k_it_begin(DevState* st) { st->w = 0; }
 
 
+// FP32 copy of stage two's directions for a mixed-precision stage three, each column scaled
+// to unit A-norm (by its 1/sqrt(gamma), the diagonal entry of R^{-1}): the last directions of
+// a stage two that ran to rounding level are tiny, and their FP32 products would underflow.
+// Columns col0 .. col0 + ncols - 1 of W (ld-strided).
+__global__ void __launch_bounds__(kBlock) k_s2_to_f32(int n, int ld, const double* __restrict__ W,
+                                                      float* __restrict__ W32, int col0, int ncols,
+                                                      const double* __restrict__ Rinv)
+{
+    const size_t total = (size_t)ncols * ld;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int c = col0 + (int)(e / ld);
+        const int i = (int)(e % ld);
+        if (i < n) W32[(size_t)c * ld + i] = float(W[(size_t)c * ld + i] * Rinv[c * kWMax + c]);
+    }
+}
+
+cudaError_t launch_s2_to_f32(int n, int ld, const double* W, float* W32, int col0, int ncols, const double* Rinv,
+                             int sms, cudaStream_t s)
+{
+    if (ncols <= 0) return cudaSuccess;
+    k_s2_to_f32<<<sms * 8, kBlock, 0, s>>>(n, ld, W, W32, col0, ncols, Rinv);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------ host side
 
 #define PODCG_S2_YB(Y, ...)                                       \

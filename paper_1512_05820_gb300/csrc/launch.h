@@ -59,9 +59,10 @@ cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, doubl
                            double* sigma2, DevState* st, double* Vprev, int prev_s, cudaStream_t str,
                            double energy_y = 1.0, int y_max = 0);
 cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str,
-                        int w_dim = -1);
+                        int w_dim = -1, int truncate = 0);
 cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
 cudaError_t launch_cs_gram(const double* cs, int ldc, int s, int q, double* G, int ldg, cudaStream_t str);
+cudaError_t launch_symmetrize(double* G, int ldg, int s, cudaStream_t str);
 
 // CG iteration (k_cg.cu): kernel pointers for graph construction
 // FP32 with w > 0 has two forms of the update/direction passes: row-parallel float4
@@ -79,6 +80,8 @@ void stage2_kernels(int y, int L, bool cond, void** bb, void** init, void** lift
 // A z -> Y^T A z with the inner solve's start, the first and later direction updates with Y,
 // and the switch of the update kernels to no basis
 void it_kernels(int y, int L, void** az, void** dir0, void** dir, void** begin);
+cudaError_t launch_s2_to_f32(int n, int ld, const double* W, float* W32, int col0, int ncols, const double* Rinv,
+                             int sms, cudaStream_t s);
 
 // mixed precision (k_mixed.cu)
 void mixed_kernels(int wb, void** proj, void** start);
