@@ -10,7 +10,8 @@ resident in HBM. A_j values (117 MB each) and the basis blocks (~1 GB) exceed th
 L2, so no L2 flush is needed between steps.
 
 Prints one JSON line on rank 0. ``--impl reference`` times the FP64 CPU oracle (the
-reference arm of this build) on a bounded sample of the same workload instead.
+reference arm: the paper has no code to run) on a bounded sample of the same workload
+instead.
 """
 from __future__ import annotations
 
