@@ -1335,7 +1335,18 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         int* tc_err = &h->st->status;
         const int p = y > w ? y : w;
         const int upper = y > w ? 0 : 1;
-        if (h->mixed) {
+        if (h->mixed && y > 0) {
+            // three-stage in mixed precision: stage two runs on FP64 products, so its
+            // deflation terms Y^T A W and the stage-one factor come from FP64 data too (an
+            // FP32-data Gram left stage two's residual at an inconsistency floor, and its
+            // later directions useless); stage three re-forms its FP32 factor below. The
+            // FP32 panel A W32 is still formed for stage three.
+            PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32, h->ld, h->AW32, h->ld, n, w, h->sms, s));
+            PODCG_CK(h, launch_spmm(A->row_ptr, A->col, A->val, h->W, h->ld, h->AW, h->ld, n, w, h->sms, s));
+            PODCG_CK(h, launch_gram(n, h->Y, h->ld, p, h->AW, h->ld, w, b, h->G, kWMax + 1, upper, h->gram_work,
+                                    h->gram_work_bytes, h->sms, s));
+            launches += 1;
+        } else if (h->mixed) {
             const float* X32 = y > w ? h->Y32 : h->W32;
             PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32, h->ld, h->AW32, h->ld, n, w, h->sms, s));
             if (h->cfg.use_tc_gram && y <= w)
@@ -1355,11 +1366,7 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     } else if (y > 0) {
         // no stage-one basis (cannot happen with y >= w unless the POD is empty): stage two
         // needs Y^T b alone, with w = 0
-        if (h->mixed)
-            PODCG_CK(h, launch_gram32(n, h->Y32, h->ld, y, nullptr, h->ld, 0, b, h->G, kWMax + 1, 0, h->gram_work,
-                                      h->gram_work_bytes, h->sms, s));
-        else
-            PODCG_CK(h, launch_gram(n, h->Y, h->ld, y, nullptr, h->ld, 0, b, h->G, kWMax + 1, 0, h->gram_work,
+        PODCG_CK(h, launch_gram(n, h->Y, h->ld, y, nullptr, h->ld, 0, b, h->G, kWMax + 1, 0, h->gram_work,
                                     h->gram_work_bytes, h->sms, s));
         launches += 2;
     }
@@ -1380,7 +1387,7 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         w3 = d.w;
         if (d.w1 < w) h->w_clobbered = true;   // stage-one basis dropped: V2 starts at column 0
         launches += 2 + 2 * h->k2_launch;
-        if (h->mixed && h->k2 > 0) {
+        if (h->mixed && w3 > 0) {
             // MIXED: stage three iterates on the FP32 basis [W32, V2_32] (V2's columns scaled
             // to unit A-norm), whose A-products come from the FP32 SpMM as A W32's do, and it
             // re-forms that basis' Gram and
@@ -1392,9 +1399,11 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
             // coordinates over range([W, V2]), which the stage-two solution equals in exact
             // arithmetic.
             const size_t off = (size_t)d.w1 * h->ld;
-            PODCG_CK(h, launch_s2_to_f32(n, h->ld, h->W, h->W32, d.w1, h->k2, h->Rinv, h->sms, s));
-            PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32 + off, h->ld, h->AW32 + off, h->ld, n,
-                                        h->k2, h->sms, s));
+            if (h->k2 > 0) {
+                PODCG_CK(h, launch_s2_to_f32(n, h->ld, h->W, h->W32, d.w1, h->k2, h->Rinv, h->sms, s));
+                PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32 + off, h->ld, h->AW32 + off, h->ld,
+                                            n, h->k2, h->sms, s));
+            }
             PODCG_CK(h, launch_gram32(n, h->W32, h->ld, w3, h->AW32, h->ld, w3, b, h->G, kWMax + 1, 1, h->gram_work,
                                       h->gram_work_bytes, h->sms, s));
             // a non-positive pivot keeps the leading columns: stage two's last directions,
