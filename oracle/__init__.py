@@ -426,3 +426,83 @@ class OracleSequence:
         if record:
             self.add_snapshot(x)
         return x, info
+
+
+class OracleKrylovSequence:
+    """The overall algorithm (Section 4.4, Algorithm 3) with the paper's own POD ingredients
+    (Section 3): the augmenting basis accumulates every system's stage-three directions
+    A_j-normalised, Z <- [Z, P_j T_j^{-1/2}] (reading of the printed P_j sqrt(T_j): the
+    normalisation the orthogonality proof uses); new directions join the stage-one basis W
+    by the rule ``nu`` (1: all, 0: none, in between: those with T_kk / sum T > nu); once the
+    basis holds more than ``y_threshold`` vectors it is compressed by POD (Algorithm 4 with
+    metric A_j and weights ``weights``: "prev" = the coordinates of the last solution in Z,
+    "rbf" = those of the solutions since the last compression combined with weights
+    2^-(i-1), Eq. (weightsRBF)) to ``y_keep`` vectors, the first ``w_keep`` of which form
+    W. Each system runs stage one on W, stage two over the augmenting basis and stage three
+    with [W, V2] (Section 4.3), x_bar = 0.
+
+    Between compressions Z only grows by appending, so the coordinates of earlier solutions
+    are prefixes of the current coordinate vector (zero-padded). The coordinates are the
+    A_j-Galerkin ones, (Z^T A Z)^+ Z^T A x, with a pseudo-inverse where Z is rank deficient
+    (a reading: the paper writes the inverse).
+    """
+
+    def __init__(self, n: int, y_threshold: int = 200, y_keep: int = 100, w_keep: int = 5, nu: float = 1.0,
+                 weights: str = "rbf", tol_stage2: float = 1e-4, kmax: int = 100000, max_refine: int = 5,
+                 p_cap: int = 5000, oracle: Oracle | None = None):
+        self.n = n
+        self.y_threshold, self.y_keep, self.w_keep, self.nu = y_threshold, y_keep, w_keep, nu
+        self.weights, self.tol_stage2 = weights, tol_stage2
+        self.kmax, self.max_refine, self.p_cap = kmax, max_refine, p_cap
+        self.orc = oracle or Oracle()
+        self.Z = np.zeros((n, 0), order="F")   # augmenting basis, append-only between compressions
+        self.w_idx: list[int] = []             # columns of Z that form the stage-one basis W
+        self.coords: list[np.ndarray] = []     # Galerkin coordinates of the solutions since the last compression
+        self.compressions = 0
+
+    def _a_coords(self, A, x):
+        """(Z^T A Z)^+ Z^T A x."""
+        AZ = self.orc.spmm(A, self.Z)
+        G = self.Z.T @ AZ
+        return np.linalg.lstsq(0.5 * (G + G.T), AZ.T @ x, rcond=1e-13)[0]
+
+    def solve(self, A, b, tol_rel):
+        n = self.n
+        w = len(self.w_idx)
+        rest = [k for k in range(self.Z.shape[1]) if k not in set(self.w_idx)]
+        Y = np.asfortranarray(self.Z[:, self.w_idx + rest]) if self.Z.shape[1] else np.zeros((n, 0), order="F")
+        x, info, P, g = self.orc.solve_system3(A, b, Y, w, tol_rel, self.tol_stage2, w3_cap=max(Y.shape[1], 1),
+                                               kmax=self.kmax, max_refine=self.max_refine, p_cap=self.p_cap)
+        k = min(info["iters"], self.p_cap)
+        P, g = P[:, :k], g[:k]
+        Pn = P / np.sqrt(g)[None, :] if k else np.zeros((n, 0))
+        # new directions for the stage-one basis (Algorithm 3, rule nu)
+        if self.nu >= 1.0:
+            new_w = list(range(k))
+        elif self.nu <= 0.0:
+            new_w = []
+        else:
+            new_w = [i for i in range(k) if g[i] / g.sum() > self.nu]
+        base = self.Z.shape[1]
+        self.Z = np.asfortranarray(np.concatenate([self.Z, Pn], axis=1))
+        self.w_idx = self.w_idx + [base + i for i in new_w]
+        info["y"] = Y.shape[1]
+        info["k"] = k
+        # coordinates of this solution in the (grown) basis
+        self.coords.append(self._a_coords(A, x))
+        if self.Z.shape[1] > self.y_threshold:       # compression (Algorithm 3, truncation steps)
+            m = self.Z.shape[1]
+            if self.weights == "prev":
+                gam = self.coords[-1]
+            else:
+                gam = np.zeros(m)
+                for i, c in enumerate(reversed(self.coords)):
+                    gam[:len(c)] += c * 0.5 ** i
+            Zg = np.asfortranarray(self.Z * gam[None, :])
+            Wk, yk, _ = self.orc.pod_evd_metric(Zg, A, 2.0, self.y_keep)
+            self.Z = np.asfortranarray(Wk)
+            self.w_idx = list(range(min(self.w_keep, yk)))
+            self.coords = []
+            self.compressions += 1
+            info["compressed_to"] = yk
+        return x, info

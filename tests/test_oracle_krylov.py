@@ -1,0 +1,67 @@
+"""The oracle's overall algorithm with Krylov-vector snapshots (Algorithm 3 with the POD
+ingredients of Section 3), against what the method fixes: recycling the directions of a
+solve reproduces that solve's solution (stage one alone solves a repeated right-hand
+side), A_j-normalised conjugate directions form an A-orthonormal basis for a constant
+operator, the previous-solution weights are that solution's exact coordinates, a
+compression leaves an A_j-orthonormal basis of the requested size, and a varying sequence
+converges with fewer stage-three iterations once directions are recycled."""
+import numpy as np
+
+import pins
+from oracle import OracleKrylovSequence
+from paper_1512_05820_gb300 import workloads as wl
+
+
+def _rhs(n, seed):
+    return np.random.default_rng(seed).normal(size=n)
+
+
+def test_repeated_rhs_solved_by_stage_one(orc):
+    A = pins.small_diffusion(8, seed=1)
+    D = A.todense()
+    b = _rhs(A.n, 2)
+    seq = OracleKrylovSequence(A.n, y_threshold=10 ** 6, nu=1.0, oracle=orc)
+    x1, i1 = seq.solve(A.arrays(), b, 1e-13)
+    x2, i2 = seq.solve(A.arrays(), b, 1e-10)
+    xs = np.linalg.solve(D, b)
+    assert i1["iters"] > 0 and i2["iters"] == 0 and i2["w"] == i1["k"]
+    assert pins.a_norm(D, x2 - xs) <= 1e-10 * pins.a_norm(D, xs)
+
+
+def test_constant_operator_basis_is_a_orthonormal(orc):
+    A = pins.small_diffusion(6, seed=3)
+    D = A.todense()
+    seq = OracleKrylovSequence(A.n, y_threshold=10 ** 6, nu=0.0, oracle=orc)
+    seq.solve(A.arrays(), _rhs(A.n, 4), 1e-6)
+    Z = seq.Z
+    G = Z.T @ D @ Z
+    assert Z.shape[1] >= 5 and np.max(np.abs(G - np.eye(Z.shape[1]))) <= 1e-8
+
+
+def test_prev_weights_are_the_solution_coordinates(orc):
+    A = pins.small_diffusion(8, seed=5)
+    D = A.todense()
+    seq = OracleKrylovSequence(A.n, y_threshold=10 ** 6, nu=1.0, oracle=orc)
+    x1, _ = seq.solve(A.arrays(), _rhs(A.n, 6), 1e-8)
+    x2, _ = seq.solve(A.arrays(), _rhs(A.n, 7), 1e-8)
+    c = seq.coords[-1]
+    assert pins.a_norm(D, seq.Z @ c - x2) <= 1e-10 * pins.a_norm(D, x2)
+
+
+def test_compression_and_sequence(orc):
+    seq = wl.diffusion2d_drift(m=20, p=6)
+    k = OracleKrylovSequence(seq.n, y_threshold=60, y_keep=20, w_keep=4, nu=1.0, weights="rbf", oracle=orc)
+    iters, compressed = [], False
+    for j, val, b in seq.systems():
+        A = (seq.row_ptr, seq.col, val)
+        x, info = k.solve(A, b, seq.tol)
+        assert info["status"] == "ok" and info["final_relres"] <= seq.tol
+        iters.append(info["iters"])
+        if "compressed_to" in info:
+            compressed = True
+            D = wl.CSR(seq.n, *A).todense()
+            Z = k.Z
+            assert Z.shape[1] == info["compressed_to"] <= 20 and len(k.w_idx) == min(4, Z.shape[1])
+            assert np.max(np.abs(Z.T @ D @ Z - np.eye(Z.shape[1]))) <= 1e-10
+    assert compressed
+    assert all(it < iters[0] for it in iters[1:]), iters
