@@ -1,6 +1,7 @@
-"""Writes tests/golden/c1_sequence_oracle.json: the FP64 oracle's record of the 64x64
-five-point sequence (10 systems, w <= 8, tol 1e-8; the synthetic stand-in described in
-the workloads module). Calls only the oracle and the seeded input generator.
+"""Writes tests/golden/c1_sequence_oracle.json and c1_three_stage_oracle.json: the FP64
+oracle's records of the 64x64 five-point sequence (10 systems, w <= 8, tol 1e-8; the
+synthetic stand-in described in the workloads module), solved by the two-stage and by the
+three-stage algorithm. Calls only the oracle and the seeded input generator.
 
 The paper prints no numeric worked example (its results are figures), so no fixture here
 holds a value printed in the paper; this one is a regression record of the oracle itself,
@@ -21,21 +22,37 @@ from oracle import Oracle, OracleSequence  # noqa: E402
 from paper_1512_05820_gb300 import workloads as wl  # noqa: E402
 
 
-def record():
+def record(three_stage: bool = False):
+    """The two-stage record, or (three_stage) the three-stage one: stage-one energy 0.99,
+    the augmenting basis all modes to energy 1 - 1e-10 (y <= 8), stage-two tolerance 1e-4."""
     seq = wl.diffusion2d_drift()
     orc = Oracle()
-    oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
+    extra = {}
+    energy = seq.energy
+    if three_stage:
+        energy = 0.99
+        extra = dict(three_stage=True, y_max=seq.s_max, energy_y=1 - 1e-10, tol_stage2=1e-4)
+    oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=energy, oracle=orc, **extra)
     out = []
     for j, val, b in seq.systems():
         x, info = oseq.solve((seq.row_ptr, seq.col, val), b, seq.tol)
-        out.append({"system": j, "iters": info["iters"], "w": info["w"], "refinements": info["refinements"],
-                    "stage1_relres": info["stage1_relres"], "final_relres": info["final_relres"],
-                    "x_norm2": float(np.linalg.norm(x)), "x_sum": float(np.sum(x))})
-    return {"workload": f"diffusion2d_drift 64x64, {seq.p} systems, w_max {seq.w_max}, s_max {seq.s_max}, "
-                        f"energy {seq.energy}, tol {seq.tol}",
-            "source": "oracle/ (FP64 C), written by tests/golden/make_golden.py", "systems": out}
+        rec = {"system": j, "iters": info["iters"], "w": info["w"], "refinements": info["refinements"],
+               "stage1_relres": info["stage1_relres"], "final_relres": info["final_relres"],
+               "x_norm2": float(np.linalg.norm(x)), "x_sum": float(np.sum(x))}
+        if three_stage:
+            rec.update({"k2": info["k2"], "y": info["y"], "stage2_relres": info["stage2_relres"]})
+        out.append(rec)
+    wl_name = (f"diffusion2d_drift 64x64, {seq.p} systems, w_max {seq.w_max}, s_max {seq.s_max}, "
+               f"energy {energy}, tol {seq.tol}")
+    if three_stage:
+        wl_name += ", three stages (energy_y 1 - 1e-10, tol_stage2 1e-4)"
+    return {"workload": wl_name, "source": "oracle/ (FP64 C), written by tests/golden/make_golden.py",
+            "systems": out}
 
 
 if __name__ == "__main__":
-    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "c1_sequence_oracle.json"), "w") as f:
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "c1_sequence_oracle.json"), "w") as f:
         json.dump(record(), f, indent=1)
+    with open(os.path.join(here, "c1_three_stage_oracle.json"), "w") as f:
+        json.dump(record(three_stage=True), f, indent=1)

@@ -92,10 +92,12 @@ def test_cg_rounding_sensitivity_elasticity(orc):
     assert err <= 1e-8
 
 
-def test_golden_c1_sequence_record():
-    """The oracle reproduces its committed record of the 64x64 sequence (written by
-    tests/golden/make_golden.py): iteration counts, w and refinements exactly, residuals
-    and solution norms to 1e-12 relative. Guards the oracle against unintended changes."""
+@pytest.mark.parametrize("three_stage", [False, True])
+def test_golden_c1_sequence_record(three_stage):
+    """The oracle reproduces its committed records of the 64x64 sequence, two-stage and
+    three-stage (written by tests/golden/make_golden.py): iteration counts, w, k2, y and
+    refinements exactly, residuals and solution norms to 1e-12 relative. Guards the oracle
+    against unintended changes."""
     import json
     import os
     import sys
@@ -105,15 +107,17 @@ def test_golden_c1_sequence_record():
         import make_golden
     finally:
         sys.path.remove(here)
-    with open(os.path.join(here, "c1_sequence_oracle.json")) as f:
+    name = "c1_three_stage_oracle.json" if three_stage else "c1_sequence_oracle.json"
+    with open(os.path.join(here, name)) as f:
         ref = json.load(f)
-    now = make_golden.record()
+    now = make_golden.record(three_stage)
     assert len(now["systems"]) == len(ref["systems"])
     for a, b in zip(now["systems"], ref["systems"]):
-        for k in ("system", "iters", "w", "refinements"):
-            assert a[k] == b[k], (k, a, b)
-        for k in ("stage1_relres", "final_relres", "x_norm2", "x_sum"):
-            assert abs(a[k] - b[k]) <= 1e-12 * max(abs(b[k]), 1e-300), (k, a[k], b[k])
+        for k in ("system", "iters", "w", "refinements", "k2", "y"):
+            assert a.get(k) == b.get(k), (k, a, b)
+        for k in ("stage1_relres", "final_relres", "x_norm2", "x_sum", "stage2_relres"):
+            if k in b:
+                assert abs(a[k] - b[k]) <= 1e-12 * max(abs(b[k]), 1e-300), (k, a[k], b[k])
 
 
 @pytest.mark.parametrize("shape", [(3, 4), (2, 3, 2), (1, 1), (4, 1, 3)])
