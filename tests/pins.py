@@ -515,10 +515,32 @@ def pin_pod_a_metric(orc):
     return ok, f"A-metric POD: lambda vs LAPACK {e1:.1e}, A-orthonormality {e2:.1e}, Eckart-Young {e3:.1e}, A = I {e4:.1e}"
 
 
+def pin_a_metric_stage_two_one_step(orc):
+    """With the POD metric A of the system being solved, the augmenting basis is
+    A-orthonormal, Y^T A Y = I, so stage two (Algorithm 1 on the reduced system, M = I)
+    converges in at most one iteration and reaches the Galerkin solution over range(Y)
+    (the well-conditioned case the three-stage algorithm is designed for)."""
+    A = small_diffusion(10, seed=8)
+    D = A.todense()
+    rng = np.random.default_rng(9)
+    xs = rng.normal(size=A.n)
+    b = D @ xs
+    S = np.asfortranarray(np.stack([xs + 0.4 * rng.normal(size=A.n) for _ in range(8)], axis=1))
+    Y, y, _ = orc.pod_evd_metric(S, A.arrays(), 2.0, 8)
+    w = 3
+    W = np.asfortranarray(Y[:, :w])
+    what, R, _ = orc.stage_one(A.arrays(), b, W)
+    out = orc.stage_two(A.arrays(), b, Y, w, R, what, 1e-12 * np.linalg.norm(b), y - w)
+    x2 = W @ what + out["V2"] @ out["alpha"]
+    xg = Y @ np.linalg.solve(Y.T @ D @ Y, Y.T @ b)
+    e = a_norm(D, x2 - xg) / a_norm(D, xg)
+    return y == 8 and out["k2"] <= 1 and e < 1e-10, f"A-metric stage two: k2 = {out['k2']}, Galerkin err {e:.1e}"
+
+
 ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
             pin_finite_termination, pin_theta_grad_complex_step, pin_stage_two_optimality,
             pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse,
             pin_stage_two_reorthogonalised, pin_stage3_full_matches_direct, pin_jacobi_svd_numpy,
-            pin_pod_output_metric, pin_pod_a_metric]
+            pin_pod_output_metric, pin_pod_a_metric, pin_a_metric_stage_two_one_step]
