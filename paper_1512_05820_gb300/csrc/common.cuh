@@ -91,6 +91,7 @@ struct ProbDesc {
 // instead of the solve in mixed precision) and forms alpha = (r, z)/gamma. Thread 0 only.
 __device__ __forceinline__ void cg_product_finish(DevState* st, double gamma)
 {
+    // read the state fields first (independent loads, one round of latency)
     int status = st->status, inner_break = st->inner_break;
     const int mixed = st->mixed;
     const double rho = st->rho;

@@ -99,22 +99,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
     }
     double acc[1] = {double(dot)};
     __shared__ double tot[1];
-    if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) {
-        // read the state fields first (independent loads, one round of latency)
-        int status = st->status, inner_break = st->inner_break;
-        const int mixed = st->mixed;
-        const double rho = st->rho;
-        const double gamma = tot[0];
-        const bool bad = !isfinite(gamma) || !(gamma > 0.0);
-        if (bad && status == 0) {
-            if (mixed) inner_break = 1;          // FP32 inner pass ends; FP64 outer goes on
-            else status = !isfinite(gamma) ? 5 : 3;
-        }
-        st->gamma = gamma;
-        st->status = status;
-        st->inner_break = inner_break;
-        st->alpha = (status == 0 && !inner_break) ? rho / gamma : 0.0;
-    }
+    if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) cg_product_finish(st, tot[0]);
 }
 
 // True residual r = b - A x in FP64 and its norm. The last block takes the outer decision:
