@@ -109,7 +109,8 @@ class Oracle:
                                           ctypes.POINTER(_Info), ctypes.POINTER(ci), ctypes.POINTER(cd),
                                           vp, vp, ci, cd]
         lib.orc_solve_system3_it.argtypes = [ci, vp, vp, vp, vp, ci, vp, ci, cd, cd, cd, ci, ci, vp,
-                                             ctypes.POINTER(_Info), ctypes.POINTER(ci), ctypes.POINTER(ci)]
+                                             ctypes.POINTER(_Info), ctypes.POINTER(ci), ctypes.POINTER(ci),
+                                             vp, vp, ci]
 
     # -- Section 2 / basic kernels -------------------------------------------------
     def spmv(self, A, x):
@@ -315,7 +316,8 @@ class Oracle:
         d["stage2_relres"] = s2.value
         return x, d, P, g
 
-    def solve_system3_it(self, A, b, Y, w, tol_rel, tol2_rel, tol_in, kmax=100000, max_refine=5):
+    def solve_system3_it(self, A, b, Y, w, tol_rel, tol2_rel, tol_in, kmax=100000, max_refine=5, p_cap=0,
+                         return_directions=False):
         """Three-stage solve with the stage-three option of Section 4.3.1: stage three
         augments with the entire Y, each augmentation solve an inner reduced solve to
         tol_in * ||Y^T A z||. info gains k2 (stage-two iterations) and inner (inner reduced
@@ -327,12 +329,16 @@ class Oracle:
         x = np.empty(n)
         info = _Info()
         k2, inner = ctypes.c_int(0), ctypes.c_int(0)
+        P = np.zeros((n, p_cap), order="F") if p_cap else None
+        g = np.zeros(p_cap) if p_cap else None
         self.lib.orc_solve_system3_it(n, _p(rp), _p(col), _p(val), _p(b), Y.shape[1], _p(Y), w, tol_rel, tol2_rel,
                                       tol_in, kmax, max_refine, _p(x), ctypes.byref(info), ctypes.byref(k2),
-                                      ctypes.byref(inner))
+                                      ctypes.byref(inner), _p(P), _p(g), p_cap)
         d = _info_dict(info)
         d["k2"] = k2.value
         d["inner"] = inner.value
+        if return_directions:
+            return x, d, P, g
         return x, d
 
 
@@ -439,7 +445,8 @@ class OracleKrylovSequence:
     "rbf" = those of the solutions since the last compression combined with weights
     2^-(i-1), Eq. (weightsRBF)) to ``y_keep`` vectors, the first ``w_keep`` of which form
     W. Each system runs stage one on W, stage two over the augmenting basis and stage three
-    with [W, V2] (Section 4.3), x_bar = 0.
+    with [W, V2] (Section 4.3), or with ``stage3_full`` over the whole basis (Section
+    4.3.1, inner reduced solves to ``tol_inner``), x_bar = 0.
 
     Between compressions Z only grows by appending, so the coordinates of earlier solutions
     are prefixes of the current coordinate vector (zero-padded). The coordinates are the
@@ -449,11 +456,13 @@ class OracleKrylovSequence:
 
     def __init__(self, n: int, y_threshold: int = 200, y_keep: int = 100, w_keep: int = 5, nu: float = 1.0,
                  weights: str = "rbf", tol_stage2: float = 1e-4, kmax: int = 100000, max_refine: int = 5,
-                 p_cap: int = 5000, oracle: Oracle | None = None):
+                 p_cap: int = 5000, oracle: Oracle | None = None, stage3_full: bool = False,
+                 tol_inner: float = 1e-12):
         self.n = n
         self.y_threshold, self.y_keep, self.w_keep, self.nu = y_threshold, y_keep, w_keep, nu
         self.weights, self.tol_stage2 = weights, tol_stage2
         self.kmax, self.max_refine, self.p_cap = kmax, max_refine, p_cap
+        self.stage3_full, self.tol_inner = stage3_full, tol_inner
         self.orc = oracle or Oracle()
         self.Z = np.zeros((n, 0), order="F")   # augmenting basis, append-only between compressions
         self.w_idx: list[int] = []             # columns of Z that form the stage-one basis W
@@ -471,8 +480,13 @@ class OracleKrylovSequence:
         w = len(self.w_idx)
         rest = [k for k in range(self.Z.shape[1]) if k not in set(self.w_idx)]
         Y = np.asfortranarray(self.Z[:, self.w_idx + rest]) if self.Z.shape[1] else np.zeros((n, 0), order="F")
-        x, info, P, g = self.orc.solve_system3(A, b, Y, w, tol_rel, self.tol_stage2, w3_cap=max(Y.shape[1], 1),
-                                               kmax=self.kmax, max_refine=self.max_refine, p_cap=self.p_cap)
+        if self.stage3_full and Y.shape[1] > 0:   # stage three over the whole basis (Section 4.3.1)
+            x, info, P, g = self.orc.solve_system3_it(A, b, Y, w, tol_rel, self.tol_stage2, self.tol_inner,
+                                                      kmax=self.kmax, max_refine=self.max_refine, p_cap=self.p_cap,
+                                                      return_directions=True)
+        else:
+            x, info, P, g = self.orc.solve_system3(A, b, Y, w, tol_rel, self.tol_stage2, w3_cap=max(Y.shape[1], 1),
+                                                   kmax=self.kmax, max_refine=self.max_refine, p_cap=self.p_cap)
         k = min(info["iters"], self.p_cap)
         P, g = P[:, :k], g[:k]
         Pn = P / np.sqrt(g)[None, :] if k else np.zeros((n, 0))

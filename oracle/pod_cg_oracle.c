@@ -969,10 +969,12 @@ static int orc_inner_solve(int n, const int* rp, const int* ci, const double* va
  *               The augmentation solve is skipped once the exit test is met (its direction
  *               would not be used).
  * info as orc_solve_system (info->w = y); *k2_out the stage-two iterations; *inner_out the
- * inner reduced iterations summed over the solve. */
+ * inner reduced iterations summed over the solve; P_out/gamma_out/p_cap: the stage-three
+ * directions as orc_aug_pcg. */
 int orc_solve_system3_it(int n, const int* rp, const int* ci, const double* va, const double* b,
                          int y, const double* Y, int w, double tol_rel, double tol2_rel, double tol_in,
-                         int kmax, int max_refine, double* x, orc_info* info, int* k2_out, int* inner_out)
+                         int kmax, int max_refine, double* x, orc_info* info, int* k2_out, int* inner_out,
+                         double* P_out, double* gamma_out, int p_cap)
 {
     memset(info, 0, sizeof(*info));
     if (w > y) w = y;
@@ -1050,6 +1052,10 @@ int orc_solve_system3_it(int n, const int* rp, const int* ci, const double* va, 
             if (iters >= kmax) { status = ORC_MAXIT; break; }
             orc_spmv(n, rp, ci, va, p, q);
             double gamma = orc_dot(n, q, p);
+            if (P_out && iters < p_cap) {
+                memcpy(P_out + (size_t)iters * n, p, nb);
+                if (gamma_out) gamma_out[iters] = gamma;
+            }
             if (!isfinite(gamma)) { status = ORC_NONFINITE; break; }
             if (!(gamma > 0.0)) { status = ORC_BREAKDOWN; break; }
             double a = rz / gamma;

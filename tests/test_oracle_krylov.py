@@ -65,3 +65,21 @@ def test_compression_and_sequence(orc):
             assert np.max(np.abs(Z.T @ D @ Z - np.eye(Z.shape[1]))) <= 1e-10
     assert compressed
     assert all(it < iters[0] for it in iters[1:]), iters
+
+
+def test_stage3_full_with_krylov_snapshots(orc):
+    """The paper's "it" methods: Krylov snapshots compressed by POD to a few vectors in the
+    stage-one basis, stage three over the whole augmenting basis. Every system meets its
+    tolerance, the basis is compressed at least once, and later systems need fewer
+    stage-three iterations than the first."""
+    seq = wl.diffusion2d_drift(m=20, p=6)
+    k = OracleKrylovSequence(seq.n, y_threshold=60, y_keep=20, w_keep=3, nu=0.0, weights="rbf", oracle=orc,
+                             stage3_full=True)
+    iters = []
+    for j, val, b in seq.systems():
+        A = (seq.row_ptr, seq.col, val)
+        x, info = k.solve(A, b, seq.tol)
+        assert info["status"] == "ok" and info["final_relres"] <= seq.tol
+        iters.append(info["iters"])
+    assert k.compressions >= 1
+    assert all(it < iters[0] for it in iters[1:]), iters
