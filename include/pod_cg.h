@@ -72,7 +72,8 @@ typedef struct {
     int    s_max;        /* snapshot window: the last s_max added snapshots are kept (1..64) */
     double energy;       /* POD energy criterion (Algorithm 4 step 3), e.g. 0.9999 */
     double rank_tol;     /* eigenvalues <= rank_tol * lambda_1 count as rank deficient (1e-13) */
-    int    k_max;        /* cap on CG iterations per solve, summed over restarts */
+    int    k_max;        /* cap on CG iterations per solve, summed over restarts (0: stage
+                            one only); at the cap x_out holds the k_max-th iterate */
     int    max_refine;   /* FP64: residual-replacement restarts; MIXED: FP64 refinement steps */
     int    precision;    /* POD_CG_FP64, or POD_CG_MIXED (FP32 inner CG, FP64 refinement) */
     double inner_tol;    /* MIXED: each inner solve reduces its residual by this factor */

@@ -91,7 +91,11 @@ __global__ void __launch_bounds__(kBlock) k_init(int n, int ld, const T* __restr
             st->alpha = 0.0;
             st->beta = 0.0;
             if (st->status == 0 && !(isfinite(tot[0]) && isfinite(tot[1]))) st->status = 5;
-            const int done = skip || (st->status != 0) || !(tot[1] > st->tol2_in);
+            int done = skip || (st->status != 0) || !(tot[1] > st->tol2_in);
+            if (!done && st->iters >= st->k_max) {   // the cap is checked before an iteration
+                st->status = 4;
+                done = 1;
+            }
             st->done = done;
             st->dir_pending = 0;
             st->inner_iters = 0;
@@ -207,7 +211,8 @@ __global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x
     if (!FIRST && !st->dir_pending) return;
     if (FIRST && st->outer_done) return;
     const int w = st->w;
-    const bool ok = st->status == 0 && !st->inner_break;
+    // the step of the iteration that reached the cap (status 4) is valid and is applied
+    const bool ok = (st->status == 0 || st->status == 4) && !st->inner_break;
     const T alpha = ok ? T(st->alpha) : T(0);
     const T beta = T(st->beta);
     const bool upd_p = FIRST || (!st->done && ok);
@@ -468,7 +473,7 @@ __global__ void __launch_bounds__(kBlock) k_dir_bulk(int n, int ld, float* __res
     if (FIRST && st->outer_done) return;
     constexpr int NV = FIRST ? 3 : 4;
     const int w = st->w;
-    const bool ok = st->status == 0 && !st->inner_break;
+    const bool ok = (st->status == 0 || st->status == 4) && !st->inner_break;
     const float alpha = ok ? float(st->alpha) : 0.0f;
     const float beta = float(st->beta);
     const bool upd_p = FIRST || (!st->done && ok);
@@ -627,7 +632,7 @@ __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4
     if (!FIRST && !st->dir_pending) return;
     if (FIRST && st->outer_done) return;
     const int w = st->w;
-    const bool ok = st->status == 0 && !st->inner_break;
+    const bool ok = (st->status == 0 || st->status == 4) && !st->inner_break;
     const float alpha = ok ? float(st->alpha) : 0.0f;
     const float beta = float(st->beta);
     const bool upd_p = FIRST || (!st->done && ok);

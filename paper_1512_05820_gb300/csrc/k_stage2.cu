@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kBlock) k_it_dir(int n, int ld, double* __rest
 {
     if (FIRST && (st->done || st->status != 0)) return;
     const int y = st->pod_y;
-    const bool ok = st->status == 0;
+    const bool ok = st->status == 0 || st->status == 4;   // 4: the cap, after a valid step
     const double alpha = ok ? st->alpha : 0.0;
     const double beta = st->beta;
     const bool upd_p = FIRST || (!st->done && ok);

@@ -491,3 +491,26 @@ def random_spd_csr(n: int, density: float, seed: int, shift: float = 1.0, empty_
     np.add.at(row_ptr, r_all + 1, 1)
     row_ptr = np.cumsum(row_ptr).astype(np.int32)
     return CSR(n, row_ptr, c_all.astype(np.int32), v_all)
+
+
+def smooth_snapshots(op: DiffusionOperator, s: int, modes: int = 24, decay: float = 0.7,
+                     seed: int = 1239) -> np.ndarray:
+    """s smooth fields on the operator's grid, an (n, s) Fortran-ordered block: each column
+    is sum_m decay^m g_mk f_m with separable sine modes
+    f_m = sin(pi a_m (x+1/2)/mx) sin(pi b_m (y+1/2)/my) sin(pi c_m (z+1/2)/mz), wave numbers
+    a_m, b_m, c_m ~ U{1..4} and g_mk ~ N(0, 1). The squared singular values fall roughly
+    like decay^(2m), so an energy cut keeps a handful to a few tens of modes.
+
+    Random draws, in order, from ``numpy.random.default_rng(seed)``: the wave numbers
+    (modes x 3 integers), then g (modes x s values)."""
+    rng = np.random.default_rng(seed)
+    mz, my, mx = op.shape3
+    waves = rng.integers(1, 5, size=(modes, 3))
+    g = rng.normal(0.0, 1.0, size=(modes, s)) * (decay ** np.arange(modes))[:, None]
+    F = np.empty((op.n, modes))
+    for m, (a, b, c) in enumerate(waves):
+        fx = np.sin(np.pi * a * (np.arange(mx) + 0.5) / mx)
+        fy = np.sin(np.pi * b * (np.arange(my) + 0.5) / my)
+        fz = np.sin(np.pi * c * (np.arange(mz) + 0.5) / mz) if op.dim == 3 else np.ones(1)
+        F[:, m] = (fz[:, None, None] * fy[None, :, None] * fx[None, None, :]).ravel()
+    return np.asfortranarray(F @ g)

@@ -1,0 +1,105 @@
+"""Parity at the full size of the 128^3 seven-point moving-source workload (n = 2,097,152,
+nnz = 14,581,760), in the handle configuration the benchmark times: w_max 32, s_max 40,
+energy 0.9999, conditional-graph loop, SpMV width and projection form chosen by the
+handle.
+
+Whole 600-iteration solves of this size take the oracle minutes, so it checks what it
+computes in seconds. Both sides get the same 40 seeded smooth snapshots (not solutions,
+so no input comes from the GPU path) and the first system of the sequence:
+- FP64, capped at 0 iterations: the POD dimension w, stage one's residual and cond(W^T A W)
+  (1e-8 relative), and its iterate x0 = W (W^T A W)^{-1} W^T b element-wise (the iterate
+  does not depend on the basis chosen within range(W));
+- FP64, capped at 20 iterations: the iterate in the A-norm (1e-10 relative) and its true
+  residual; the step of the iteration that reaches the cap belongs to the iterate (the
+  20th and 19th iterates differ by 0.12 in the A-norm here);
+- mixed precision, solved to tol 1e-8: the same w, stage one's residual within the FP32
+  rounding of W, AW and their Gram (1e-4 relative: cond(W^T A W) is about 16, and an
+  FP32 model of the three roundings moves the residual by 2e-7), and the true residual
+  <= tol recomputed with the oracle's SpMV.
+"""
+import numpy as np
+import pytest
+
+from paper_1512_05820_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_05820_gb300 import _lib
+    _lib.load()
+    return torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def case(orc):
+    seq = wl.diffusion3d_moving()
+    S = wl.smooth_snapshots(seq.op, seq.s_max)
+    _, val, b = next(iter(seq.systems()))
+    A = (seq.row_ptr, seq.col, val)
+    W, w, _ = orc.pod_evd(S, seq.energy, seq.w_max)
+    return seq, S, A, b, W, w
+
+
+def to_dev(a, dev):
+    return torch.as_tensor(np.ascontiguousarray(a), device=dev)
+
+
+def make_solver(dev, seq, S, **cfg):
+    from paper_1512_05820_gb300.solver import PodCG
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, **cfg)
+    solver.add_snapshots(torch.as_tensor(S, device=dev))
+    return solver
+
+
+def solve(dev, solver, A, b, tol):
+    from paper_1512_05820_gb300.solver import DeviceCSR
+    x, st = solver.solve(DeviceCSR.from_numpy(*A, device=dev), to_dev(b, dev), tol, raise_on_error=False)
+    return x.cpu().numpy(), st
+
+
+def a_err(orc, A, x, xo):
+    dx = x - xo
+    return float(np.sqrt(max(dx @ orc.spmv(A, dx), 0.0) / (xo @ orc.spmv(A, xo))))
+
+
+def test_full_size_stage_one(dev, orc, case):
+    seq, S, A, b, W, w = case
+    xo, info, _, _ = orc.solve_system(A, b, W, seq.tol, kmax=0, max_refine=0)
+    solver = make_solver(dev, seq, S, precision=0, k_max=0, max_refine=0, cond_diag=1)
+    x, st = solve(dev, solver, A, b, seq.tol)
+    solver.close()
+    assert st["status"] == info["status"] == "maxit" and st["iters"] == 0
+    assert st["w"] == info["w"] == w and w > 0
+    assert abs(st["stage1_relres"] - info["stage1_relres"]) <= 1e-8 * info["stage1_relres"]
+    assert abs(st["cond_gram"] - info["cond_gram"]) <= 1e-8 * info["cond_gram"]
+    assert np.max(np.abs(x - xo)) <= 1e-10 * np.max(np.abs(xo))
+
+
+def test_full_size_capped_iterations(dev, orc, case):
+    seq, S, A, b, W, w = case
+    k = 20
+    xo, info, _, _ = orc.solve_system(A, b, W, seq.tol, kmax=k, max_refine=0)
+    solver = make_solver(dev, seq, S, precision=0, k_max=k, max_refine=0)
+    x, st = solve(dev, solver, A, b, seq.tol)
+    solver.close()
+    assert st["status"] == info["status"] == "maxit" and st["iters"] == info["iters"] == k
+    assert a_err(orc, A, x, xo) <= 1e-10
+    assert abs(st["final_relres"] - info["final_relres"]) <= 1e-8 * info["final_relres"]
+
+
+def test_full_size_mixed_solve(dev, orc, case):
+    seq, S, A, b, W, w = case
+    _, info, _, _ = orc.solve_system(A, b, W, seq.tol, kmax=0, max_refine=0)
+    solver = make_solver(dev, seq, S, precision=1)
+    x, st = solve(dev, solver, A, b, seq.tol)
+    solver.close()
+    assert st["status"] == "ok", st
+    assert st["w"] == w
+    assert abs(st["stage1_relres"] - info["stage1_relres"]) <= 1e-4 * info["stage1_relres"]
+    true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= seq.tol and st["final_relres"] <= seq.tol
