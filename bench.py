@@ -103,8 +103,21 @@ def config_dict(seq, args, precision):
     return {"workload": f"diffusion3d_moving {args.grid}^3 7-point, {seq.p} systems",
             "n": seq.n, "nnz": seq.nnz, "systems": seq.p, "s_max": seq.s_max, "w_max": seq.w_max,
             "energy": seq.energy, "tol": seq.tol, "precision": precision, "preconditioner": "jacobi",
-            "l2": "inputs larger than L2 (A_j values 117 MB each, W/AW/S blocks ~1.9 GB); no flush",
-            "parallelism": "replicas" if args.gpus > 1 else "single"}
+            "l2": l2_note(seq), "parallelism": "replicas" if args.gpus > 1 else "single"}
+
+
+L2_BYTES = 129e6   # GB300 L2
+
+
+def l2_note(seq):
+    """How the data one iteration reads compares with L2 (no flush between iterations):
+    the matrix (values, column indices, row pointers) and the W and A W blocks."""
+    mat_mb = (12 * seq.nnz + 4 * (seq.n + 1)) / 1e6
+    blocks_mb = 2 * seq.w_max * seq.n * 4 / 1e6   # W and A W in FP32, at w_max
+    if (mat_mb + blocks_mb) * 1e6 > L2_BYTES:
+        return (f"inputs larger than L2 (matrix {mat_mb:.0f} MB per system, W and AW up to "
+                f"{blocks_mb:.0f} MB); no flush")
+    return f"inputs fit in L2 (matrix {mat_mb:.1f} MB); no flush: a small case, not the benchmark size"
 
 
 def b_spmv(n, nnz, fp32=False):
