@@ -2,6 +2,7 @@
 
 No compute call is made (no GPU here); the GPU tests call every entry point.
 """
+import ctypes
 import glob
 import os
 import re
@@ -47,3 +48,34 @@ def test_config_default_is_host_only():
     c = _lib.Config()
     assert L.pod_cg_config_default(ctypes.byref(c)) == 0
     assert c.w_max == 32 and c.s_max == 40 and abs(c.energy - 0.9999) < 1e-15 and c.precision == 0
+
+
+STRUCTS = {"pod_cg_config": "Config", "pod_cg_csr": "CSRStruct", "pod_cg_stats": "Stats",
+           "pod_cg_batch_seq": "BatchSeq", "pod_cg_batch_sysstat": "BatchSysStat"}
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every struct the binding passes through the ABI has the header's size and field
+    offsets (a C program compiled against include/pod_cg.h prints them)."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pod_cg.h"', "int main(void) {"]
+    for cname, pyname in STRUCTS.items():
+        S = getattr(_lib, pyname)
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in S._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            c, field, v = ln.split()
+            got[(c, field)] = int(v)
+    for cname, pyname in STRUCTS.items():
+        S = getattr(_lib, pyname)
+        assert got[(cname, "size")] == ctypes.sizeof(S), cname
+        for f, _ in S._fields_:
+            assert got[(cname, f)] == getattr(S, f).offset, (cname, f)
