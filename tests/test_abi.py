@@ -79,3 +79,34 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(S), cname
         for f, _ in S._fields_:
             assert got[(cname, f)] == getattr(S, f).offset, (cname, f)
+
+
+BAD_CONFIGS = [
+    dict(w_max=0), dict(w_max=65), dict(s_max=0), dict(s_max=65), dict(energy=1.5), dict(energy=float("nan")),
+    dict(k_max=-1), dict(max_refine=-1), dict(precision=2), dict(keep_factors=-1), dict(loop_mode=2),
+    dict(proj_form=2), dict(spmv_lanes=3), dict(spmv_lanes=64), dict(inner_tol=0.0), dict(inner_tol=1.0),
+    dict(three_stage=3), dict(three_stage=1, y_max=41), dict(three_stage=1, y_max=0),
+    dict(three_stage=1, energy_y=1.5), dict(three_stage=1, tol_stage2=-1.0),
+    dict(three_stage=1, tol_stage2=float("inf")), dict(three_stage=2, tol_inner=1.0),
+    dict(three_stage=2, precision=1), dict(bsr=2), dict(pod_metric=2), dict(use_tc_gram=1, precision=0),
+    dict(use_tc_gram=2, precision=1),
+]
+
+
+def test_create_rejects_bad_configuration():
+    """pod_cg_create checks the configuration on the host before any device call: each bad
+    field gives ERR_ARG (1), no handle, and a message from pod_cg_last_error(NULL)."""
+    L = _lib.load()
+    for bad in BAD_CONFIGS:
+        c = _lib.Config()
+        assert L.pod_cg_config_default(ctypes.byref(c)) == 0
+        for k, v in bad.items():
+            setattr(c, k, v)
+        h = ctypes.c_void_p(123)
+        st = L.pod_cg_create(1000, ctypes.byref(c), None, ctypes.byref(h))
+        assert st == 1, (bad, st)
+        assert not h.value, bad
+        assert L.pod_cg_last_error(None), bad
+    h = ctypes.c_void_p()
+    assert L.pod_cg_create(0, None, None, ctypes.byref(h)) == 1
+    assert L.pod_cg_create(10, None, None, None) == 1
