@@ -452,12 +452,18 @@ class OracleKrylovSequence:
     are prefixes of the current coordinate vector (zero-padded). The coordinates are the
     A_j-Galerkin ones, (Z^T A Z)^+ Z^T A x, with a pseudo-inverse where Z is rank deficient
     (a reading: the paper writes the inverse).
+
+    ``normalise`` = "sqrt" appends P_j T_j^{1/2} as printed instead; it exists so that a
+    test can show which of the two readings Theorem 5 holds for.
     """
 
     def __init__(self, n: int, y_threshold: int = 200, y_keep: int = 100, w_keep: int = 5, nu: float = 1.0,
                  weights: str = "rbf", tol_stage2: float = 1e-4, kmax: int = 100000, max_refine: int = 5,
                  p_cap: int = 5000, oracle: Oracle | None = None, stage3_full: bool = False,
-                 tol_inner: float = 1e-12):
+                 tol_inner: float = 1e-12, normalise: str = "inv_sqrt"):
+        if normalise not in ("inv_sqrt", "sqrt"):
+            raise ValueError("normalise must be 'inv_sqrt' or 'sqrt'")
+        self.normalise = normalise
         self.n = n
         self.y_threshold, self.y_keep, self.w_keep, self.nu = y_threshold, y_keep, w_keep, nu
         self.weights, self.tol_stage2 = weights, tol_stage2
@@ -489,7 +495,8 @@ class OracleKrylovSequence:
                                                    kmax=self.kmax, max_refine=self.max_refine, p_cap=self.p_cap)
         k = min(info["iters"], self.p_cap)
         P, g = P[:, :k], g[:k]
-        Pn = P / np.sqrt(g)[None, :] if k else np.zeros((n, 0))
+        scale = 1.0 / np.sqrt(g) if self.normalise == "inv_sqrt" else np.sqrt(g)
+        Pn = P * scale[None, :] if k else np.zeros((n, 0))
         # new directions for the stage-one basis (Algorithm 3, rule nu)
         if self.nu >= 1.0:
             new_w = list(range(k))

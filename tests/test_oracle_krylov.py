@@ -83,3 +83,48 @@ def test_stage3_full_with_krylov_snapshots(orc):
         iters.append(info["iters"])
     assert k.compressions >= 1
     assert all(it < iters[0] for it in iters[1:]), iters
+
+
+def _theorem5_run(orc, normalise, n_systems=8):
+    """The slowly varying 12x12 sequence A_j = A_0 + diag(0.01 j u) with Theorem 5's second
+    hypothesis: stage three over the whole basis with inner reduced solves to 1e-12
+    (standing in for exact ones), stage two to 1e-4 of the tolerance, and a compression
+    every other system. Returns per system (||Y_j^T A_j Y_j - I||_2, the theorem's bound),
+    the bound summing ||Y_k||^2 ||A_k - A_{k-1}|| over the systems since the last
+    compression (which leaves Y^T A Y = I for the system it follows)."""
+    seq = wl.diffusion2d_drift(m=12, p=8)
+    k = OracleKrylovSequence(seq.n, y_threshold=50, y_keep=15, w_keep=3, nu=0.0, weights="rbf", oracle=orc,
+                             stage3_full=True, tol_stage2=1e-4, tol_inner=1e-12, kmax=3000, normalise=normalise)
+    out, terms, A_prev = [], [], None
+    for j, val, b in seq.systems():
+        A = (seq.row_ptr, seq.col, val)
+        D = wl.CSR(seq.n, *A).todense()
+        Y = k.Z.copy()
+        if A_prev is not None:
+            terms.append(np.linalg.norm(Y, 2) ** 2 * np.linalg.norm(D - A_prev, 2) if Y.shape[1] else 0.0)
+        if Y.shape[1]:
+            out.append((np.linalg.norm(Y.T @ D @ Y - np.eye(Y.shape[1]), 2), sum(terms)))
+        if j > n_systems:
+            break
+        x, info = k.solve(A, b, 1e-8)
+        assert info["status"] == "ok"
+        if "compressed_to" in info:
+            terms = []
+        A_prev = D
+    return out, k.compressions
+
+
+def test_theorem5_reduced_matrix_bound(orc):
+    """Theorem 5 (Section 4.4): ||Y_j^T A_j Y_j - I|| <= sum over the systems since the
+    last compression of ||Y_k||^2 ||A_k - A_{k-1}||, because each system appends its
+    A_k-normalised stage-three directions, which are A_k-orthonormal to the basis they
+    extend. It holds with the reading P_j T_j^{-1/2} (here with a factor of about two to
+    spare); with the printed P_j T_j^{1/2} the appended columns are not A-normalised and
+    the bound fails at the first system that uses them."""
+    ok, compressions = _theorem5_run(orc, "inv_sqrt")
+    assert len(ok) == 7 and compressions >= 3
+    for lhs, bound in ok:
+        assert 0.0 < lhs <= bound, (lhs, bound)
+    printed, _ = _theorem5_run(orc, "sqrt", n_systems=1)
+    lhs, bound = printed[0]
+    assert lhs > 100 * bound, (lhs, bound)
