@@ -63,3 +63,18 @@ def test_shard_single_rank_and_errors():
     assert shard_by_work([1.0, 2.0], 0, 1) == [0, 1]
     with pytest.raises(ValueError):
         shard_by_work([1.0], 2, 2)
+
+
+def test_shard_properties_many_ranks():
+    """Greedy longest-processing-time plans for 3 to 8 ranks on random heavy-tailed work:
+    disjoint, covering, identical for every rank's call, and no rank more than one item
+    above the lightest."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    for world in range(3, 9):
+        work = [float(v) for v in rng.pareto(1.5, 40) + 0.1]
+        plans = [shard_by_work(work, r, world) for r in range(world)]
+        assert sorted(i for p in plans for i in p) == list(range(len(work)))
+        assert plans == [shard_by_work(work, r, world) for r in range(world)]
+        loads = [sum(work[i] for i in p) for p in plans]
+        assert max(loads) - min(loads) <= max(work)
