@@ -14,7 +14,6 @@ products (lo*mid, lo*lo when p > 42) weigh <= 2^-24. Altogether
 import numpy as np
 import pytest
 
-from oracle import Oracle
 from paper_1512_05820_gb300 import workloads as wl
 
 torch = pytest.importorskip("torch")
