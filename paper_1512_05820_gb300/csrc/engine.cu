@@ -862,7 +862,9 @@ cudaError_t dalloc(T** p, size_t count)
 
 void reset_state(pod_cg_t* h, const pod_cg_csr* A, const double* b, double tol)
 {
-    *h->pd_host = ProbDesc{A->row_ptr, A->col, A->val, h->val32, b, nullptr, h->n, h->ld};
+    // the block form's fields are filled by setup_bsr when the pattern has one
+    *h->pd_host = ProbDesc{A->row_ptr, A->col, A->val, h->val32, b, nullptr, h->n, h->ld,
+                           nullptr, nullptr, nullptr, nullptr, 0, 0};
     DevState& sh = *h->st_host;
     std::memset(&sh, 0, sizeof(DevState));
     sh.k_max = h->cfg.k_max;
