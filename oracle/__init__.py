@@ -14,6 +14,7 @@ system j is computed (Algorithm 4, identity metric, unit weights) from the last
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -111,6 +112,20 @@ class Oracle:
         lib.orc_solve_system3_it.argtypes = [ci, vp, vp, vp, vp, ci, vp, ci, cd, cd, cd, ci, ci, vp,
                                              ctypes.POINTER(_Info), ctypes.POINTER(ci), ctypes.POINTER(ci),
                                              vp, vp, ci]
+        lib.orc_set_dependence_stop.argtypes = [ci]
+        lib.orc_set_dependence_stop.restype = ci
+
+    @contextlib.contextmanager
+    def dependence_stop(self, on: bool = True):
+        """Within the block, stage two and the inner reduced solves stop before a direction
+        that the re-A-orthogonalisation pass found numerically dependent on the stored ones
+        (its A-norm squared at most the part the pass removed); off by default. The setting
+        belongs to the loaded library, so it is restored on exit."""
+        old = self.lib.orc_set_dependence_stop(int(on))
+        try:
+            yield
+        finally:
+            self.lib.orc_set_dependence_stop(old)
 
     # -- Section 2 / basic kernels -------------------------------------------------
     def spmv(self, A, x):

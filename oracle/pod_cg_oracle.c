@@ -35,6 +35,25 @@
 
 enum { ORC_OK = 0, ORC_NOT_SPD = 2, ORC_BREAKDOWN = 3, ORC_MAXIT = 4, ORC_NONFINITE = 5, ORC_ARG = 1 };
 
+/* Reading (not in the paper; off unless orc_set_dependence_stop(1)): stage two and the
+ * inner reduced solves of Section 4.3.1 stop before a direction that was numerically in
+ * the span of the directions stored before it: its A-norm squared after the
+ * re-A-orthogonalisation pass, gamma = phat^T (Y^T A Y) phat, is at most the A-norm
+ * squared that the pass removed, sum_i c_i^2 gamma_i (Pythagoras, were the stored
+ * directions exactly A-orthogonal). In exact arithmetic Algorithm 1 ends with a zero
+ * residual within the reduced dimension and the pass removes nothing; in floating point,
+ * once the reduced residual is rounding noise, the new directions are noise that is not
+ * A-orthogonal, one Gram-Schmidt pass against them amplifies instead of removing, and the
+ * iterate grows without bound. */
+static int orc_dep_stop = 0;
+
+int orc_set_dependence_stop(int on)
+{
+    const int old = orc_dep_stop;
+    orc_dep_stop = on != 0;
+    return old;
+}
+
 typedef struct {
     int status;          /* ORC_* code */
     int iters;           /* Algorithm 1 loop passes, summed over restarts */
@@ -705,11 +724,13 @@ static int orc_stage_two_hist(int n, const int* rp, const int* ci, const double*
     double rz = 0.0, rr = 0.0;
     for (int l = 0; l < y; ++l) { rz += rh[l] * zh[l]; rr += rh[l] * rh[l]; }
     double rnorm = sqrt(rr);
+    double removed = 0.0;   /* A-norm squared removed from the next direction by the pass */
     while (rnorm > tol_abs && k < kcap) {
         orc_reduced_product(n, rp, ci, va, y, Y, ph, v, Av, qh);
         double gamma = 0.0;
         for (int l = 0; l < y; ++l) gamma += qh[l] * ph[l];
         if (!isfinite(gamma) || !(gamma > 0.0)) { status = ORC_BREAKDOWN; break; }
+        if (orc_dep_stop && gamma <= removed) break;   /* numerically dependent direction */
         double a = rz / gamma;
         alpha[k] = a;
         T2[k] = gamma;
@@ -729,10 +750,12 @@ static int orc_stage_two_hist(int n, const int* rp, const int* ci, const double*
         }
         for (int l = 0; l < y; ++l)
             ph[l] = zh[l] + beta * ph[l] - ((l < w && !MUT(12)) ? mu[l] : 0.0);
+        removed = 0.0;
         for (int i = 0; i <= k && !MUT(15); ++i) {          /* re-A-orthogonalisation */
             double c = 0.0;
             for (int l = 0; l < y; ++l) c += Qh[(size_t)i * y + l] * ph[l];
             cf[i] = c / T2[i];
+            removed += cf[i] * c;
         }
         for (int l = 0; l < y && !MUT(15); ++l) {
             double t = 0.0;
@@ -900,10 +923,12 @@ static int orc_inner_solve(int n, const int* rp, const int* ci, const double* va
         orc_chol_solve(w, R, th, nu);
     }
     for (int l = 0; l < y; ++l) ph[l] = rh[l] - ((l < w) ? nu[l] : 0.0);
+    double removed = 0.0;   /* A-norm squared removed from the next direction by the pass */
     for (int i = 0; i < *m; ++i) {
         double c = 0.0;
         for (int l = 0; l < y; ++l) c += qpsi[(size_t)i * y + l] * ph[l];
         cf[i] = c / g[i];
+        removed += cf[i] * c;
     }
     for (int l = 0; l < y; ++l) {
         double t = 0.0;
@@ -918,11 +943,12 @@ static int orc_inner_solve(int n, const int* rp, const int* ci, const double* va
         double gamma = 0.0;
         for (int l = 0; l < y; ++l) gamma += qh[l] * ph[l];
         if (!isfinite(gamma) || !(gamma > 0.0)) break;
+        if (orc_dep_stop && gamma <= removed) break;   /* numerically dependent direction */
+        double a = rz / gamma;
         memcpy(psi + (size_t)(*m) * y, ph, yb);
         memcpy(qpsi + (size_t)(*m) * y, qh, yb);
         g[*m] = gamma;
         *m += 1;
-        double a = rz / gamma;
         for (int l = 0; l < y; ++l) mu[l] += a * ph[l];
         for (int l = 0; l < y; ++l) rh[l] -= a * qh[l];
         double rz_new = 0.0;
@@ -933,10 +959,12 @@ static int orc_inner_solve(int n, const int* rp, const int* ci, const double* va
             orc_chol_solve(w, R, th, nu);
         }
         for (int l = 0; l < y; ++l) ph[l] = rh[l] + beta * ph[l] - ((l < w) ? nu[l] : 0.0);
+        removed = 0.0;
         for (int i = 0; i < *m; ++i) {
             double c = 0.0;
             for (int l = 0; l < y; ++l) c += qpsi[(size_t)i * y + l] * ph[l];
             cf[i] = c / g[i];
+            removed += cf[i] * c;
         }
         for (int l = 0; l < y; ++l) {
             double t = 0.0;

@@ -537,10 +537,51 @@ def pin_a_metric_stage_two_one_step(orc):
     return y == 8 and out["k2"] <= 1 and e < 1e-10, f"A-metric stage two: k2 = {out['k2']}, Galerkin err {e:.1e}"
 
 
+def _near_identity_reduced_problem(seed=5, y=40):
+    """Y: y columns A_1-orthonormal (Cholesky of Z^T A_1 Z, Z random) for a 12x12 diffusion
+    operator A_1; the system is A_2 = A_1 + diag(0.01 u), so cond(Y^T A_2 Y) is about 1.002:
+    the well-conditioned reduced system Theorem 5 describes."""
+    A1 = small_diffusion(12, seed=3)
+    D1 = A1.todense()
+    rng = np.random.default_rng(seed)
+    Z = rng.normal(size=(A1.n, y))
+    Lc = np.linalg.cholesky(Z.T @ D1 @ Z)
+    Y = np.asfortranarray(Z @ np.linalg.inv(Lc).T)
+    u = rng.uniform(0.0, 1.0, A1.n)
+    rp, col, val = A1.arrays()
+    rows = np.repeat(np.arange(A1.n), np.diff(rp))
+    val2 = val + np.where(col == rows, 0.01 * u[rows], 0.0)
+    b = rng.normal(size=A1.n)
+    return (rp, col, val2), D1 + np.diag(0.01 * u), b, Y
+
+
+def pin_stage_two_dependence_stop(orc):
+    """Stage two with tolerance 0 on a reduced system with cond(Y^T A Y) = 1.002 reaches the
+    rounding floor within a few iterations; with the dependence stop on (a direction whose
+    A-norm squared after re-A-orthogonalisation is at most the part removed is not taken)
+    it ends there, well before y - w iterations, at the Galerkin solution over range(Y)
+    (dense LAPACK solve) to 1e-12, with and without deflated stage-one directions."""
+    A, D, b, Y = _near_identity_reduced_problem()
+    y = Y.shape[1]
+    xg = Y @ np.linalg.solve(Y.T @ D @ Y, Y.T @ b)
+    worst, ks = 0.0, []
+    for w in (0, 3):
+        W = np.asfortranarray(Y[:, :w])
+        what, R, _ = orc.stage_one(A, b, W) if w else (None, None, 0)
+        with orc.dependence_stop():
+            out = orc.stage_two(A, b, Y, w, R, what, 0.0, y - w)
+        x2 = out["V2"] @ out["alpha"] + (W @ what if w else 0.0)
+        worst = max(worst, a_norm(D, x2 - xg) / a_norm(D, xg))
+        ks.append(out["k2"])
+    ok = worst < 1e-12 and all(0 < k < y // 2 for k in ks)
+    return ok, f"dependence stop: Galerkin err {worst:.1e}, k2 {ks} of {y}"
+
+
 ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
             pin_finite_termination, pin_theta_grad_complex_step, pin_stage_two_optimality,
             pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse,
             pin_stage_two_reorthogonalised, pin_stage3_full_matches_direct, pin_jacobi_svd_numpy,
-            pin_pod_output_metric, pin_pod_a_metric, pin_a_metric_stage_two_one_step]
+            pin_pod_output_metric, pin_pod_a_metric, pin_a_metric_stage_two_one_step,
+            pin_stage_two_dependence_stop]

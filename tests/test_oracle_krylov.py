@@ -86,15 +86,22 @@ def test_stage3_full_with_krylov_snapshots(orc):
 
 
 def _theorem5_run(orc, normalise, n_systems=8):
-    """The slowly varying 12x12 sequence A_j = A_0 + diag(0.01 j u) with Theorem 5's second
-    hypothesis: stage three over the whole basis with inner reduced solves to 1e-12
-    (standing in for exact ones), stage two to 1e-4 of the tolerance, and a compression
-    every other system. Returns per system (||Y_j^T A_j Y_j - I||_2, the theorem's bound),
-    the bound summing ||Y_k||^2 ||A_k - A_{k-1}|| over the systems since the last
-    compression (which leaves Y^T A Y = I for the system it follows)."""
+    """The slowly varying 12x12 sequence A_j = A_0 + diag(0.01 j u) under Theorem 5's second
+    hypothesis: stage three over the whole basis with exact stage-two and inner reduced
+    solves (tolerances 0; they end at the rounding floor through the dependence stop), and
+    a compression every other system. Returns per system (||Y_j^T A_j Y_j - I||_2, the
+    theorem's bound), the bound summing ||Y_k||^2 ||A_k - A_{k-1}|| over the systems since
+    the last compression (which leaves Y^T A Y = I for the system it follows)."""
     seq = wl.diffusion2d_drift(m=12, p=8)
     k = OracleKrylovSequence(seq.n, y_threshold=50, y_keep=15, w_keep=3, nu=0.0, weights="rbf", oracle=orc,
-                             stage3_full=True, tol_stage2=1e-4, tol_inner=1e-12, kmax=3000, normalise=normalise)
+                             stage3_full=True, tol_stage2=0.0, tol_inner=0.0, kmax=3000, normalise=normalise)
+    with orc.dependence_stop():
+        out, compressions = _theorem5_loop(k, seq, normalise, n_systems)
+    return out, compressions
+
+
+def _theorem5_loop(k, seq, normalise, n_systems):
+    """One pass over the sequence for _theorem5_run."""
     out, terms, A_prev = [], [], None
     for j, val, b in seq.systems():
         A = (seq.row_ptr, seq.col, val)

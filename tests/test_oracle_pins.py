@@ -183,3 +183,21 @@ def test_adjoint_gradient_end_to_end(orc):
             L = L + c @ np.linalg.solve(M, B[j])
         ref[cc] = np.imag(L) / h
     assert np.max(np.abs(g - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_stage_two_past_the_rounding_floor(orc):
+    """Why the dependence stop exists: on the cond-1.002 reduced system of
+    pins.pin_stage_two_dependence_stop, stage two with tolerance 0 and no stop runs all y
+    iterations, and once its residual is rounding noise the single re-A-orthogonalisation
+    pass against noise directions amplifies them: the iterate ends far from the Galerkin
+    solution. With the stop it ends at the floor, at that solution."""
+    A, D, b, Y = pins._near_identity_reduced_problem()
+    y = Y.shape[1]
+    xg = Y @ np.linalg.solve(Y.T @ D @ Y, Y.T @ b)
+    with orc.dependence_stop(False):
+        off = orc.stage_two(A, b, Y, 0, None, None, 0.0, y)
+    with orc.dependence_stop(True):
+        on = orc.stage_two(A, b, Y, 0, None, None, 0.0, y)
+    err = lambda o: pins.a_norm(D, o["V2"] @ o["alpha"] - xg) / pins.a_norm(D, xg)
+    assert off["k2"] == y and err(off) > 1.0
+    assert on["k2"] < y // 2 and err(on) < 1e-12
