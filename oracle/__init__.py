@@ -465,8 +465,8 @@ class OracleKrylovSequence:
 
     Between compressions Z only grows by appending, so the coordinates of earlier solutions
     are prefixes of the current coordinate vector (zero-padded). The coordinates are the
-    A_j-Galerkin ones, (Z^T A Z)^+ Z^T A x, with a pseudo-inverse where Z is rank deficient
-    (a reading: the paper writes the inverse).
+    previous weights of Eq. (weightsPrevious), (Z^T A_j Z)^+ Z^T b_j with x_bar = 0, with a
+    pseudo-inverse where Z is rank deficient (a reading: the paper writes the inverse).
 
     ``normalise`` = "sqrt" appends P_j T_j^{1/2} as printed instead; it exists so that a
     test can show which of the two readings Theorem 5 holds for.
@@ -490,11 +490,12 @@ class OracleKrylovSequence:
         self.coords: list[np.ndarray] = []     # Galerkin coordinates of the solutions since the last compression
         self.compressions = 0
 
-    def _a_coords(self, A, x):
-        """(Z^T A Z)^+ Z^T A x."""
+    def _prev_weights(self, A, b):
+        """The previous weights of Eq. (weightsPrevious) with x_bar = 0: (Z^T A Z)^+ Z^T b,
+        the Galerkin coordinates of the system's exact solution in range(Z)."""
         AZ = self.orc.spmm(A, self.Z)
         G = self.Z.T @ AZ
-        return np.linalg.lstsq(0.5 * (G + G.T), AZ.T @ x, rcond=1e-13)[0]
+        return np.linalg.lstsq(0.5 * (G + G.T), self.Z.T @ b, rcond=1e-13)[0]
 
     def solve(self, A, b, tol_rel):
         n = self.n
@@ -525,7 +526,7 @@ class OracleKrylovSequence:
         info["y"] = Y.shape[1]
         info["k"] = k
         # coordinates of this solution in the (grown) basis
-        self.coords.append(self._a_coords(A, x))
+        self.coords.append(self._prev_weights(A, b))
         if self.Z.shape[1] > self.y_threshold:       # compression (Algorithm 3, truncation steps)
             m = self.Z.shape[1]
             if self.weights == "prev":

@@ -39,13 +39,24 @@ def test_constant_operator_basis_is_a_orthonormal(orc):
 
 
 def test_prev_weights_are_the_solution_coordinates(orc):
+    """Eq. (weightsPrevious): the previous weights (Z^T A Z)^{-1} Z^T b are the coefficients
+    of the solution's expansion in Z when the solution lies in range(Z), as the paper notes.
+    Solved tightly, the second solution is in range(Z) (its stage-three directions were
+    appended), so Z eta equals it; at a loose tolerance Z eta is the A-norm best
+    approximation of the exact solution from range(Z), no worse than the computed one."""
     A = pins.small_diffusion(8, seed=5)
     D = A.todense()
-    seq = OracleKrylovSequence(A.n, y_threshold=10 ** 6, nu=1.0, oracle=orc)
-    x1, _ = seq.solve(A.arrays(), _rhs(A.n, 6), 1e-8)
-    x2, _ = seq.solve(A.arrays(), _rhs(A.n, 7), 1e-8)
-    c = seq.coords[-1]
-    assert pins.a_norm(D, seq.Z @ c - x2) <= 1e-10 * pins.a_norm(D, x2)
+    for tol, bound in ((1e-12, 1e-9), (1e-4, None)):
+        seq = OracleKrylovSequence(A.n, y_threshold=10 ** 6, nu=1.0, oracle=orc)
+        seq.solve(A.arrays(), _rhs(A.n, 6), tol)
+        b2 = _rhs(A.n, 7)
+        x2, _ = seq.solve(A.arrays(), b2, tol)
+        xz = seq.Z @ seq.coords[-1]
+        xs = np.linalg.solve(D, b2)
+        if bound is not None:
+            assert pins.a_norm(D, xz - x2) <= bound * pins.a_norm(D, x2)
+        else:
+            assert pins.a_norm(D, xz - xs) <= pins.a_norm(D, x2 - xs) * (1 + 1e-9)
 
 
 def test_compression_and_sequence(orc):
