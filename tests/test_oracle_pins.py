@@ -201,3 +201,24 @@ def test_stage_two_past_the_rounding_floor(orc):
     err = lambda o: pins.a_norm(D, o["V2"] @ o["alpha"] - xg) / pins.a_norm(D, xg)
     assert off["k2"] == y and err(off) > 1.0
     assert on["k2"] < y // 2 and err(on) < 1e-12
+
+
+def test_exact_stage_two_in_a_sequence():
+    """The same effect in a sequence: metric-A POD (Y^T A Y = I to rounding), stage-one
+    energy 0.9 and stage-two tolerance 0 on the 20^3 moving-source sequence. Without the
+    dependence stop, stage two runs past the rounding floor on systems 7 and 8 and their
+    solves fail (the iteration cap is reached far from the tolerance); with it, every system
+    converges and stage two takes at most two steps."""
+    from oracle import Oracle, OracleSequence
+    from paper_1512_05820_gb300 import workloads as wl
+    orc = Oracle()
+    seq = wl.diffusion3d_moving(m=20, p=8, s_max=12, w_max=32, period=14)
+    res = {}
+    for on in (False, True):
+        oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=0.9, oracle=orc, three_stage=True,
+                              metric_a=True, y_max=12, energy_y=1 - 1e-10, tol_stage2=0.0, kmax=3000)
+        with orc.dependence_stop(on):
+            res[on] = [oseq.solve((seq.row_ptr, seq.col, val), b, seq.tol)[1] for _, val, b in seq.systems()]
+    assert any(i["status"] != "ok" for i in res[False])
+    assert all(i["status"] == "ok" and i["final_relres"] <= seq.tol for i in res[True])
+    assert max(i["k2"] for i in res[True]) <= 2 and max(i["k2"] for i in res[True]) >= 1
