@@ -109,6 +109,10 @@ typedef struct {
     double tol_stage2;   /* three_stage: stage two stops when ||Y^T (b - A x)||_2 <=
                             tol_stage2 * tol * ||b||_2, or after min(y, 64) - w iterations
                             (the reduced system is then solved exactly in exact arithmetic).
+                            Keep it above the reduced residual's rounding floor (the paper's
+                            1e-4 .. 1e-7 are): when Y^T A Y is well conditioned (metric A) and
+                            stage two runs past that floor, its later directions are rounding
+                            noise and re-A-orthogonalisation against them amplifies it.
                             Stage two runs in FP64 in both precisions (MIXED converts its
                             directions to FP32 for stage three) */
     double tol_inner;    /* three_stage = 2: each inner reduced solve stops when its residual
