@@ -92,12 +92,16 @@ def test_cg_rounding_sensitivity_elasticity(orc):
     assert err <= 1e-8
 
 
-@pytest.mark.parametrize("three_stage", [False, True])
-def test_golden_c1_sequence_record(three_stage):
-    """The oracle reproduces its committed records of the 64x64 sequence, two-stage and
-    three-stage (written by tests/golden/make_golden.py): iteration counts, w, k2, y and
-    refinements exactly, residuals and solution norms to 1e-12 relative. Guards the oracle
-    against unintended changes."""
+GOLDEN = {"c1_sequence_oracle.json": dict(), "c1_three_stage_oracle.json": dict(three_stage=True),
+          "c1_output_pod_oracle.json": dict(metric="output"), "c1_metric_a_oracle.json": dict(metric="a")}
+
+
+@pytest.mark.parametrize("name", sorted(GOLDEN))
+def test_golden_c1_sequence_record(name):
+    """The oracle reproduces its committed records of the 64x64 sequence: two stages, three
+    stages, and the POD metrics C^T C and A (written by tests/golden/make_golden.py):
+    iteration counts, w, k2, y and refinements exactly, residuals and solution norms to
+    1e-12 relative. Guards the oracle against unintended changes."""
     import json
     import os
     import sys
@@ -107,10 +111,9 @@ def test_golden_c1_sequence_record(three_stage):
         import make_golden
     finally:
         sys.path.remove(here)
-    name = "c1_three_stage_oracle.json" if three_stage else "c1_sequence_oracle.json"
     with open(os.path.join(here, name)) as f:
         ref = json.load(f)
-    now = make_golden.record(three_stage)
+    now = make_golden.record(**GOLDEN[name])
     assert len(now["systems"]) == len(ref["systems"])
     for a, b in zip(now["systems"], ref["systems"]):
         for k in ("system", "iters", "w", "refinements", "k2", "y"):
