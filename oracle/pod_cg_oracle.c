@@ -755,7 +755,7 @@ static int orc_stage_two_hist(int n, const int* rp, const int* ci, const double*
             double c = 0.0;
             for (int l = 0; l < y; ++l) c += Qh[(size_t)i * y + l] * ph[l];
             cf[i] = c / T2[i];
-            removed += cf[i] * c;
+            removed += MUT(20) ? cf[i] : cf[i] * c;
         }
         for (int l = 0; l < y && !MUT(15); ++l) {
             double t = 0.0;

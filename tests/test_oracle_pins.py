@@ -36,6 +36,7 @@ MUTANTS = {
     17: "one-sided Jacobi SVD rotates the second column with the wrong sign",
     18: "output-metric POD lift without 1/sigma",
     19: "A-metric POD Gram symmetrised with a sign error",
+    20: "stage two's dependence test sums the Gram-Schmidt coefficients instead of the A-norm they remove",
 }
 
 
