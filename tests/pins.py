@@ -55,6 +55,22 @@ def pin_spmv_dense(orc):
     return err < 1e-14, f"spmv rel err {err:.2e}"
 
 
+def pin_gram_spmm_dense(orc):
+    """G = X^T Y and AW = A W against the dense products (a tall X with a ragged row count,
+    the ragged random SPD matrix with diagonal-only rows)."""
+    rng = np.random.default_rng(11)
+    X = np.asfortranarray(rng.normal(size=(97, 5)))
+    Y = np.asfortranarray(rng.normal(size=(97, 7)))
+    G = orc.gram(X, Y)
+    e1 = np.max(np.abs(G - X.T @ Y)) / np.max(np.abs(X.T @ Y))
+    A = random_spd_csr(60, 0.1, seed=3, empty_rows=4)
+    W = np.asfortranarray(rng.normal(size=(60, 4)))
+    AW = orc.spmm(A.arrays(), W)
+    ref = A.todense() @ W
+    e2 = np.max(np.abs(AW - ref)) / np.max(np.abs(ref))
+    return e1 < 1e-14 and e2 < 1e-14, f"gram {e1:.1e}, spmm {e2:.1e}"
+
+
 def pin_cholesky_numpy(orc):
     """R^T R = G and R equals the transposed LAPACK lower factor; a non-SPD matrix fails."""
     rng = np.random.default_rng(5)
@@ -577,7 +593,7 @@ def pin_stage_two_dependence_stop(orc):
     return ok, f"dependence stop: Galerkin err {worst:.1e}, k2 {ks} of {y}"
 
 
-ALL_PINS = [pin_spmv_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
+ALL_PINS = [pin_spmv_dense, pin_gram_spmm_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
             pin_finite_termination, pin_theta_grad_complex_step, pin_stage_two_optimality,
