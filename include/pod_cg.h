@@ -7,8 +7,10 @@
  * ||b_j - A_j x_j||_2 <= tol ||b_j||_2 (Eq. (sequenceInexact), with a relative tolerance).
  * For system j the library, with the stages numbered as in Section 4,
  *   1. computes a POD basis W_j of the retained snapshots (previous solutions) with the
- *      eigenvalue route of Algorithm 4 (identity metric, unit weights): Gram S^T S,
- *      symmetric eigensolve, energy truncation, lift W = S V Sigma^{-1};
+ *      eigenvalue route of Algorithm 4 (unit weights): Gram S^T S, symmetric eigensolve,
+ *      energy truncation, lift W = S V Sigma^{-1}; in the identity metric by default, in
+ *      the metric A_j with pod_metric = 1 (Gram S^T A_j S), or in the output metric C^T C
+ *      after pod_cg_set_output_functionals (Section 3.3);
  *   2. stage one (Section 4.1, Algorithm 2): AW = A_j W, Ahat = W^T AW, Cholesky
  *      Ahat = R^T R, Ahat what = W^T b, x0 = W what, r0 = b - AW what;
  *   3. (three_stage = 1 only) stage two (Section 4.2): the POD also gives a larger
@@ -21,7 +23,9 @@
  *      two): Jacobi-preconditioned CG whose directions are A_j-orthogonalised against the
  *      basis through mu = R^{-1} R^{-T} (AW)^T z and p = z + beta p - W mu; or
  *      (three_stage = 2, Section 4.3.1) against all of Y, mu from an inner reduced solve
- *      of Y^T A Y mu = Y^T A z that reuses the reduced directions stored so far.
+ *      of Y^T A Y mu = Y^T A z that reuses the reduced directions stored so far. The CG
+ *      product A p runs in CSR form, or in 3x3 block form for patterns made of full 3x3
+ *      blocks (bsr).
  * Every step runs in hand-written CUDA kernels; this header is the only interface.
  *
  * Conventions for every entry point:
