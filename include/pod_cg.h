@@ -172,7 +172,8 @@ typedef struct {
 
 /* ------------------------------------------------------------------ handle lifecycle */
 
-/* Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
+/* Handle lifecycle: no counterpart in the paper (a library's housekeeping).
+ * Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
  * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
  * loop_mode 0, proj_form -1, spmv_lanes 0, three_stage 0, y_max 40, energy_y 0.99999999,
  * tol_stage2 1e-4, tol_inner 1e-12, bsr -1, pod_metric 0. */
@@ -185,11 +186,11 @@ pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg /* host, NULL = defaults */,
                             void* cuda_stream, pod_cg_t** out /* host, out */);
 
-/* Release everything the handle owns. NULL is accepted. */
+/* Release everything the handle owns (no counterpart in the paper). NULL is accepted. */
 pod_cg_status pod_cg_destroy(pod_cg_t* h);
 
-/* Message of the last failure on this handle (NULL: of the last stateless call on this
- * thread). The string stays valid until the next call on the same handle/thread. */
+/* Message of the last failure on this handle (no counterpart in the paper; NULL: of the
+ * last stateless call on this thread). The string stays valid until the next call on the same handle/thread. */
 const char* pod_cg_last_error(const pod_cg_t* h);
 
 /* ---------------------------------------------------------------------- the sequence */
@@ -208,7 +209,8 @@ pod_cg_status pod_cg_add_snapshots(pod_cg_t* h, const double* X, int m);
  * returns to the identity metric. Errors: ERR_ARG, ERR_STATE (pod_metric = 1), ERR_CUDA. */
 pod_cg_status pod_cg_set_output_functionals(pod_cg_t* h, const double* C, int q);
 
-/* Forget all snapshots (the next solve is plain Jacobi PCG). */
+/* Forget all snapshots: the snapshot set of Algorithm 4 becomes empty, so the next solve
+ * is Algorithm 1 with an empty basis (plain Jacobi PCG, Section 2.1). */
 pod_cg_status pod_cg_clear_snapshots(pod_cg_t* h);
 
 /* Solve A x = b to ||b - A x||_2 <= tol ||b||_2 (Eq. (sequenceInexact)) with the
@@ -223,7 +225,8 @@ pod_cg_status pod_cg_clear_snapshots(pod_cg_t* h);
 pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, double tol,
                            double* x_out, pod_cg_stats* st);
 
-/* Adjoint solve for a loss L(x_j): lambda = A_j^{-1} g (A_j symmetric, so A_j^{-T} = A_j^{-1}),
+/* Adjoint solve for a loss L(x_j): lambda = A_j^{-1} g (A_j symmetric, Section 2, so
+ * A_j^{-T} = A_j^{-1}; no counterpart in the paper beyond that symmetry),
  * by the same POD-augmented method reusing the stage-one basis W_j, A_j W_j and the factor
  * R_j saved by the forward solve whose stats reported `system_id` (three-stage handles keep
  * the stage-one basis only; the adjoint runs stages one and three) (requires
@@ -234,11 +237,12 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
                                    const double* g, double tol, double* lambda_out,
                                    pod_cg_stats* st);
 
-/* Copy the basis W used by the last solve (device out, n-by-w column-major, room for
- * w_max columns) and its dimension (host out). */
+/* Copy the POD basis W of the last solve (Algorithm 4's output, Eq.
+ * (podAlgebraicDefinition); device out, n-by-w column-major, room for w_max columns) and
+ * its dimension (host out). */
 pod_cg_status pod_cg_get_basis(pod_cg_t* h, double* W_out, int* w_out);
 
-/* Copy stage three's augmenting basis [W, V2] of the last solve and its product
+/* Copy stage three's augmenting basis [W, V2] of the last solve (Section 4.3) and its product
  * A [W, V2] (device outs, n-by-w3 column-major, room for 64 columns; either may be NULL)
  * and w3 = w + k2 (host out, may be NULL). FP64 handles only (ERR_STATE in MIXED, where
  * the basis is held in FP32). */
@@ -258,8 +262,8 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
  * 64): forms[6] receives 0 (row-parallel float4 passes), 1 (tiles staged in shared memory
  * by bulk copies) or -1 (bucket not used yet); ms[12] the update + direction times (ms)
  * of form 0 then form 1 for each bucket, as measured by the handle's one-time timing on the
- * first MIXED system of at least 65,536 rows in that bucket (0 where not timed). The
- * paper has no counterpart: this is the project's own tuning record. Host outputs;
+ * first MIXED system of at least 65,536 rows in that bucket (0 where not timed). This is
+ * the project's own tuning record, with no counterpart in the paper. Host outputs;
  * either pointer may be NULL. */
 pod_cg_status pod_cg_proj_tuning(const pod_cg_t* h, int* forms, float* ms);
 
@@ -280,7 +284,8 @@ pod_cg_status pod_cg_spmv(const pod_cg_csr* A, const double* x, double* y, void*
 pod_cg_status pod_cg_spmm(const pod_cg_csr* A, const double* W, int w, double* AW,
                           void* cuda_stream);
 
-/* Bytes of device workspace pod_cg_gram needs for an n-row, p-by-q product. */
+/* Bytes of device workspace pod_cg_gram needs for an n-row, p-by-q product (the Gram of
+ * Algorithm 2 step 1 and Algorithm 4 step 1). */
 size_t pod_cg_gram_workspace(int n, int p, int q);
 
 /* G = X^T Y for device X (n-by-p) and Y (n-by-q), column-major; G device row-major p-by-q.
@@ -290,7 +295,8 @@ size_t pod_cg_gram_workspace(int n, int p, int q);
 pod_cg_status pod_cg_gram(int n, const double* X, int p, const double* Y, int q, double* G,
                           void* work, size_t work_bytes, void* cuda_stream);
 
-/* Bytes of device workspace pod_cg_gram_tc needs for an n-row, p-by-q product. */
+/* Bytes of device workspace pod_cg_gram_tc needs for an n-row, p-by-q product (the Gram
+ * of Algorithm 2 step 1). */
 size_t pod_cg_gram_tc_workspace(int n, int p, int q);
 
 /* G = X^T [Y, e] on the tensor cores: the reduced matrix of stage one (Algorithm 2 step 1,
@@ -313,7 +319,8 @@ pod_cg_status pod_cg_gram_tc(int n, int elem_bytes, const void* X, int p, const 
  * of pod_cg_gram). It is for callers that cannot allocate device memory at the point of
  * use: latency-bound loops where cudaMalloc/cudaFree may synchronise the whole device, and
  * host applications that hand out all device memory themselves under a fixed budget.
- * Arguments as pod_cg_gram without the workspace: the scratch is a fixed 512 KiB array
+ * The Gram of pod_cg_gram (Algorithm 2 step 1, Algorithm 4 step 1), arguments as
+ * pod_cg_gram without the workspace: the scratch is a fixed 512 KiB array
  * compiled into the library (held on every GPU that loads the library until exit); this
  * call allocates nothing. p, q <= 65; a product whose scratch would exceed the array
  * (possible only on a GPU with far more than 152 SMs) is rejected with ERR_ARG and a
@@ -379,14 +386,16 @@ pod_cg_status pod_cg_batch_create(const pod_cg_batch_seq* seqs /* host, nseq */,
                                   const pod_cg_config* cfg, int cluster, void* cuda_stream,
                                   pod_cg_batch_t** out);
 
-/* Solve every system of every sequence (one graph launch; synchronises). stats (host,
+/* Solve every system of every sequence (one graph launch; synchronises) by the method of
+ * pod_cg_batch_create (Section 4.4 per sequence). stats (host,
  * may be NULL) receives one entry per system, sequences in the order given and systems
  * in order within each; ms (host, may be NULL) the device time of the launch. Returns
  * the first non-OK system status, if any. */
 pod_cg_status pod_cg_batch_solve(pod_cg_batch_t* h, pod_cg_batch_sysstat* stats, float* ms);
 
 /* Chosen cluster size, number of concurrent workers and the autotuner's timings (ms of
- * the whole batch for cluster 2, 4, 8; 0 when not tuned, -1 when not schedulable). */
+ * the whole batch for cluster 2, 4, 8; 0 when not tuned, -1 when not schedulable).
+ * Measurement support, no counterpart in the paper; so are the two calls after it. */
 pod_cg_status pod_cg_batch_info(const pod_cg_batch_t* h, int* cluster, int* workers, float* tune_ms3);
 const char* pod_cg_batch_last_error(const pod_cg_batch_t* h);
 pod_cg_status pod_cg_batch_destroy(pod_cg_batch_t* h);
@@ -404,7 +413,8 @@ pod_cg_status pod_cg_batch_destroy(pod_cg_batch_t* h);
 pod_cg_status pod_cg_diffusion_assemble(int mx, int my, int mz, const double* theta, const double* extra_diag,
                                         const int32_t* row_ptr, double* val_out, void* cuda_stream);
 
-/* Accumulate grad -= sum_j lambda_j^T (dA/dtheta) x_j for nsys systems of the operator
+/* Accumulate grad -= sum_j lambda_j^T (dA/dtheta) x_j for nsys systems (the adjoint
+ * gradient of a loss over the sequence of Section 2; the paper has no such step) of the operator
  * above: for each cell c, the sum over its faces of dk_f/dtheta_c (lambda_c - lambda_m)
  * (x_c - x_m) with dk_f/dtheta_c = k_f k_m/(k_c + k_m), plus 2 k_c lambda_c x_c per
  * boundary face. With lambda_j the adjoint solutions (pod_cg_solve_adjoint) of a loss

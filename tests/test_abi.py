@@ -110,3 +110,14 @@ def test_create_rejects_bad_configuration():
     h = ctypes.c_void_p()
     assert L.pod_cg_create(0, None, None, ctypes.byref(h)) == 1
     assert L.pod_cg_create(10, None, None, None) == 1
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment in include/pod_cg.h names the passage of the paper that
+    defines its operation (a Section, Algorithm, Equation or Theorem), or says that it has
+    no counterpart in the paper."""
+    text = open(os.path.join(ROOT, "include", "pod_cg.h")).read()
+    decl = r"/\*((?:(?!\*/).)*)\*/\s*(?:pod_cg_status|const char\*|size_t)\s+(pod_cg_\w+)\s*\("
+    missing = [name for com, name in re.findall(decl, text, flags=re.S)
+               if not re.search(r"Section|Algorithm|Eq\.|Theorem|no counterpart in the paper", com)]
+    assert not missing, missing
