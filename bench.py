@@ -320,12 +320,9 @@ def batch_section(args, rank=0, world=1):
         t_single += e0.elapsed_time(e1)
         n_single += dseq.p
         solver.close()
-    sub_sys = sum(len(sy) for sy in systems[:32])
-    frac = sub_sys / total
     out["single_sequence_fp64"] = {"systems_per_s": n_single / (t_single / 1e3), "sample": "first 32 sequences",
                                    "ms": t_single}
     out["speedup_vs_single_fp64"] = out["systems_per_s"] / out["single_sequence_fp64"]["systems_per_s"]
-    del frac
     return out
 
 

@@ -288,6 +288,11 @@ pod_cg_status pod_cg_spmm(const pod_cg_csr* A, const double* W, int w, double* A
  * Algorithm 2 step 1 and Algorithm 4 step 1). */
 size_t pod_cg_gram_workspace(int n, int p, int q);
 
+/* Sizing support with no counterpart in the paper: pod_cg_gram_workspace for a GPU with
+ * `sms` multiprocessors, with no device query, so a caller can size the workspace before
+ * a CUDA context exists. 0 for bad sizes. */
+size_t pod_cg_gram_workspace_for(int n, int p, int q, int sms);
+
 /* G = X^T Y for device X (n-by-p) and Y (n-by-q), column-major; G device row-major p-by-q.
  * This is the snapshot Gram S^T S (Algorithm 4 step 1) and the reduced matrix W^T (A W)
  * (Algorithm 2 step 1). p, q <= 65. work: device, at least pod_cg_gram_workspace(n,p,q)
@@ -315,20 +320,23 @@ size_t pod_cg_gram_tc_workspace(int n, int p, int q);
 pod_cg_status pod_cg_gram_tc(int n, int elem_bytes, const void* X, int p, const void* Y, int qy,
                              const double* e, double* G, void* work, size_t work_bytes, void* cuda_stream);
 
-/* Allocation-free G = X^T Y (the paper has no counterpart: this is a deployment variant
- * of pod_cg_gram). It is for callers that cannot allocate device memory at the point of
- * use: latency-bound loops where cudaMalloc/cudaFree may synchronise the whole device, and
- * host applications that hand out all device memory themselves under a fixed budget.
- * The Gram of pod_cg_gram (Algorithm 2 step 1, Algorithm 4 step 1), arguments as
- * pod_cg_gram without the workspace: the scratch is a fixed 512 KiB array
- * compiled into the library (held on every GPU that loads the library until exit); this
- * call allocates nothing. p, q <= 65; a product whose scratch would exceed the array
- * (possible only on a GPU with far more than 152 SMs) is rejected with ERR_ARG and a
- * message naming both sizes. The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Every call shares the one array: calls that may overlap on the GPU
- * (different streams, or different host threads) race on it and must be serialised by
- * the caller. Each call overwrites all the scratch it reads, so no clearing is needed. */
+/* Allocation-free G = X^T Y (no counterpart in the paper): a deployment variant
+ * of pod_cg_gram with the same arguments minus the workspace, and the same result bit for
+ * bit. It is for callers that cannot allocate device memory at the point of use:
+ * latency-bound loops where cudaMalloc/cudaFree may synchronise the whole device, and host
+ * applications that hand out all device memory themselves under a fixed budget. The
+ * scratch is a fixed 512 KiB array compiled into the library (held on every GPU that loads
+ * the library until exit); this call allocates nothing. p, q <= 65; a product whose scratch
+ * would exceed the array (possible only on a GPU with far more than 152 SMs) is rejected
+ * with ERR_ARG and a message naming both sizes. cuda_stream (NULL = legacy default stream)
+ * must belong to the current device (else ERR_ARG). The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current and keeps it
+ * for the process; make that first call before any stream capture. After cudaDeviceReset
+ * on a device the kept address is stale, so this entry point must not be called on that
+ * device again in the same process. Every call shares the one array: calls that may overlap
+ * on the GPU (different streams, or different host threads) race on it and must be
+ * serialised by the caller. Each call overwrites all the scratch it reads, so no clearing
+ * is needed. */
 pod_cg_status pod_cg_gram_noalloc(int n, const double* X, int p, const double* Y, int q, double* G,
                                   void* cuda_stream);
 

@@ -1615,6 +1615,12 @@ size_t pod_cg_gram_workspace(int n, int p, int q)
     return gram_workspace_bytes(n, p, q, device_sms());
 }
 
+size_t pod_cg_gram_workspace_for(int n, int p, int q, int sms)
+{
+    if (n < 1 || p < 1 || q < 1 || sms < 1) return 0;
+    return gram_workspace_bytes(n, p, q, sms);
+}
+
 pod_cg_status pod_cg_gram(int n, const double* X, int p, const double* Y, int q, double* G, void* work,
                           size_t work_bytes, void* stream)
 {

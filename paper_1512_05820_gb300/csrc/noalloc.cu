@@ -41,6 +41,16 @@ extern "C" pod_cg_status pod_cg_gram_noalloc(int n, const double* X, int p, cons
         podcg::set_last_error("pod_cg_gram_noalloc: no usable current device");
         return POD_CG_ERR_CUDA;
     }
+    if (cuda_stream) {
+        // the scratch used is the current device's, so the stream must run on that device
+        int sdev = -1;
+        e = cudaStreamGetDevice((cudaStream_t)cuda_stream, &sdev);
+        if (e != cudaSuccess || sdev != dev) {
+            podcg::set_last_error("pod_cg_gram_noalloc: the stream does not belong to the current device (" +
+                                  std::to_string(sdev) + " vs " + std::to_string(dev) + ")");
+            return e != cudaSuccess ? POD_CG_ERR_CUDA : POD_CG_ERR_ARG;
+        }
+    }
     double* scratch = nullptr;
     {
         // once per device, with that device current: the host-side name of the array is

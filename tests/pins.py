@@ -593,6 +593,42 @@ def pin_stage_two_dependence_stop(orc):
     return ok, f"dependence stop: Galerkin err {worst:.1e}, k2 {ks} of {y}"
 
 
+def pin_sequence_window(orc, seq_cls=None):
+    """The sequence driver's snapshot set (Section 3.1 with previous solutions as snapshots,
+    the window of the last s_max): after p > s_max solves, the basis for the next system is
+    the POD of exactly the last s_max recorded solutions. Checked against LAPACK's SVD of
+    those solutions: the eigenvalues are their squared singular values, w is the smallest
+    index whose energy fraction reaches the criterion, and range(W) is the span of the
+    leading w left singular vectors. Each solution is the solution (residual <= tol), not the
+    right-hand side. ``seq_cls`` lets a test substitute a driver with a planted mistake."""
+    from oracle import OracleSequence
+    cls = seq_cls or OracleSequence
+    A = small_diffusion(8, seed=6)
+    D = A.todense()
+    n, s_max, p, energy = A.n, 4, 7, 0.999
+    rng = np.random.default_rng(21)
+    c = rng.normal(size=n)
+    seq = cls(n, s_max=s_max, w_max=6, energy=energy, oracle=orc)
+    xs = []
+    for j in range(p):
+        b = D @ (c + 0.05 * rng.normal(size=n))   # solutions share one dominant direction
+        x, info = seq.solve(A.arrays(), b, 1e-12)
+        if np.linalg.norm(b - D @ x) > 1e-11 * np.linalg.norm(b):
+            return False, f"system {j}: the recorded iterate is not the solution"
+        xs.append(x)
+    W, w, sig2 = seq.basis()
+    S = np.stack(xs[-s_max:], axis=1)
+    U, sv, _ = np.linalg.svd(S, full_matrices=False)
+    frac = np.cumsum(sv ** 2) / np.sum(sv ** 2)
+    w_ref = int(np.argmax(frac >= energy)) + 1
+    if len(sig2) != s_max or w != w_ref or not 1 <= w < s_max:
+        return False, f"window: {len(sig2)} eigenvalues (want {s_max}), w={w} (want {w_ref})"
+    e_sig = np.max(np.abs(np.asarray(sig2) - sv ** 2)) / sv[0] ** 2
+    cos = np.linalg.svd(U[:, :w].T @ W, compute_uv=False)
+    ok = e_sig < 1e-12 and cos.min() > 1 - 1e-10
+    return ok, f"window sig2 err {e_sig:.1e} w={w} cos {cos.min():.12f}"
+
+
 ALL_PINS = [pin_spmv_dense, pin_gram_spmm_dense, pin_cholesky_numpy, pin_jacobi_closed_form, pin_jacobi_vs_eigh,
             pin_pod_svd, pin_pod_nested, pin_stage_one_exact, pin_stage_one_galerkin,
             pin_empty_basis_is_pcg, pin_dense_agreement, pin_a_orthogonality, pin_optimality,
@@ -600,4 +636,4 @@ ALL_PINS = [pin_spmv_dense, pin_gram_spmm_dense, pin_cholesky_numpy, pin_jacobi_
             pin_stage_two_full, pin_three_stage_optimality, pin_three_stage_collapse,
             pin_stage_two_reorthogonalised, pin_stage3_full_matches_direct, pin_jacobi_svd_numpy,
             pin_pod_output_metric, pin_pod_a_metric, pin_a_metric_stage_two_one_step,
-            pin_stage_two_dependence_stop]
+            pin_stage_two_dependence_stop, pin_sequence_window]

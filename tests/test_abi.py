@@ -121,3 +121,20 @@ def test_every_declaration_cites_its_passage():
     missing = [name for com, name in re.findall(decl, text, flags=re.S)
                if not re.search(r"Section|Algorithm|Eq\.|Theorem|no counterpart in the paper", com)]
     assert not missing, missing
+
+
+def test_gram_noalloc_scratch_covers_every_shape():
+    """The allocation-free Gram keeps its scratch in a fixed array of 65,536 doubles. On a
+    152-SM GB300 every product it accepts (p, q <= 65) must fit: the split-K shape gives
+    about four partial 8x8 tiles per SM, whatever n."""
+    L = _lib.load()
+    cap = 65536 * 8
+    worst = 0
+    for n in (1, 31, 256, 4097, 100_000, 2_097_152, 2**31 - 1):
+        for p in range(1, 66):
+            for q in range(1, 66):
+                need = L.pod_cg_gram_workspace_for(n, p, q, 152)
+                assert 0 < need <= cap, (n, p, q, need)
+                worst = max(worst, need)
+    assert worst <= 352_256   # (4 * 152 + 81 - 1) tiles of 64 doubles
+    assert L.pod_cg_gram_workspace_for(0, 1, 1, 152) == 0

@@ -226,3 +226,37 @@ def test_exact_stage_two_in_a_sequence():
     assert any(i["status"] != "ok" for i in res[False])
     assert all(i["status"] == "ok" and i["final_relres"] <= seq.tol for i in res[True])
     assert max(i["k2"] for i in res[True]) <= 2 and max(i["k2"] for i in res[True]) >= 1
+
+
+class _KeepFirst:
+    """Planted mistake: the window keeps the first s_max snapshots and drops later ones."""
+
+    def add_snapshot(self, x):
+        if len(self.snaps) < self.s_max:
+            self.snaps.append(np.array(x, dtype=np.float64))
+
+
+class _EvictNewest:
+    """Planted mistake: a full window replaces its newest snapshot instead of its oldest."""
+
+    def add_snapshot(self, x):
+        self.snaps.append(np.array(x, dtype=np.float64))
+        if len(self.snaps) > self.s_max:
+            self.snaps.pop(-2)
+
+
+class _ShortWindow:
+    """Planted mistake: off by one, the window holds s_max - 1 snapshots."""
+
+    def add_snapshot(self, x):
+        self.snaps.append(np.array(x, dtype=np.float64))
+        while len(self.snaps) >= self.s_max:
+            self.snaps.pop(0)
+
+
+@pytest.mark.parametrize("mistake", [_KeepFirst, _EvictNewest, _ShortWindow], ids=lambda c: c.__name__)
+def test_sequence_window_mistake_is_caught(orc, mistake):
+    from oracle import OracleSequence
+    cls = type("Mutated" + mistake.__name__, (mistake, OracleSequence), {})
+    ok, detail = pins.pin_sequence_window(orc, cls)
+    assert not ok, f"{mistake.__doc__} passed the window pin: {detail}"
