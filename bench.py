@@ -229,36 +229,94 @@ def traffic_from_profiles(kernel: str, precision: str, w: int):
 # ----------------------------------------------------------------------- reference arm
 
 
+CPU_PREFIX = 2   # the oracle's sample: systems 1..CPU_PREFIX of the sequence
+
+
+def oracle_prefix_sample(grid: int, systems_total: int, k: int = CPU_PREFIX) -> dict:
+    """One bounded sample of the workload on the FP64 oracle, single-threaded: the first k
+    systems of the sequence solved in order by the POD-augmented method (OracleSequence:
+    POD of the solutions so far, stage one, Algorithm 1, each solution recorded as a
+    snapshot), then plain Jacobi PCG on the same systems. System 1 has no snapshots, so its
+    POD-augmented solve is plain PCG (pinned bit for bit), and its time counts for both."""
+    from oracle import Oracle, OracleSequence
+    from paper_1512_05820_gb300 import workloads as wl
+    seq = wl.diffusion3d_moving(m=grid, p=systems_total)
+    it = seq.systems()
+    sy = [next(it) for _ in range(k)]
+    orc = Oracle()
+    oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
+    xs, t_sys, its, ws = [], [], [], []
+    for j, val, b in sy:
+        t0 = time.perf_counter()
+        x, info = oseq.solve((seq.row_ptr, seq.col, val), b, seq.tol)
+        t_sys.append(time.perf_counter() - t0)
+        xs.append(x)
+        its.append(info["iters"])
+        ws.append(info["w"])
+    t_plain, its_plain = [t_sys[0]], [its[0]]
+    for j, val, b in sy[1:]:
+        t0 = time.perf_counter()
+        _, info, _, _ = orc.solve_system((seq.row_ptr, seq.col, val), b, None, seq.tol)
+        t_plain.append(time.perf_counter() - t0)
+        its_plain.append(info["iters"])
+    return {"xs": xs, "t_pod_aug": sum(t_sys), "t_plain": sum(t_plain), "iters": its, "w": ws,
+            "iters_plain": its_plain, "k": k}
+
+
+def _reference_worker(task):
+    grid, systems_total, k = task
+    r = oracle_prefix_sample(grid, systems_total, k)
+    del r["xs"]
+    return r
+
+
 def run_reference(args, rank, world):
-    """The FP64 CPU oracle (single thread) on a bounded sample of the workload: system 1
-    of the sequence (no snapshots yet, so Algorithm 1 with an empty basis)."""
+    """The FP64 CPU oracle on the host cores. One step = one bounded sample of the workload
+    (oracle_prefix_sample: systems 1-2 by the POD-augmented method, then plain PCG on the
+    same systems, one thread). The W warm-up steps, then the K timed steps, run as
+    independent single-threaded processes, min(cores, K) at a time; value = K x 2 systems
+    over the wall time of the timed steps (the host's aggregate rate), ms_per_step = that
+    wall time / K."""
     if rank != 0:
         return 0
-    from oracle import Oracle, OracleSequence
-    seq = workload(args)
-    j, val, b = next(iter(seq.systems()))
-    A = (seq.row_ptr, seq.col, val)
-    orc = Oracle()
-    times = []
-    info = None
-    for it in range(args.warmup + args.steps):
-        oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
+    import multiprocessing as mp
+    from paper_1512_05820_gb300 import workloads as wl
+    seq = wl.diffusion3d_moving(m=args.grid, p=args.systems)
+    ncpu = os.cpu_count() or 1
+    procs = max(1, min(ncpu, args.steps))
+    task = (args.grid, args.systems, CPU_PREFIX)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        if args.warmup:
+            pool.map(_reference_worker, [task] * args.warmup, chunksize=1)
         t0 = time.perf_counter()
-        x, info = oseq.solve(A, b, seq.tol)
-        dt = time.perf_counter() - t0
-        if it >= args.warmup:
-            times.append(dt)
-    t = statistics.mean(times)
-    value = 1.0 / t
-    sample = f"system 1 of {seq.p} (no snapshots: Algorithm 1 with an empty basis), {info['iters']} iterations"
+        res = pool.map(_reference_worker, [task] * args.steps, chunksize=1)
+        wall = time.perf_counter() - t0
+    systems = args.steps * CPU_PREFIX
+    value = systems / wall
+    one = statistics.mean(r["t_pod_aug"] for r in res)
+    plain = statistics.mean(r["t_plain"] for r in res)
+    r0 = res[0]
+    sample = (f"systems 1-{CPU_PREFIX} of {seq.p} at full size by the oracle's POD-augmented method "
+              f"(w {r0['w']}, iterations {r0['iters']}), then plain PCG on the same systems (iterations "
+              f"{r0['iters_plain']}); {args.steps} independent single-threaded copies, {procs} at a time on "
+              f"{ncpu} host cores; per copy (one thread): POD-aug {CPU_PREFIX / one:.4f} systems/s, plain PCG "
+              f"{CPU_PREFIX / plain:.4f} systems/s")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(seq, args, args.precision),   # the timed arm's config; dtype says f64
-            "cpu_baseline": {"value": value, "unit": "systems/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "systems/s", "cores": procs, "kind": "oracle",
+                             "nproc": ncpu, "sample": sample},
             "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def a_norm_rel(orc, A, x, xo) -> float:
+    """||x - xo||_A / ||xo||_A with the oracle's FP64 SpMV."""
+    d = np.asarray(x, dtype=np.float64) - xo
+    return float(np.sqrt(max(d @ orc.spmv(A, d), 0.0) / max(xo @ orc.spmv(A, xo), 1e-300)))
 
 
 # ----------------------------------------------------------------------------- ours
@@ -300,6 +358,7 @@ def batch_section(args, rank=0, world=1):
            "mean_iters": float(np.mean([s["iters"] for s in stats])),
            "cluster": info["cluster"], "workers": info["workers"],
            "autotune_ms": {str(k): v for k, v in info["tune_ms"].items()}, "setup_s": tune_s}
+    out["err_vs_fp64_oracle"] = batch_oracle_error(seqs, systems, bs)
     bs.close()
     if world > 1:
         return out
@@ -326,17 +385,45 @@ def batch_section(args, rank=0, world=1):
     return out
 
 
-def cpu_baseline(seq, systems):
-    from oracle import Oracle, OracleSequence
-    j, val, b = systems[0]
+def cpu_baseline(args, seq, gpu_xs):
+    """The oracle sample of the reference arm (systems 1-2, POD-augmented then plain PCG),
+    once, single-threaded. Returns the cpu_baseline record and the error of the GPU's
+    solutions of the same systems (gpu_xs: host arrays per precision) against the FP64
+    oracle's, in the A-norm."""
+    from oracle import Oracle
+    r = oracle_prefix_sample(args.grid, args.systems)
+    k = r["k"]
+    rec = {"value": k / r["t_pod_aug"], "unit": "systems/s", "cores": 1, "kind": "oracle",
+           "nproc": os.cpu_count() or 1,
+           "sample": f"systems 1-{k} of {seq.p} at full size by the oracle's POD-augmented method (w {r['w']}, "
+                     f"iterations {r['iters']}, {r['t_pod_aug']:.1f} s); plain PCG on the same systems: "
+                     f"{k / r['t_plain']:.4f} systems/s (iterations {r['iters_plain']}); one thread"}
     orc = Oracle()
-    oseq = OracleSequence(seq.n, s_max=seq.s_max, w_max=seq.w_max, energy=seq.energy, oracle=orc)
-    t0 = time.perf_counter()
-    x, info = oseq.solve((seq.row_ptr, seq.col, val), b, seq.tol)
-    dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "systems/s", "cores": 1, "kind": "oracle",
-            "sample": f"system 1 of {seq.p} at full size (no snapshots yet: Algorithm 1 with an empty basis, "
-                      f"{info['iters']} iterations, {dt:.1f} s); systems/s = 1/time"}
+    it = seq.systems()
+    mats = [(seq.row_ptr, seq.col, next(it)[1]) for _ in range(k)]
+    err = {}
+    for name, xs in gpu_xs.items():
+        e = [a_norm_rel(orc, mats[j], xs[j], r["xs"][j]) for j in range(min(k, len(xs)))]
+        err[name] = {"max_a_norm_rel": max(e), "systems": f"1-{k}", "per_system": e}
+    return rec, err
+
+
+def batch_oracle_error(seqs, systems, bs, count=4):
+    """A-norm error of the batch's solutions against the FP64 oracle's solve of the same
+    sequences (each side recycling its own solutions), on the `count` smallest sequences."""
+    from oracle import Oracle, OracleSequence
+    orc = Oracle()
+    order = sorted(range(len(seqs)), key=lambda i: seqs[i].n)[:count]
+    worst = 0.0
+    for i in order:
+        seq, sy = seqs[i], systems[i]
+        X = bs.solutions(i).cpu().numpy()
+        oseq = OracleSequence(seq.n, s_max=min(seq.s_max, 16), w_max=seq.w_max, energy=seq.energy, oracle=orc)
+        for j, (_, val, b) in enumerate(sy):
+            A = (seq.row_ptr, seq.col, val)
+            xo, _ = oseq.solve(A, b, seq.tol)
+            worst = max(worst, a_norm_rel(orc, A, X[j], xo))
+    return {"max_a_norm_rel": worst, "sample": f"the {len(order)} smallest sequences, all systems"}
 
 
 def kernel_profile(args):
@@ -810,6 +897,8 @@ def main():
     torch.cuda.synchronize()
     clocks = sampler.stop()
     from paper_1512_05820_gb300.dist import combine
+    # the GPU's solutions of the first systems, for the error against the FP64 oracle
+    gpu_xs = {("mixed" if prec == 1 else "fp64"): [xs[j].cpu().numpy() for j in range(CPU_PREFIX)]}
     ms_total, systems_done = combine(e0.elapsed_time(e1), float(seq.p * args.steps))
     ms_step = ms_total / args.steps
     value = systems_done / (ms_total / 1e3)
@@ -862,6 +951,8 @@ def main():
         torch.cuda.synchronize()
         pms = a0.elapsed_time(a1)
         sv.close()
+        if recycle:
+            gpu_xs["mixed" if precision == 1 else "fp64"] = [xs[j].cpu().numpy() for j in range(CPU_PREFIX)]
         return {"systems_per_s": seq.p / (pms / 1e3), "ms_per_step": pms,
                 "mean_iters": float(np.mean([s["iters"] for s in pst])),
                 "spmv_equiv_gbs": sum(s["spmv_count"] for s in pst) * bsp / (pms / 1e3) / 1e9,
@@ -953,7 +1044,16 @@ def main():
     out["gpu_launches"] = launches
     out["clocks"] = clocks
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(seq, systems)
+        out["cpu_baseline"], out["err_vs_fp64_oracle"] = cpu_baseline(args, seq, gpu_xs)
+    # the comparison the metric names, last on the line (a reader of the line's tail sees it)
+    for key in ("pod_aug_fp64", "pod_aug_mixed", "plain_cg_mixed", "plain_cg_fp64",
+                "speedup_vs_plain_cg_same_precision", "speedup_vs_fp64_pod_aug", "err_vs_fp64_oracle"):
+        if key in out:
+            out[key] = out.pop(key)
+    if batch_out is not None and "err_vs_fp64_oracle" in batch_out:
+        out["batch_err_vs_fp64_oracle"] = batch_out["err_vs_fp64_oracle"]
+    out["headline"] = {"pod_aug_" + ("mixed" if prec == 1 else "fp64"): value, "roofline_frac": out["roofline"]["frac"],
+                       "roofline_kernel": out["roofline"]["kernel"]}
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -95,3 +95,52 @@ def test_elasticity_full_size_properties(dev):
         assert st["status"] == "ok" and rel <= seq.tol, (j, rel, st)
     assert all(st["stage1_relres"] < 1.0 for st in stats[1:])
     assert solver.tuning()["spmv_lanes"] >= 2
+
+
+def cantilever_shapes(op, s, seed=1240):
+    """s displacement fields on the cantilever's free nodes, an (n, s) Fortran block: the
+    tip-load bending shape v(x) = x^2 (3L - x)/(2 L^3) deflecting in direction
+    (0, cos phi_k, sin phi_k), phi_k = 2 pi k/s, plus 1% of a seeded smooth sine field per
+    component (wave numbers U{1..3})."""
+    rng = np.random.default_rng(seed)
+    L = float(op.ex)
+    x, y, z = op.fix.astype(float), op.fiy.astype(float), op.fiz.astype(float)
+    v = x ** 2 * (3 * L - x) / (2 * L ** 3)
+    S = np.zeros((op.nfree, 3, s))
+    for k in range(s):
+        phi = 2 * np.pi * k / s
+        S[:, 1, k] = v * np.cos(phi)
+        S[:, 2, k] = v * np.sin(phi)
+        for c in range(3):
+            a, b_, d = rng.integers(1, 4, size=3)
+            S[:, c, k] += 0.01 * np.sin(np.pi * a * x / L) * np.sin(np.pi * b_ * y / op.ey) * np.sin(np.pi * d * z / op.ez)
+    return np.asfortranarray(S.reshape(op.n, s))
+
+
+def test_elasticity_full_size_fp64_block_product(dev):
+    """64^3 elements (n = 811,200, 63.7M entries), system 1 of the sequence, FP64, CG product
+    in 3x3 block form (bsr = 1), with six seeded bending-shape snapshots given to both sides:
+    equal w, stage one's residual to 1e-8, and after 60 capped iterations the iterate
+    against the oracle's in the A-norm at this operator's FP64 floor, 5e-9 (reading 11:
+    two FP64 CG runs that differ only in summation order differ by ~1e-9 here)."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.elasticity_cantilever(e=64, p=1)
+    j, val, b = next(iter(seq.systems()))
+    A = (seq.row_ptr, seq.col, val)
+    S = cantilever_shapes(seq.op, 6)
+    orc = Oracle()
+    W, w, _ = orc.pod_evd(S, seq.energy, seq.w_max)
+    k = 60
+    xo, info, _, _ = orc.solve_system(A, b, W, seq.tol, kmax=k, max_refine=0)
+    solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=0, bsr=1, k_max=k,
+                   max_refine=0)
+    solver.add_snapshots(to_dev(S, dev))
+    x, st = solver.solve(DeviceCSR.from_numpy(*A, device=dev), to_dev(b, dev), seq.tol, raise_on_error=False)
+    solver.close()
+    x = x.cpu().numpy()
+    assert st["status"] == info["status"] == "maxit" and st["iters"] == info["iters"] == k
+    assert st["w"] == info["w"] == w and w > 0
+    assert abs(st["stage1_relres"] - info["stage1_relres"]) <= 1e-8 * info["stage1_relres"]
+    err = a_err(orc, A, x, xo)
+    print(f"elasticity 64^3, FP64 block product: w={w}, {k} iterations, A-norm difference {err:.2e}")
+    assert err <= 5e-9

@@ -16,6 +16,18 @@ so no input comes from the GPU path) and the first system of the sequence:
   rounding of W, AW and their Gram (1e-4 relative: cond(W^T A W) is about 16, and an
   FP32 model of the three roundings moves the residual by 2e-7), and the true residual
   <= tol recomputed with the oracle's SpMV.
+
+Whole solves with a basis, on the second system of the sequence: the snapshot set is 39
+seeded smooth fields plus the oracle's own FP64 solution of system 1 (so no input comes
+from the GPU path), and the oracle solves system 2 to tol 1e-8 with the POD of that set
+(about 500 iterations, half a minute on one core):
+- FP64, in the benchmark's handle configuration: the solution in the A-norm (1e-10
+  relative) and the iteration count within one (reading 10: at an unequal count the GPU
+  iterate is compared with the oracle's after the same number of steps);
+- mixed precision (FP32 inner solves, FP64 refinement): the A-norm difference from the
+  FP64 oracle's solution, which the test prints, within 1e-5 (both solutions only satisfy
+  ||b - A x|| <= 1e-8 ||b||, so they differ by the error the tolerance leaves), and the
+  true residual <= tol.
 """
 import numpy as np
 import pytest
@@ -101,5 +113,53 @@ def test_full_size_mixed_solve(dev, orc, case):
     assert st["status"] == "ok", st
     assert st["w"] == w
     assert abs(st["stage1_relres"] - info["stage1_relres"]) <= 1e-4 * info["stage1_relres"]
+    true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= seq.tol and st["final_relres"] <= seq.tol
+
+
+@pytest.fixture(scope="module")
+def second_system(orc):
+    seq = wl.diffusion3d_moving()
+    it = seq.systems()
+    _, val1, b1 = next(it)
+    _, val2, b2 = next(it)
+    A1, A2 = (seq.row_ptr, seq.col, val1), (seq.row_ptr, seq.col, val2)
+    x1, info1, _, _ = orc.solve_system(A1, b1, None, seq.tol)
+    assert info1["status"] == "ok"
+    S = np.asfortranarray(np.concatenate([wl.smooth_snapshots(seq.op, seq.s_max - 1), x1[:, None]], axis=1))
+    W, w, _ = orc.pod_evd(S, seq.energy, seq.w_max)
+    xo, info, _, _ = orc.solve_system(A2, b2, W, seq.tol)
+    assert info["status"] == "ok" and w > 0
+    return seq, S, A2, b2, W, w, xo, info
+
+
+def test_full_size_fp64_solve_with_basis(dev, orc, second_system):
+    seq, S, A, b, W, w, xo, info = second_system
+    solver = make_solver(dev, seq, S, precision=0)
+    x, st = solve(dev, solver, A, b, seq.tol)
+    solver.close()
+    assert st["status"] == "ok" and st["w"] == w, st
+    assert abs(st["iters"] - info["iters"]) <= 1, (st["iters"], info["iters"])
+    if st["iters"] != info["iters"] and st["refinements"] == 0 and info["refinements"] == 0:
+        xo, info_k, _, _ = orc.solve_system(A, b, W, 0.0, kmax=st["iters"], max_refine=0)
+        assert info_k["iters"] == st["iters"]
+    err = a_err(orc, A, x, xo)
+    print(f"128^3 system 2, FP64: w={w}, iterations {st['iters']} (oracle {info['iters']}), A-norm difference {err:.2e}")
+    assert err <= 1e-10
+    true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
+    assert true_rel <= seq.tol and st["final_relres"] <= seq.tol
+    assert abs(st["stage1_relres"] - info["stage1_relres"]) <= 1e-8 * info["stage1_relres"]
+
+
+def test_full_size_mixed_solve_with_basis(dev, orc, second_system):
+    seq, S, A, b, W, w, xo, info = second_system
+    solver = make_solver(dev, seq, S, precision=1)
+    x, st = solve(dev, solver, A, b, seq.tol)
+    solver.close()
+    assert st["status"] == "ok" and st["w"] == w, st
+    err = a_err(orc, A, x, xo)
+    print(f"128^3 system 2, mixed: w={w}, iterations {st['iters']} (FP64 oracle {info['iters']}), "
+          f"A-norm difference from the FP64 oracle {err:.2e}")
+    assert err <= 1e-5
     true_rel = np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b)
     assert true_rel <= seq.tol and st["final_relres"] <= seq.tol
