@@ -320,6 +320,17 @@ size_t pod_cg_gram_tc_workspace(int n, int p, int q);
 pod_cg_status pod_cg_gram_tc(int n, int elem_bytes, const void* X, int p, const void* Y, int qy,
                              const double* e, double* G, void* work, size_t work_bytes, void* cuda_stream);
 
+/* Test support with no counterpart in the paper: exercise the failure path of the bounded
+ * device waits without a GPU fault. While bit 1 (the tensor-core Gram, pod_cg_gram_tc and
+ * use_tc_gram solves) or bit 2 (the FP32 update and direction passes staged by bulk copies,
+ * proj_form = 1) is set in `mask`, those kernels issue no copies and every wait of theirs
+ * gives up after `cycles` SM clocks (1e3 .. 4e9), so each runs its timeout path with nothing
+ * in flight: a solve then ends with ERR_TIMEOUT (the handle stays usable) and
+ * pod_cg_gram_tc leaves NaN in G. mask = 0 restores normal operation (4e9-clock waits).
+ * Applies to the current device, from the next launch on, captured graphs included; meant
+ * for tests of the failure path only. Errors: ERR_ARG, ERR_CUDA. */
+pod_cg_status pod_cg_debug_wait_timeout(int mask, long long cycles);
+
 /* Allocation-free G = X^T Y (no counterpart in the paper): a deployment variant
  * of pod_cg_gram with the same arguments minus the workspace, and the same result bit for
  * bit. It is for callers that cannot allocate device memory at the point of use:

@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "ok", 1: "arg", 2: "not_spd", 3: "breakdown", 4: "maxit", 5: 
 # every function the header declares (checked by the symbol-export test)
 EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_last_error",
            "pod_cg_add_snapshots", "pod_cg_clear_snapshots", "pod_cg_set_output_functionals", "pod_cg_solve", "pod_cg_solve_adjoint",
-           "pod_cg_get_basis", "pod_cg_get_stage3_basis", "pod_cg_time_kernels", "pod_cg_tuning", "pod_cg_proj_tuning", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram_workspace_for", "pod_cg_gram", "pod_cg_gram_noalloc",
+           "pod_cg_get_basis", "pod_cg_get_stage3_basis", "pod_cg_time_kernels", "pod_cg_tuning", "pod_cg_proj_tuning", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram_workspace_for", "pod_cg_gram", "pod_cg_gram_noalloc", "pod_cg_debug_wait_timeout",
            "pod_cg_gram_tc_workspace", "pod_cg_gram_tc", "pod_cg_diffusion_assemble",
            "pod_cg_diffusion_theta_grad", "pod_cg_batch_create", "pod_cg_batch_solve", "pod_cg_batch_info",
            "pod_cg_batch_last_error", "pod_cg_batch_destroy",
@@ -105,6 +105,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_gram_workspace_for.restype = sz
     L.pod_cg_gram.argtypes = [ci, vp, ci, vp, ci, vp, vp, sz, vp]
     L.pod_cg_gram_noalloc.argtypes = [ci, vp, ci, vp, ci, vp, vp]
+    L.pod_cg_debug_wait_timeout.argtypes = [ci, ctypes.c_longlong]
     L.pod_cg_gram_tc_workspace.argtypes = [ci, ci, ci]
     L.pod_cg_gram_tc_workspace.restype = sz
     L.pod_cg_gram_tc.argtypes = [ci, ci, vp, ci, vp, ci, vp, vp, vp, sz, vp]

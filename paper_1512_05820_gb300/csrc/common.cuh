@@ -106,6 +106,19 @@ __device__ __forceinline__ void cg_product_finish(DevState* st, double gamma)
     st->alpha = (status == 0 && !inner_break) ? rho / gamma : 0.0;
 }
 
+// Test support for the failure path of the bounded device waits
+// (pod_cg_debug_wait_timeout): while a kernel's bit is set in `mask`, its producers issue no
+// copies and each of its waits gives up after `cycles` SM clocks, so the timeout path runs
+// with nothing in flight. Each translation unit with bounded waits keeps its own copy in
+// device memory, read by the kernels at run time (captured graphs see changes).
+struct WaitTest {
+    long long cycles;
+    int mask;
+    int pad_;
+};
+constexpr int kWaitTestGramTc = 1;   // k_gram_tc
+constexpr int kWaitTestStaged = 2;   // k_update_bulk, k_dir_bulk
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {

@@ -1615,6 +1615,17 @@ size_t pod_cg_gram_workspace(int n, int p, int q)
     return gram_workspace_bytes(n, p, q, device_sms());
 }
 
+pod_cg_status pod_cg_debug_wait_timeout(int mask, long long cycles)
+{
+    if (mask < 0 || mask > (kWaitTestGramTc | kWaitTestStaged) || (mask != 0 && (cycles < 1000 || cycles > 4000000000LL)))
+        return fail(nullptr, POD_CG_ERR_ARG, "pod_cg_debug_wait_timeout: mask 0..3 and 1e3 <= cycles <= 4e9");
+    const long long c = mask ? cycles : 0;
+    cudaError_t e = gram_tc_set_wait_test(mask & kWaitTestGramTc, c);
+    if (e == cudaSuccess) e = cg_set_wait_test(mask & kWaitTestStaged, c);
+    if (e != cudaSuccess) return cuda_fail(nullptr, "pod_cg_debug_wait_timeout", e);
+    return POD_CG_OK;
+}
+
 size_t pod_cg_gram_workspace_for(int n, int p, int q, int sms)
 {
     if (n < 1 || p < 1 || q < 1 || sms < 1) return 0;

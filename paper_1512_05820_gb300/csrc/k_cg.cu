@@ -285,15 +285,18 @@ __device__ __forceinline__ bool bulk_try(uint32_t mbar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait: the SM clock is read only once the first try fails.
-__device__ __forceinline__ bool bulk_wait(uint32_t mbar, uint32_t parity)
+// Bounded wait of `budget` SM clocks: the clock is read only once the first try fails.
+__device__ __forceinline__ bool bulk_wait(uint32_t mbar, uint32_t parity, long long budget)
 {
     if (bulk_try(mbar, parity)) return true;
     const long long c0 = clock64();
     while (!bulk_try(mbar, parity))
-        if (clock64() - c0 > kBulkWaitCycles) return false;
+        if (clock64() - c0 > budget) return false;
     return true;
 }
+
+// The wait override of pod_cg_debug_wait_timeout for the staged passes (zero: normal).
+static __device__ WaitTest g_cg_wait_test;
 
 // The ring of one block: tile range, run-time stage size and count, copy issue and waits.
 // Stage layout: w panel column tiles, then the NV vector tiles, 1 KB each.
@@ -302,9 +305,14 @@ struct BulkRing {
     unsigned char* smem;
     uint64_t* full;
     int t0, nloc, issued, S, w, stage_bytes;
+    long long budget;   // SM clocks a wait may take
+    bool starve;        // test of the timeout path: no copy is ever issued
 
     __device__ void init(unsigned char* sm, int n, int w_)
     {
+        const WaitTest wt = g_cg_wait_test;
+        starve = (wt.mask & kWaitTestStaged) != 0;
+        budget = starve ? wt.cycles : kBulkWaitCycles;
         full = reinterpret_cast<uint64_t*>(sm);
         smem = sm + kBulkBarBytes;
         w = w_;
@@ -318,7 +326,7 @@ struct BulkRing {
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bulk_smem_u32(&full[i])));
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
-        issued = nloc < S ? nloc : S;
+        issued = starve ? 0 : (nloc < S ? nloc : S);
         __syncthreads();
     }
     __device__ const float* stage(int t) const
@@ -331,6 +339,7 @@ struct BulkRing {
     // together; lane 0 posts the byte count first
     __device__ void issue(int t, int ld, const float* panel, const float* const* vec)
     {
+        if (starve) return;
         const int lane = threadIdx.x & 31;
         const int r0 = row0(t);
         const int rows = min(kBlock, ld - r0);
@@ -358,7 +367,7 @@ struct BulkRing {
     }
     __device__ bool wait(int t) const
     {
-        return bulk_wait(bulk_smem_u32(&full[t % S]), (uint32_t)((t / S) & 1));
+        return bulk_wait(bulk_smem_u32(&full[t % S]), (uint32_t)((t / S) & 1), budget);
     }
     // after a timeout: bounded waits for the copies still in flight
     __device__ void drain(int consumed) const
@@ -396,7 +405,7 @@ __global__ void __launch_bounds__(kBlock) k_update_bulk(int n, int ld, float* __
         if (!__syncthreads_and(ring.wait(t))) break;
         if (t > 0 && t - 1 + ring.S < ring.nloc) {
             if (threadIdx.x < 32) ring.issue(t - 1 + ring.S, ld, AW, vec);   // refill tile t-1's stage
-            ++ring.issued;
+            if (!ring.starve) ++ring.issued;
         }
         const float* sg = ring.stage(t);
         const float* sr = sg + w * kBlock;
@@ -506,7 +515,7 @@ __global__ void __launch_bounds__(kBlock) k_dir_bulk(int n, int ld, float* __res
         if (!__syncthreads_and(ring.wait(t))) break;
         if (t > 0 && t - 1 + ring.S < ring.nloc) {
             if (threadIdx.x < 32) ring.issue(t - 1 + ring.S, ld, W, vec);
-            ++ring.issued;
+            if (!ring.starve) ++ring.issued;
         }
         const float* sg = ring.stage(t);
         const float* sv = sg + wc * kBlock;
@@ -778,6 +787,12 @@ void cg_kernels(int wb, bool fp32, bool cond, int form, void** init, void** upd,
         if (cond) pick<double, true>(wb, init, upd, dir0, dir);
         else pick<double, false>(wb, init, upd, dir0, dir);
     }
+}
+
+cudaError_t cg_set_wait_test(int mask, long long cycles)
+{
+    const WaitTest wt{cycles, mask, 0};
+    return cudaMemcpyToSymbol(g_cg_wait_test, &wt, sizeof(wt));
 }
 
 int wb_bucket(int w)

@@ -105,16 +105,20 @@ __device__ __forceinline__ bool tc_try(uint32_t mbar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for the phase of parity `parity` of an mbarrier; false after kTcWaitCycles SM
-// clocks (about 2 s at the maximum clock). The clock is read only once the first try fails.
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+// Wait for the phase of parity `parity` of an mbarrier; false after `budget` SM clocks
+// (kTcWaitCycles, about 2 s at the maximum clock, unless a test shortened it). The clock is
+// read only once the first try fails.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, long long budget)
 {
     if (tc_try(mbar, parity)) return true;
     const long long c0 = clock64();
     while (!tc_try(mbar, parity))
-        if (clock64() - c0 > kTcWaitCycles) return false;
+        if (clock64() - c0 > budget) return false;
     return true;
 }
+
+// The wait override of pod_cg_debug_wait_timeout for this kernel (zero: normal operation).
+static __device__ WaitTest g_tc_wait_test;
 
 // 4 consecutive values -> three packed bf16 quads (hi, mid, lo) with v = hi + mid + lo
 // exactly. Truncation split: hi keeps the top 8 significant bits of v (its bf16 bit pattern
@@ -236,6 +240,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int nloc = (int)(((long long)(blockIdx.x + 1) * nchunks) / gridDim.x) - c0;
     const int nwin = (nloc + kTcFlush - 1) / kTcFlush;
     const uint32_t tx_bytes = (uint32_t)(G::kBoxes * 128 * (p + qy) + (has_extra ? 256 : 0));
+    const WaitTest wt = g_tc_wait_test;
+    const bool starve = (wt.mask & kWaitTestGramTc) != 0;   // test: no copies, short waits
+    const long long budget = starve ? wt.cycles : kTcWaitCycles;
     auto B = [&](int i) { return tc_smem_u32(&bar[i]); };
 
     // zero the MMA tiles (rows beyond the used ones stay zero) and the Kahan sums
@@ -277,9 +284,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == kTcProducerWarp) {
         if (lane == 0) {
             int issued = 0;
-            for (int c = 0; c < nloc && !*s_err; ++c) {
+            for (int c = 0; c < nloc && !*s_err && !starve; ++c) {
                 const int s = c % S;
-                if (c >= S && !tc_wait(B(kBarRingFree + s), (uint32_t)((c / S - 1) & 1))) {
+                if (c >= S && !tc_wait(B(kBarRingFree + s), (uint32_t)((c / S - 1) & 1), budget)) {
                     fail();
                     break;
                 }
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             // every copy this CTA issued has landed before the CTA may exit (bounded)
             for (int s = 0; s < S && s < issued; ++s)
-                tc_wait(B(kBarFull + s), (uint32_t)(((issued - s + S - 1) / S - 1) & 1));
+                tc_wait(B(kBarFull + s), (uint32_t)(((issued - s + S - 1) / S - 1) & 1), budget);
         }
     } else if (warp == kTcMmaWarp) {
         if (lane == 0) {
@@ -315,8 +322,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int wnd = c / kTcFlush, a = wnd & 1;
                 const bool first = (c % kTcFlush) == 0;
                 const bool last = (c % kTcFlush) == kTcFlush - 1 || c == nloc - 1;
-                if (!tc_wait(B(kBarTileFull + st), (uint32_t)((c >> 1) & 1)) ||
-                    (first && wnd >= 2 && !tc_wait(B(kBarAccFree + a), (uint32_t)(((wnd >> 1) - 1) & 1)))) {
+                if (!tc_wait(B(kBarTileFull + st), (uint32_t)((c >> 1) & 1), budget) ||
+                    (first && wnd >= 2 && !tc_wait(B(kBarAccFree + a), (uint32_t)(((wnd >> 1) - 1) & 1), budget))) {
                     fail();
                     break;
                 }
@@ -342,7 +349,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 last_c = c;
             }
             // the CTA's MMAs are complete before TMEM is freed (bounded)
-            if (last_c >= 0) tc_wait(B(kBarTileFree + (last_c & 1)), (uint32_t)((last_c >> 1) & 1));
+            if (last_c >= 0) tc_wait(B(kBarTileFree + (last_c & 1)), (uint32_t)((last_c >> 1) & 1), budget);
         }
     } else if (warp < kTcEpiWarp0) {
         // converters: split the chunk in ring slot s into the bf16 tiles of stage st
@@ -350,8 +357,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int groups = (ncols + 7) >> 3;
         for (int c = 0; c < nloc && !*s_err; ++c) {
             const int s = c % S, st = c & 1;
-            if (!tc_wait(B(kBarFull + s), (uint32_t)((c / S) & 1)) ||
-                (c >= 2 && !tc_wait(B(kBarTileFree + st), (uint32_t)(((c >> 1) - 1) & 1)))) {
+            if (!tc_wait(B(kBarFull + s), (uint32_t)((c / S) & 1), budget) ||
+                (c >= 2 && !tc_wait(B(kBarTileFree + st), (uint32_t)(((c >> 1) - 1) & 1), budget))) {
                 fail();
                 break;
             }
@@ -399,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
         for (int wnd = 0; wnd < nwin && !*s_err; ++wnd) {
             const int a = wnd & 1;
-            if (!tc_wait(B(kBarAccFull + a), (uint32_t)((wnd >> 1) & 1))) {
+            if (!tc_wait(B(kBarAccFull + a), (uint32_t)((wnd >> 1) & 1), budget)) {
                 fail();
                 break;
             }
@@ -570,6 +577,12 @@ cudaError_t launch_gram_tc(int n, const double* X, int ldx, int p, const double*
                            int sms, cudaStream_t s)
 {
     return launch_gram_tc_t<double>(n, X, ldx, p, Y, ldy, qy, extra, G, ldg, work, work_bytes, err_flag, sms, s);
+}
+
+cudaError_t gram_tc_set_wait_test(int mask, long long cycles)
+{
+    const WaitTest wt{cycles, mask, 0};
+    return cudaMemcpyToSymbol(g_tc_wait_test, &wt, sizeof(wt));
 }
 
 }  // namespace podcg

@@ -94,6 +94,10 @@ cudaError_t launch_gram32(int n, const float* X, int ldx, int p, const float* Y,
                           double* G, int ldg, int upper_only, double* work, size_t work_bytes, int sms,
                           cudaStream_t s);
 
+// the wait override of pod_cg_debug_wait_timeout for the current device, per unit
+cudaError_t gram_tc_set_wait_test(int mask, long long cycles);
+cudaError_t cg_set_wait_test(int mask, long long cycles);
+
 // tensor-core Gram with split-bf16 products (k_gram_tc.cu); G = X^T [Y, extra]
 size_t gram_tc_workspace_bytes(int n, int p, int q, int sms);
 bool gram_tc_aligned(const void* ptr, size_t ld_bytes);

@@ -133,7 +133,8 @@ class PodCG:
         A_s = A.struct()
         rc = self.L.pod_cg_solve(self.h, ctypes.byref(A_s), b.data_ptr(), float(tol), x_out.data_ptr(),
                                  ctypes.byref(st))
-        if rc != 0 and (raise_on_error or rc not in (2, 3, 4, 5)):
+        # statuses that end a solve with x_out holding the last iterate
+        if rc != 0 and (raise_on_error or rc not in (2, 3, 4, 5, 7)):
             _check(rc, self.h)
         return x_out, st.as_dict()
 
