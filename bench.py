@@ -198,8 +198,8 @@ class ClockSampler:
                 "reasons": reasons}
 
 
-KERNEL_SOURCE = {"k_update": "k_cg.cu", "k_dir": "k_cg.cu", "k_init": "k_cg.cu", "k_update_bulk": "k_cg.cu",
-                 "k_dir_bulk": "k_cg.cu", "k_update_v4": "k_cg.cu", "k_dir_v4": "k_cg.cu", "k_spmv_cg": "k_sparse.cu", "k_residual": "k_sparse.cu",
+KERNEL_SOURCE = {"k_update": "k_cg.cu", "k_dir": "k_cg.cu", "k_init": "k_cg.cu", "k_update_tma": "k_cg.cu",
+                 "k_dir_tma": "k_cg.cu", "k_update_v4": "k_cg.cu", "k_dir_v4": "k_cg.cu", "k_spmv_cg": "k_sparse.cu", "k_residual": "k_sparse.cu",
                  "k_gram_tc": "k_gram_tc.cu"}
 
 
@@ -989,7 +989,7 @@ def main():
     # FP32 with a basis runs the projection form the handle timed for the bucket
     wb = next(b for b in (0, 8, 16, 32, 48, 64) if w_meas <= b)
     form = out["autotune"].get("projection", {}).get(f"w<={wb}", {}).get("form")
-    suffix = {"staged": "_bulk", "direct": "_v4"}.get(form, "") if (prec == 1 and w_meas > 0) else ""
+    suffix = {"staged": "_tma", "direct": "_v4"}.get(form, "") if (prec == 1 and w_meas > 0) else ""
     names = {"spmv_cg": "k_spmv_cg", "update": "k_update" + suffix, "direction": "k_dir" + suffix,
              "residual": "k_residual"}
     out["roofline"] = {"bound": "hbm", "kernel": names[dominant], "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -95,8 +95,10 @@ typedef struct {
                             (same kernels; a form that kernel profilers can attribute) */
     int    proj_form;    /* MIXED, FP32 update/direction passes: -1 = timed once per basis-
                             width bucket on the handle's first system of >= 65,536 rows in
-                            it (else row-parallel); 0 = row-parallel float4; 1 = tiles staged
-                            in shared memory by bulk copies (see pod_cg_proj_tuning) */
+                            it (else row-parallel); 0 = row-parallel float4; 1 = 256-row
+                            tiles streamed into shared memory by the TMA engine, the
+                            direction pass reading a 16-bit copy of W in two-stage solves
+                            (see pod_cg_proj_tuning) */
     int    spmv_lanes;   /* CSR SpMV lanes per row: 0 = timed once per sparsity pattern
                             (systems of >= 65,536 rows; the pattern's heuristic width is kept
                             unless another is >= 10% faster); 1, 2, 4, 8, 16 or 32 = forced */
@@ -260,7 +262,7 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
 
 /* The FP32 projection form chosen per basis-width bucket (buckets w <= 0, 8, 16, 32, 48,
  * 64): forms[6] receives 0 (row-parallel float4 passes), 1 (tiles staged in shared memory
- * by bulk copies) or -1 (bucket not used yet); ms[12] the update + direction times (ms)
+ * by the TMA engine) or -1 (bucket not used yet); ms[12] the update + direction times (ms)
  * of form 0 then form 1 for each bucket, as measured by the handle's one-time timing on the
  * first MIXED system of at least 65,536 rows in that bucket (0 where not timed). This is
  * the project's own tuning record, with no counterpart in the paper. Host outputs;
@@ -322,7 +324,7 @@ pod_cg_status pod_cg_gram_tc(int n, int elem_bytes, const void* X, int p, const 
 
 /* Test support with no counterpart in the paper: exercise the failure path of the bounded
  * device waits without a GPU fault. While bit 1 (the tensor-core Gram, pod_cg_gram_tc and
- * use_tc_gram solves) or bit 2 (the FP32 update and direction passes staged by bulk copies,
+ * use_tc_gram solves) or bit 2 (the FP32 update and direction passes staged by the TMA engine,
  * proj_form = 1) is set in `mask`, those kernels issue no copies and every wait of theirs
  * gives up after `cycles` SM clocks (1e3 .. 4e9), so each runs its timeout path with nothing
  * in flight: a solve then ends with ERR_TIMEOUT (the handle stays usable) and

@@ -145,6 +145,7 @@ __device__ __forceinline__ void sum_rows(const double* __restrict__ partials, in
                                          double* s_out)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid >= kWarps) return;   // blocks with more warps (a producer warp) sum with the first kWarps
     constexpr int kR = (NV + kWarps - 1) / kWarps;
     double t[kR][U];
 #pragma unroll

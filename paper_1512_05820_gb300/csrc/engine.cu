@@ -59,7 +59,7 @@ int device_sms()
 // Kernel arguments stored by value with stable addresses (a spec is built in place and
 // never copied, so the pointer array stays valid for graph-node creation and launches).
 struct KArgs {
-    alignas(16) unsigned char buf[512];
+    alignas(64) unsigned char buf[512];
     size_t off = 0;
     void* ptrs[24];
     int count = 0;
@@ -76,7 +76,8 @@ struct KArgs {
 struct KSpec {
     void* f = nullptr;
     int grid = 1;
-    int smem = 0;   // dynamic shared memory bytes
+    int block = kBlock;   // threads per block
+    int smem = 0;         // dynamic shared memory bytes
     KArgs a;
     KSpec() = default;
     KSpec(const KSpec&) = delete;
@@ -114,7 +115,7 @@ cudaError_t add_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, K
     cudaKernelNodeParams p = {};
     p.func = k.f;
     p.gridDim = dim3(k.grid);
-    p.blockDim = dim3(kBlock);
+    p.blockDim = dim3(k.block);
     p.sharedMemBytes = (unsigned int)k.smem;
     p.kernelParams = k.a.ptrs;
     p.extra = nullptr;
@@ -136,7 +137,7 @@ cudaError_t add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, 
 
 cudaError_t launch_spec(KSpec& k, cudaStream_t s)
 {
-    return cudaLaunchKernel(k.f, dim3(k.grid), dim3(kBlock), k.a.ptrs, (size_t)k.smem, s);
+    return cudaLaunchKernel(k.f, dim3(k.grid), dim3(k.block), k.a.ptrs, (size_t)k.smem, s);
 }
 
 }  // namespace
@@ -166,6 +167,14 @@ struct pod_cg_t {
     double* AW = nullptr;       // ld x wcap: A W, then A V2
     float* W32 = nullptr;       // mixed
     float* AW32 = nullptr;      // mixed
+    __half* W16 = nullptr;      // mixed, two-stage: 16-bit copy of W32 (W32 = W16 * wscale exactly)
+    float* wscale = nullptr;    // its power-of-two column scales (kWMax)
+    unsigned int* wmax = nullptr;   // scratch of the column maxima (kWMax)
+    CUtensorMap* tm_dev = nullptr;    // tensor maps of the panels A W32, W32, W16 (device, 3)
+    CUtensorMap* tm_host = nullptr;   // their host copy (pinned)
+    int tm_cols = -1;           // basis width the maps were encoded for
+    bool tm_ok = false;         // maps can be encoded (else only the float4 form is used)
+    bool w16 = false;           // the staged direction pass reads W16
     int wcap = 0;               // columns of the basis buffers: w_max, or kWMax in three-stage mode
     double* Y = nullptr;        // three-stage: augmenting basis, ld x max(y_max, w_max)
     float* Y32 = nullptr;       // three-stage, mixed: its FP32 copy (stage-one panels)
@@ -348,11 +357,26 @@ pod_cg_status read_state(pod_cg_t* h);
 // the faster pair is kept for the bucket. The device state is saved first and restored
 // after; the FP32 vectors the passes touch are scratch until the loop starts. Systems
 // under 65,536 rows take the direct form untimed.
+// The panels' tensor maps for a basis of `cols` columns (the TMA-staged passes): encoded on
+// the host and copied to the device when the width changes (stream-ordered before the loop).
+pod_cg_status set_panel_maps(pod_cg_t* h, int cols)
+{
+    if (!h->tm_ok || cols < 1 || cols == h->tm_cols) return POD_CG_OK;
+    if (!encode_panel_map(&h->tm_host[0], h->AW32, 4, h->ld, cols, 8) ||
+        !encode_panel_map(&h->tm_host[1], h->W32, 4, h->ld, cols, 8) ||
+        !encode_panel_map(&h->tm_host[2], h->W16, 2, h->ld, cols, 16))
+        return fail(h, POD_CG_ERR_CUDA, "tensor map encoding failed");
+    PODCG_CK(h, cudaMemcpyAsync(h->tm_dev, h->tm_host, 3 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, h->stream));
+    PODCG_CK(h, cudaStreamSynchronize(h->stream));   // the host copy may be rewritten by the next solve
+    h->tm_cols = cols;
+    return POD_CG_OK;
+}
+
 pod_cg_status choose_proj_form(pod_cg_t* h, int wb, int L)
 {
     const int bi = bucket_index(wb);
     if (!h->mixed || wb == 0 || h->proj_form[bi] >= 0) return POD_CG_OK;
-    if (h->n < 65536) {
+    if (h->n < 65536 || !h->tm_ok) {
         h->proj_form[bi] = kProjDirect;
         return POD_CG_OK;
     }
@@ -415,8 +439,8 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
     const int n = h->n, ld = h->ld;
     void *f_init, *f_upd, *f_dir0, *f_dir;
     int sm_upd = 0, sm_dir = 0;
-    const int form = h->proj_form[bucket_index(wb)] == kProjStaged ? kProjStaged : kProjDirect;
-    cg_kernels(wb, mixed, use_cond != 0, form, &f_init, &f_upd, &f_dir0, &f_dir, &sm_upd, &sm_dir);
+    const int form = (h->proj_form[bucket_index(wb)] == kProjStaged && h->tm_ok) ? kProjStaged : kProjDirect;
+    cg_kernels(wb, mixed, use_cond != 0, form, h->w16, &f_init, &f_upd, &f_dir0, &f_dir, &sm_upd, &sm_dir);
     // the CG product: CSR, or the 3x3 block form when the pattern has one (k_bsr.cu)
     void* f_spmv = h->use_bsr ? kernel_bsr_spmv_cg(h->bsr_L, mixed) : kernel_spmv_cg(L, mixed);
     void* f_res = kernel_residual(L, use_cond != 0);
@@ -465,6 +489,23 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
     P.upd.smem = sm_upd;
     P.dir0.smem = sm_dir;
     P.dir.smem = sm_dir;
+    if (mixed && wb > 0 && form == kProjStaged) {
+        // TMA-staged passes: the panels as tensor maps, ring and grid by the bucket's stage size
+        const CUtensorMap* tmW = h->tm_dev + (h->w16 ? 2 : 1);
+        int gu, ru, su, gd, rd, sd;
+        tma_shape(n, h->sms, wb, 8, 3, &gu, &ru, &su);
+        tma_shape(n, h->sms, wb, h->w16 ? 16 : 8, 4, &gd, &rd, &sd);
+        P.upd.set(f_upd, gu, n, ld, ru, h->r32, (const float*)h->q32, (const float*)h->dinv32,
+                  (const CUtensorMap*)h->tm_dev, h->partials,
+                  c + 3 * kCounterStride, st, h_inner, use_cond);
+        P.dir0.set(f_dir0, gd, n, ld, rd, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32, tmW,
+                   (const float*)h->wscale, Rinv, cst);
+        P.dir.set(f_dir, gd, n, ld, rd, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32, tmW,
+                  (const float*)h->wscale, Rinv, cst);
+        P.upd.block = P.dir0.block = P.dir.block = tma_block_threads();
+        P.upd.smem = su;
+        P.dir0.smem = P.dir.smem = sd;
+    }
 }
 
 void destroy_graph(GraphSlot& gs)
@@ -970,7 +1011,7 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     for (auto& g : h->graphs) destroy_graph(g);
     for (auto& g : h->chunks) destroy_graph(g);
     destroy_graph(h->s2graph);
-    void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->Y, h->Y32,
+    void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->W16, h->wscale, h->wmax, h->Y, h->Y32,
                     h->s2_hist, h->s2tmp, h->brp, h->bcol, h->bval, h->bval32, h->bsr_flag, h->Cout, h->CSv,
                     h->GSC, h->out_work, h->AS, h->GA,
                     h->G, h->Rinv,
@@ -978,6 +1019,8 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
                     h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    if (h->tm_dev) cudaFree(h->tm_dev);
+    if (h->tm_host) cudaFreeHost(h->tm_host);
     if (h->st_host) cudaFreeHost(h->st_host);
     if (h->pd_host) cudaFreeHost(h->pd_host);
     for (auto& e : h->ev)
@@ -1069,6 +1112,9 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
         PODCG_ALLOC(h->S32, ld * c.s_max)
         PODCG_ALLOC(h->W32, ld * h->wcap)
         PODCG_ALLOC(h->AW32, ld * h->wcap)
+        PODCG_ALLOC(h->W16, ld * h->wcap)
+        PODCG_ALLOC(h->wscale, (size_t)kWMax)
+        PODCG_ALLOC(h->wmax, (size_t)kWMax)
         if (c.three_stage) PODCG_ALLOC(h->Y32, ld * ycols)
         PODCG_ALLOC(h->r32, ld)
         PODCG_ALLOC(h->p32, ld)
@@ -1101,6 +1147,16 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
         if (c.use_tc_gram)
             h->gram_work_bytes = std::max(h->gram_work_bytes, gram_tc_workspace_bytes(n, gp, c.w_max + 1, h->sms));
         e = cudaMalloc((void**)&h->gram_work, h->gram_work_bytes);
+    }
+    if (e == cudaSuccess && h->mixed) {
+        e = cudaMalloc((void**)&h->tm_dev, 3 * sizeof(CUtensorMap));
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&h->tm_host, 3 * sizeof(CUtensorMap));
+        if (e == cudaSuccess) {
+            h->tm_ok = encode_panel_map(&h->tm_host[0], h->AW32, 4, h->ld, h->wcap, 8) &&
+                       encode_panel_map(&h->tm_host[1], h->W32, 4, h->ld, h->wcap, 8) &&
+                       encode_panel_map(&h->tm_host[2], h->W16, 2, h->ld, h->wcap, 16);
+            h->w16 = h->tm_ok && !c.three_stage;   // three-stage W32 also holds stage two's directions
+        }
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->st_host, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&h->pd_host, sizeof(ProbDesc));
@@ -1290,7 +1346,13 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         if (three) {
             PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->Y, h->ld, h->sms, s, 1));
         } else {
-            if (h->mixed) PODCG_CK(h, launch_lift32(n, h->S32, h->ld, h->s_count, h->C, h->st, h->W32, h->ld, h->sms, s));
+            if (h->mixed) {
+                PODCG_CK(h, launch_lift32(n, h->S32, h->ld, h->s_count, h->C, h->st, h->W32, h->ld, h->sms, s));
+                if (h->w16) {
+                    PODCG_CK(h, launch_quant16(n, h->ld, h->W32, h->W16, h->wmax, h->wscale, h->st, h->sms, s));
+                    launches += 2;
+                }
+            }
             else PODCG_CK(h, launch_lift(n, h->S, h->ld, h->s_count, h->C, h->st, h->W, h->ld, h->sms, s));
         }
         launches += 2;
@@ -1433,6 +1495,10 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         if (its != POD_CG_OK) return its;
         const int sysid = h->system_counter++;
         return finish_solve(h, x_out, w, launches, stats, sysid);
+    }
+    if (h->mixed) {
+        pod_cg_status ms = set_panel_maps(h, w3);
+        if (ms != POD_CG_OK) return ms;
     }
     pod_cg_status ps = choose_proj_form(h, wb, L);
     if (ps != POD_CG_OK) return ps;

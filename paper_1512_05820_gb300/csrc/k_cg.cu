@@ -15,6 +15,9 @@
 // immediately: k_spmv_cg and k_update skip once `done` is set, and k_dir runs only when
 // the k_update of its iteration did (`dir_pending`). COND = false compiles the variants
 // with no graph-condition call at all, for plain graphs and direct launches.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -238,27 +241,41 @@ __global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x
     }
 }
 
-// ------------------------------------------------------------------ FP32 loop with staged tiles
+// ------------------------------------------------------------------ FP32 loop, TMA-staged
 //
-// The FP32 update and direction passes stream 256-row tiles of the basis panel (A W for the
-// update, W for the direction) and of the per-row vectors through a ring of shared-memory
-// stages filled by bulk asynchronous copies (cp.async.bulk, the TMA engine) that complete
-// on one mbarrier per stage. One block per SM owns a contiguous range of tiles. The ring is
-// sized at run time from the basis width: a stage holds w + NV column tiles of 1 KB, and
-// as many stages as fit in kBulkSmem are kept in flight (7 at w = 22), because under full
-// load this GPU needs about 200 KB of reads in flight per SM to reach its HBM bandwidth.
-// Copies are issued per basis column j < w (w from the device state), one per lane of
-// warp 0. Every copy stays inside its buffer: a tile spans min(256, ld - row0) rows and all
-// panels and vectors are allocated with the padded leading dimension ld (a multiple of 32
-// >= n). Rows >= n inside a tile are never used. Every mbarrier wait is bounded (4e9 SM
-// clocks, about 2 s); on expiry the block records status 7 (timeout), waits (bounded) for
-// its own copies in flight and leaves the loop, and the pass ends with that status.
+// The second FP32 form of the update and direction passes (proj_form = 1). Every CTA
+// takes every gridDim-th 256-row tile. One producer lane streams every tile into a
+// ring of shared-memory stages: the basis panel (A W for the update, W for the direction)
+// as 2D tensor copies (cp.async.bulk.tensor) of 256 rows x 8 FP32 columns, or 256 rows x
+// 16 fp16 columns for the direction pass's 16-bit W, and the per-row vectors as 1 KB bulk
+// copies (cp.async.bulk), all completing on the stage's `full` mbarrier. The panels' tensor
+// maps span exactly the basis width in use, so the columns of a last, partial box past it
+// are filled with zeros by the copy engine and cost no memory traffic. Eight consumer
+// warps compute from shared memory and release a stage through its `empty` mbarrier (one
+// arrival per warp): no block-wide barrier sits in the loop, and the reads in flight do not
+// depend on the consumers' register count. A probe streaming the same copies (a 22-column
+// panel, three vectors, one vector written back) reached 6.1 TB/s with 130-190 KB in
+// flight per SM and less with more (5.8 TB/s at 200 KB in one CTA): two CTAs per SM with
+// 96 KB rings each when a stage is at most 40 KB, else one CTA with a 200 KB ring
+// (tma_shape).
+//
+// Every copy stays inside its buffer: vectors and panels are allocated with the padded
+// leading dimension ld (a multiple of 32 >= n), a vector copy spans min(256, ld - row0)
+// rows, and the tensor maps' row extent is ld (rows past it are filled with zeros). Rows
+// >= n inside a tile are never used. Every mbarrier wait is bounded (4e9 SM clocks, about
+// 2 s); on expiry the warp records status 7 (timeout) and leaves its loop, the producer
+// waits (bounded) for the copies it issued, and the pass ends with that status.
 
 constexpr long long kBulkWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
-constexpr int kBulkSmem = 200 * 1024;                  // ring bytes per block (one block per SM)
-constexpr int kBulkMaxStages = 32;
-constexpr int kBulkBarBytes = kBulkMaxStages * 8;
-constexpr int kBulkTile = kBlock * 4;                  // bytes of one 256-row FP32 column tile
+constexpr int kTmTile = 256;                           // rows per tile
+constexpr int kTmBoxBytes = 8192;                      // panel box: 256 x 8 FP32 or 256 x 16 fp16
+constexpr int kTmVecBytes = kTmTile * 4;               // one FP32 vector tile
+constexpr int kTmRingMax = 200 * 1024;                 // ring bytes of a CTA alone on its SM
+constexpr int kTmRingPair = 96 * 1024;                 // ring bytes of each of two CTAs per SM
+constexpr int kTmMaxStages = 16;
+constexpr int kTmConsumers = 8;                        // consumer warps (one row per thread)
+constexpr int kTmThreads = 32 * (kTmConsumers + 1);    // + the producer warp
+constexpr int kTmSmemMax = kTmRingMax + 1024;          // + alignment slack of the ring base
 
 __device__ __forceinline__ uint32_t bulk_smem_u32(const void* p)
 {
@@ -270,6 +287,15 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(mbar)
                  : "memory");
+}
+
+__device__ __forceinline__ void tensor_copy_2d(uint32_t dst, const CUtensorMap* tm, int x, int y, uint32_t mbar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
 }
 
 __device__ __forceinline__ bool bulk_try(uint32_t mbar, uint32_t parity)
@@ -298,185 +324,221 @@ __device__ __forceinline__ bool bulk_wait(uint32_t mbar, uint32_t parity, long l
 // The wait override of pod_cg_debug_wait_timeout for the staged passes (zero: normal).
 static __device__ WaitTest g_cg_wait_test;
 
-// The ring of one block: tile range, run-time stage size and count, copy issue and waits.
-// Stage layout: w panel column tiles, then the NV vector tiles, 1 KB each.
+// The ring of one CTA: its tiles, the run-time stage size and count, and the waits.
+// Stage layout: nbox panel boxes of 8 KB, then NV vector tiles of 1 KB (1024-aligned).
 template <int NV>
-struct BulkRing {
-    unsigned char* smem;
+struct TmaRing {
+    unsigned char* base;
     uint64_t* full;
-    int t0, nloc, issued, S, w, stage_bytes;
+    uint64_t* empty;
+    int t0, nloc, S, nbox, cols_per_box, vec_off, stage_bytes;
     long long budget;   // SM clocks a wait may take
     bool starve;        // test of the timeout path: no copy is ever issued
 
-    __device__ void init(unsigned char* sm, int n, int w_)
+    __device__ void init(unsigned char* raw, uint64_t* f, uint64_t* e, int n, int ncols, int cpb, int ring_bytes)
     {
         const WaitTest wt = g_cg_wait_test;
         starve = (wt.mask & kWaitTestStaged) != 0;
         budget = starve ? wt.cycles : kBulkWaitCycles;
-        full = reinterpret_cast<uint64_t*>(sm);
-        smem = sm + kBulkBarBytes;
-        w = w_;
-        stage_bytes = (w + NV) * kBulkTile;
-        S = min(kBulkMaxStages, (kBulkSmem - kBulkBarBytes) / stage_bytes);
-        const int ntiles = (n + kBlock - 1) / kBlock;
-        t0 = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
-        nloc = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x) - t0;
+        base = raw + ((1024u - (bulk_smem_u32(raw) & 1023u)) & 1023u);
+        full = f;
+        empty = e;
+        cols_per_box = cpb;
+        nbox = (ncols + cpb - 1) / cpb;
+        vec_off = nbox * kTmBoxBytes;
+        stage_bytes = vec_off + NV * kTmVecBytes;
+        S = max(1, min(kTmMaxStages, ring_bytes / stage_bytes));
+        // tiles interleaved over the CTAs (tile blockIdx.x + k gridDim.x): at any moment the
+        // CTAs read neighbouring tiles, so every column is read in long sequential runs
+        const int ntiles = (n + kTmTile - 1) / kTmTile;
+        t0 = blockIdx.x;
+        nloc = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
         if (threadIdx.x == 0) {
-            for (int i = 0; i < S; ++i)
+            for (int i = 0; i < S; ++i) {
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bulk_smem_u32(&full[i])));
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bulk_smem_u32(&empty[i])),
+                             "r"(kTmConsumers));
+            }
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
-        issued = starve ? 0 : (nloc < S ? nloc : S);
         __syncthreads();
     }
-    __device__ const float* stage(int t) const
-    {
-        return reinterpret_cast<const float*>(smem + (t % S) * stage_bytes);
-    }
-    __device__ int row0(int t) const { return (t0 + t) * kBlock; }
+    __device__ unsigned char* stage(int t) const { return base + (t % S) * stage_bytes; }
+    __device__ int row0(int t) const { return (t0 + t * (int)gridDim.x) * kTmTile; }
 
-    // warp 0: copies of local tile t, one copy per lane so the w + NV copies leave
-    // together; lane 0 posts the byte count first
-    __device__ void issue(int t, int ld, const float* panel, const float* const* vec)
+    // Producer lane: stream every local tile (waiting for its stage to be released), then
+    // wait (bounded) until every copy issued has landed, so none is in flight at exit. The
+    // tensor map lives in global memory (rewritten by the host when the basis width
+    // changes), so the tensor-map proxy acquires it first.
+    __device__ void produce(int ld, const CUtensorMap* tm, const float* const* vec)
     {
         if (starve) return;
-        const int lane = threadIdx.x & 31;
-        const int r0 = row0(t);
-        const int rows = min(kBlock, ld - r0);
-        const uint32_t bytes = (uint32_t)rows * 4u;
-        unsigned char* sg = smem + (t % S) * stage_bytes;
-        const uint32_t mb = bulk_smem_u32(&full[t % S]);
-        if (lane == 0)
+        if (nbox > 0) asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tm) : "memory");
+        int t = 0;
+        for (; t < nloc; ++t) {
+            const int s = t % S;
+            if (t >= S && !bulk_wait(bulk_smem_u32(&empty[s]), (uint32_t)((t / S - 1) & 1), budget)) break;
+            const int r0 = row0(t);
+            const uint32_t vbytes = (uint32_t)min(kTmTile, ld - r0) * 4u;
+            unsigned char* sg = stage(t);
+            const uint32_t mb = bulk_smem_u32(&full[s]);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
-                         "r"(bytes * (uint32_t)(w + NV))
+                         "r"((uint32_t)(nbox * kTmBoxBytes) + (uint32_t)NV * vbytes)
                          : "memory");
-        __syncwarp();
-        for (int c = lane; c < w + NV; c += 32) {
-            const float* src;
-            if (c < w) {
-                src = panel + (size_t)c * ld;
-            } else {
-                const int v = c - w;   // select without indexing the array at run time
-                src = vec[0];
+            for (int b = 0; b < nbox; ++b) tensor_copy_2d(bulk_smem_u32(sg + b * kTmBoxBytes), tm, r0, b * cols_per_box, mb);
 #pragma unroll
-                for (int u = 1; u < NV; ++u)
-                    if (v == u) src = vec[u];
-            }
-            bulk_copy(bulk_smem_u32(sg + c * kBulkTile), src + r0, bytes, mb);
+            for (int v = 0; v < NV; ++v) bulk_copy(bulk_smem_u32(sg + vec_off + v * kTmVecBytes), vec[v] + r0, vbytes, mb);
         }
+        for (int u = t > S ? t - S : 0; u < t; ++u) bulk_wait(bulk_smem_u32(&full[u % S]), (uint32_t)((u / S) & 1), budget);
     }
-    __device__ bool wait(int t) const
+    // consumer warp: wait for tile t (every lane), false after a timeout (warp-uniform)
+    __device__ bool acquire(int t) const
     {
-        return bulk_wait(bulk_smem_u32(&full[t % S]), (uint32_t)((t / S) & 1), budget);
+        const bool ok = bulk_wait(bulk_smem_u32(&full[t % S]), (uint32_t)((t / S) & 1), budget);
+        return __all_sync(0xffffffffu, ok);
     }
-    // after a timeout: bounded waits for the copies still in flight
-    __device__ void drain(int consumed) const
+    __device__ void release(int t) const
     {
-        for (int t = consumed; t < issued; ++t) wait(t);
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bulk_smem_u32(&empty[t % S])) : "memory");
     }
 };
 
+__device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+
+// Update pass: r -= alpha q, z = M^{-1} r, (r, z), ||r||^2, c = (A W)^T z. Consumer warp cw
+// takes rows 32 cw + lane for the row part and basis columns cw, cw + 8, ... for the
+// column part, whose lanes cover the tile's 256 rows as two float4 groups each (z is
+// formed again from the staged r, q, M^{-1} by every warp, so no warp waits for another).
 template <int WB, bool COND>
-__global__ void __launch_bounds__(kBlock) k_update_bulk(int n, int ld, float* __restrict__ r,
-                                                        const float* __restrict__ q, const float* __restrict__ dinv,
-                                                        const float* __restrict__ AW, double* __restrict__ partials,
-                                                        unsigned int* counter, DevState* st,
-                                                        cudaGraphConditionalHandle h_inner, int use_cond)
+__global__ void __launch_bounds__(kTmThreads, 2) k_update_tma(int n, int ld, int ring_bytes, float* __restrict__ r,
+                                                              const float* __restrict__ q,
+                                                              const float* __restrict__ dinv,
+                                                              const CUtensorMap* __restrict__ tmAW,
+                                                              double* __restrict__ partials, unsigned int* counter,
+                                                              DevState* st, cudaGraphConditionalHandle h_inner,
+                                                              int use_cond)
 {
     if (st->done) return;   // uniform: only the last block of a pass writes `done`
-    constexpr int CPW = (WB + kWarps - 1) / kWarps;
-    extern __shared__ __align__(128) unsigned char bulk_sm[];
+    constexpr int CPW = (WB + kTmConsumers - 1) / kTmConsumers;
+    extern __shared__ __align__(1024) unsigned char tm_raw[];
+    __shared__ uint64_t full[kTmMaxStages], empty[kTmMaxStages];
+    __shared__ float s_red[kTmConsumers][2];
     __shared__ double s_blk[WB + 2];
     const int w = st->w;
     const float alpha = (st->status == 0) ? float(st->alpha) : 0.0f;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    BulkRing<3> ring;
-    ring.init(bulk_sm, n, w);
-    const float* const vec[3] = {r, q, dinv};
-    if (threadIdx.x < 32)
-        for (int t = 0; t < ring.issued; ++t) ring.issue(t, ld, AW, vec);
-    float cacc[CPW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    TmaRing<3> ring;
+    ring.init(tm_raw, full, empty, n, w, 8, ring_bytes);
+    float acc[CPW];
 #pragma unroll
-    for (int k = 0; k < CPW; ++k) cacc[k] = 0.0f;
+    for (int k = 0; k < CPW; ++k) acc[k] = 0.0f;
     float rho = 0.0f, rr = 0.0f;
-    int t = 0;
-    for (; t < ring.nloc; ++t) {
-        // one barrier per tile: tile t has landed and every thread is done with tile t-1
-        if (!__syncthreads_and(ring.wait(t))) break;
-        if (t > 0 && t - 1 + ring.S < ring.nloc) {
-            if (threadIdx.x < 32) ring.issue(t - 1 + ring.S, ld, AW, vec);   // refill tile t-1's stage
-            if (!ring.starve) ++ring.issued;
+    bool timeout = false;
+    if (warp == kTmConsumers) {
+        if (lane == 0) {
+            const float* const vec[3] = {r, q, dinv};
+            ring.produce(ld, tmAW, vec);
         }
-        const float* sg = ring.stage(t);
-        const float* sr = sg + w * kBlock;
-        const float* sq = sr + kBlock;
-        const float* sd = sq + kBlock;
-        const int row0 = ring.row0(t);
-        const int valid = min(kBlock, n - row0);
-        // row part: r -= alpha q (written back), z = M^{-1} r, (r, z), ||r||^2
-        if ((int)threadIdx.x < valid) {
-            const float ri = sr[threadIdx.x] - alpha * sq[threadIdx.x];
-            r[row0 + threadIdx.x] = ri;
-            const float zi = sd[threadIdx.x] * ri;
-            rho += ri * zi;
-            rr += ri * ri;
-        }
-        // column part: every warp forms z for the whole tile in registers (the same
-        // arithmetic as the row part) and accumulates (A W)^T z for its columns
-        if (valid == kBlock) {
-            float4 z4[kBlock / 128];
-#pragma unroll
-            for (int m = 0; m < kBlock / 128; ++m) {
-                const float4 a = reinterpret_cast<const float4*>(sr)[lane + 32 * m];
-                const float4 b = reinterpret_cast<const float4*>(sq)[lane + 32 * m];
-                const float4 d = reinterpret_cast<const float4*>(sd)[lane + 32 * m];
-                z4[m] = make_float4(d.x * (a.x - alpha * b.x), d.y * (a.y - alpha * b.y), d.z * (a.z - alpha * b.z),
-                                    d.w * (a.w - alpha * b.w));
+    } else {
+        for (int t = 0; t < ring.nloc; ++t) {
+            if (!ring.acquire(t)) {
+                timeout = true;
+                break;
             }
-#pragma unroll
-            for (int k = 0; k < CPW; ++k) {
-                const int j = wid + kWarps * k;
-                if (j < w) {
-                    const float4* col = reinterpret_cast<const float4*>(sg + j * kBlock);
-                    float a = 0.0f;
-#pragma unroll
-                    for (int m = 0; m < kBlock / 128; ++m) {
-                        const float4 av = col[lane + 32 * m];
-                        a += av.x * z4[m].x + av.y * z4[m].y + av.z * z4[m].z + av.w * z4[m].w;
-                    }
-                    cacc[k] += a;
+            const unsigned char* sg = ring.stage(t);
+            const float* sP = reinterpret_cast<const float*>(sg);
+            const float* sr = reinterpret_cast<const float*>(sg + ring.vec_off);
+            const float* sq = sr + kTmTile;
+            const float* sd = sq + kTmTile;
+            const int row0 = ring.row0(t);
+            const int valid = min(kTmTile, n - row0);
+            {
+                const int i = 32 * warp + lane;
+                if (i < valid) {
+                    const float ri = sr[i] - alpha * sq[i];
+                    r[row0 + i] = ri;
+                    const float zi = sd[i] * ri;
+                    rho += ri * zi;
+                    rr += ri * ri;
                 }
             }
-        } else {
-            for (int k = 0; k < CPW; ++k) {
-                const int j = wid + kWarps * k;
-                if (j < w) {
-                    const float* col = sg + j * kBlock;
-                    float a = 0.0f;
-                    for (int m = 0; m < kBlock / 32; ++m) {
-                        const int rr2 = lane + 32 * m;
-                        if (rr2 < valid) a += col[rr2] * (sd[rr2] * (sr[rr2] - alpha * sq[rr2]));
+            if (valid == kTmTile) {
+                float4 z4[2];
+#pragma unroll
+                for (int m = 0; m < 2; ++m) {
+                    const float4 a = reinterpret_cast<const float4*>(sr)[lane + 32 * m];
+                    const float4 b = reinterpret_cast<const float4*>(sq)[lane + 32 * m];
+                    const float4 d = reinterpret_cast<const float4*>(sd)[lane + 32 * m];
+                    z4[m] = make_float4(d.x * (a.x - alpha * b.x), d.y * (a.y - alpha * b.y),
+                                        d.z * (a.z - alpha * b.z), d.w * (a.w - alpha * b.w));
+                }
+#pragma unroll
+                for (int k = 0; k < CPW; ++k) {
+                    const int j = warp + kTmConsumers * k;
+                    if (j < w) {
+                        const float4* col = reinterpret_cast<const float4*>(sP + (j >> 3) * 2048 + (j & 7) * kTmTile);
+                        acc[k] += dot4(col[lane], z4[0]) + dot4(col[lane + 32], z4[1]);
                     }
-                    cacc[k] += a;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < CPW; ++k) {
+                    const int j = warp + kTmConsumers * k;
+                    if (j < w) {
+                        const float* col = sP + (j >> 3) * 2048 + (j & 7) * kTmTile;
+                        float a = 0.0f;
+                        for (int m = 0; m < kTmTile / 32; ++m) {
+                            const int i = lane + 32 * m;
+                            if (i < valid) a += col[i] * (sd[i] * (sr[i] - alpha * sq[i]));
+                        }
+                        acc[k] += a;
+                    }
                 }
             }
+            ring.release(t);
         }
     }
-    if (t < ring.nloc) {
-        if (threadIdx.x == 0) atomicExch(&st->status, 7);
-        ring.drain(t);
+    if (timeout && lane == 0) atomicExch(&st->status, 7);
+    if (warp < kTmConsumers) {
+        rho = warp_sum(rho);
+        rr = warp_sum(rr);
+#pragma unroll
+        for (int k = 0; k < CPW; ++k) {
+            const int j = warp + kTmConsumers * k;
+            const float t = warp_sum(acc[k]);
+            if (lane == 0 && j < w) s_blk[2 + j] = (double)t;
+        }
+        if (lane == 0) {
+            s_red[warp][0] = rho;
+            s_red[warp][1] = rr;
+        }
     }
-    update_tail<WB, float, COND>(rho, rr, cacc, w, s_blk, partials, counter, st, h_inner, use_cond);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0.0, t1 = 0.0;
+        for (int k = 0; k < kTmConsumers; ++k) {
+            t0 += (double)s_red[k][0];
+            t1 += (double)s_red[k][1];
+        }
+        s_blk[0] = t0;
+        s_blk[1] = t1;
+    }
+    __syncthreads();
+    update_finish<WB, COND>(s_blk, w, partials, counter, st, h_inner, use_cond);
 }
 
-// FP32 direction pass with staged W tiles: mu = R^{-1} R^{-T} c, x += alpha p,
-// p = z + beta p - W mu (FIRST: p0 = z0 - W mu0, x untouched), as k_dir. x is staged too,
-// except in the FIRST pass, which does not read it.
-template <int WB, bool FIRST>
-__global__ void __launch_bounds__(kBlock) k_dir_bulk(int n, int ld, float* __restrict__ x, float* __restrict__ p,
-                                                     const float* __restrict__ r, const float* __restrict__ dinv,
-                                                     const float* __restrict__ W, const double* __restrict__ Rinv,
-                                                     const DevState* st)
+// Direction pass: mu = R^{-1} R^{-T} c, x += alpha p, p = z + beta p - W mu (FIRST: p0 =
+// z0 - W mu0, x untouched), one row per consumer thread. H: W is the 16-bit copy W16 with
+// one power-of-two scale per column (W32 = W16 * wscale exactly), folded into mu.
+template <int WB, bool FIRST, bool H>
+__global__ void __launch_bounds__(kTmThreads, 2) k_dir_tma(int n, int ld, int ring_bytes, float* __restrict__ x,
+                                                           float* __restrict__ p,
+                                                           const float* __restrict__ r, const float* __restrict__ dinv,
+                                                           const CUtensorMap* __restrict__ tmW,
+                                                           const float* __restrict__ wscale,
+                                                           const double* __restrict__ Rinv, const DevState* st)
 {
     if (!FIRST && !st->dir_pending) return;
     if (FIRST && st->outer_done) return;
@@ -486,57 +548,128 @@ __global__ void __launch_bounds__(kBlock) k_dir_bulk(int n, int ld, float* __res
     const float alpha = ok ? float(st->alpha) : 0.0f;
     const float beta = float(st->beta);
     const bool upd_p = FIRST || (!st->done && ok);
-    extern __shared__ __align__(128) unsigned char bulk_sm[];
+    extern __shared__ __align__(1024) unsigned char tm_raw[];
+    __shared__ uint64_t full[kTmMaxStages], empty[kTmMaxStages];
     __shared__ float s_mu[WB];
     if (upd_p) {
-        // the ring's memory is scratch for mu until the first copy is issued
-        double* s_R = reinterpret_cast<double*>(bulk_sm);
+        // the ring's memory is scratch for mu until the ring is set up
+        double* s_R = reinterpret_cast<double*>(tm_raw);
         double* s_c = s_R + WB * WB;
         double* s_t = s_c + WB;
         double* s_mud = s_t + WB;
         block_mu<WB>(Rinv, st->c, w, s_R, s_c, s_t, s_mud);
-        for (int j = threadIdx.x; j < WB; j += blockDim.x) s_mu[j] = (j < w) ? float(s_mud[j]) : 0.0f;
-        __syncthreads();
+        for (int j = threadIdx.x; j < WB; j += blockDim.x)
+            s_mu[j] = (j < w) ? float(s_mud[j]) * (H ? wscale[j] : 1.0f) : 0.0f;
     }
+    __syncthreads();
     // without a p update only x += alpha p remains: no panel needed
     const int wc = upd_p ? w : 0;
-    BulkRing<NV> ring;
-    ring.init(bulk_sm, n, wc);
-    const float* vec[NV];
-    vec[0] = p;
-    vec[1] = r;
-    vec[2] = dinv;
-    if constexpr (!FIRST) vec[NV - 1] = x;
-    if (threadIdx.x < 32)
-        for (int t = 0; t < ring.issued; ++t) ring.issue(t, ld, W, vec);
-    int t = 0;
-    for (; t < ring.nloc; ++t) {
-        // one barrier per tile: tile t has landed and every thread is done with tile t-1
-        if (!__syncthreads_and(ring.wait(t))) break;
-        if (t > 0 && t - 1 + ring.S < ring.nloc) {
-            if (threadIdx.x < 32) ring.issue(t - 1 + ring.S, ld, W, vec);
-            if (!ring.starve) ++ring.issued;
+    TmaRing<NV> ring;
+    ring.init(tm_raw, full, empty, n, wc, H ? 16 : 8, ring_bytes);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    bool timeout = false;
+    if (warp == kTmConsumers) {
+        if (lane == 0) {
+            const float* vec[NV];
+            vec[0] = p;
+            vec[1] = r;
+            vec[2] = dinv;
+            if constexpr (!FIRST) vec[NV - 1] = x;
+            ring.produce(ld, tmW, vec);
         }
-        const float* sg = ring.stage(t);
-        const float* sv = sg + wc * kBlock;
-        const int i = ring.row0(t) + threadIdx.x;
-        if (i < n) {
-            const float pi = sv[threadIdx.x];
-            if constexpr (!FIRST) x[i] = sv[3 * kBlock + threadIdx.x] + alpha * pi;
-            if (upd_p) {
-                float v = sv[2 * kBlock + threadIdx.x] * sv[kBlock + threadIdx.x];
-                if (!FIRST) v += beta * pi;
-#pragma unroll
-                for (int j = 0; j < WB; ++j)
-                    if (j < wc) v -= sg[j * kBlock + threadIdx.x] * s_mu[j];
-                p[i] = v;
+    } else {
+        const int i = threadIdx.x;
+        for (int t = 0; t < ring.nloc; ++t) {
+            if (!ring.acquire(t)) {
+                timeout = true;
+                break;
             }
+            const unsigned char* sg = ring.stage(t);
+            const float* sv = reinterpret_cast<const float*>(sg + ring.vec_off);
+            const int row0 = ring.row0(t);
+            if (row0 + i < n) {
+                const float pi = sv[i];
+                if constexpr (!FIRST) x[row0 + i] = sv[3 * kTmTile + i] + alpha * pi;
+                if (upd_p) {
+                    float v = sv[2 * kTmTile + i] * sv[kTmTile + i];
+                    if (!FIRST) v += beta * pi;
+                    if constexpr (H) {
+                        const __half* sW = reinterpret_cast<const __half*>(sg);
+#pragma unroll
+                        for (int j = 0; j < WB; ++j)
+                            if (j < wc) v -= __half2float(sW[(j >> 4) * 4096 + (j & 15) * kTmTile + i]) * s_mu[j];
+                    } else {
+                        const float* sW = reinterpret_cast<const float*>(sg);
+#pragma unroll
+                        for (int j = 0; j < WB; ++j)
+                            if (j < wc) v -= sW[(j >> 3) * 2048 + (j & 7) * kTmTile + i] * s_mu[j];
+                    }
+                    p[row0 + i] = v;
+                }
+            }
+            ring.release(t);
         }
     }
-    if (t < ring.nloc) {
-        if (threadIdx.x == 0) atomicExch(const_cast<int*>(&st->status), 7);
-        ring.drain(t);
+    if (timeout && lane == 0) atomicExch(const_cast<int*>(&st->status), 7);
+}
+
+// W16 = fp16(W32 / 2^e_j) with 2^e_j the smallest power of two >= max_i |W32[i][j]|, then
+// W32 = float(W16) * 2^e_j, which FP32 holds exactly: W32 becomes the 16-bit basis, so
+// every use of W32 (stage one, the correction's projection, A W32 formed after this) and
+// the direction pass's W16 see the same basis. cmax: per-column maxima as float bit
+// patterns (non-negative floats order as unsigned integers, so atomicMax gives a result
+// that does not depend on the order); zero on entry.
+__global__ void __launch_bounds__(kBlock) k_colmax(int n, int ld, const float* __restrict__ W, const DevState* st,
+                                                   unsigned int* cmax)
+{
+    __shared__ float s_m[kWarps];
+    const int w = st->pod_w;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = 0; j < w; ++j) {
+        float m = 0.0f;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+            m = fmaxf(m, fabsf(W[(size_t)j * ld + i]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) s_m[wid] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float b = 0.0f;
+            for (int k = 0; k < kWarps; ++k) b = fmaxf(b, s_m[k]);
+            atomicMax(cmax + j, __float_as_uint(b));
+        }
+        __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kBlock) k_quant16(int n, int ld, float* __restrict__ W, __half* __restrict__ W16,
+                                                    const unsigned int* __restrict__ cmax, float* __restrict__ wscale,
+                                                    const DevState* st)
+{
+    const int w = st->pod_w;
+    for (int j = 0; j < w; ++j) {
+        const float m = __uint_as_float(cmax[j]);
+        int e = 0;
+        if (m > 0.0f && isfinite(m)) frexpf(m, &e);   // m = f 2^e, 0.5 <= f < 1, so m <= 2^e
+        const float scale = ldexpf(1.0f, e), inv = ldexpf(1.0f, -e);
+        if (blockIdx.x == 0 && threadIdx.x == 0) wscale[j] = scale;
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+            const __half hv = __float2half_rn(W[(size_t)j * ld + i] * inv);
+            W16[(size_t)j * ld + i] = hv;
+            W[(size_t)j * ld + i] = __half2float(hv) * scale;
+        }
+    }
+}
+
+cudaError_t launch_quant16(int n, int ld, float* W32, __half* W16, unsigned int* cmax, float* wscale,
+                           const DevState* st, int sms, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(unsigned int) * kWMax, s);
+    if (e != cudaSuccess) return e;
+    const int grid = grid_rows(n, kBlock, sms);
+    k_colmax<<<grid, kBlock, 0, s>>>(n, ld, W32, st, cmax);
+    k_quant16<<<grid, kBlock, 0, s>>>(n, ld, W32, W16, cmax, wscale, st);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ FP32 loop, row-parallel float4
@@ -721,32 +854,33 @@ static void pick(int wb, void** init, void** upd, void** dir0, void** dir)
 #undef PODCG_PICK
 }
 
-// FP32 with a basis: the staged-tile update and direction passes.
+// FP32 with a basis: the TMA-staged update and direction passes (one CTA of kTmThreads
+// threads per SM, kTmSmem bytes of dynamic shared memory).
 template <int WB, bool COND>
-static void pick_bulk(void** upd, void** dir0, void** dir, int* smem_upd, int* smem_dir)
+static void pick_tma(bool w16, void** upd, void** dir0, void** dir)
 {
-    *upd = (void*)k_update_bulk<WB, COND>;
-    *dir0 = (void*)k_dir_bulk<WB, true>;
-    *dir = (void*)k_dir_bulk<WB, false>;
-    *smem_upd = kBulkSmem;
-    *smem_dir = kBulkSmem;
+    *upd = (void*)k_update_tma<WB, COND>;
+    *dir0 = w16 ? (void*)k_dir_tma<WB, true, true> : (void*)k_dir_tma<WB, true, false>;
+    *dir = w16 ? (void*)k_dir_tma<WB, false, true> : (void*)k_dir_tma<WB, false, false>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_update_bulk<WB, COND>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem_upd);
-        cudaFuncSetAttribute(k_dir_bulk<WB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem_dir);
-        cudaFuncSetAttribute(k_dir_bulk<WB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem_dir);
+        cudaFuncSetAttribute(k_update_tma<WB, COND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
+        cudaFuncSetAttribute(k_dir_tma<WB, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
+        cudaFuncSetAttribute(k_dir_tma<WB, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
+        cudaFuncSetAttribute(k_dir_tma<WB, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
+        cudaFuncSetAttribute(k_dir_tma<WB, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
         attr = true;
     }
 }
 
 template <bool COND>
-static void pick_bulk_wb(int wb, void** upd, void** dir0, void** dir, int* su, int* sd)
+static void pick_tma_wb(int wb, bool w16, void** upd, void** dir0, void** dir)
 {
-    if (wb <= 8) pick_bulk<8, COND>(upd, dir0, dir, su, sd);
-    else if (wb <= 16) pick_bulk<16, COND>(upd, dir0, dir, su, sd);
-    else if (wb <= 32) pick_bulk<32, COND>(upd, dir0, dir, su, sd);
-    else if (wb <= 48) pick_bulk<48, COND>(upd, dir0, dir, su, sd);
-    else pick_bulk<64, COND>(upd, dir0, dir, su, sd);
+    if (wb <= 8) pick_tma<8, COND>(w16, upd, dir0, dir);
+    else if (wb <= 16) pick_tma<16, COND>(w16, upd, dir0, dir);
+    else if (wb <= 32) pick_tma<32, COND>(w16, upd, dir0, dir);
+    else if (wb <= 48) pick_tma<48, COND>(w16, upd, dir0, dir);
+    else pick_tma<64, COND>(w16, upd, dir0, dir);
 }
 
 // FP32 with a basis, row-parallel float4 form.
@@ -768,7 +902,7 @@ static void pick_v4_wb(int wb, void** upd, void** dir0, void** dir)
     else pick_v4<64, COND>(upd, dir0, dir);
 }
 
-void cg_kernels(int wb, bool fp32, bool cond, int form, void** init, void** upd, void** dir0, void** dir,
+void cg_kernels(int wb, bool fp32, bool cond, int form, bool w16, void** init, void** upd, void** dir0, void** dir,
                 int* smem_upd, int* smem_dir)
 {
     *smem_upd = 0;
@@ -777,8 +911,10 @@ void cg_kernels(int wb, bool fp32, bool cond, int form, void** init, void** upd,
         if (cond) pick<float, true>(wb, init, upd, dir0, dir);
         else pick<float, false>(wb, init, upd, dir0, dir);
         if (wb > 0 && form == kProjStaged) {
-            if (cond) pick_bulk_wb<true>(wb, upd, dir0, dir, smem_upd, smem_dir);
-            else pick_bulk_wb<false>(wb, upd, dir0, dir, smem_upd, smem_dir);
+            if (cond) pick_tma_wb<true>(wb, w16, upd, dir0, dir);
+            else pick_tma_wb<false>(wb, w16, upd, dir0, dir);
+            *smem_upd = kTmSmemMax;
+            *smem_dir = kTmSmemMax;
         } else if (wb > 0) {
             if (cond) pick_v4_wb<true>(wb, upd, dir0, dir);
             else pick_v4_wb<false>(wb, upd, dir0, dir);
@@ -793,6 +929,19 @@ cudaError_t cg_set_wait_test(int mask, long long cycles)
 {
     const WaitTest wt{cycles, mask, 0};
     return cudaMemcpyToSymbol(g_cg_wait_test, &wt, sizeof(wt));
+}
+
+int tma_block_threads() { return kTmThreads; }
+
+void tma_shape(int n, int sms, int ncols, int cols_per_box, int nvec, int* grid, int* ring_bytes, int* smem)
+{
+    const int stage = (ncols + cols_per_box - 1) / cols_per_box * kTmBoxBytes + nvec * kTmVecBytes;
+    const int pair = stage <= 40 * 1024;
+    *ring_bytes = pair ? kTmRingPair : kTmRingMax;
+    *smem = *ring_bytes + 1024;
+    const int ntiles = (n + kTmTile - 1) / kTmTile;
+    const int g = sms * (pair ? 2 : 1);
+    *grid = ntiles < g ? ntiles : g;
 }
 
 int wb_bucket(int w)

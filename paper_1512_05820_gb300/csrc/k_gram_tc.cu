@@ -485,6 +485,25 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
+bool encode_panel_map(CUtensorMap* tm, const void* base, int elem_bytes, int ld, int cols, int box_cols)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || !base || cols < 1 || ld < 1 || (reinterpret_cast<uintptr_t>(base) & 15) ||
+        ((size_t)ld * elem_bytes) % 16)
+        return false;
+    const CUtensorMapDataType dt = elem_bytes == 2   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    memset(tm, 0, sizeof(*tm));
+    const cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)cols};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * (cuuint64_t)elem_bytes};
+    const cuuint32_t box[2] = {256u, (cuuint32_t)box_cols};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(tm, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static int tc_grid(int n, int sms)
 {
     const int nchunks = (n + kTcRows - 1) / kTcRows;

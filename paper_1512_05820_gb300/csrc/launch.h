@@ -1,6 +1,8 @@
 // Internal host-side launchers and kernel pointers (not part of the public C ABI).
 #pragma once
 
+#include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -66,12 +68,26 @@ cudaError_t launch_symmetrize(double* G, int ldg, int s, cudaStream_t str);
 
 // CG iteration (k_cg.cu): kernel pointers for graph construction
 // FP32 with w > 0 has two forms of the update/direction passes: row-parallel float4
-// (kProjDirect) and tiles staged by bulk copies (kProjStaged, with dynamic shared memory
-// returned in bytes; 0 for every other kernel).
+// (kProjDirect) and tiles staged by the TMA engine (kProjStaged: one CTA of
+// tma_block_threads() threads per SM, tma_grid() CTAs, dynamic shared memory returned in
+// bytes, the panels passed as tensor maps; 0 for every other kernel). w16: the staged
+// direction pass reads the 16-bit copy of W (with its column scales).
 constexpr int kProjDirect = 0;
 constexpr int kProjStaged = 1;
-void cg_kernels(int wb, bool fp32, bool cond, int form, void** init, void** upd, void** dir0, void** dir,
+void cg_kernels(int wb, bool fp32, bool cond, int form, bool w16, void** init, void** upd, void** dir0, void** dir,
                 int* smem_upd, int* smem_dir);
+int tma_block_threads();
+// launch shape of a TMA-staged pass over ncols panel columns (cols_per_box per box: 8 FP32,
+// 16 fp16) and nvec vector tiles per stage: grid, ring bytes (a kernel argument) and the
+// dynamic shared memory
+void tma_shape(int n, int sms, int ncols, int cols_per_box, int nvec, int* grid, int* ring_bytes, int* smem);
+// W16 = the 16-bit copy of the FP32 basis W32 with power-of-two column scales, and W32
+// replaced by its exact dequantised value (k_cg.cu); cmax: kWMax words of scratch
+cudaError_t launch_quant16(int n, int ld, float* W32, __half* W16, unsigned int* cmax, float* wscale,
+                           const DevState* st, int sms, cudaStream_t s);
+// a 2D tensor map over a column-major panel (rows = ld, cols columns, element 2, 4 or 8
+// bytes) with boxes of 256 rows x box_cols columns, no swizzle, zero fill past the rows
+bool encode_panel_map(CUtensorMap* tm, const void* base, int elem_bytes, int ld, int cols, int box_cols);
 
 // stage two of the three-stage algorithm (k_stage2.cu, FP64): kernel pointers for graph
 // construction, y = the augmenting-basis dimension (selects the width bucket), L = SpMV lanes

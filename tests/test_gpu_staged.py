@@ -1,5 +1,5 @@
 """Both forms of the FP32 update and direction passes (row-parallel float4, and tiles staged
-in shared memory by bulk copies) across every basis-width bucket, against the FP64 oracle
+in shared memory by the TMA engine) across every basis-width bucket, against the FP64 oracle
 with the same snapshots.
 
 n = 23^3 = 12,167 is not a multiple of the 256-row tile, so every solve ends on a ragged

@@ -1,6 +1,6 @@
 """The failure path of the bounded device waits, exercised without a GPU fault.
 
-The tensor-core Gram and the FP32 passes staged by bulk copies wait on mbarriers that their
+The tensor-core Gram and the FP32 passes staged by the TMA engine wait on mbarriers that their
 own copies complete. pod_cg_debug_wait_timeout makes those kernels issue no copies and cut
 every wait to 2e6 SM clocks (about a millisecond), so each wait expires with nothing in
 flight: the kernel records the timeout status (7) and returns. The tests check that the
