@@ -988,9 +988,13 @@ def main():
     achieved = kbytes[dominant] / (kms[dominant] / 1e3) / 1e9
     # FP32 with a basis runs the projection form the handle timed for the bucket
     wb = next(b for b in (0, 8, 16, 32, 48, 64) if w_meas <= b)
-    form = out["autotune"].get("projection", {}).get(f"w<={wb}", {}).get("form")
-    suffix = {"staged": "_tma", "direct": "_v4"}.get(form, "") if (prec == 1 and w_meas > 0) else ""
-    names = {"spmv_cg": "k_spmv_cg", "update": "k_update" + suffix, "direction": "k_dir" + suffix,
+    rec = out["autotune"].get("projection", {}).get(f"w<={wb}", {})
+
+    def suffix(p):
+        if prec != 1:
+            return ""
+        return "_tma" if (w_meas > 0 and rec.get(p) == "staged") else "_v4"
+    names = {"spmv_cg": "k_spmv_cg", "update": "k_update" + suffix("update"), "direction": "k_dir" + suffix("direction"),
              "residual": "k_residual"}
     out["roofline"] = {"bound": "hbm", "kernel": names[dominant], "achieved": achieved, "peak": peak, "unit": "GB/s",
                        "frac": achieved / peak, "peak_source": peak_kind,

@@ -260,13 +260,14 @@ pod_cg_status pod_cg_get_stage3_basis(pod_cg_t* h, double* B_out, double* AB_out
  * iteration vectors are overwritten (the next solve resets them). Errors: ERR_ARG, ERR_CUDA. */
 pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double* b, int reps, float* ms_out);
 
-/* The FP32 projection form chosen per basis-width bucket (buckets w <= 0, 8, 16, 32, 48,
- * 64): forms[6] receives 0 (row-parallel float4 passes), 1 (tiles staged in shared memory
- * by the TMA engine) or -1 (bucket not used yet); ms[12] the update + direction times (ms)
- * of form 0 then form 1 for each bucket, as measured by the handle's one-time timing on the
- * first MIXED system of at least 65,536 rows in that bucket (0 where not timed). This is
- * the project's own tuning record, with no counterpart in the paper. Host outputs;
- * either pointer may be NULL. */
+/* The FP32 projection forms chosen per basis-width bucket (buckets w <= 0, 8, 16, 32, 48,
+ * 64): forms[6] receives a bit mask per bucket, bit 0 set when the update pass runs on tiles
+ * staged in shared memory by the TMA engine (else row-parallel float4), bit 1 the same for
+ * the direction pass, or -1 (bucket not used yet); ms[24] the times (ms) of each bucket as
+ * [form 0 update, form 0 direction, form 1 update, form 1 direction], as measured by the
+ * handle's one-time timing on the first MIXED system of at least 65,536 rows in that bucket
+ * (0 where not timed); each pass keeps its faster form. This is the project's own tuning
+ * record, with no counterpart in the paper. Host outputs; either pointer may be NULL. */
 pod_cg_status pod_cg_proj_tuning(const pod_cg_t* h, int* forms, float* ms);
 
 /* Autotuner record (no counterpart in the paper): the CSR SpMV lanes-per-row used by the

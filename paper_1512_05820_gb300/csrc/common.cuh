@@ -64,6 +64,11 @@ struct DevState {
     double rh[kSMax];  // reduced residual
     double ph[kSMax];  // reduced direction
     double xh[kSMax];  // solution of the current inner reduced solve (whole-Y stage three)
+    // FP32 inner loop without grid-reduction tails: copies the direction pass reads while its
+    // block 0 rewrites the originals (written by block 0 of the update pass)
+    double rho_prev;   // (r, z) before this iteration
+    int iters_prev;    // iterations before this iteration
+    int inner_prev;    // inner iterations before this iteration
 };
 
 // Borrowed problem pointers of the current solve, read by the kernels of a captured
@@ -265,6 +270,223 @@ __device__ __forceinline__ bool partials_to_last_block(const double* s_blk, int 
         __threadfence();
     }
     return grid_tail<kWMax + 2, 1>(partials, nv, counter, s_tot);
+}
+
+// ------------------------------------------------------------------ reductions without tails
+//
+// The FP32 inner loop (mixed precision) reduces across the grid without a last-block tail,
+// whose fences, tickets and serialised sums cost about 7 us per launch on this GPU: every
+// block of a producing kernel stores its partials and exits; every block of the consuming
+// kernel sums all of them itself in one fixed order, so all blocks hold identical totals and
+// the kernel boundary orders the stores before the loads. The SpMV's (A p, p) partials sit
+// in row kSpmvRow of `partials`, the update pass's (r, z), ||r||^2 and (A W)^T z in rows
+// 0 .. w+1 (value-major, kPartialStride apart). The helpers below synchronise the first
+// kBlock threads of the block only (named barrier 1), so a TMA producer warp past them keeps
+// streaming while they run.
+constexpr int kSpmvRow = kWMax + 2;
+constexpr int kPartialRows = kWMax + 3;
+
+__device__ __forceinline__ void bar_compute() { asm volatile("bar.sync 1, %0;" ::"n"(kBlock) : "memory"); }
+
+// s_out[v] = sum over b < G of partials[v * kPartialStride + b] for v < nv, in a fixed order:
+// a group of TPV threads (the largest power of two with TPV nv <= kBlock, aligned) takes one
+// value; thread k of the group sums b = k, k + TPV, ... into U interleaved accumulators (U
+// independent loads in flight), combined in a fixed tree; then the group combines by a
+// shuffle tree (and, for groups wider than a warp, the warp sums in order). Called by
+// threads 0 .. kBlock-1 only (named barrier).
+template <int U>
+__device__ __forceinline__ void block_sum_rows(const double* __restrict__ partials, int nv, int G, double* s_out)
+{
+    __shared__ double s_wsum[kWarps];
+    const int t = threadIdx.x;
+    int tpv = kBlock;
+    while (tpv * nv > kBlock) tpv >>= 1;
+    const int v = t / tpv, k = t % tpv;
+    double acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0;
+    if (v < nv) {
+        const double* row = partials + (size_t)v * kPartialStride;
+        for (int b0 = k; b0 < G; b0 += U * tpv) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int b = b0 + u * tpv;
+                if (b < G) acc[u] += __ldcg(row + b);
+            }
+        }
+    }
+#pragma unroll
+    for (int h = U / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int u = 0; u < h; ++u) acc[u] += acc[u + h];
+    double a = acc[0];
+    if (tpv <= 32) {
+        for (int o = tpv / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (k == 0 && v < nv) s_out[v] = a;
+    } else {
+        a = warp_sum(a);
+        if ((t & 31) == 0) s_wsum[t >> 5] = a;
+        bar_compute();
+        if (t < nv) {
+            const int wpg = tpv >> 5;   // warps per group
+            double b = 0.0;
+            for (int j = 0; j < wpg; ++j) b += s_wsum[t * wpg + j];
+            s_out[t] = b;
+        }
+    }
+    bar_compute();
+}
+
+// mu = R^{-1} R^{-T} c (reading R^{-1}, row stride kWMax, from global memory) into s_mu,
+// c in shared or global memory; s_t: w doubles of shared scratch. Threads 0 .. kBlock-1 only.
+__device__ __forceinline__ void block_mu_global(const double* __restrict__ Rinv, const double* c, int w, double* s_t,
+                                                double* s_mu)
+{
+    for (int a = threadIdx.x; a < w; a += kBlock) {
+        double v = 0.0;
+        for (int k = 0; k <= a; ++k) v += __ldg(Rinv + (size_t)k * kWMax + a) * c[k];
+        s_t[a] = v;
+    }
+    bar_compute();
+    for (int a = threadIdx.x; a < w; a += kBlock) {
+        double v = 0.0;
+        for (int k = a; k < w; ++k) v += __ldg(Rinv + (size_t)a * kWMax + k) * s_t[k];
+        s_mu[a] = v;
+    }
+    bar_compute();
+}
+
+// Update-pass prologue: gamma = (A p, p) from the SpMV's G partials, then the scalar step of
+// cg_product_finish computed by every block from the same gamma (a breakdown ends an FP32
+// inner pass, or the solve in FP64). Block 0 records gamma, alpha and the status, the copies
+// the direction pass reads (rho, iters, inner_iters) and that the direction pass has work.
+// Returns alpha (0 when the step is not valid). Threads 0 .. kBlock-1 only.
+__device__ __forceinline__ double chain_alpha(DevState* st, const double* __restrict__ partials, int G)
+{
+    __shared__ double s_g[1];
+    block_sum_rows<8>(partials + (size_t)kSpmvRow * kPartialStride, 1, G, s_g);
+    const double gamma = s_g[0];
+    int status = st->status, inner_break = st->inner_break;
+    const int mixed = st->mixed;
+    const double rho = st->rho;
+    const bool bad = !isfinite(gamma) || !(gamma > 0.0);
+    if (bad && status == 0) {
+        if (mixed) inner_break = 1;
+        else status = !isfinite(gamma) ? 5 : 3;
+    }
+    const double alpha = (status == 0 && !inner_break) ? rho / gamma : 0.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int iters = st->iters, inner = st->inner_iters;
+        st->gamma = gamma;
+        st->alpha = alpha;
+        st->status = status;
+        st->inner_break = inner_break;
+        st->rho_prev = rho;
+        st->iters_prev = iters;
+        st->inner_prev = inner;
+        st->dir_pending = 1;
+    }
+    return alpha;
+}
+
+// SpMV epilogue without a tail: this block's share of (A p, p) (fixed shuffle tree, warps in
+// order) stored as its partial in row kSpmvRow. Every thread of the block must call.
+__device__ __forceinline__ void chain_store_gamma(double v, double* __restrict__ partials)
+{
+    __shared__ double s_g[kWarps];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_g[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kWarps; ++k) t += s_g[k];
+        partials[(size_t)kSpmvRow * kPartialStride + blockIdx.x] = t;
+    }
+}
+
+// Store this block's nv totals s_blk[0..nv) as its partials in rows 0 .. nv-1 (no tail).
+__device__ __forceinline__ void chain_store(const double* s_blk, int nv, double* __restrict__ partials)
+{
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) partials[(size_t)v * kPartialStride + blockIdx.x] = s_blk[v];
+}
+
+// What a direction pass needs from the update pass it follows.
+struct ChainStep {
+    double beta;
+    double alpha;   // 0 when the step of this iteration is not applied
+    bool upd_p;     // the direction is updated (the pass has not finished)
+};
+
+// Direction-pass prologue: the update pass's totals ((r, z), ||r||^2, c = (A W)^T z) from its
+// G partials into s_tot[0 .. w+2), then the decisions update_finish takes in the tailed form
+// (beta, the iteration count, the exit test, the iteration cap, non-finite scalars), taken by
+// every block from the same totals and the copies chain_alpha made, so they agree, and
+// mu = M c into s_mu with M = R^{-1} R^{-T} (row stride kWMax), read into s_M (w x w, FP32:
+// mu is used in FP32) in the same round as the partials. Block 0 writes the state and the graph condition. Threads
+// 0 .. kBlock-1 only.
+template <int WB, bool COND>
+__device__ __forceinline__ ChainStep chain_direction(DevState* st, const double* __restrict__ partials, int G, int w,
+                                                     const double* __restrict__ M, double* s_tot, float* s_M,
+                                                     double* s_mu, cudaGraphConditionalHandle h_inner, int use_cond)
+{
+    constexpr int MPT = (WB * WB + kBlock - 1) / kBlock;   // entries of M per thread
+    double m[MPT > 0 ? MPT : 1];
+#pragma unroll
+    for (int u = 0; u < MPT; ++u) {
+        const int e = threadIdx.x + u * kBlock;
+        m[u] = (e < w * w) ? __ldg(M + (size_t)(e / w) * kWMax + e % w) : 0.0;
+    }
+    block_sum_rows<16>(partials, w + 2, G, s_tot);
+#pragma unroll
+    for (int u = 0; u < MPT; ++u) {
+        const int e = threadIdx.x + u * kBlock;
+        if (e < w * w) s_M[e] = float(m[u]);
+    }
+    bar_compute();
+    for (int a = threadIdx.x; a < w; a += kBlock) {
+        double v = 0.0;
+        for (int k = 0; k < w; ++k) v += (double)s_M[a * w + k] * s_tot[2 + k];
+        s_mu[a] = v;
+    }
+    bar_compute();
+    const double rho_old = st->rho_prev, tol2_in = st->tol2_in;
+    const int iters = st->iters_prev + 1, inner_iters = st->inner_prev + 1, k_max = st->k_max;
+    int status = st->status, inner_break = st->inner_break;
+    const int mixed = st->mixed;
+    const double rho_new = s_tot[0], rr = s_tot[1];
+    if (status == 0 && !(isfinite(rho_new) && isfinite(rr))) {
+        if (mixed) inner_break = 1;
+        else status = 5;
+    }
+    int done = (status != 0) || inner_break || !(rr > tol2_in);
+    if (!done && iters >= k_max) {
+        status = 4;
+        done = 1;
+    }
+    ChainStep cs;
+    cs.beta = rho_new / rho_old;
+    // the step of the iteration that reached the cap (status 4) is valid and is applied
+    const bool ok = (status == 0 || status == 4) && !inner_break;
+    cs.alpha = ok ? st->alpha : 0.0;
+    cs.upd_p = !done && ok;
+    if (blockIdx.x == 0) {
+        for (int a = threadIdx.x; a < w; a += kBlock) st->c[a] = s_tot[2 + a];
+        if (threadIdx.x == 0) {
+            st->beta = cs.beta;
+            st->rho = rho_new;
+            st->rr = rr;
+            st->iters = iters;
+            st->inner_iters = inner_iters;
+            st->status = status;
+            st->inner_break = inner_break;
+            st->done = done;
+            if constexpr (COND) {
+                if (use_cond) cudaGraphSetConditional(h_inner, done ? 0u : 1u);
+            }
+        }
+    }
+    return cs;
 }
 
 // Column-parallel accumulation of c_j += sum_rows col_j[row] * s_z[row - row0] over one

@@ -212,6 +212,7 @@ struct pod_cg_t {
     int* bsr_flag = nullptr;
     double* G = nullptr;        // kWMax x (kWMax + 1) row-major
     double* Rinv = nullptr;     // kWMax x kWMax
+    double* Mmu = nullptr;      // R^{-1} R^{-T} (mixed: the direction passes' mu = M c), kWMax x kWMax
 
     // vectors
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr;
@@ -244,8 +245,8 @@ struct pod_cg_t {
     int last_L = 0;
     // FP32 projection form per width bucket (kProjDirect / kProjStaged, -1 = not chosen yet)
     // and the update + direction times that chose it (ms, [bucket][form])
-    int proj_form[6] = {-1, -1, -1, -1, -1, -1};
-    float proj_ms[6][2] = {};
+    int proj_form[6] = {-1, -1, -1, -1, -1, -1};   // bit 0: update pass staged, bit 1: direction
+    float proj_ms[6][2][2] = {};                     // [bucket][form][update, direction]
     DevState* st_save = nullptr;   // device copy of the state while the form is timed
 
     GraphSlot graphs[6];                // conditional graphs [width bucket]
@@ -397,13 +398,15 @@ pod_cg_status choose_proj_form(pod_cg_t* h, int wb, int L)
     t.outer_done = 0;
     for (int a = 0; a < kWMax; ++a) t.c[a] = 0.0;
     *h->st_host = t;
+    // each form times its update pass, then its direction pass (which reads the partials of
+    // the update pass of the same form); each pass keeps its faster form
     for (int form = kProjDirect; form <= kProjStaged; ++form) {
-        h->proj_form[bi] = form;
+        h->proj_form[bi] = form == kProjStaged ? 3 : 0;
         Plan pl;
         make_plan(h, wb, L, true, 0, 0, 0, pl);
         KSpec* ks[2] = {&pl.upd, &pl.dir};
-        float total = 0.0f;
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < 2; ++k) {
+            float total = 0.0f;
             for (int rep = 0; rep < 4; ++rep) {
                 PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
                 PODCG_CK(h, cudaEventRecord(h->tev[0], s));
@@ -414,9 +417,11 @@ pod_cg_status choose_proj_form(pod_cg_t* h, int wb, int L)
                 cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]);
                 if (rep > 0) total += ms;
             }
-        h->proj_ms[bi][form] = total / 3.0f;
+            h->proj_ms[bi][form][k] = total / 3.0f;
+        }
     }
-    h->proj_form[bi] = h->proj_ms[bi][kProjStaged] < h->proj_ms[bi][kProjDirect] ? kProjStaged : kProjDirect;
+    h->proj_form[bi] = (h->proj_ms[bi][kProjStaged][0] < h->proj_ms[bi][kProjDirect][0] ? 1 : 0) |
+                       (h->proj_ms[bi][kProjStaged][1] < h->proj_ms[bi][kProjDirect][1] ? 2 : 0);
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_save, sizeof(DevState), cudaMemcpyDeviceToDevice, s));
     return read_state(h);
 }
@@ -439,8 +444,16 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
     const int n = h->n, ld = h->ld;
     void *f_init, *f_upd, *f_dir0, *f_dir;
     int sm_upd = 0, sm_dir = 0;
-    const int form = (h->proj_form[bucket_index(wb)] == kProjStaged && h->tm_ok) ? kProjStaged : kProjDirect;
-    cg_kernels(wb, mixed, use_cond != 0, form, h->w16, &f_init, &f_upd, &f_dir0, &f_dir, &sm_upd, &sm_dir);
+    // FP32 with a basis: the form of each pass (bit 0 of the bucket's choice: the update pass
+    // staged by the TMA engine, bit 1: the direction pass)
+    const int pf = (mixed && wb > 0 && h->tm_ok && h->proj_form[bucket_index(wb)] > 0) ? h->proj_form[bucket_index(wb)] : 0;
+    const int form_u = (pf & 1) ? kProjStaged : kProjDirect, form_d = (pf & 2) ? kProjStaged : kProjDirect;
+    cg_kernels(wb, mixed, use_cond != 0, form_d, h->w16, &f_init, &f_upd, &f_dir0, &f_dir, &sm_upd, &sm_dir);
+    if (form_u != form_d) {
+        void *i2, *d02, *d2;
+        int sd2 = 0;
+        cg_kernels(wb, mixed, use_cond != 0, form_u, h->w16, &i2, &f_upd, &d02, &d2, &sm_upd, &sd2);
+    }
     // the CG product: CSR, or the 3x3 block form when the pattern has one (k_bsr.cu)
     void* f_spmv = h->use_bsr ? kernel_bsr_spmv_cg(h->bsr_L, mixed) : kernel_spmv_cg(L, mixed);
     void* f_res = kernel_residual(L, use_cond != 0);
@@ -477,34 +490,55 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
                       (const float*)h->AW32, Rinv, cst);
         P.init.set(f_init, g_init, n, ld, (const float*)h->r32, (const float*)h->dinv32, (const float*)h->AW32,
                    h->partials, c + 0 * kCounterStride, st, h_inner, use_cond);
-        P.dir0.set(f_dir0, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
-                   (const float*)h->W32, Rinv, cst);
+        // the FP32 loop reduces without tails: the SpMV's partials feed the update pass, the
+        // update pass's feed the direction pass, which sets the graph condition
         P.spmv.set(f_spmv, g_spmv, pd, (const float*)h->p32, h->q32, h->partials, c + 2 * kCounterStride, st);
-        P.upd.set(f_upd, g_upd, n, ld, h->r32, (const float*)h->q32, (const float*)h->dinv32,
-                  (const float*)h->AW32, h->partials, c + 3 * kCounterStride, st, h_inner, use_cond);
+        // the update pass at two blocks per SM at most: its partials feed every direction block
+        const int gu = std::min(g_upd, 2 * h->sms);
+        const double* M = h->Mmu;
+        P.upd.set(f_upd, gu, n, ld, h->r32, (const float*)h->q32, (const float*)h->dinv32, (const float*)h->AW32,
+                  h->partials, g_spmv, st);
+        P.dir0.set(f_dir0, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
+                   (const float*)h->W32, Rinv, M, (const double*)h->partials, gu, st, h_inner, 0);
         P.dir.set(f_dir, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
-                  (const float*)h->W32, Rinv, cst);
+                  (const float*)h->W32, Rinv, M, (const double*)h->partials, gu, st, h_inner, use_cond);
         P.mxaccum.set(f_acc, occ_grid(h, f_acc, n, kBlock), n, h->x, (const float*)h->d32, cst);
     }
     P.upd.smem = sm_upd;
     P.dir0.smem = sm_dir;
     P.dir.smem = sm_dir;
-    if (mixed && wb > 0 && form == kProjStaged) {
-        // TMA-staged passes: the panels as tensor maps, ring and grid by the bucket's stage size
-        const CUtensorMap* tmW = h->tm_dev + (h->w16 ? 2 : 1);
-        int gu, ru, su, gd, rd, sd;
-        tma_shape(n, h->sms, wb, 8, 3, &gu, &ru, &su);
-        tma_shape(n, h->sms, wb, h->w16 ? 16 : 8, 4, &gd, &rd, &sd);
-        P.upd.set(f_upd, gu, n, ld, ru, h->r32, (const float*)h->q32, (const float*)h->dinv32,
-                  (const CUtensorMap*)h->tm_dev, h->partials,
-                  c + 3 * kCounterStride, st, h_inner, use_cond);
-        P.dir0.set(f_dir0, gd, n, ld, rd, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32, tmW,
-                   (const float*)h->wscale, Rinv, cst);
-        P.dir.set(f_dir, gd, n, ld, rd, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32, tmW,
-                  (const float*)h->wscale, Rinv, cst);
-        P.upd.block = P.dir0.block = P.dir.block = tma_block_threads();
-        P.upd.smem = su;
-        P.dir0.smem = P.dir.smem = sd;
+    if (mixed && wb > 0 && pf != 0) {
+        // TMA-staged passes: the panels as tensor maps, ring and grid by the bucket's stage size;
+        // the direction pass sums one partial per block of whichever update pass runs
+        int gu = std::min(g_upd, 2 * h->sms);
+        if (form_u == kProjStaged) {
+            int ru, su;
+            tma_shape(n, h->sms, wb, 8, 3, false, &gu, &ru, &su);
+            P.upd.set(f_upd, gu, n, ld, ru, h->r32, (const float*)h->q32, (const float*)h->dinv32,
+                      (const CUtensorMap*)h->tm_dev, h->partials, g_spmv, st);
+            P.upd.block = tma_block_threads();
+            P.upd.smem = su;
+        }
+        if (form_d == kProjStaged) {
+            const CUtensorMap* tmW = h->tm_dev + (h->w16 ? 2 : 1);
+            int gd, rd, sd;
+            tma_shape(n, h->sms, wb, h->w16 ? 16 : 8, 4, true, &gd, &rd, &sd);
+            P.dir0.set(f_dir0, gd, n, ld, rd, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32, tmW,
+                       (const float*)h->wscale, Rinv, (const double*)h->Mmu, (const double*)h->partials, gu, st,
+                       h_inner, 0);
+            P.dir.set(f_dir, gd, n, ld, rd, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32, tmW,
+                      (const float*)h->wscale, Rinv, (const double*)h->Mmu, (const double*)h->partials, gu, st,
+                      h_inner, use_cond);
+            P.dir0.block = P.dir.block = tma_block_threads();
+            P.dir0.smem = P.dir.smem = sd;
+        } else {
+            P.dir0.set(f_dir0, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
+                       (const float*)h->W32, Rinv, (const double*)h->Mmu, (const double*)h->partials, gu, st, h_inner,
+                       0);
+            P.dir.set(f_dir, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
+                      (const float*)h->W32, Rinv, (const double*)h->Mmu, (const double*)h->partials, gu, st, h_inner,
+                      use_cond);
+        }
     }
 }
 
@@ -1014,7 +1048,7 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
     void* bufs[] = {h->S, h->S32, h->GS, h->grow, h->C, h->sigma2, h->Vprev, h->W, h->AW, h->W32, h->AW32, h->W16, h->wscale, h->wmax, h->Y, h->Y32,
                     h->s2_hist, h->s2tmp, h->brp, h->bcol, h->bval, h->bval32, h->bsr_flag, h->Cout, h->CSv,
                     h->GSC, h->out_work, h->AS, h->GA,
-                    h->G, h->Rinv,
+                    h->G, h->Rinv, h->Mmu,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
                     h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
     for (void* b : bufs)
@@ -1069,7 +1103,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     // three-stage mode appends up to y - w stage-two directions after W: room for kWMax
     h->wcap = c.three_stage ? kWMax : c.w_max;
     if (c.proj_form >= 0)
-        for (int& f : h->proj_form) f = c.proj_form;
+        for (int& f : h->proj_form) f = c.proj_form == 1 ? 3 : 0;   // both passes in the forced form
     h->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&h->device);
     h->sms = device_sms();
@@ -1097,13 +1131,14 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     }
     PODCG_ALLOC(h->G, (size_t)kWMax * (kWMax + 1))
     PODCG_ALLOC(h->Rinv, (size_t)kWMax * kWMax)
+    PODCG_ALLOC(h->Mmu, (size_t)kWMax * kWMax)
     PODCG_ALLOC(h->x, ld)
     PODCG_ALLOC(h->r, ld)
     PODCG_ALLOC(h->p, ld)
     PODCG_ALLOC(h->q, ld)
     PODCG_ALLOC(h->dinv, ld)
     PODCG_ALLOC(h->dinv32, ld)
-    PODCG_ALLOC(h->partials, (size_t)(kWMax + 2) * kPartialStride)
+    PODCG_ALLOC(h->partials, (size_t)kPartialRows * kPartialStride)
     PODCG_ALLOC(h->counters, (size_t)8 * kCounterStride)
     PODCG_ALLOC(h->st, 1)
     PODCG_ALLOC(h->st_save, 1)
@@ -1499,6 +1534,9 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     if (h->mixed) {
         pod_cg_status ms = set_panel_maps(h, w3);
         if (ms != POD_CG_OK) return ms;
+        // the direction passes' mu = M c, M = R^{-1} R^{-T} of this solve's factor
+        PODCG_CK(h, launch_mu_matrix(h->Rinv, h->st, h->Mmu, s));
+        launches += 1;
     }
     pod_cg_status ps = choose_proj_form(h, wb, L);
     if (ps != POD_CG_OK) return ps;
@@ -1633,10 +1671,9 @@ pod_cg_status pod_cg_proj_tuning(const pod_cg_t* h, int* forms, float* ms)
     if (!h) return POD_CG_ERR_ARG;
     for (int b = 0; b < 6; ++b) {
         if (forms) forms[b] = h->proj_form[b];
-        if (ms) {
-            ms[2 * b] = h->proj_ms[b][0];
-            ms[2 * b + 1] = h->proj_ms[b][1];
-        }
+        if (ms)
+            for (int f = 0; f < 2; ++f)
+                for (int k = 0; k < 2; ++k) ms[4 * b + 2 * f + k] = h->proj_ms[b][f][k];
     }
     return POD_CG_OK;
 }

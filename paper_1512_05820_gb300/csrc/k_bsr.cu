@@ -67,7 +67,9 @@ __global__ void __launch_bounds__(kBlock) k_bsr_values(const int32_t* __restrict
 
 // q = A p and gamma = (A p, p): L lanes per block row stride through its blocks (lane l
 // takes blocks l, l + L, ...: consecutive lanes read consecutive value words), then the
-// group sums its three row sums by shuffles.
+// group sums its three row sums by shuffles. In FP32 (the inner loop of mixed precision)
+// every block stores its share of gamma and the update pass forms alpha (chain_alpha); in
+// FP64 the last block does.
 template <int L, typename T>
 __global__ void __launch_bounds__(kBlock) k_bsr_spmv_cg(const ProbDesc* __restrict__ pd, const T* __restrict__ p,
                                                         T* __restrict__ q, double* __restrict__ partials,
@@ -115,9 +117,13 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv_cg(const ProbDesc* __restri
             dot += s0 * p[3 * I] + s1 * p[3 * I + 1] + s2 * p[3 * I + 2];
         }
     }
-    double acc[1] = {double(dot)};
-    __shared__ double tot[1];
-    if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) cg_product_finish(st, tot[0]);
+    if constexpr (sizeof(T) == 4) {
+        chain_store_gamma(double(dot), partials);
+    } else {
+        double acc[1] = {double(dot)};
+        __shared__ double tot[1];
+        if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) cg_product_finish(st, tot[0]);
+    }
 }
 
 // ------------------------------------------------------------------------------ host side

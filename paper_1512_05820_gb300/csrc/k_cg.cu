@@ -255,9 +255,10 @@ __global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x
 // arrival per warp): no block-wide barrier sits in the loop, and the reads in flight do not
 // depend on the consumers' register count. A probe streaming the same copies (a 22-column
 // panel, three vectors, one vector written back) reached 6.1 TB/s with 130-190 KB in
-// flight per SM and less with more (5.8 TB/s at 200 KB in one CTA): two CTAs per SM with
-// 96 KB rings each when a stage is at most 40 KB, else one CTA with a 200 KB ring
-// (tma_shape).
+// flight per SM and less with more (5.8 TB/s at 200 KB in one CTA). The update pass runs
+// one CTA per SM with a 160 KB ring (its partials feed every block of the direction pass,
+// so fewer CTAs make that pass's prologue shorter); the direction pass two CTAs per SM with
+// 88 KB rings when a stage is at most 40 KB, else one with 160 KB (tma_shape).
 //
 // Every copy stays inside its buffer: vectors and panels are allocated with the padded
 // leading dimension ld (a multiple of 32 >= n), a vector copy spans min(256, ld - row0)
@@ -270,8 +271,8 @@ constexpr long long kBulkWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 constexpr int kTmTile = 256;                           // rows per tile
 constexpr int kTmBoxBytes = 8192;                      // panel box: 256 x 8 FP32 or 256 x 16 fp16
 constexpr int kTmVecBytes = kTmTile * 4;               // one FP32 vector tile
-constexpr int kTmRingMax = 200 * 1024;                 // ring bytes of a CTA alone on its SM
-constexpr int kTmRingPair = 96 * 1024;                 // ring bytes of each of two CTAs per SM
+constexpr int kTmRingMax = 160 * 1024;                 // ring bytes of a CTA alone on its SM
+constexpr int kTmRingPair = 88 * 1024;                 // ring bytes of each of two CTAs per SM
 constexpr int kTmMaxStages = 16;
 constexpr int kTmConsumers = 8;                        // consumer warps (one row per thread)
 constexpr int kTmThreads = 32 * (kTmConsumers + 1);    // + the producer warp
@@ -411,23 +412,21 @@ __device__ __forceinline__ float dot4(float4 a, float4 b) { return a.x * b.x + a
 // takes rows 32 cw + lane for the row part and basis columns cw, cw + 8, ... for the
 // column part, whose lanes cover the tile's 256 rows as two float4 groups each (z is
 // formed again from the staged r, q, M^{-1} by every warp, so no warp waits for another).
-template <int WB, bool COND>
+template <int WB>
 __global__ void __launch_bounds__(kTmThreads, 2) k_update_tma(int n, int ld, int ring_bytes, float* __restrict__ r,
                                                               const float* __restrict__ q,
                                                               const float* __restrict__ dinv,
                                                               const CUtensorMap* __restrict__ tmAW,
-                                                              double* __restrict__ partials, unsigned int* counter,
-                                                              DevState* st, cudaGraphConditionalHandle h_inner,
-                                                              int use_cond)
+                                                              double* __restrict__ partials, int g_spmv,
+                                                              DevState* st)
 {
-    if (st->done) return;   // uniform: only the last block of a pass writes `done`
+    if (st->done) return;   // uniform: `done` is written by k_init / the direction pass only
     constexpr int CPW = (WB + kTmConsumers - 1) / kTmConsumers;
     extern __shared__ __align__(1024) unsigned char tm_raw[];
     __shared__ uint64_t full[kTmMaxStages], empty[kTmMaxStages];
     __shared__ float s_red[kTmConsumers][2];
     __shared__ double s_blk[WB + 2];
     const int w = st->w;
-    const float alpha = (st->status == 0) ? float(st->alpha) : 0.0f;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TmaRing<3> ring;
     ring.init(tm_raw, full, empty, n, w, 8, ring_bytes);
@@ -442,6 +441,8 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_update_tma(int n, int ld, int
             ring.produce(ld, tmAW, vec);
         }
     } else {
+        // alpha from the SpMV's partials while the producer already streams (consumers only)
+        const float alpha = float(chain_alpha(st, partials, g_spmv));
         for (int t = 0; t < ring.nloc; ++t) {
             if (!ring.acquire(t)) {
                 timeout = true;
@@ -526,46 +527,37 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_update_tma(int n, int ld, int
         s_blk[1] = t1;
     }
     __syncthreads();
-    update_finish<WB, COND>(s_blk, w, partials, counter, st, h_inner, use_cond);
+    chain_store(s_blk, w + 2, partials);
 }
 
 // Direction pass: mu = R^{-1} R^{-T} c, x += alpha p, p = z + beta p - W mu (FIRST: p0 =
-// z0 - W mu0, x untouched), one row per consumer thread. H: W is the 16-bit copy W16 with
-// one power-of-two scale per column (W32 = W16 * wscale exactly), folded into mu.
-template <int WB, bool FIRST, bool H>
+// z0 - W mu0 from st->c, x untouched), one row per consumer thread; otherwise the update
+// pass's totals come from its partials (chain_direction, with COND the graph condition).
+// H: W is the 16-bit copy W16 with one power-of-two scale per column (W32 = W16 * wscale
+// exactly), folded into mu.
+template <int WB, bool FIRST, bool H, bool COND>
 __global__ void __launch_bounds__(kTmThreads, 2) k_dir_tma(int n, int ld, int ring_bytes, float* __restrict__ x,
                                                            float* __restrict__ p,
                                                            const float* __restrict__ r, const float* __restrict__ dinv,
                                                            const CUtensorMap* __restrict__ tmW,
                                                            const float* __restrict__ wscale,
-                                                           const double* __restrict__ Rinv, const DevState* st)
+                                                           const double* __restrict__ Rinv,
+                                                           const double* __restrict__ M,
+                                                           const double* __restrict__ partials, int g_upd, DevState* st,
+                                                           cudaGraphConditionalHandle h_inner, int use_cond)
 {
     if (!FIRST && !st->dir_pending) return;
     if (FIRST && st->outer_done) return;
     constexpr int NV = FIRST ? 3 : 4;
     const int w = st->w;
-    const bool ok = (st->status == 0 || st->status == 4) && !st->inner_break;
-    const float alpha = ok ? float(st->alpha) : 0.0f;
-    const float beta = float(st->beta);
-    const bool upd_p = FIRST || (!st->done && ok);
     extern __shared__ __align__(1024) unsigned char tm_raw[];
     __shared__ uint64_t full[kTmMaxStages], empty[kTmMaxStages];
-    __shared__ float s_mu[WB];
-    if (upd_p) {
-        // the ring's memory is scratch for mu until the ring is set up
-        double* s_R = reinterpret_cast<double*>(tm_raw);
-        double* s_c = s_R + WB * WB;
-        double* s_t = s_c + WB;
-        double* s_mud = s_t + WB;
-        block_mu<WB>(Rinv, st->c, w, s_R, s_c, s_t, s_mud);
-        for (int j = threadIdx.x; j < WB; j += blockDim.x)
-            s_mu[j] = (j < w) ? float(s_mud[j]) * (H ? wscale[j] : 1.0f) : 0.0f;
-    }
-    __syncthreads();
-    // without a p update only x += alpha p remains: no panel needed
-    const int wc = upd_p ? w : 0;
+    __shared__ double s_tot[WB + 2], s_t[WB > 0 ? WB : 1], s_mud[WB > 0 ? WB : 1];
+    __shared__ float s_mu[WB > 0 ? WB : 1], s_M[WB > 0 ? WB * WB : 1];
+    // the producer streams the whole panel from the start (the loads do not depend on the
+    // update pass's totals); a pass that has finished does not use it (its last iteration)
     TmaRing<NV> ring;
-    ring.init(tm_raw, full, empty, n, wc, H ? 16 : 8, ring_bytes);
+    ring.init(tm_raw, full, empty, n, w, H ? 16 : 8, ring_bytes);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bool timeout = false;
     if (warp == kTmConsumers) {
@@ -578,6 +570,24 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_dir_tma(int n, int ld, int ri
             ring.produce(ld, tmW, vec);
         }
     } else {
+        // consumers only (named barrier): the update pass's totals and decisions, then mu
+        float alpha = 0.0f, beta = 0.0f;
+        bool upd_p = true;
+        if constexpr (!FIRST) {
+            const ChainStep cs = chain_direction<WB, COND>(st, partials, g_upd, w, M, s_tot, s_M, s_mud, h_inner,
+                                                           use_cond);
+            alpha = float(cs.alpha);
+            beta = float(cs.beta);
+            upd_p = cs.upd_p;
+        } else {
+            block_mu_global(Rinv, st->c, w, s_t, s_mud);
+        }
+        if (upd_p) {
+            for (int j = threadIdx.x; j < WB; j += kBlock)
+                s_mu[j] = (j < w) ? float(s_mud[j]) * (H ? wscale[j] : 1.0f) : 0.0f;
+            bar_compute();
+        }
+        const int wc = upd_p ? w : 0;
         const int i = threadIdx.x;
         for (int t = 0; t < ring.nloc; ++t) {
             if (!ring.acquire(t)) {
@@ -610,7 +620,7 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_dir_tma(int n, int ld, int ri
             ring.release(t);
         }
     }
-    if (timeout && lane == 0) atomicExch(const_cast<int*>(&st->status), 7);
+    if (timeout && lane == 0) atomicExch(&st->status, 7);
 }
 
 // W16 = fp16(W32 / 2^e_j) with 2^e_j the smallest power of two >= max_i |W32[i][j]|, then
@@ -690,21 +700,23 @@ cudaError_t launch_quant16(int n, int ld, float* W32, __half* W16, unsigned int*
 constexpr int kV4Batch = 8;
 constexpr int kV4Blocks = 6;   // resident blocks per SM the register budget is set for
 
-template <int WB, bool COND>
-__global__ void __launch_bounds__(kBlock, 2) k_update_v4(int n, int ld, float* __restrict__ r,
-                                                         const float* __restrict__ q, const float* __restrict__ dinv,
-                                                         const float* __restrict__ AW, double* __restrict__ partials,
-                                                         unsigned int* counter, DevState* st,
-                                                         cudaGraphConditionalHandle h_inner, int use_cond)
+template <int WB>
+__global__ void __launch_bounds__(kBlock, WB <= 8 ? 4 : 2) k_update_v4(int n, int ld, float* __restrict__ r,
+                                                                     const float* __restrict__ q,
+                                                                     const float* __restrict__ dinv,
+                                                                     const float* __restrict__ AW,
+                                                                     double* __restrict__ partials, int g_spmv,
+                                                                     DevState* st)
 {
-    if (st->done) return;   // uniform: only the last block of a pass writes `done`
+    if (st->done) return;   // uniform: `done` is written by k_init / the direction pass only
+    constexpr int NA = WB > 0 ? WB : 1;
     __shared__ float s_red[kWarps][WB + 2];
     __shared__ double s_blk[WB + 2];
     const int w = st->w;
-    const float alpha = (st->status == 0) ? float(st->alpha) : 0.0f;
-    float acc[WB];
+    const float alpha = float(chain_alpha(st, partials, g_spmv));
+    float acc[NA];
 #pragma unroll
-    for (int j = 0; j < WB; ++j) acc[j] = 0.0f;
+    for (int j = 0; j < NA; ++j) acc[j] = 0.0f;
     float rho = 0.0f, rr = 0.0f;
     const int n4 = n >> 2;
     const int stride = gridDim.x * blockDim.x;
@@ -761,28 +773,43 @@ __global__ void __launch_bounds__(kBlock, 2) k_update_v4(int n, int ld, float* _
         s_blk[v] = t;
     }
     __syncthreads();
-    update_finish<WB, COND>(s_blk, w, partials, counter, st, h_inner, use_cond);
+    chain_store(s_blk, w + 2, partials);
 }
 
-template <int WB, bool FIRST>
+// FIRST: mu0 from st->c (k_init), p0 = z0 - W mu0, x untouched. Otherwise the update pass's
+// totals come from its partials (chain_direction, which also takes the exit decisions and,
+// with COND, sets the graph condition), then mu = R^{-1} R^{-T} c, x += alpha p and
+// p = z + beta p - W mu.
+template <int WB, bool FIRST, bool COND>
 __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4(int n, int ld, float* __restrict__ x,
                                                               float* __restrict__ p, const float* __restrict__ r,
                                                               const float* __restrict__ dinv,
                                                               const float* __restrict__ W,
-                                                              const double* __restrict__ Rinv, const DevState* st)
+                                                              const double* __restrict__ Rinv,
+                                                              const double* __restrict__ M,
+                                                              const double* __restrict__ partials, int g_upd,
+                                                              DevState* st, cudaGraphConditionalHandle h_inner,
+                                                              int use_cond)
 {
     if (!FIRST && !st->dir_pending) return;
     if (FIRST && st->outer_done) return;
+    constexpr int NB = WB > 0 ? WB : 1;
     const int w = st->w;
-    const bool ok = (st->status == 0 || st->status == 4) && !st->inner_break;
-    const float alpha = ok ? float(st->alpha) : 0.0f;
-    const float beta = float(st->beta);
-    const bool upd_p = FIRST || (!st->done && ok);
-    __shared__ double s_R[WB * WB];
-    __shared__ double s_c[WB], s_t[WB], s_mud[WB];
-    __shared__ float s_mu[WB];
-    if (upd_p) {
-        block_mu<WB>(Rinv, st->c, w, s_R, s_c, s_t, s_mud);
+    __shared__ double s_tot[WB + 2];
+    __shared__ float s_M[NB * NB];
+    __shared__ double s_c[NB], s_t[NB], s_mud[NB];
+    __shared__ float s_mu[NB];
+    float alpha = 0.0f, beta = 0.0f;
+    bool upd_p = true;
+    if constexpr (!FIRST) {
+        const ChainStep cs = chain_direction<WB, COND>(st, partials, g_upd, w, M, s_tot, s_M, s_mud, h_inner, use_cond);
+        alpha = float(cs.alpha);
+        beta = float(cs.beta);
+        upd_p = cs.upd_p;
+    } else if (WB > 0) {
+        block_mu_global(Rinv, st->c, w, s_t, s_mud);
+    }
+    if (WB > 0 && upd_p) {
         for (int j = threadIdx.x; j < WB; j += blockDim.x) s_mu[j] = (j < w) ? float(s_mud[j]) : 0.0f;
         __syncthreads();
     }
@@ -809,14 +836,16 @@ __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4
                 v.z += beta * p4.z;
                 v.w += beta * p4.w;
             }
+            if constexpr (WB > 0) {
 #pragma unroll 4
-            for (int j = 0; j < wc; ++j) {
-                const float4 a = __ldg(reinterpret_cast<const float4*>(W + (size_t)j * ld) + g);
-                const float m = s_mu[j];
-                v.x -= a.x * m;
-                v.y -= a.y * m;
-                v.z -= a.z * m;
-                v.w -= a.w * m;
+                for (int j = 0; j < wc; ++j) {
+                    const float4 a = __ldg(reinterpret_cast<const float4*>(W + (size_t)j * ld) + g);
+                    const float m = s_mu[j];
+                    v.x -= a.x * m;
+                    v.y -= a.y * m;
+                    v.z -= a.z * m;
+                    v.w -= a.w * m;
+                }
             }
             reinterpret_cast<float4*>(p)[g] = v;
         }
@@ -859,16 +888,16 @@ static void pick(int wb, void** init, void** upd, void** dir0, void** dir)
 template <int WB, bool COND>
 static void pick_tma(bool w16, void** upd, void** dir0, void** dir)
 {
-    *upd = (void*)k_update_tma<WB, COND>;
-    *dir0 = w16 ? (void*)k_dir_tma<WB, true, true> : (void*)k_dir_tma<WB, true, false>;
-    *dir = w16 ? (void*)k_dir_tma<WB, false, true> : (void*)k_dir_tma<WB, false, false>;
+    *upd = (void*)k_update_tma<WB>;
+    *dir0 = w16 ? (void*)k_dir_tma<WB, true, true, false> : (void*)k_dir_tma<WB, true, false, false>;
+    *dir = w16 ? (void*)k_dir_tma<WB, false, true, COND> : (void*)k_dir_tma<WB, false, false, COND>;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_update_tma<WB, COND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
-        cudaFuncSetAttribute(k_dir_tma<WB, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
-        cudaFuncSetAttribute(k_dir_tma<WB, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
-        cudaFuncSetAttribute(k_dir_tma<WB, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
-        cudaFuncSetAttribute(k_dir_tma<WB, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
+        const void* fs[] = {(void*)k_update_tma<WB>, (void*)k_dir_tma<WB, true, true, false>,
+                            (void*)k_dir_tma<WB, true, false, false>, (void*)k_dir_tma<WB, false, true, true>,
+                            (void*)k_dir_tma<WB, false, false, true>, (void*)k_dir_tma<WB, false, true, false>,
+                            (void*)k_dir_tma<WB, false, false, false>};
+        for (const void* f : fs) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTmSmemMax);
         attr = true;
     }
 }
@@ -887,15 +916,16 @@ static void pick_tma_wb(int wb, bool w16, void** upd, void** dir0, void** dir)
 template <int WB, bool COND>
 static void pick_v4(void** upd, void** dir0, void** dir)
 {
-    *upd = (void*)k_update_v4<WB, COND>;
-    *dir0 = (void*)k_dir_v4<WB, true>;
-    *dir = (void*)k_dir_v4<WB, false>;
+    *upd = (void*)k_update_v4<WB>;
+    *dir0 = (void*)k_dir_v4<WB, true, false>;
+    *dir = (void*)k_dir_v4<WB, false, COND>;
 }
 
 template <bool COND>
 static void pick_v4_wb(int wb, void** upd, void** dir0, void** dir)
 {
-    if (wb <= 8) pick_v4<8, COND>(upd, dir0, dir);
+    if (wb <= 0) pick_v4<0, COND>(upd, dir0, dir);
+    else if (wb <= 8) pick_v4<8, COND>(upd, dir0, dir);
     else if (wb <= 16) pick_v4<16, COND>(upd, dir0, dir);
     else if (wb <= 32) pick_v4<32, COND>(upd, dir0, dir);
     else if (wb <= 48) pick_v4<48, COND>(upd, dir0, dir);
@@ -915,7 +945,7 @@ void cg_kernels(int wb, bool fp32, bool cond, int form, bool w16, void** init, v
             else pick_tma_wb<false>(wb, w16, upd, dir0, dir);
             *smem_upd = kTmSmemMax;
             *smem_dir = kTmSmemMax;
-        } else if (wb > 0) {
+        } else {   // every FP32 width, 0 included: row-parallel float4, reductions without tails
             if (cond) pick_v4_wb<true>(wb, upd, dir0, dir);
             else pick_v4_wb<false>(wb, upd, dir0, dir);
         }
@@ -933,10 +963,11 @@ cudaError_t cg_set_wait_test(int mask, long long cycles)
 
 int tma_block_threads() { return kTmThreads; }
 
-void tma_shape(int n, int sms, int ncols, int cols_per_box, int nvec, int* grid, int* ring_bytes, int* smem)
+void tma_shape(int n, int sms, int ncols, int cols_per_box, int nvec, bool allow_pair, int* grid, int* ring_bytes,
+               int* smem)
 {
     const int stage = (ncols + cols_per_box - 1) / cols_per_box * kTmBoxBytes + nvec * kTmVecBytes;
-    const int pair = stage <= 40 * 1024;
+    const int pair = allow_pair && stage <= 40 * 1024;
     *ring_bytes = pair ? kTmRingPair : kTmRingMax;
     *smem = *ring_bytes + 1024;
     const int ntiles = (n + kTmTile - 1) / kTmTile;

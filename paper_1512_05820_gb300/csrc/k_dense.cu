@@ -637,6 +637,29 @@ __global__ void __launch_bounds__(kBlock) k_chol(const double* __restrict__ G, i
     }
 }
 
+// M = R^{-1} R^{-T} (w x w of st->w, row stride kWMax; R^{-1} upper triangular, row stride
+// kWMax): the operator of the reduced solve mu = M c that every augmented direction takes
+// (Section 4.3: the stage-one factor reused), formed once per solve so a direction pass
+// needs one matrix-vector product instead of two triangular solves.
+__global__ void __launch_bounds__(kBlock) k_mu_matrix(const double* __restrict__ Rinv, const DevState* st,
+                                                      double* __restrict__ M)
+{
+    const int w = st->w;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < w * w; e += gridDim.x * blockDim.x) {
+        const int a = e / w, b = e % w;
+        const int k0 = a > b ? a : b;   // R^{-1}[a][k] R^{-1}[b][k] vanish below the diagonal
+        double v = 0.0;
+        for (int k = k0; k < w; ++k) v += Rinv[(size_t)a * kWMax + k] * Rinv[(size_t)b * kWMax + k];
+        M[(size_t)a * kWMax + b] = v;
+    }
+}
+
+cudaError_t launch_mu_matrix(const double* Rinv, const DevState* st, double* M, cudaStream_t str)
+{
+    k_mu_matrix<<<(kWMax * kWMax + kBlock - 1) / kBlock, kBlock, 0, str>>>(Rinv, st, M);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str,
                         int w_dim, int truncate)
 {

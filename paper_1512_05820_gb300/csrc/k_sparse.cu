@@ -69,8 +69,10 @@ __global__ void __launch_bounds__(kBlock) k_spmv_plain(const int32_t* __restrict
 }
 
 // CG product: q = A p and gamma = (A p, p); the last block forms alpha = (r, z)/gamma and
-// flags a breakdown when gamma is not positive (the matrix is then not SPD).
-template <int L, typename T>
+// flags a breakdown when gamma is not positive (the matrix is then not SPD). CHAIN (the FP32
+// inner loop): every block stores its share of gamma instead and the update pass forms
+// alpha (chain_alpha).
+template <int L, typename T, bool CHAIN>
 __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__ pd, const T* __restrict__ p,
                                                     T* __restrict__ q, double* __restrict__ partials,
                                                     unsigned int* counter, DevState* st)
@@ -97,9 +99,13 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
             dot += s * p[row];
         }
     }
-    double acc[1] = {double(dot)};
-    __shared__ double tot[1];
-    if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) cg_product_finish(st, tot[0]);
+    if constexpr (CHAIN) {
+        chain_store_gamma(double(dot), partials);
+    } else {
+        double acc[1] = {double(dot)};
+        __shared__ double tot[1];
+        if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) cg_product_finish(st, tot[0]);
+    }
 }
 
 // True residual r = b - A x in FP64 and its norm. The last block takes the outer decision:
@@ -265,8 +271,8 @@ cudaError_t launch_spmv_plain32(int L, const int32_t* rp, const int32_t* col, co
 void* kernel_spmv_cg(int L, bool fp32)
 {
     void* f = nullptr;
-    if (fp32) { PODCG_LANES(L, f = (void*)k_spmv_cg<LL, float>); }
-    else { PODCG_LANES(L, f = (void*)k_spmv_cg<LL, double>); }
+    if (fp32) { PODCG_LANES(L, f = (void*)k_spmv_cg<LL, float, true>); }
+    else { PODCG_LANES(L, f = (void*)k_spmv_cg<LL, double, false>); }
     return f;
 }
 

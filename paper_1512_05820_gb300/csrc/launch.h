@@ -60,6 +60,8 @@ cudaError_t launch_stage1(int wb, const ProbDesc* pd, int n, const double* W, co
 cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, double rank_tol, int w_max, double* C,
                            double* sigma2, DevState* st, double* Vprev, int prev_s, cudaStream_t str,
                            double energy_y = 1.0, int y_max = 0);
+// M = R^{-1} R^{-T} of the current basis (st->w), row stride kWMax (k_dense.cu)
+cudaError_t launch_mu_matrix(const double* Rinv, const DevState* st, double* M, cudaStream_t str);
 cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, int want_cond, cudaStream_t str,
                         int w_dim = -1, int truncate = 0);
 cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
@@ -78,9 +80,10 @@ void cg_kernels(int wb, bool fp32, bool cond, int form, bool w16, void** init, v
                 int* smem_upd, int* smem_dir);
 int tma_block_threads();
 // launch shape of a TMA-staged pass over ncols panel columns (cols_per_box per box: 8 FP32,
-// 16 fp16) and nvec vector tiles per stage: grid, ring bytes (a kernel argument) and the
-// dynamic shared memory
-void tma_shape(int n, int sms, int ncols, int cols_per_box, int nvec, int* grid, int* ring_bytes, int* smem);
+// 16 fp16) and nvec vector tiles per stage (two CTAs per SM when allow_pair and the stage is
+// small): grid, ring bytes (a kernel argument) and the dynamic shared memory
+void tma_shape(int n, int sms, int ncols, int cols_per_box, int nvec, bool allow_pair, int* grid, int* ring_bytes,
+               int* smem);
 // W16 = the 16-bit copy of the FP32 basis W32 with power-of-two column scales, and W32
 // replaced by its exact dequantised value (k_cg.cu); cmax: kWMax words of scratch
 cudaError_t launch_quant16(int n, int ld, float* W32, __half* W16, unsigned int* cmax, float* wscale,

@@ -164,10 +164,14 @@ class PodCG:
         ms = (ctypes.c_float * 6)()
         _check(self.L.pod_cg_tuning(self.h, ctypes.byref(L), ms), self.h)
         forms = (ctypes.c_int * 6)()
-        pms = (ctypes.c_float * 12)()
+        pms = (ctypes.c_float * 24)()
         _check(self.L.pod_cg_proj_tuning(self.h, forms, pms), self.h)
-        names = {-1: None, 0: "direct", 1: "staged"}
-        proj = {f"w<={wb}": {"form": names[forms[b]], "ms_direct": pms[2 * b], "ms_staged": pms[2 * b + 1]}
+
+        def name(f, bit):
+            return "staged" if f & bit else "direct"
+        proj = {f"w<={wb}": {"update": name(forms[b], 1), "direction": name(forms[b], 2),
+                             "ms_update_direct": pms[4 * b], "ms_direction_direct": pms[4 * b + 1],
+                             "ms_update_staged": pms[4 * b + 2], "ms_direction_staged": pms[4 * b + 3]}
                 for b, wb in enumerate((0, 8, 16, 32, 48, 64)) if forms[b] >= 0}
         return {"spmv_lanes": L.value, "lane_ms": {str(1 << k): ms[k] for k in range(6)}, "projection": proj}
 
