@@ -80,7 +80,9 @@ typedef struct {
                             one only); at the cap x_out holds the k_max-th iterate */
     int    max_refine;   /* FP64: residual-replacement restarts; MIXED: FP64 refinement steps */
     int    precision;    /* POD_CG_FP64, or POD_CG_MIXED (FP32 inner CG, FP64 refinement) */
-    double inner_tol;    /* MIXED: each inner solve reduces its residual by this factor */
+    double inner_tol;    /* MIXED: each inner solve reduces its residual by this factor, or
+                            only by half the factor that reaches the tolerance when that is
+                            larger (the last refinement step stops where it is needed) */
     int    use_tc_gram;  /* MIXED only (else ERR_ARG at create): stage-one Gram W^T [AW, b] of
                             the FP32 panels on the tensor cores with split-bf16 products
                             (pod_cg_gram_tc); 0 = CUDA cores. Solves that run stage two keep

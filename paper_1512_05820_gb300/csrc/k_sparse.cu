@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
 //   FP64 mode (mixed = 0): stop when ||r|| <= tol ||b|| or on an error status; otherwise
 //     restart the CG from this residual (residual replacement), at most max_refine times.
 //   Mixed mode (mixed = 1): same test; otherwise it is the start of the next refinement
-//     step, whose inner solve must reduce ||r|| by inner_tol.
+//     step, whose inner solve must reduce ||r|| by inner_tol, or by half the factor that
+//     reaches the tolerance when that is larger.
 // The decision is published to the graph's outer while-loop through `h_outer`.
 template <int L, bool COND>
 __global__ void __launch_bounds__(kBlock) k_residual(const ProbDesc* __restrict__ pd, const double* __restrict__ x, double* __restrict__ r,
@@ -153,7 +154,10 @@ __global__ void __launch_bounds__(kBlock) k_residual(const ProbDesc* __restrict_
             if (mixed) {
                 st->rr_outer = rt;
                 st->rnorm = sqrt(rt);
-                st->tol2_in = inner_tol * inner_tol;   // the inner solve sees r/||r||
+                // the inner solve sees r/||r||: it reduces that by inner_tol, or only by half of
+                // the factor that reaches tol ||b|| when that is the larger (the last refinement
+                // step stops where the tolerance needs it to)
+                st->tol2_in = fmax(inner_tol * inner_tol, 0.25 * st->tol2 / rt);
             }
         }
         st->outer_done = stop;
