@@ -2,12 +2,16 @@
 
 ``SequenceSolve.apply(theta, B, problem)`` returns X with X[j] = A_j(theta)^{-1} B[j] for
 the diffusion operator A_j(theta) = A(exp(theta)) + diag(shift_j). Forward: the matrices
-are assembled on the GPU, the systems solved in order with POD recycling (the solver keeps
-each system's basis W_j, A_j W_j and stage-one Gram), and the solutions are checkpointed.
-Backward, for an incoming gradient G = dL/dX: adjoint solves A_j lambda_j = G[j] that
-reuse W_j (A_j is symmetric), then one fused edge-wise pass
-dL/dtheta = -sum_j lambda_j^T (dA_j/dtheta) x_j; dL/dB[j] = lambda_j.
-All arithmetic runs in the library's kernels; torch holds the tensors.
+are assembled on the GPU, the systems solved in order with POD recycling, and the solutions
+X are checkpointed (the only per-system state kept). Backward, for an incoming gradient
+G = dL/dX: adjoint solves A_j lambda_j = G[j] with the recycled basis of system j (A_j is
+symmetric), then one fused edge-wise pass dL/dtheta = -sum_j lambda_j^T (dA_j/dtheta) x_j;
+dL/dB[j] = lambda_j. With ``problem.checkpoint`` (the default) the backward recomputes
+W_j, A_j W_j and the stage-one factor from the checkpointed solutions: W_j is the POD of
+the same snapshot set the forward solve of system j used (the solutions before it, at most
+s_max), so memory stays at X. Without it the forward handle keeps every system's W_j,
+A_j W_j and stage-one Gram (pod_cg_solve_adjoint). All arithmetic runs in the library's
+kernels; torch holds the tensors.
 """
 from __future__ import annotations
 
@@ -32,6 +36,7 @@ class DiffusionProblem:
     w_max: int = 32
     s_max: int = 40
     energy: float = 0.9999
+    checkpoint: bool = True
 
     @property
     def n(self) -> int:
@@ -76,7 +81,8 @@ class SequenceSolve(torch.autograd.Function):
     def forward(ctx, theta, B, problem: DiffusionProblem):
         theta = theta.detach().contiguous()
         p, n = B.shape
-        solver = PodCG(n, w_max=problem.w_max, s_max=problem.s_max, energy=problem.energy, keep_factors=p)
+        keep = 0 if problem.checkpoint else p
+        solver = PodCG(n, w_max=problem.w_max, s_max=problem.s_max, energy=problem.energy, keep_factors=keep)
         val = torch.empty(problem.col.numel(), dtype=torch.float64, device=B.device)
         X = torch.empty_like(B)
         sysids = []
@@ -87,7 +93,12 @@ class SequenceSolve(torch.autograd.Function):
             solver.add_snapshots(x)
             sysids.append(st["system_id"])
         ctx.save_for_backward(theta, X)
-        ctx.problem, ctx.solver, ctx.sysids = problem, solver, sysids
+        ctx.problem, ctx.sysids = problem, sysids
+        if problem.checkpoint:
+            solver.close()
+            ctx.solver = None
+        else:
+            ctx.solver = solver
         ctx.stats = None
         return X
 
@@ -99,10 +110,21 @@ class SequenceSolve(torch.autograd.Function):
         Lam = torch.empty_like(X)
         val = torch.empty(problem.col.numel(), dtype=torch.float64, device=X.device)
         gX = gX.contiguous()
-        for j in reversed(range(p)):
-            assemble(problem, theta, j, out=val)
-            A = DeviceCSR(problem.row_ptr, problem.col, val)
-            solver.solve_adjoint(ctx.sysids[j], A, gX[j], problem.tol, lam_out=Lam[j])
+        if problem.checkpoint:
+            # W_j recomputed: the POD of the snapshots the forward solve of system j held
+            solver = PodCG(n, w_max=problem.w_max, s_max=problem.s_max, energy=problem.energy)
+            for j in reversed(range(p)):
+                assemble(problem, theta, j, out=val)
+                A = DeviceCSR(problem.row_ptr, problem.col, val)
+                solver.clear_snapshots()
+                if j > 0:
+                    solver.add_snapshots(X[max(0, j - problem.s_max):j].t())
+                solver.solve(A, gX[j], problem.tol, x_out=Lam[j])
+        else:
+            for j in reversed(range(p)):
+                assemble(problem, theta, j, out=val)
+                A = DeviceCSR(problem.row_ptr, problem.col, val)
+                solver.solve_adjoint(ctx.sysids[j], A, gX[j], problem.tol, lam_out=Lam[j])
         grad_theta = theta_grad(problem, theta, Lam, X)
         solver.close()
         return grad_theta, Lam, None

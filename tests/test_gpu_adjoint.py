@@ -126,3 +126,54 @@ def test_theta_grad_kernel_vs_oracle(dev, orc, shape):
     # 2 k_max * 2|lam|_max * 2|x|_max in magnitude
     bound = 1e-13 * (6 * 3 * 8 * np.exp(np.abs(theta)).max() * np.abs(lam).max() * np.abs(xs).max())
     assert np.max(np.abs(g - ref)) <= bound, np.max(np.abs(g - ref))
+
+
+def test_checkpointed_backward_matches_kept_factors(dev):
+    """16^3 grid, 5 systems, window 3: the default backward recomputes each W_j, A_j W_j and
+    stage-one factor from the checkpointed solutions; the gradient equals the one from the
+    forward handle's kept factors (pod_cg_solve_adjoint) to the solves' accuracy (1e-13)."""
+    import dataclasses
+    op, theta, shifts, B, c, prob = _problem(16, 5, 4, dev)
+    prob = dataclasses.replace(prob, s_max=3)
+    _, g1, gB1, X1 = _gpu_loss_grad(theta, B, c, prob, dev)
+    _, g2, gB2, X2 = _gpu_loss_grad(theta, B, c, dataclasses.replace(prob, checkpoint=False), dev)
+    assert np.array_equal(X1, X2)
+    assert np.max(np.abs(g1 - g2)) <= 1e-10 * np.max(np.abs(g2))
+    assert np.max(np.abs(gB1 - gB2)) <= 1e-10 * np.max(np.abs(gB2))
+
+
+def test_gradient_full_size_96_central_differences(dev):
+    """The differentiation workload at full grid size: 96^3 cells (n = 884,736), theta ~
+    N(0, 0.5^2), 8 systems of the sequence, loss sum_j c^T x_j, checkpointed backward.
+    dL/dtheta at the three cells of largest |g| among 64 seeded random ones against the
+    fourth-order central difference (h = 1e-3), solves at 1e-13: norm-wise relative error
+    <= 1e-6."""
+    from paper_1512_05820_gb300.adjoint import DiffusionProblem, solve_sequence
+    seq = wl.diffusion3d_theta(m=96, p=8)
+    r = seq.recipe
+    shifts = np.stack([0.01 * (j + 1) * r["u"] for j in range(seq.p)])
+    B = torch.as_tensor(np.stack([b for _, _, b in seq.systems()]), device=dev)
+    c = torch.as_tensor(r["c"], device=dev)
+    prob = DiffusionProblem.from_operator(seq.op, shifts=shifts, device=dev, tol=1e-13, w_max=32, s_max=40)
+    th = torch.as_tensor(r["theta"], device=dev).requires_grad_(True)
+    X = solve_sequence(th, B, prob)
+    (X * c).sum().backward()
+    g = th.grad.cpu().numpy()
+
+    def L(theta):
+        with torch.no_grad():
+            return float((solve_sequence(torch.as_tensor(theta, device=dev), B, prob) * c).sum())
+
+    rng = np.random.default_rng(5)
+    cand = rng.choice(seq.n, size=64, replace=False)
+    cells = cand[np.argsort(-np.abs(g[cand]))[:3]]
+    h = 1e-3
+    fds = []
+    for cc in cells:
+        e = np.zeros(seq.n)
+        e[cc] = h
+        th0 = r["theta"]
+        fds.append((-L(th0 + 2 * e) + 8 * L(th0 + e) - 8 * L(th0 - e) + L(th0 - 2 * e)) / (12 * h))
+    err = np.linalg.norm(np.array(fds) - g[cells]) / np.linalg.norm(g[cells])
+    print(f"96^3, 8 systems: gradient at cells {list(cells)}, norm-wise error vs finite differences {err:.2e}")
+    assert err <= 1e-6
