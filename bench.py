@@ -350,6 +350,16 @@ def batch_section(args, rank=0, world=1):
     total = int(total)
     ok = int(combine(0.0, float(sum(1 for s in stats if s["status"] == "ok")))[1])
     info = bs.info()
+    # algorithmic bytes of every FP32 inner iteration (SpMV 8 nnz + 4(n+1) + 8n; update: d, r
+    # read and written, p, q, M^{-1}, A W read: 28n + 4wn; direction: M^{-1}, r, W read, p
+    # read and written: 16n + 4wn); setup, POD and FP64 residuals are not counted
+    it_bytes, k = 0.0, 0
+    for sq in seqs:
+        for _ in range(sq.p):
+            st_ = stats[k]
+            it_bytes += st_["iters"] * (8 * sq.nnz + 4 * (sq.n + 1) + 52 * sq.n + 8 * st_["w"] * sq.n)
+            k += 1
+    peak, _ = peaks()
     out = {"workload": f"{len(all_seqs)} sequences x {all_seqs[0].p} systems, n in [2k, 260k] log-uniform, 2D/3D",
            "rows_per_layer": int(sum(s.n for s in all_seqs)), "systems": total, "converged": ok,
            "sharding": "independent sequences, no collective" if world > 1 else "single GPU",
@@ -357,7 +367,10 @@ def batch_section(args, rank=0, world=1):
            "max_final_relres": max(s["final_relres"] for s in stats),
            "mean_iters": float(np.mean([s["iters"] for s in stats])),
            "cluster": info["cluster"], "workers": info["workers"],
-           "autotune_ms": {str(k): v for k, v in info["tune_ms"].items()}, "setup_s": tune_s}
+           "autotune_ms": {str(k): v for k, v in info["tune_ms"].items()}, "tiles": info["tiles"], "setup_s": tune_s,
+           "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": it_bytes / (ms_local / 1e3) / 1e9, "peak": peak,
+                        "unit": "GB/s", "frac": it_bytes / (ms_local / 1e3) / 1e9 / peak,
+                        "bytes": "inner FP32 iterations only (lower bound on the bytes moved)"}}
     out["err_vs_fp64_oracle"] = batch_oracle_error(seqs, systems, bs)
     bs.close()
     if world > 1:

@@ -404,7 +404,8 @@ typedef struct {
  * solutions (Algorithm 4), stage one (Algorithm 2), FP32 augmented PCG (Algorithm 1)
  * inside FP64 refinement. cfg supplies k_max, max_refine, inner_tol, rank_tol (NULL =
  * defaults). cluster: CTAs per worker, 1, 2, 4 or 8, or 0 to autotune (each candidate
- * 2, 4, 8 runs the whole batch once; the fastest is kept). The handle owns the workspace.
+ * 2, 4, 8 runs the whole batch once; the fastest is kept; then the inner loop's tiles are
+ * tuned per size class, pod_cg_batch_tiles). The handle owns the workspace.
  * Errors: ERR_ARG (a bad sequence is named in the message), ERR_OOM, ERR_CUDA. */
 pod_cg_status pod_cg_batch_create(const pod_cg_batch_seq* seqs /* host, nseq */, int nseq,
                                   const pod_cg_config* cfg, int cluster, void* cuda_stream,
@@ -423,6 +424,21 @@ pod_cg_status pod_cg_batch_solve(pod_cg_batch_t* h, pod_cg_batch_sysstat* stats,
 pod_cg_status pod_cg_batch_info(const pod_cg_batch_t* h, int* cluster, int* workers, float* tune_ms3);
 const char* pod_cg_batch_last_error(const pod_cg_batch_t* h);
 pod_cg_status pod_cg_batch_destroy(pod_cg_batch_t* h);
+
+/* Tile autotuner record of a batch created with cluster = 0 (no counterpart in the paper):
+ * per size class (n < 16,384; < 65,536; larger), the lanes per CSR row of the inner CG
+ * product (lanes3) and the rows per thread of the update and direction passes (rows3: 1, or
+ * 4 as float4 for sequences with n a multiple of 4) chosen by running the whole batch once
+ * per candidate (lanes, rows) = (1, 1), (1, 4), (2, 4), (4, 4), each sequence timing its own
+ * solve on the device; ms12 (3 x 4) the summed device time of each class per candidate. All
+ * pointers host, each may be NULL. Before tuning, or with a forced cluster size: 1 and 1. */
+pod_cg_status pod_cg_batch_tiles(const pod_cg_batch_t* h, int* lanes3, int* rows3, float* ms12);
+
+/* Set the inner loop's tiles per size class instead of the autotuner's choice
+ * (no counterpart in the paper): lanes3[3] in {1, 2, 4, 8}, rows3[3] in {1, 4} (4 applies to
+ * sequences with n a multiple of 4; others use 1). Host arrays. Takes effect from the next
+ * pod_cg_batch_solve. Errors: ERR_ARG, ERR_CUDA. */
+pod_cg_status pod_cg_batch_set_tiles(pod_cg_batch_t* h, const int* lanes3, const int* rows3);
 
 /* --------------------------------------- differentiation through a sequence of solves */
 

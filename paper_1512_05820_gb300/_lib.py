@@ -15,7 +15,7 @@ EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_l
            "pod_cg_get_basis", "pod_cg_get_stage3_basis", "pod_cg_time_kernels", "pod_cg_tuning", "pod_cg_proj_tuning", "pod_cg_spmv", "pod_cg_spmm", "pod_cg_gram_workspace", "pod_cg_gram_workspace_for", "pod_cg_gram", "pod_cg_gram_noalloc", "pod_cg_debug_wait_timeout",
            "pod_cg_gram_tc_workspace", "pod_cg_gram_tc", "pod_cg_diffusion_assemble",
            "pod_cg_diffusion_theta_grad", "pod_cg_batch_create", "pod_cg_batch_solve", "pod_cg_batch_info",
-           "pod_cg_batch_last_error", "pod_cg_batch_destroy",
+           "pod_cg_batch_last_error", "pod_cg_batch_destroy", "pod_cg_batch_tiles", "pod_cg_batch_set_tiles",
            "pod_cg_pod"]
 
 
@@ -117,6 +117,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_batch_last_error.argtypes = [vp]
     L.pod_cg_batch_last_error.restype = ctypes.c_char_p
     L.pod_cg_batch_destroy.argtypes = [vp]
+    L.pod_cg_batch_tiles.argtypes = [vp, P(ci), P(ci), P(ctypes.c_float)]
+    L.pod_cg_batch_set_tiles.argtypes = [vp, P(ci), P(ci)]
     L.pod_cg_pod.argtypes = [ci, ci, vp, cd, cd, ci, vp, vp, P(ci), vp, sz, vp]
     for name in EXPORTS:
         if name not in ("pod_cg_last_error", "pod_cg_gram_workspace", "pod_cg_gram_workspace_for",

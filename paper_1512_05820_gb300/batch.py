@@ -55,6 +55,13 @@ class BatchSolver:
             raise RuntimeError(self.L.pod_cg_batch_last_error(self.h).decode())
         return out, ms.value
 
+    def set_tiles(self, lanes: int, rows: int):
+        """The same inner-loop tiles for every size class (instead of the autotuner's)."""
+        a, b = (ctypes.c_int * 3)(lanes, lanes, lanes), (ctypes.c_int * 3)(rows, rows, rows)
+        rc = self.L.pod_cg_batch_set_tiles(self.h, a, b)
+        if rc != 0:
+            raise RuntimeError(self.L.pod_cg_batch_last_error(self.h).decode())
+
     def solutions(self, i: int) -> torch.Tensor:
         return self._keep[i][4]
 
@@ -62,7 +69,14 @@ class BatchSolver:
         cl, wk = ctypes.c_int(0), ctypes.c_int(0)
         tm = (ctypes.c_float * 3)()
         self.L.pod_cg_batch_info(self.h, ctypes.byref(cl), ctypes.byref(wk), tm)
-        return {"cluster": cl.value, "workers": wk.value, "tune_ms": {2: tm[0], 4: tm[1], 8: tm[2]}}
+        lanes, rows, ms = (ctypes.c_int * 3)(), (ctypes.c_int * 3)(), (ctypes.c_float * 12)()
+        self.L.pod_cg_batch_tiles(self.h, lanes, rows, ms)
+        cands = [(1, 1), (1, 4), (2, 4), (4, 4)]
+        classes = ["n<16k", "16k<=n<64k", "n>=64k"]
+        tiles = {classes[c]: {"spmv_lanes": lanes[c], "rows_per_thread": rows[c],
+                              "ms": {f"lanes{a}_rows{b}": ms[4 * c + k] for k, (a, b) in enumerate(cands)}}
+                 for c in range(3)}
+        return {"cluster": cl.value, "workers": wk.value, "tune_ms": {2: tm[0], 4: tm[1], 8: tm[2]}, "tiles": tiles}
 
     def close(self):
         if getattr(self, "h", None):

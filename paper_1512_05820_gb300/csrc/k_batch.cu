@@ -54,6 +54,11 @@ struct BatchSeqDev {
     float* val32;        // nnz
     double* r64;         // n
     float *r, *p32, *q, *d, *dinv;   // n each
+    // tiles of the inner CG loop (chosen per size class by the autotuner): lanes per row of
+    // the CSR product (1, 2, 4 or 8) and rows per thread of the update and direction passes
+    // (1, or 4 as float4 when n is a multiple of 4)
+    int lanes, vec;
+    unsigned long long* t_ns;   // device time of this sequence's solve (global timer, ns)
     // per-system statistics
     int* st_status;
     int* st_iters;
@@ -233,6 +238,117 @@ __device__ void apply_rinv_small(BatchSmem& sm, int w, int off)
     __syncthreads();
 }
 
+// q = A p (FP32) and (A p, p): groups of q.lanes consecutive threads take one row, their
+// lanes striding through its entries, then a shuffle tree; loop bounds are uniform per warp
+// so the shuffles never diverge.
+__device__ float batch_spmv(const Team& T, const BatchSeqDev& q, int n)
+{
+    const int L = q.lanes;
+    float dot = 0.0f;
+    if (L <= 1) {
+        for (int i = T.tid; i < n; i += T.nthr) {
+            float s = 0.0f;
+            for (int k = q.rp[i]; k < q.rp[i + 1]; ++k) s += q.val32[k] * q.p32[q.col[k]];
+            q.q[i] = s;
+            dot += s * q.p32[i];
+        }
+        return dot;
+    }
+    const int lane = T.tid & 31, gl = lane & (L - 1);
+    const int gpw = 32 / L;                 // row groups per warp
+    const int wg = T.tid >> 5, nw = T.nthr >> 5;
+    for (int r0 = wg * gpw; r0 < n; r0 += nw * gpw) {
+        const int row = r0 + lane / L;
+        float s = 0.0f;
+        if (row < n)
+            for (int k = q.rp[row] + gl; k < q.rp[row + 1]; k += L) s += q.val32[k] * q.p32[q.col[k]];
+        for (int o = L / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (gl == 0 && row < n) {
+            q.q[row] = s;
+            dot += s * q.p32[row];
+        }
+    }
+    return dot;
+}
+
+// Update pass of one inner iteration over V rows per thread (V = 4: float4 loads of every
+// vector and basis column; n a multiple of 4): d += alpha p, r -= alpha q, z = M^{-1} r,
+// (r, z), ||r||^2 and c = (A W)^T z, summed into the thread's registers.
+template <int V>
+__device__ void batch_update(const Team& T, const BatchSeqDev& q, int n, int w, float alpha, float (&cl)[kBW],
+                             float& rho_l, float& rr_l)
+{
+    if constexpr (V == 1) {
+        for (int i = T.tid; i < n; i += T.nthr) {
+            q.d[i] += alpha * q.p32[i];
+            const float ri = q.r[i] - alpha * q.q[i];
+            q.r[i] = ri;
+            const float zi = q.dinv[i] * ri;
+            rho_l += ri * zi;
+            rr_l += ri * ri;
+#pragma unroll
+            for (int c = 0; c < kBW; ++c)
+                if (c < w) cl[c] += q.AW[(size_t)c * n + i] * zi;
+        }
+    } else {
+        const int n4 = n >> 2;
+        for (int g = T.tid; g < n4; g += T.nthr) {
+            float4 d4 = reinterpret_cast<const float4*>(q.d)[g];
+            const float4 p4 = reinterpret_cast<const float4*>(q.p32)[g];
+            float4 r4 = reinterpret_cast<const float4*>(q.r)[g];
+            const float4 q4 = reinterpret_cast<const float4*>(q.q)[g];
+            const float4 m4 = reinterpret_cast<const float4*>(q.dinv)[g];
+            d4.x += alpha * p4.x; d4.y += alpha * p4.y; d4.z += alpha * p4.z; d4.w += alpha * p4.w;
+            r4.x -= alpha * q4.x; r4.y -= alpha * q4.y; r4.z -= alpha * q4.z; r4.w -= alpha * q4.w;
+            reinterpret_cast<float4*>(q.d)[g] = d4;
+            reinterpret_cast<float4*>(q.r)[g] = r4;
+            const float4 z4 = make_float4(m4.x * r4.x, m4.y * r4.y, m4.z * r4.z, m4.w * r4.w);
+            rho_l += r4.x * z4.x + r4.y * z4.y + r4.z * z4.z + r4.w * z4.w;
+            rr_l += r4.x * r4.x + r4.y * r4.y + r4.z * r4.z + r4.w * r4.w;
+#pragma unroll
+            for (int c = 0; c < kBW; ++c) {
+                if (c < w) {
+                    const float4 a = reinterpret_cast<const float4*>(q.AW + (size_t)c * n)[g];
+                    cl[c] += a.x * z4.x + a.y * z4.y + a.z * z4.z + a.w * z4.w;
+                }
+            }
+        }
+    }
+}
+
+// Direction pass: p = M^{-1} r + beta p - W mu, V rows per thread as batch_update.
+template <int V>
+__device__ void batch_direction(const Team& T, const BatchSmem& sm, const BatchSeqDev& q, int n, int w, float beta)
+{
+    if constexpr (V == 1) {
+        for (int i = T.tid; i < n; i += T.nthr) {
+            float v = q.dinv[i] * q.r[i] + beta * q.p32[i];
+#pragma unroll
+            for (int c = 0; c < kBW; ++c)
+                if (c < w) v -= q.W[(size_t)c * n + i] * sm.muf[c];
+            q.p32[i] = v;
+        }
+    } else {
+        const int n4 = n >> 2;
+        for (int g = T.tid; g < n4; g += T.nthr) {
+            const float4 r4 = reinterpret_cast<const float4*>(q.r)[g];
+            const float4 m4 = reinterpret_cast<const float4*>(q.dinv)[g];
+            const float4 p4 = reinterpret_cast<const float4*>(q.p32)[g];
+            float4 v = make_float4(m4.x * r4.x + beta * p4.x, m4.y * r4.y + beta * p4.y, m4.z * r4.z + beta * p4.z,
+                                   m4.w * r4.w + beta * p4.w);
+#pragma unroll
+            for (int c = 0; c < kBW; ++c) {
+                if (c < w) {
+                    const float4 a = reinterpret_cast<const float4*>(q.W + (size_t)c * n)[g];
+                    const float m = sm.muf[c];
+                    v.x -= a.x * m; v.y -= a.y * m; v.z -= a.z * m; v.w -= a.w * m;
+                }
+            }
+            reinterpret_cast<float4*>(q.p32)[g] = v;
+        }
+    }
+}
+
 __device__ void solve_sequence(Team& T, BatchSmem& sm, const BatchSeqDev& q, int k_max, int max_refine,
                                double inner_tol, double rank_tol)
 {
@@ -391,7 +507,9 @@ __device__ void solve_sequence(Team& T, BatchSmem& sm, const BatchSeqDev& q, int
             ++refine;
             // the FP32 inner solve works on r/||r|| (no underflow or overflow in FP32)
             const double rnorm = sqrt(rr_true), rinv = 1.0 / rnorm;
-            const double tol2_in = inner_tol * inner_tol;
+            // reduce r/||r|| by inner_tol, or only by half of the factor that reaches the
+            // tolerance when that is the larger (the last refinement step stops where needed)
+            const double tol2_in = fmax(inner_tol * inner_tol, 0.25 * tol2 / rr_true);
             // projection of the correction onto W: c = W^T r
             {
                 double acc[kBW];
@@ -458,16 +576,7 @@ __device__ void solve_sequence(Team& T, BatchSmem& sm, const BatchSeqDev& q, int
                 if (iters >= k_max) { status = 4; break; }
                 T.cl.sync();   // p complete
                 double acc1[1] = {0.0};
-                {
-                    float dot = 0.0f;
-                    for (int i = T.tid; i < n; i += T.nthr) {
-                        float s = 0.0f;
-                        for (int k = q.rp[i]; k < q.rp[i + 1]; ++k) s += q.val32[k] * q.p32[q.col[k]];
-                        q.q[i] = s;
-                        dot += s * q.p32[i];
-                    }
-                    acc1[0] = dot;
-                }
+                acc1[0] = batch_spmv(T, q, n);
                 team_sum<1>(T, sm, acc1, 1);
                 const double gamma = sm.tot[0];
                 if (!(gamma > 0.0) || !isfinite(gamma)) break;   // FP32 breakdown ends this inner pass
@@ -476,17 +585,8 @@ __device__ void solve_sequence(Team& T, BatchSmem& sm, const BatchSeqDev& q, int
 #pragma unroll
                 for (int c = 0; c < kBW; ++c) cl[c] = 0.0f;
                 float rho_l = 0.0f, rr_l = 0.0f;
-                for (int i = T.tid; i < n; i += T.nthr) {
-                    q.d[i] += alpha * q.p32[i];
-                    const float ri = q.r[i] - alpha * q.q[i];
-                    q.r[i] = ri;
-                    const float zi = q.dinv[i] * ri;
-                    rho_l += ri * zi;
-                    rr_l += ri * ri;
-#pragma unroll
-                    for (int c = 0; c < kBW; ++c)
-                        if (c < w) cl[c] += q.AW[(size_t)c * n + i] * zi;
-                }
+                if (q.vec == 4) batch_update<4>(T, q, n, w, alpha, cl, rho_l, rr_l);
+                else batch_update<1>(T, q, n, w, alpha, cl, rho_l, rr_l);
                 double acc[kBW + 2];
                 acc[0] = rho_l;
                 acc[1] = rr_l;
@@ -502,13 +602,8 @@ __device__ void solve_sequence(Team& T, BatchSmem& sm, const BatchSeqDev& q, int
                 inner_done = !(rr > tol2_in);
                 if (inner_done) break;
                 if (w > 0) apply_rinv_small(sm, w, 2);
-                for (int i = T.tid; i < n; i += T.nthr) {
-                    float v = q.dinv[i] * q.r[i] + beta * q.p32[i];
-#pragma unroll
-                    for (int c = 0; c < kBW; ++c)
-                        if (c < w) v -= q.W[(size_t)c * n + i] * sm.muf[c];
-                    q.p32[i] = v;
-                }
+                if (q.vec == 4) batch_direction<4>(T, sm, q, n, w, beta);
+                else batch_direction<1>(T, sm, q, n, w, beta);
             }
             for (int i = T.tid; i < n; i += T.nthr) x[i] += rnorm * double(q.d[i]);
             if (status != 0) break;
@@ -570,7 +665,12 @@ __global__ void __launch_bounds__(kBThreads, 1) k_batch(const BatchSeqDev* __res
         const int id = *T.cl.map_shared_rank(&sm.seq, 0);
         T.cl.sync();   // rank 0 may not take the next ticket before everyone read this one
         if (id >= nseq) break;
+        unsigned long long t0 = 0, t1 = 0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
         solve_sequence(T, sm, seqs[order[id]], k_max, max_refine, inner_tol, rank_tol);
+        T.cl.sync();
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        if (T.rank == 0 && threadIdx.x == 0 && seqs[order[id]].t_ns) *seqs[order[id]].t_ns = t1 - t0;
     }
     T.cl.sync();   // no CTA leaves while another may still read its shared memory
 }
@@ -623,6 +723,11 @@ int batch_max_clusters(int cluster)
 
 // ======================================================================== host side
 
+// Tile candidates of the batch autotuner: lanes per CSR row, rows per thread.
+constexpr int kBatchTileCands = 4;
+constexpr int kBatchTileLanes[kBatchTileCands] = {1, 1, 2, 4};
+constexpr int kBatchTileVec[kBatchTileCands] = {1, 4, 4, 4};
+
 struct pod_cg_batch_t {
     int nseq = 0, total_sys = 0;
     cudaStream_t stream = nullptr;
@@ -639,6 +744,9 @@ struct pod_cg_batch_t {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     std::vector<float> tune_ms;   // autotuner timings for cluster 2, 4, 8
+    unsigned long long* t_ns = nullptr;   // per-sequence solve time (device, nseq)
+    int tile_lanes[3] = {1, 1, 1}, tile_vec[3] = {1, 1, 1};   // per size class (n < 16k, < 64k, larger)
+    float tile_ms[3][kBatchTileCands] = {};                   // autotuner: per class, per candidate
     std::string err;
 };
 
@@ -681,6 +789,47 @@ pod_cg_status batch_run(pod_cg_batch_t* h, float* ms)
     if (e == cudaSuccess && ms) e = cudaEventElapsedTime(ms, h->e0, h->e1);
     if (e != cudaSuccess) return bfail(h, POD_CG_ERR_CUDA, std::string("batch solve: ") + cudaGetErrorString(e));
     return POD_CG_OK;
+}
+
+int size_class(int n) { return n < 16384 ? 0 : n < 65536 ? 1 : 2; }
+
+// Per-sequence tiles: the class's lanes, and 4 rows per thread only where n % 4 == 0.
+pod_cg_status batch_apply_tiles(pod_cg_batch_t* h, const int* lanes3, const int* vec3)
+{
+    for (auto& d : h->hseq) {
+        const int c = size_class(d.n);
+        d.lanes = lanes3[c];
+        d.vec = (vec3[c] == 4 && d.n % 4 == 0) ? 4 : 1;
+    }
+    cudaError_t e = cudaMemcpy(h->dseq, h->hseq.data(), sizeof(podcg::BatchSeqDev) * h->nseq, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bfail(h, POD_CG_ERR_CUDA, std::string("batch tiles: ") + cudaGetErrorString(e));
+    return POD_CG_OK;
+}
+
+// Tile autotuner: the whole batch runs once per candidate (lanes per row of the CSR product,
+// rows per thread of the update and direction passes), every sequence timing its own solve
+// on the device; each size class keeps the candidate with the least total time.
+pod_cg_status batch_tune_tiles(pod_cg_batch_t* h)
+{
+    std::vector<unsigned long long> t(h->nseq);
+    for (int k = 0; k < kBatchTileCands; ++k) {
+        const int lanes3[3] = {kBatchTileLanes[k], kBatchTileLanes[k], kBatchTileLanes[k]};
+        const int vec3[3] = {kBatchTileVec[k], kBatchTileVec[k], kBatchTileVec[k]};
+        pod_cg_status st = batch_apply_tiles(h, lanes3, vec3);
+        if (st == POD_CG_OK) st = batch_run(h, nullptr);
+        if (st != POD_CG_OK) return st;
+        cudaError_t e = cudaMemcpy(t.data(), h->t_ns, sizeof(unsigned long long) * h->nseq, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return bfail(h, POD_CG_ERR_CUDA, std::string("batch tiles: ") + cudaGetErrorString(e));
+        for (int i = 0; i < h->nseq; ++i) h->tile_ms[size_class(h->hseq[i].n)][k] += float(t[i] * 1e-6);
+    }
+    for (int c = 0; c < 3; ++c) {
+        int best = 0;
+        for (int k = 1; k < kBatchTileCands; ++k)
+            if (h->tile_ms[c][k] < h->tile_ms[c][best]) best = k;
+        h->tile_lanes[c] = kBatchTileLanes[best];
+        h->tile_vec[c] = kBatchTileVec[best];
+    }
+    return batch_apply_tiles(h, h->tile_lanes, h->tile_vec);
 }
 
 pod_cg_status batch_set_cluster(pod_cg_batch_t* h, int cl)
@@ -736,6 +885,7 @@ pod_cg_status pod_cg_batch_create(const pod_cg_batch_seq* seqs, int nseq, const 
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->dseq, sizeof(podcg::BatchSeqDev) * nseq);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->dorder, sizeof(int) * nseq);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->dticket, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->t_ns, sizeof(unsigned long long) * nseq);
     if (e == cudaSuccess) e = cudaEventCreate(&h->e0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->e1);
     if (e != cudaSuccess) {
@@ -766,6 +916,9 @@ pod_cg_status pod_cg_batch_create(const pod_cg_batch_seq* seqs, int nseq, const 
         d.q = (float*)take(4 * n);
         d.d = (float*)take(4 * n);
         d.dinv = (float*)take(4 * n);
+        d.lanes = 1;
+        d.vec = 1;
+        d.t_ns = h->t_ns + i;
         d.st_status = h->st_i + 0 * h->total_sys + sys_off;
         d.st_iters = h->st_i + 1 * h->total_sys + sys_off;
         d.st_refine = h->st_i + 2 * h->total_sys + sys_off;
@@ -809,6 +962,7 @@ pod_cg_status pod_cg_batch_create(const pod_cg_batch_seq* seqs, int nseq, const 
             if (st == POD_CG_OK && (best_cl == 0 || ms < best)) { best = ms; best_cl = cands[k]; }
         }
         if (st == POD_CG_OK) st = best_cl ? batch_set_cluster(h, best_cl) : bfail(h, POD_CG_ERR_CUDA, "no cluster size runs");
+        if (st == POD_CG_OK) st = batch_tune_tiles(h);
     }
     if (st != POD_CG_OK) {
         podcg::set_last_error(h->err);
@@ -856,6 +1010,33 @@ pod_cg_status pod_cg_batch_info(const pod_cg_batch_t* h, int* cluster, int* work
     return POD_CG_OK;
 }
 
+pod_cg_status pod_cg_batch_set_tiles(pod_cg_batch_t* h, const int* lanes3, const int* rows3)
+{
+    if (!h || !lanes3 || !rows3) return bfail(h, POD_CG_ERR_ARG, "pod_cg_batch_set_tiles: NULL argument");
+    for (int c = 0; c < 3; ++c) {
+        const int L = lanes3[c], r = rows3[c];
+        if (!(L == 1 || L == 2 || L == 4 || L == 8) || !(r == 1 || r == 4))
+            return bfail(h, POD_CG_ERR_ARG, "pod_cg_batch_set_tiles: lanes 1, 2, 4 or 8 and rows 1 or 4");
+    }
+    for (int c = 0; c < 3; ++c) {
+        h->tile_lanes[c] = lanes3[c];
+        h->tile_vec[c] = rows3[c];
+    }
+    return batch_apply_tiles(h, h->tile_lanes, h->tile_vec);
+}
+
+pod_cg_status pod_cg_batch_tiles(const pod_cg_batch_t* h, int* lanes3, int* rows3, float* ms12)
+{
+    if (!h) return POD_CG_ERR_ARG;
+    for (int c = 0; c < 3; ++c) {
+        if (lanes3) lanes3[c] = h->tile_lanes[c];
+        if (rows3) rows3[c] = h->tile_vec[c];
+        if (ms12)
+            for (int k = 0; k < kBatchTileCands; ++k) ms12[c * kBatchTileCands + k] = h->tile_ms[c][k];
+    }
+    return POD_CG_OK;
+}
+
 const char* pod_cg_batch_last_error(const pod_cg_batch_t* h) { return h ? h->err.c_str() : ""; }
 
 pod_cg_status pod_cg_batch_destroy(pod_cg_batch_t* h)
@@ -863,7 +1044,7 @@ pod_cg_status pod_cg_batch_destroy(pod_cg_batch_t* h)
     if (!h) return POD_CG_OK;
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    void* bufs[] = {h->arena, h->st_i, h->st_d, h->dseq, h->dorder, h->dticket};
+    void* bufs[] = {h->arena, h->st_i, h->st_d, h->dseq, h->dorder, h->dticket, h->t_ns};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->e0) cudaEventDestroy(h->e0);

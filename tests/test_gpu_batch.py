@@ -70,3 +70,58 @@ def test_batch_repeatable(dev):
     for i in range(len(seqs)):
         assert torch.equal(first[i], bs.solutions(i))
     bs.close()
+
+
+def tile_batch():
+    """Sequences of all three size classes of the tile autotuner (n < 16k, < 64k, larger),
+    with n a multiple of 4 and not, so both row widths run."""
+    return [wl.diffusion2d_drift(m=63, p=3, seed=2, w_max=6, s_max=4),          # n = 3969
+            wl.diffusion3d_moving(m=22, p=3, s_max=4, w_max=8, period=6),       # n = 10648
+            wl.diffusion3d_moving(m=31, p=3, s_max=4, w_max=8, period=6),       # n = 29791
+            wl.diffusion3d_moving(m=42, p=3, s_max=4, w_max=8, period=6)]       # n = 74088
+
+
+@pytest.mark.parametrize("lanes,rows", [(1, 1), (1, 4), (2, 4), (4, 4), (8, 1), (8, 4)])
+def test_batch_tiles_match_oracle(dev, lanes, rows):
+    """Every tile shape of the inner loop (lanes per CSR row, rows per thread) on sequences
+    of every size class against the oracle's run of the same sequences."""
+    from paper_1512_05820_gb300.batch import BatchSolver
+    seqs = tile_batch()
+    systems = [s.all_systems() for s in seqs]
+    bs = BatchSolver(seqs, device=dev, cluster=4, systems=systems)
+    bs.set_tiles(lanes, rows)
+    stats, _ = bs.solve()
+    orc = Oracle()
+    k = 0
+    for i, (seq, sy) in enumerate(zip(seqs, systems)):
+        X = bs.solutions(i).cpu().numpy()
+        oseq = OracleSequence(seq.n, s_max=min(seq.s_max, 16), w_max=seq.w_max, energy=seq.energy, oracle=orc)
+        for j, (_, val, b) in enumerate(sy):
+            A = (seq.row_ptr, seq.col, val)
+            xo, info = oseq.solve(A, b, seq.tol)
+            st = stats[k]
+            k += 1
+            x = X[j]
+            assert st["status"] == "ok", (i, j, st)
+            assert np.linalg.norm(b - orc.spmv(A, x)) / np.linalg.norm(b) <= seq.tol
+            dx = x - xo
+            assert np.sqrt(max(dx @ orc.spmv(A, dx), 0.0) / (xo @ orc.spmv(A, xo))) <= 1e-5, (i, j)
+    bs.close()
+
+
+def test_batch_tile_autotuner_record(dev):
+    """With cluster = 0 the handle tunes the cluster size, then the tiles per size class:
+    every class present has timings for all four candidates and keeps the fastest."""
+    from paper_1512_05820_gb300.batch import BatchSolver
+    seqs = tile_batch()
+    bs = BatchSolver(seqs, device=dev, cluster=0)
+    tiles = bs.info()["tiles"]
+    stats, _ = bs.solve()
+    bs.close()
+    assert all(s["status"] == "ok" for s in stats)
+    for cls in ("n<16k", "16k<=n<64k", "n>=64k"):
+        rec = tiles[cls]
+        ms = rec["ms"]
+        assert all(v > 0 for v in ms.values()), (cls, ms)
+        best = min(ms, key=ms.get)
+        assert best == f"lanes{rec['spmv_lanes']}_rows{rec['rows_per_thread']}"
