@@ -42,6 +42,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--grid", type=int, default=128, help="grid edge m (m^3 cells)")
     ap.add_argument("--systems", type=int, default=50)
+    ap.add_argument("--w-max", type=int, default=32, help="largest POD basis (the sequence's w_max)")
+    ap.add_argument("--energy", type=float, default=0.9999, help="POD energy fraction kept")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -95,7 +97,7 @@ def dist_env():
 
 def workload(args):
     from paper_1512_05820_gb300 import workloads as wl
-    return wl.diffusion3d_moving(m=args.grid, p=args.systems)
+    return wl.diffusion3d_moving(m=args.grid, p=args.systems, w_max=args.w_max, energy=args.energy)
 
 
 def config_dict(seq, args, precision):

@@ -279,6 +279,65 @@ pod_cg_status pod_cg_proj_tuning(const pod_cg_t* h, int* forms, float* ms);
  * actual matrix; later solves on the same pattern reuse the choice. lane_ms: host, 6. */
 pod_cg_status pod_cg_tuning(const pod_cg_t* h, int* spmv_lanes, float* lane_ms);
 
+/* --------------------------------- the paper's snapshots: accumulated Krylov vectors */
+
+/* Settings of the overall algorithm with Krylov-vector snapshots (Section 3.1, Section 3.2,
+ * Algorithm 3). */
+typedef struct {
+    int    y_threshold;  /* storage threshold: after a solve whose directions take the
+                            augmenting basis Z past y_threshold columns, Z is compressed
+                            (Algorithm 3's truncation); 0 = never automatically (the caller
+                            compresses with pod_cg_krylov_compress). y_threshold + p_cap <= 64 */
+    int    y_keep;       /* columns kept by a compression (1..64; <= y_threshold when > 0) */
+    int    w_keep;       /* after a compression the stage-one basis W is its first w_keep
+                            columns (0..y_keep) */
+    double nu;           /* stage-one set rule of Algorithm 3: a new direction k joins W when
+                            T_kk / sum_i T_ii > nu (nu >= 1: every direction, nu <= 0: none) */
+    int    weights;      /* POD weights of a compression: 0 = RBF weights (Eq. (weightsRBF),
+                            rho(r) = 2^-(r-1) over the systems since the last compression),
+                            1 = previous weights (Eq. (weightsPrevious)) of the last system */
+    int    p_cap;        /* directions kept per system: the first p_cap of stage three (1..64),
+                            fewer when Z has less room */
+    int    frozen;       /* 1: solves use Z but append nothing and compress nothing */
+} pod_cg_krylov_config;
+
+/* Switch the handle to the paper's POD ingredients (Section 3): the augmenting basis Z holds
+ * every system's stage-three directions, A_j-normalised, Z <- [Z, P_j T_j^{-1/2}] (T_j the
+ * diagonal of (A_j p_k, p_k)); each system runs stage one on W (the columns of Z chosen by
+ * nu), stage two over range(Z) and stage three with [W, V2] (Algorithm 3 with the stage-three
+ * option of Section 4.3). After each solve the previous weights of its solution,
+ * (Z^T A_j Z)^+ Z^T b_j (Eq. (weightsPrevious) with x_bar = 0), are formed; when Z exceeds
+ * y_threshold it is replaced by its weighted POD in the metric A_j (Algorithm 4 with
+ * Theta = A_j and the chosen weights; the result is A_j-orthonormal, so Algorithm 3's
+ * Cholesky re-orthogonalisation is the identity), keeping y_keep columns, the first w_keep
+ * of which form W. Requires an FP64 handle with three_stage = 1, pod_metric = 0, no output
+ * functionals, no solution snapshots and keep_factors = 0 (else ERR_STATE); the CG product
+ * runs in CSR form. Called again, it changes the settings and keeps Z. cfg: host.
+ * Errors: ERR_ARG (settings out of range), ERR_STATE, ERR_OOM. pod_cg_clear_snapshots
+ * empties Z. */
+pod_cg_status pod_cg_set_krylov(pod_cg_t* h, const pod_cg_krylov_config* cfg);
+
+/* The augmenting basis of Section 3.1's accumulated Krylov vectors (Algorithm 3): z, its
+ * column count; w, the stage-one columns; compressions so far (host outs, each may be NULL);
+ * Z_out (device, n-by-z column-major in Z's storage order, or NULL) a copy of Z and
+ * w_cols (host, room for 64, or NULL) the indices of the stage-one columns.
+ * Errors: ERR_STATE (Krylov mode off), ERR_CUDA. */
+pod_cg_status pod_cg_krylov_state(pod_cg_t* h, int* z, int* w, int* compressions, double* Z_out, int* w_cols);
+
+/* The coordinates (Z^T A Z)^+ Z^T b of a right-hand side in the current Z (Eq.
+ * (weightsPrevious) with x_bar = 0; for A, b of the next system these are the ideal weights
+ * of Section 3.2 that Section 5's weights experiment compares against). A: device CSR; b:
+ * device, length n; coords_out: device, z entries. weights_out (device, z, or NULL): the
+ * weights the next compression would use. Errors: ERR_ARG, ERR_STATE, ERR_CUDA. */
+pod_cg_status pod_cg_krylov_coords(pod_cg_t* h, const pod_cg_csr* A, const double* b, double* coords_out,
+                                   double* weights_out);
+
+/* Compress Z now (Algorithm 3's truncation): Z <- the first y_keep modes of the POD of
+ * Z diag(eta) in the metric A (Algorithm 4, Theta = A), W <- its first w_keep columns.
+ * eta: device, z entries, or NULL for the accumulated weights of the handle's setting.
+ * A: device CSR. Errors: ERR_ARG, ERR_STATE, ERR_CUDA. */
+pod_cg_status pod_cg_krylov_compress(pod_cg_t* h, const pod_cg_csr* A, const double* eta, int y_keep, int w_keep);
+
 /* ------------------------------------------------------ stateless steps of the path */
 
 /* y = A x (the product of Algorithm 1's gamma = (A p, p)); x, y device length n. */

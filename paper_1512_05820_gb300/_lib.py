@@ -16,7 +16,8 @@ EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_l
            "pod_cg_gram_tc_workspace", "pod_cg_gram_tc", "pod_cg_diffusion_assemble",
            "pod_cg_diffusion_theta_grad", "pod_cg_batch_create", "pod_cg_batch_solve", "pod_cg_batch_info",
            "pod_cg_batch_last_error", "pod_cg_batch_destroy", "pod_cg_batch_tiles", "pod_cg_batch_set_tiles",
-           "pod_cg_pod"]
+           "pod_cg_pod", "pod_cg_set_krylov", "pod_cg_krylov_state", "pod_cg_krylov_coords",
+           "pod_cg_krylov_compress"]
 
 
 class Config(ctypes.Structure):
@@ -27,6 +28,11 @@ class Config(ctypes.Structure):
                 ("proj_form", ctypes.c_int), ("spmv_lanes", ctypes.c_int), ("three_stage", ctypes.c_int),
                 ("y_max", ctypes.c_int), ("energy_y", ctypes.c_double), ("tol_stage2", ctypes.c_double),
                 ("tol_inner", ctypes.c_double), ("bsr", ctypes.c_int), ("pod_metric", ctypes.c_int)]
+
+
+class KrylovConfig(ctypes.Structure):
+    _fields_ = [("y_threshold", ctypes.c_int), ("y_keep", ctypes.c_int), ("w_keep", ctypes.c_int),
+                ("nu", ctypes.c_double), ("weights", ctypes.c_int), ("p_cap", ctypes.c_int), ("frozen", ctypes.c_int)]
 
 
 class CSRStruct(ctypes.Structure):
@@ -120,6 +126,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_batch_tiles.argtypes = [vp, P(ci), P(ci), P(ctypes.c_float)]
     L.pod_cg_batch_set_tiles.argtypes = [vp, P(ci), P(ci)]
     L.pod_cg_pod.argtypes = [ci, ci, vp, cd, cd, ci, vp, vp, P(ci), vp, sz, vp]
+    L.pod_cg_set_krylov.argtypes = [vp, P(KrylovConfig)]
+    L.pod_cg_krylov_state.argtypes = [vp, P(ci), P(ci), P(ci), vp, P(ci)]
+    L.pod_cg_krylov_coords.argtypes = [vp, P(CSRStruct), vp, vp, vp]
+    L.pod_cg_krylov_compress.argtypes = [vp, P(CSRStruct), vp, ci, ci]
     for name in EXPORTS:
         if name not in ("pod_cg_last_error", "pod_cg_gram_workspace", "pod_cg_gram_workspace_for",
                         "pod_cg_gram_tc_workspace",

@@ -89,6 +89,12 @@ struct ProbDesc {
     const float* bval32;  // the same in FP32 (mixed precision)
     int nb;               // block rows (n / 3)
     int nnzb;             // blocks (nnz / 9)
+    // record of the stage-three search directions (accumulated Krylov vectors, Section 3.1):
+    // while iters < krec_cap the FP64 CSR CG product stores p_k in column k of krec (row
+    // stride ld) and (A p_k, p_k) in krec_gamma[k]; krec = NULL records nothing
+    double* krec;
+    double* krec_gamma;
+    int krec_cap;
 };
 
 // The scalar step after the CG product (Algorithm 1): gamma = (A p, p) given, the last

@@ -249,6 +249,22 @@ struct pod_cg_t {
     float proj_ms[6][2][2] = {};                     // [bucket][form][update, direction]
     DevState* st_save = nullptr;   // device copy of the state while the form is timed
 
+    // the paper's snapshots (Section 3.1, Algorithm 3): accumulated Krylov vectors
+    bool kry_on = false;
+    pod_cg_krylov_config kc{};
+    double* Z = nullptr;        // ld x kSMax: augmenting basis, columns in append order
+    double* Zalt = nullptr;     // ld x kSMax: Z diag(eta) during a compression
+    double* AZ = nullptr;       // ld x kSMax: A Z (A Z diag(eta) during a compression)
+    double* kgam = nullptr;     // kSMax: (A p_k, p_k) of the recorded directions
+    double* zG = nullptr;       // kSMax x (kSMax + 1) row-major: Z^T [A Z, b]
+    double* zG2 = nullptr;      // kSMax x kSMax: the weighted Gram of a compression
+    double* zcoord = nullptr;   // kSMax: coordinates of the last solution in Z
+    double* zeta = nullptr;     // kSMax: POD weights accumulated since the last compression
+    int z = 0;                  // columns of Z
+    std::vector<int> w_idx;     // columns of Z that form the stage-one basis
+    int compressions = 0;
+    int kry_cap = 0;            // directions the current solve may record
+
     GraphSlot graphs[6];                // conditional graphs [width bucket]
     GraphSlot chunks[6];                // plain chunk graphs [width bucket]
     GraphSlot s2graph;                  // stage-two conditional graph
@@ -998,6 +1014,97 @@ pod_cg_status finish_solve(pod_cg_t* h, double* out, int w_pod, int launches, po
     return POD_CG_OK;
 }
 
+// Krylov-vector mode (Section 3.1, Algorithm 3). The augmenting basis of the next solve:
+// Y = Z with the stage-one columns first (w of them), so that W is Y's first w columns as
+// the three-stage solve expects.
+pod_cg_status krylov_gather(pod_cg_t* h)
+{
+    const size_t ld = (size_t)h->ld;
+    std::vector<char> in_w(h->z, 0);
+    std::vector<int> order(h->w_idx);
+    for (int c : h->w_idx) in_w[c] = 1;
+    for (int c = 0; c < h->z; ++c)
+        if (!in_w[c]) order.push_back(c);
+    for (size_t i = 0; i < order.size(); ++i)
+        PODCG_CK(h, cudaMemcpyAsync(h->Y + i * ld, h->Z + (size_t)order[i] * ld, sizeof(double) * h->n,
+                                    cudaMemcpyDeviceToDevice, h->stream));
+    h->pod_w = (int)h->w_idx.size();
+    h->pod_y = h->z;
+    h->w_clobbered = h->pod_w > 0;
+    h->pod_dirty = false;
+    return POD_CG_OK;
+}
+
+// Compression (Algorithm 3's truncation): Z <- the first y_keep modes of the POD of
+// Z diag(eta) with the metric A (Algorithm 4, Theta = A: Gram (Z diag(eta))^T A (Z diag(eta)),
+// symmetrised, eigen-decomposed, lifted; the modes are A-orthonormal); W <- the first w_keep.
+pod_cg_status krylov_compress_now(pod_cg_t* h, const pod_cg_csr* A, const double* eta, int y_keep, int w_keep)
+{
+    cudaStream_t s = h->stream;
+    const int n = h->n, z = h->z;
+    if (z == 0) return POD_CG_OK;
+    PODCG_CK(h, launch_scale_cols(h->Z, h->Zalt, h->ld, n, z, eta, 0, h->sms, s));
+    PODCG_CK(h, launch_spmm(A->row_ptr, A->col, A->val, h->Zalt, h->ld, h->AZ, h->ld, n, z, h->sms, s));
+    PODCG_CK(h, launch_gram(n, h->Zalt, h->ld, z, h->AZ, h->ld, z, nullptr, h->zG2, kSMax, 0, h->gram_work,
+                            h->gram_work_bytes, h->sms, s));
+    PODCG_CK(h, launch_symmetrize(h->zG2, kSMax, z, s));
+    PODCG_CK(h, launch_pod_eig(h->zG2, kSMax, z, 2.0, h->cfg.rank_tol, y_keep, h->C, h->sigma2, h->st, nullptr, 0, s,
+                               0.0, 0));
+    PODCG_CK(h, launch_lift(n, h->Zalt, h->ld, z, h->C, h->st, h->Z, h->ld, h->sms, s, 0));
+    pod_cg_status rs = read_state(h);
+    if (rs != POD_CG_OK) return rs;
+    const int yk = h->st_host->pod_w;
+    h->z = yk;
+    h->w_idx.clear();
+    for (int c = 0; c < std::min(w_keep, yk); ++c) h->w_idx.push_back(c);
+    PODCG_CK(h, cudaMemsetAsync(h->zeta, 0, sizeof(double) * kSMax, s));
+    ++h->compressions;
+    return POD_CG_OK;
+}
+
+// Coordinates (Z^T A Z)^+ Z^T b (Eq. (weightsPrevious), x_bar = 0) into zcoord; with
+// accumulate, the weights zeta are updated from them (RBF or previous weights).
+pod_cg_status krylov_coords_now(pod_cg_t* h, const pod_cg_csr* A, const double* b, bool accumulate)
+{
+    cudaStream_t s = h->stream;
+    const int n = h->n, z = h->z;
+    if (z == 0) return POD_CG_OK;
+    PODCG_CK(h, launch_spmm(A->row_ptr, A->col, A->val, h->Z, h->ld, h->AZ, h->ld, n, z, h->sms, s));
+    PODCG_CK(h, launch_gram(n, h->Z, h->ld, z, h->AZ, h->ld, z, b, h->zG, kSMax + 1, 0, h->gram_work,
+                            h->gram_work_bytes, h->sms, s));
+    double* eta = accumulate ? h->zeta : h->zG2;   // zG2 is scratch outside compressions
+    PODCG_CK(h, launch_krylov_coords(h->zG, kSMax + 1, z, 1e-13, h->zcoord, eta, h->kc.weights == 0 ? 1 : 0, s));
+    return POD_CG_OK;
+}
+
+// After a solve: append its recorded directions, A-normalised (P T^{-1/2}), choose the new
+// stage-one columns by nu, form the solution's previous weights and compress when Z has
+// passed the storage threshold (Algorithm 3).
+pod_cg_status krylov_update(pod_cg_t* h, const pod_cg_csr* A, const double* b)
+{
+    cudaStream_t s = h->stream;
+    const int k = std::min(h->st_host->iters, h->kry_cap);
+    if (k > 0) {
+        std::vector<double> g(k);
+        PODCG_CK(h, cudaMemcpyAsync(g.data(), h->kgam, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        double* cols = h->Z + (size_t)h->z * h->ld;
+        PODCG_CK(h, launch_scale_cols(cols, cols, h->ld, h->n, k, h->kgam, 1, h->sms, s));
+        PODCG_CK(h, cudaStreamSynchronize(s));
+        double sum = 0.0;
+        for (double v : g) sum += v;
+        for (int i = 0; i < k; ++i) {
+            const bool take = h->kc.nu >= 1.0 ? true : h->kc.nu <= 0.0 ? false : g[i] / sum > h->kc.nu;
+            if (take) h->w_idx.push_back(h->z + i);
+        }
+        h->z += k;
+    }
+    pod_cg_status cs = krylov_coords_now(h, A, b, true);
+    if (cs != POD_CG_OK) return cs;
+    if (h->kc.y_threshold > 0 && h->z > h->kc.y_threshold)
+        return krylov_compress_now(h, A, h->zeta, h->kc.y_keep, h->kc.w_keep);
+    return POD_CG_OK;
+}
+
 }  // namespace
 
 void podcg::set_last_error(const std::string& msg) { g_last_error = msg; }
@@ -1050,7 +1157,8 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
                     h->GSC, h->out_work, h->AS, h->GA,
                     h->G, h->Rinv, h->Mmu,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
-                    h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG};
+                    h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG,
+                    h->Z, h->Zalt, h->AZ, h->kgam, h->zG, h->zG2, h->zcoord, h->zeta};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->tm_dev) cudaFree(h->tm_dev);
@@ -1222,6 +1330,11 @@ pod_cg_status pod_cg_clear_snapshots(pod_cg_t* h)
     h->pod_dirty = false;
     h->pod_w = 0;
     h->vprev_s = 0;
+    if (h->kry_on) {
+        h->z = 0;
+        h->w_idx.clear();
+        PODCG_CK(h, cudaMemsetAsync(h->zeta, 0, sizeof(double) * kSMax, h->stream));
+    }
     return POD_CG_OK;
 }
 
@@ -1229,6 +1342,8 @@ pod_cg_status pod_cg_add_snapshots(pod_cg_t* h, const double* X, int m)
 {
     if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
     if (m < 0 || (m > 0 && !X)) return fail(h, POD_CG_ERR_ARG, "bad snapshot block");
+    if (h->kry_on && m > 0)
+        return fail(h, POD_CG_ERR_STATE, "the handle's snapshots are its Krylov vectors (pod_cg_set_krylov)");
     const int n = h->n;
     for (int c = 0; c < m; ++c) {
         const int slot = h->s_next;
@@ -1335,9 +1450,20 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         h->val32_cap = A->nnz;
     }
 
+    if (h->kry_on) {   // the basis sizes of this solve are known on the host (the state starts from them)
+        h->pod_w = (int)h->w_idx.size();
+        h->pod_y = h->z;
+    }
     reset_state(h, A, b, tol);
     pod_cg_status bst = setup_bsr(h, A);
     if (bst != POD_CG_OK) return bst;
+    h->kry_cap = 0;
+    if (h->kry_on && !h->kc.frozen) {   // stage three records its first directions into Z
+        h->kry_cap = std::min(h->kc.p_cap, kSMax - h->z);
+        h->pd_host->krec = h->Z + (size_t)h->z * h->ld;
+        h->pd_host->krec_gamma = h->kgam;
+        h->pd_host->krec_cap = h->kry_cap;
+    }
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
@@ -1360,7 +1486,10 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     // basis Y, whose first w columns are W (nested POD bases)
     const bool three = h->cfg.three_stage != 0;
     if (h->cfg.pod_metric == 1 && h->s_count > 0) h->pod_dirty = true;   // the metric is this system's A
-    if (h->s_count > 0 && h->pod_dirty) {
+    if (h->kry_on) {
+        pod_cg_status ks = krylov_gather(h);
+        if (ks != POD_CG_OK) return ks;
+    } else if (h->s_count > 0 && h->pod_dirty) {
         const double* Gpod = h->GS;
         if (h->out_q > 0) {   // metric C^T C: the Gram of the snapshots' output images
             PODCG_CK(h, launch_cs_gram(h->CSv, kQMax, h->s_count, h->out_q, h->GSC, kSMax, s));
@@ -1544,6 +1673,7 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     if (ls != POD_CG_OK) return ls;
     const int sysid = h->system_counter++;
     pod_cg_status fs = finish_solve(h, x_out, w, launches, stats, sysid);
+    if (fs == POD_CG_OK && h->kry_on && !h->kc.frozen) fs = krylov_update(h, A, b);
 
     // keep this system's factors for the adjoint
     if (h->cfg.keep_factors > 0 && !h->mixed && fs == POD_CG_OK) {
@@ -1622,6 +1752,121 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
     pod_cg_status ls = run_loop(h, wb, L);
     if (ls != POD_CG_OK) return ls;
     return finish_solve(h, lambda_out, w, launches, stats, system_id);
+}
+
+pod_cg_status pod_cg_set_krylov(pod_cg_t* h, const pod_cg_krylov_config* kc)
+{
+    if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
+    if (!kc) return fail(h, POD_CG_ERR_ARG, "cfg is NULL");
+    const pod_cg_krylov_config& c = *kc;
+    if (c.p_cap < 1 || c.p_cap > kSMax || c.y_threshold < 0 || (c.y_threshold > 0 && c.y_threshold + c.p_cap > kSMax) ||
+        c.y_keep < 1 || c.y_keep > kSMax || (c.y_threshold > 0 && c.y_keep > c.y_threshold) || c.w_keep < 0 ||
+        c.w_keep > c.y_keep || !std::isfinite(c.nu) || (c.weights != 0 && c.weights != 1) ||
+        (c.frozen != 0 && c.frozen != 1))
+        return fail(h, POD_CG_ERR_ARG,
+                    "invalid Krylov settings (1 <= p_cap <= 64, y_threshold 0 or y_threshold + p_cap <= 64, "
+                    "1 <= y_keep <= y_threshold, 0 <= w_keep <= y_keep, finite nu, weights 0/1, frozen 0/1)");
+    if (!h->kry_on) {
+        if (h->mixed || h->cfg.three_stage != 1 || h->cfg.pod_metric != 0 || h->out_q > 0 || h->s_count > 0 ||
+            h->cfg.keep_factors > 0)
+            return fail(h, POD_CG_ERR_STATE,
+                        "Krylov-vector snapshots need an FP64 handle with three_stage = 1, pod_metric = 0, no output "
+                        "functionals, no solution snapshots and keep_factors = 0");
+        const size_t ld = (size_t)h->ld;
+        cudaError_t e = cudaSuccess;
+        // the augmenting basis of a solve can reach kSMax columns
+        if (std::max(h->cfg.y_max, h->cfg.w_max) < kSMax) {
+            if (h->Y) cudaFree(h->Y);
+            h->Y = nullptr;
+            e = dalloc(&h->Y, ld * kSMax);
+        }
+        if (e == cudaSuccess) e = dalloc(&h->Z, ld * kSMax);
+        if (e == cudaSuccess) e = dalloc(&h->Zalt, ld * kSMax);
+        if (e == cudaSuccess) e = dalloc(&h->AZ, ld * kSMax);
+        if (e == cudaSuccess) e = dalloc(&h->kgam, (size_t)kSMax);
+        if (e == cudaSuccess) e = dalloc(&h->zG, (size_t)kSMax * (kSMax + 1));
+        if (e == cudaSuccess) e = dalloc(&h->zG2, (size_t)kSMax * kSMax);
+        if (e == cudaSuccess) e = dalloc(&h->zcoord, (size_t)kSMax);
+        if (e == cudaSuccess) e = dalloc(&h->zeta, (size_t)kSMax);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->zeta, 0, sizeof(double) * kSMax, h->stream);
+        // Gram workspace for Z^T [A Z, b], the compression's Gram and the stage-one Gram of a
+        // basis up to kSMax columns wide
+        size_t need = h->gram_work_bytes;
+        for (int k = 1; k <= kSMax; ++k) {
+            need = std::max(need, gram_workspace_bytes(h->n, k, k + 1, h->sms));
+            need = std::max(need, gram_workspace_bytes(h->n, k, k, h->sms));
+            for (int j = 1; j <= k + 1 && j <= kWMax + 1; ++j)
+                need = std::max(need, gram_workspace_bytes(h->n, k, j, h->sms));
+        }
+        if (e == cudaSuccess && need > h->gram_work_bytes) {
+            cudaFree(h->gram_work);
+            h->gram_work = nullptr;
+            e = cudaMalloc((void**)&h->gram_work, need);
+            if (e == cudaSuccess) h->gram_work_bytes = need;
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return fail(h, POD_CG_ERR_OOM, std::string("pod_cg_set_krylov: ") + cudaGetErrorString(e));
+        h->kry_on = true;
+        h->cfg.bsr = 0;   // the direction record lives in the CSR product
+        h->z = 0;
+        h->w_idx.clear();
+        h->compressions = 0;
+    }
+    h->kc = c;
+    return POD_CG_OK;
+}
+
+pod_cg_status pod_cg_krylov_state(pod_cg_t* h, int* z, int* w, int* compressions, double* Z_out, int* w_cols)
+{
+    if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
+    if (!h->kry_on) return fail(h, POD_CG_ERR_STATE, "Krylov-vector mode is off (pod_cg_set_krylov)");
+    if (z) *z = h->z;
+    if (w) *w = (int)h->w_idx.size();
+    if (compressions) *compressions = h->compressions;
+    if (w_cols)
+        for (size_t i = 0; i < h->w_idx.size(); ++i) w_cols[i] = h->w_idx[i];
+    if (Z_out && h->z > 0) {
+        PODCG_CK(h, cudaMemcpy2DAsync(Z_out, sizeof(double) * h->n, h->Z, sizeof(double) * h->ld, sizeof(double) * h->n,
+                                      h->z, cudaMemcpyDeviceToDevice, h->stream));
+        PODCG_CK(h, cudaStreamSynchronize(h->stream));
+    }
+    return POD_CG_OK;
+}
+
+pod_cg_status pod_cg_krylov_coords(pod_cg_t* h, const pod_cg_csr* A, const double* b, double* coords_out,
+                                   double* weights_out)
+{
+    if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
+    if (!h->kry_on) return fail(h, POD_CG_ERR_STATE, "Krylov-vector mode is off (pod_cg_set_krylov)");
+    pod_cg_status cs = check_csr(h, A, h->n);
+    if (cs != POD_CG_OK) return cs;
+    if (!b || (!coords_out && h->z > 0)) return fail(h, POD_CG_ERR_ARG, "b and coords_out must be non-NULL");
+    if (h->z == 0) return POD_CG_OK;
+    cs = krylov_coords_now(h, A, b, false);
+    if (cs != POD_CG_OK) return cs;
+    PODCG_CK(h, cudaMemcpyAsync(coords_out, h->zcoord, sizeof(double) * h->z, cudaMemcpyDeviceToDevice, h->stream));
+    if (weights_out)
+        PODCG_CK(h, cudaMemcpyAsync(weights_out, h->zeta, sizeof(double) * h->z, cudaMemcpyDeviceToDevice, h->stream));
+    PODCG_CK(h, cudaStreamSynchronize(h->stream));
+    return POD_CG_OK;
+}
+
+pod_cg_status pod_cg_krylov_compress(pod_cg_t* h, const pod_cg_csr* A, const double* eta, int y_keep, int w_keep)
+{
+    if (!h) return fail(nullptr, POD_CG_ERR_ARG, "handle is NULL");
+    if (!h->kry_on) return fail(h, POD_CG_ERR_STATE, "Krylov-vector mode is off (pod_cg_set_krylov)");
+    pod_cg_status cs = check_csr(h, A, h->n);
+    if (cs != POD_CG_OK) return cs;
+    if (y_keep < 1 || y_keep > kSMax || w_keep < 0 || w_keep > y_keep)
+        return fail(h, POD_CG_ERR_ARG, "1 <= y_keep <= 64 and 0 <= w_keep <= y_keep");
+    if (eta && h->z > 0) {   // the caller's weights, copied: the accumulated ones stay untouched
+        PODCG_CK(h, cudaMemcpyAsync(h->zcoord, eta, sizeof(double) * h->z, cudaMemcpyDeviceToDevice, h->stream));
+        eta = h->zcoord;
+    }
+    cs = krylov_compress_now(h, A, eta ? eta : h->zeta, y_keep, w_keep);
+    if (cs != POD_CG_OK) return cs;
+    PODCG_CK(h, cudaStreamSynchronize(h->stream));
+    return POD_CG_OK;
 }
 
 pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double* b, int reps, float* ms_out)

@@ -530,6 +530,90 @@ cudaError_t launch_pod_eig(const double* G, int ldg, int s, double energy, doubl
     return cudaGetLastError();
 }
 
+// Previous weights of the accumulated Krylov vectors (Section 3.2, Eq. (weightsPrevious) with
+// x_bar = 0): coords = (Z^T A Z)^+ Z^T b from G = Z^T [A Z, b] (z x (z + 1), row-major, row
+// stride ldg). The symmetric part of Z^T A Z is eigen-decomposed by the parallel Jacobi
+// method; eigenvalues of magnitude below rcond * max |lambda| count as zero (the minimum-norm
+// least-squares solution: the directions of several systems can be nearly dependent; a
+// singular value at or below the cut-off is dropped). The
+// weights for the next compression follow: weights 0 (Eq. (weightsRBF), rho(r) = 2^-(r-1)):
+// eta <- coords + eta / 2 (the older coordinates, zero-padded, halve with each newer system);
+// weights 1 (previous weights alone): eta <- coords. eta holds kSMax entries, zero past z.
+__global__ void __launch_bounds__(kBlock) k_krylov_coords(const double* __restrict__ G, int ldg, int z, double rcond,
+                                                          double* __restrict__ coords, double* __restrict__ eta,
+                                                          int rbf)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmallSmem& sm = *reinterpret_cast<SmallSmem*>(smem_raw);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int m = z + (z & 1);
+    double* rhs = sm.T;              // Z^T b
+    double* t = sm.T + kSMax;        // V^T Z^T b / lambda
+    __shared__ double s_cut;
+    for (int e = tid; e < kSMax * kSMax; e += nt) {
+        const int i = e / kSMax, j = e % kSMax;
+        sm.A[e] = (i < z && j < z) ? 0.5 * (G[(size_t)i * ldg + j] + G[(size_t)j * ldg + i]) : 0.0;
+    }
+    for (int i = tid; i < kSMax; i += nt) rhs[i] = (i < z) ? G[(size_t)i * ldg + z] : 0.0;
+    __syncthreads();
+    if (z > 0) jacobi_parallel(sm.A, sm.V, m, 60, sm.pos, sm.cs, sm.sn, sm.pp, sm.qq, sm.red);
+    if (tid == 0) {
+        double lmax = 0.0;
+        for (int i = 0; i < z; ++i) lmax = fmax(lmax, fabs(sm.A[i * kSMax + i]));
+        s_cut = rcond * lmax;
+    }
+    __syncthreads();
+    for (int k = tid; k < z; k += nt) {
+        const double lam = sm.A[k * kSMax + k];
+        double v = 0.0;
+        for (int j = 0; j < z; ++j) v += sm.V[j * kSMax + k] * rhs[j];
+        t[k] = (fabs(lam) > s_cut) ? v / lam : 0.0;
+    }
+    __syncthreads();
+    for (int i = tid; i < kSMax; i += nt) {
+        double c = 0.0;
+        if (i < z)
+            for (int k = 0; k < z; ++k) c += sm.V[i * kSMax + k] * t[k];
+        coords[i] = c;
+        eta[i] = rbf ? c + 0.5 * eta[i] : c;
+    }
+}
+
+cudaError_t launch_krylov_coords(const double* G, int ldg, int z, double rcond, double* coords, double* eta, int rbf,
+                                 cudaStream_t str)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_krylov_coords, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(SmallSmem));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_krylov_coords<<<1, kBlock, sizeof(SmallSmem), str>>>(G, ldg, z, rcond, coords, eta, rbf);
+    return cudaGetLastError();
+}
+
+// Column scaling of an n x k block (row stride ld): dst[:, c] = src[:, c] / sqrt(f[c])
+// (inv_sqrt = 1: the A-normalisation P T^{-1/2} of recorded directions) or src[:, c] * f[c]
+// (inv_sqrt = 0: the POD weights, Z diag(eta)). dst may equal src.
+__global__ void k_scale_cols(const double* src, double* dst, int ld, int n, int k, const double* __restrict__ f,
+                             int inv_sqrt)
+{
+    const int c = blockIdx.y;
+    const double sc = inv_sqrt ? 1.0 / sqrt(f[c]) : f[c];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[(size_t)c * ld + i] = src[(size_t)c * ld + i] * sc;
+}
+
+cudaError_t launch_scale_cols(const double* src, double* dst, int ld, int n, int k, const double* f, int inv_sqrt,
+                              int sms, cudaStream_t str)
+{
+    if (k <= 0 || n <= 0) return cudaSuccess;
+    const int gx = std::max(1, std::min((n + kBlock - 1) / kBlock, (4 * sms + k - 1) / k));
+    k_scale_cols<<<dim3(gx, k), kBlock, 0, str>>>(src, dst, ld, n, k, f, inv_sqrt);
+    return cudaGetLastError();
+}
+
 // Stage one, small part (Algorithm 2 step 2): upper Cholesky R^T R of Ahat = G[:, :w]
 // (row-major, row stride ldg, upper triangle read; w = w_dim, or st->pod_w when w_dim < 0),
 // then R^{-1} (stored upper, row stride kWMax) and what = R^{-1} R^{-T} bhat with

@@ -86,6 +86,14 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
     const int g = threadIdx.x / L;
     const int wg0 = (threadIdx.x & ~31) / L;
     const int stride = gridDim.x * gpb;
+    // direction record (FP64): column `iters` of the Krylov-vector store while below its cap
+    double* rec = nullptr;
+    if constexpr (!CHAIN) {
+        if (pd->krec != nullptr) {
+            const int it = st->iters;
+            if (it < pd->krec_cap) rec = pd->krec + (size_t)it * pd->ld;
+        }
+    }
     T dot = T(0);
     for (int base = blockIdx.x * gpb + wg0; base < n; base += stride) {
         const int row = base + (g - wg0);
@@ -95,8 +103,10 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
         else
             spmv_rows<L, float, float>(rp, col, pd->val32, p, n, row, row < n, s);
         if ((threadIdx.x & (L - 1)) == 0 && row < n) {
+            const T pr = p[row];
             q[row] = s;
-            dot += s * p[row];
+            dot += s * pr;
+            if (rec) rec[row] = double(pr);
         }
     }
     if constexpr (CHAIN) {
@@ -104,7 +114,10 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
     } else {
         double acc[1] = {double(dot)};
         __shared__ double tot[1];
-        if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) cg_product_finish(st, tot[0]);
+        if (reduce_to_last_block<1>(acc, 1, partials, counter, tot) && threadIdx.x == 0) {
+            if (rec) pd->krec_gamma[st->iters] = tot[0];
+            cg_product_finish(st, tot[0]);
+        }
     }
 }
 

@@ -67,6 +67,11 @@ cudaError_t launch_chol(const double* G, int ldg, double* Rinv, DevState* st, in
 cudaError_t launch_gram_scatter(const double* row, int s, int q, double* G, int ldg, cudaStream_t str);
 cudaError_t launch_cs_gram(const double* cs, int ldc, int s, int q, double* G, int ldg, cudaStream_t str);
 cudaError_t launch_symmetrize(double* G, int ldg, int s, cudaStream_t str);
+// accumulated Krylov vectors (k_dense.cu): previous / RBF weights and column scaling
+cudaError_t launch_krylov_coords(const double* G, int ldg, int z, double rcond, double* coords, double* eta, int rbf,
+                                 cudaStream_t str);
+cudaError_t launch_scale_cols(const double* src, double* dst, int ld, int n, int k, const double* f, int inv_sqrt,
+                              int sms, cudaStream_t str);
 
 // CG iteration (k_cg.cu): kernel pointers for graph construction
 // FP32 with w > 0 has two forms of the update/direction passes: row-parallel float4

@@ -188,6 +188,47 @@ class PodCG:
         _check(self.L.pod_cg_get_basis(self.h, buf.data_ptr(), ctypes.byref(w)), self.h)
         return buf[: w.value].t()
 
+    # -- the paper's snapshots: accumulated Krylov vectors (Section 3, Algorithm 3) ----------
+    def set_krylov(self, y_threshold: int = 40, y_keep: int = 20, w_keep: int = 5, nu: float = 1.0,
+                   weights: str = "rbf", p_cap: int = 24, frozen: bool = False):
+        """Switch to Krylov-vector snapshots (pod_cg_set_krylov); the handle must be FP64 with
+        three_stage = 1. weights: "rbf" or "prev"; y_threshold = 0: compress only on request."""
+        if weights not in ("rbf", "prev"):
+            raise ValueError("weights must be 'rbf' or 'prev'")
+        kc = _lib.KrylovConfig(int(y_threshold), int(y_keep), int(w_keep), float(nu), 0 if weights == "rbf" else 1,
+                               int(p_cap), 1 if frozen else 0)
+        _check(self.L.pod_cg_set_krylov(self.h, ctypes.byref(kc)), self.h)
+
+    def krylov_state(self, with_basis: bool = False) -> dict:
+        """z (columns of Z), the stage-one columns, compressions, and optionally Z (n, z)."""
+        z, w, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        cols = (ctypes.c_int * 64)()
+        _check(self.L.pod_cg_krylov_state(self.h, ctypes.byref(z), ctypes.byref(w), ctypes.byref(c), None, cols),
+               self.h)
+        out = {"z": z.value, "w": w.value, "compressions": c.value, "w_cols": list(cols[: w.value])}
+        if with_basis:
+            Z = torch.empty((max(z.value, 1), self.n), dtype=torch.float64, device="cuda")
+            _check(self.L.pod_cg_krylov_state(self.h, None, None, None, Z.data_ptr(), None), self.h)
+            out["Z"] = Z[: z.value].t()
+        return out
+
+    def krylov_coords(self, A: DeviceCSR, b: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
+        """(Z^T A Z)^+ Z^T b in the current Z and the weights the next compression would use."""
+        z = self.krylov_state()["z"]
+        c = torch.zeros(max(z, 1), dtype=torch.float64, device="cuda")
+        eta = torch.zeros(max(z, 1), dtype=torch.float64, device="cuda")
+        A_s = A.struct()
+        _check(self.L.pod_cg_krylov_coords(self.h, ctypes.byref(A_s), b.contiguous().data_ptr(), c.data_ptr(),
+                                           eta.data_ptr()), self.h)
+        return c[:z], eta[:z]
+
+    def krylov_compress(self, A: DeviceCSR, eta: torch.Tensor | None, y_keep: int, w_keep: int):
+        """Compress Z now with weights eta (None: the accumulated ones) to y_keep columns."""
+        A_s = A.struct()
+        e = eta.contiguous() if eta is not None else None
+        _check(self.L.pod_cg_krylov_compress(self.h, ctypes.byref(A_s), e.data_ptr() if e is not None else None,
+                                             int(y_keep), int(w_keep)), self.h)
+
     def stage3_basis(self) -> tuple[torch.Tensor, torch.Tensor]:
         """Stage three's augmenting basis [W, V2] of the last solve and A [W, V2], as (n, w3)
         tensors (FP64 handles)."""
