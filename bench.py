@@ -83,6 +83,9 @@ def parse_args():
     ap.add_argument("--bsr", type=int, default=-1, choices=[-1, 0, 1],
                     help="CG product in 3x3 block form: -1 when the pattern allows (default), 0 never, 1 required")
     ap.add_argument("--batch-seqs", type=int, default=256)
+    ap.add_argument("--krylov", action="store_true",
+                    help="the paper's Krylov-vector snapshots (Algorithm 3): the 128^3 sequence against "
+                         "POD of previous solutions, and the POD-weights study (ideal / previous / RBF)")
     ap.add_argument("--loop-mode", choices=["graph", "chunked"], default="graph",
                     help="graph: conditional CUDA graph; chunked: plain graphs of 16 iterations (profilable)")
     return ap.parse_args()
@@ -704,6 +707,115 @@ def output_pod_bench(args):
     return 0
 
 
+def weights_study(seq, systems, tol, p_cap, ks):
+    """Section 5's POD-weights experiment on a synthetic sequence: systems 1-10 recycle every
+    Krylov vector (the first p_cap directions per system, no compression), Z is compressed
+    after system 10 by the A_10-metric POD with the ideal weights (the coordinates of system
+    11's solution in Z), the previous weights (those of system 10's) or the RBF weights, to k
+    vectors; system 11 is solved with that k-dimensional basis. Reported per k: the relative
+    residual before stage three and the stage-three iterations to tol."""
+    import torch
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz))
+    mats = [A0.with_values(torch.as_tensor(v, device="cuda")) for _, v, _ in systems[:11]]
+    bs = [torch.as_tensor(b, device="cuda") for _, _, b in systems[:11]]
+    out = {"relres_before_stage3": {}, "stage3_iters": {}}
+    for kind in ("ideal", "prev", "rbf"):
+        rel, its = [], []
+        for k in ks:
+            h = PodCG(seq.n, three_stage=1, tol_stage2=1e-4)
+            h.set_krylov(y_threshold=0, y_keep=min(k, 64), w_keep=min(k, 64), nu=1.0, weights="rbf", p_cap=p_cap)
+            for j in range(10):
+                h.solve(mats[j], bs[j], tol)
+            if kind == "ideal":
+                eta, _ = h.krylov_coords(mats[10], bs[10])
+            elif kind == "prev":
+                eta, _ = h.krylov_coords(mats[9], bs[9])
+            else:
+                _, eta = h.krylov_coords(mats[9], bs[9])
+            z = h.krylov_state()["z"]
+            kk = min(k, z)
+            h.krylov_compress(mats[9], eta, kk, kk)
+            h.set_krylov(y_threshold=0, y_keep=min(k, 64), w_keep=min(k, 64), nu=1.0, weights="rbf", p_cap=p_cap,
+                         frozen=True)
+            _, st = h.solve(mats[10], bs[10], tol)
+            rel.append(st["stage1_relres"])
+            its.append(st["iters"])
+            h.close()
+        out["relres_before_stage3"][kind] = rel
+        out["stage3_iters"][kind] = its
+    h = PodCG(seq.n, three_stage=1, tol_stage2=1e-4)
+    _, st = h.solve(mats[10], bs[10], tol)
+    h.close()
+    out["k"] = list(ks)
+    out["stage3_iters_without_recycling"] = st["iters"]
+    out["z_before_compression"] = z
+    return out
+
+
+def krylov_bench(args):
+    """The overall algorithm with the paper's own snapshots (Algorithm 3, FP64): systems/s on
+    the 128^3 sequence with Krylov-vector snapshots (storage threshold 40, compression to 20,
+    W = the first 5 after a compression and every new direction between (nu = 1), RBF
+    weights, 24 directions kept per system) against the three-stage method on the POD of
+    previous solutions, both end to end on the device; then the POD-weights study."""
+    import torch
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = workload(args)
+    systems = seq.all_systems()
+    A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz))
+    mats = [A0.with_values(torch.as_tensor(v, device="cuda")) for _, v, _ in systems]
+    bs = [torch.as_tensor(b, device="cuda") for _, _, b in systems]
+    xs = [torch.empty(seq.n, dtype=torch.float64, device="cuda") for _ in systems]
+
+    def run(kind):
+        h = PodCG(seq.n, three_stage=1, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, tol_stage2=1e-4)
+        if kind == "krylov":
+            h.set_krylov(y_threshold=40, y_keep=20, w_keep=5, nu=1.0, weights="rbf", p_cap=24)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        iters, comp = [], 0
+        for j in range(len(systems)):
+            _, st = h.solve(mats[j], bs[j], seq.tol, x_out=xs[j])
+            if kind != "krylov":
+                h.add_snapshots(xs[j])
+            iters.append(st["iters"])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if kind == "krylov":
+            comp = h.krylov_state()["compressions"]
+        h.close()
+        rel = max(float(torch.linalg.norm(bs[j] - spmv_dev(mats[j], xs[j])) / torch.linalg.norm(bs[j]))
+                  for j in range(len(systems)))
+        return {"systems_per_s": len(systems) / (ms / 1e3), "mean_iters": float(np.mean(iters)),
+                "iters_first": iters[0], "iters_last": iters[-1], "max_final_relres": rel,
+                **({"compressions": comp} if kind == "krylov" else {})}
+
+    res = {"krylov_vectors": run("krylov"), "pod_of_solutions": run("solutions")}
+    wseq = wl_weights_workload()
+    wsys = wseq.all_systems()
+    study = weights_study(wseq, wsys, 1e-6, 6, [1, 2, 4, 8, 12, 16, 24, 32, 40, 48, 60])
+    study["workload"] = f"{wseq.name} n = {wseq.n}, first 11 systems, 6 directions kept per system, tol 1e-6"
+    line = {"metric": "systems/s, Krylov-vector snapshots (Algorithm 3) vs POD of previous solutions, FP64",
+            "unit": "systems/s", "value": res["krylov_vectors"]["systems_per_s"], "higher_is_better": True,
+            "config": {"workload": f"diffusion3d_moving {args.grid}^3 7-point, {seq.p} systems", "n": seq.n,
+                       "tol": seq.tol, "precision": "fp64", "three_stage": 1},
+            "data": "synthetic", **res, "weights_study": study}
+    print(json.dumps(line))
+
+
+def spmv_dev(A, x):
+    from paper_1512_05820_gb300.solver import spmv
+    return spmv(A, x)
+
+
+def wl_weights_workload():
+    from paper_1512_05820_gb300 import workloads as wl
+    return wl.elasticity_cantilever(e=16, p=11)
+
+
 def three_stage_bench(args):
     """Three-stage solves (stage one on the dominant POD modes, stage two over all retained
     modes, stage three augmented with [W, V2]) against the two-stage form (stage one on the
@@ -868,6 +980,8 @@ def main():
         return output_pod_bench(args)
     if args.elasticity:
         return elasticity_bench(args)
+    if args.krylov:
+        return krylov_bench(args)
 
     import torch
     from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence

@@ -165,7 +165,8 @@ typedef struct {
     int    y;               /* augmenting-basis dimension when stage two ran, else 0 */
     int    stage2_iters;    /* stage-two iterations k2 (stage three's basis is w + k2 wide) */
     int    inner_iters;     /* three_stage = 2: inner reduced iterations, summed */
-    double stage1_relres;   /* ||b - A x0||/||b|| after stage one */
+    double stage1_relres;   /* ||b - A x0||/||b|| at the start of stage three: after stage
+                               one (three_stage: after stages one and two) */
     double final_relres;    /* ||b - A x||/||b|| at exit, from an FP64 product */
     double cond_gram;       /* cond_2(W^T A W) when cond_diag = 1, else 0 */
     float  ms_pod;          /* device time of the POD update (eigensolve + lift) */
