@@ -138,6 +138,15 @@ typedef struct {
                             per solve: W is A-orthonormal, the metric under which POD bounds
                             the A-norm error). Output functionals (pod_cg_set_output_
                             functionals) need 0. */
+    int    w_select;     /* 0: w from the energy criterion alone (Algorithm 4 step 3); 1: the
+                            energy criterion under a cap on w chosen by measured cost (no
+                            counterpart in the paper): once 8 snapshots are held, the next
+                            solves try the caps 2, 4, 8, ... (powers of two below w_max) and
+                            w_max, each twice in the order c1 .. ck ck .. c1 so that a steady
+                            drift of the sequence's difficulty cancels, timing each solve on
+                            the device (POD, stages one and two, the stage-three loop); the
+                            cap with the least mean time is kept for the rest of the
+                            sequence (pod_cg_w_tuning reports it) */
 } pod_cg_config;
 
 /* CSR matrix, device arrays, borrowed. */
@@ -181,7 +190,7 @@ typedef struct {
  * Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
  * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
  * loop_mode 0, proj_form -1, spmv_lanes 0, three_stage 0, y_max 40, energy_y 0.99999999,
- * tol_stage2 1e-4, tol_inner 1e-12, bsr -1, pod_metric 0. */
+ * tol_stage2 1e-4, tol_inner 1e-12, bsr -1, pod_metric 0, w_select 0. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);
 
 /* Create a solver for systems of order n (the problem statement of Section 2) whose work
@@ -272,6 +281,12 @@ pod_cg_status pod_cg_time_kernels(pod_cg_t* h, const pod_cg_csr* A, const double
  * (0 where not timed); each pass keeps its faster form. This is the project's own tuning
  * record, with no counterpart in the paper. Host outputs; either pointer may be NULL. */
 pod_cg_status pod_cg_proj_tuning(const pod_cg_t* h, int* forms, float* ms);
+
+/* Record of the cost-tuned basis cap (w_select = 1; no counterpart in the paper): cap (host
+ * out) the cap in force, w_max while the caps are still being timed or with w_select = 0;
+ * caps[8] the candidates (0 past the last) and ms[8] their mean device time per solve
+ * (0 = not timed yet). Either array may be NULL. */
+pod_cg_status pod_cg_w_tuning(const pod_cg_t* h, int* cap, int* caps, float* ms);
 
 /* Autotuner record (no counterpart in the paper): the CSR SpMV lanes-per-row used by the
  * last solve (1, 2, ..., 32) and, for systems of at least 65,536 rows, the measured

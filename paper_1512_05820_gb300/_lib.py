@@ -17,7 +17,7 @@ EXPORTS = ["pod_cg_config_default", "pod_cg_create", "pod_cg_destroy", "pod_cg_l
            "pod_cg_diffusion_theta_grad", "pod_cg_batch_create", "pod_cg_batch_solve", "pod_cg_batch_info",
            "pod_cg_batch_last_error", "pod_cg_batch_destroy", "pod_cg_batch_tiles", "pod_cg_batch_set_tiles",
            "pod_cg_pod", "pod_cg_set_krylov", "pod_cg_krylov_state", "pod_cg_krylov_coords",
-           "pod_cg_krylov_compress"]
+           "pod_cg_krylov_compress", "pod_cg_w_tuning"]
 
 
 class Config(ctypes.Structure):
@@ -27,7 +27,8 @@ class Config(ctypes.Structure):
                 ("cond_diag", ctypes.c_int), ("keep_factors", ctypes.c_int), ("loop_mode", ctypes.c_int),
                 ("proj_form", ctypes.c_int), ("spmv_lanes", ctypes.c_int), ("three_stage", ctypes.c_int),
                 ("y_max", ctypes.c_int), ("energy_y", ctypes.c_double), ("tol_stage2", ctypes.c_double),
-                ("tol_inner", ctypes.c_double), ("bsr", ctypes.c_int), ("pod_metric", ctypes.c_int)]
+                ("tol_inner", ctypes.c_double), ("bsr", ctypes.c_int), ("pod_metric", ctypes.c_int),
+                ("w_select", ctypes.c_int)]
 
 
 class KrylovConfig(ctypes.Structure):
@@ -130,6 +131,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
     L.pod_cg_krylov_state.argtypes = [vp, P(ci), P(ci), P(ci), vp, P(ci)]
     L.pod_cg_krylov_coords.argtypes = [vp, P(CSRStruct), vp, vp, vp]
     L.pod_cg_krylov_compress.argtypes = [vp, P(CSRStruct), vp, ci, ci]
+    L.pod_cg_w_tuning.argtypes = [vp, P(ci), P(ci), P(ctypes.c_float)]
     for name in EXPORTS:
         if name not in ("pod_cg_last_error", "pod_cg_gram_workspace", "pod_cg_gram_workspace_for",
                         "pod_cg_gram_tc_workspace",

@@ -268,7 +268,16 @@ struct pod_cg_t {
     GraphSlot graphs[6];                // conditional graphs [width bucket]
     GraphSlot chunks[6];                // plain chunk graphs [width bucket]
     GraphSlot s2graph;                  // stage-two conditional graph
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // solve timeline
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // solve timeline (ev[5]: loop start)
+    // cost-tuned cap on w (w_select = 1): candidates, visit order, summed device ms and counts
+    std::vector<int> wsel_caps, wsel_order;
+    std::vector<double> wsel_ms;
+    std::vector<int> wsel_n;
+    int wsel_pos = 0;           // next position in wsel_order
+    bool wsel_done = false;
+    int w_cap = 0;              // cap chosen (valid when wsel_done)
+    int cap_now = 0;            // cap of the current solve
+    int wsel_slot = -1;         // candidate index timed by the current solve (-1: none)
     cudaEvent_t tev[2] = {nullptr, nullptr};                              // autotuner timing
     int system_counter = 0;
 };
@@ -1138,6 +1147,7 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->tol_inner = 1e-12;
     c->bsr = -1;
     c->pod_metric = 0;
+    c->w_select = 0;
     return POD_CG_OK;
 }
 
@@ -1197,6 +1207,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
                     "tol_stage2 >= 0, 0 <= tol_inner < 1)");
     if (c.bsr < -1 || c.bsr > 1) return fail(nullptr, POD_CG_ERR_ARG, "bsr must be -1 (auto), 0 or 1");
     if (c.pod_metric < 0 || c.pod_metric > 1) return fail(nullptr, POD_CG_ERR_ARG, "pod_metric must be 0 or 1");
+    if (c.w_select < 0 || c.w_select > 1) return fail(nullptr, POD_CG_ERR_ARG, "w_select must be 0 or 1");
     if (c.three_stage == 2 && c.precision != POD_CG_FP64)
         return fail(nullptr, POD_CG_ERR_ARG, "three_stage = 2 (stage three over the whole Y) runs in FP64 only");
     if (c.use_tc_gram != 0 && (c.use_tc_gram != 1 || c.precision != POD_CG_MIXED))
@@ -1210,6 +1221,15 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     h->mixed = c.precision == POD_CG_MIXED;
     // three-stage mode appends up to y - w stage-two directions after W: room for kWMax
     h->wcap = c.three_stage ? kWMax : c.w_max;
+    if (c.w_select) {   // caps 2, 4, 8, ... below w_max, then w_max; visited c1 .. ck ck .. c1
+        for (int cp = 2; cp < c.w_max && h->wsel_caps.size() < 7; cp *= 2) h->wsel_caps.push_back(cp);
+        h->wsel_caps.push_back(c.w_max);
+        const int k = (int)h->wsel_caps.size();
+        for (int i = 0; i < k; ++i) h->wsel_order.push_back(i);
+        for (int i = k - 1; i >= 0; --i) h->wsel_order.push_back(i);
+        h->wsel_ms.assign(k, 0.0);
+        h->wsel_n.assign(k, 0);
+    }
     if (c.proj_form >= 0)
         for (int& f : h->proj_form) f = c.proj_form == 1 ? 3 : 0;   // both passes in the forced form
     h->stream = (cudaStream_t)cuda_stream;
@@ -1485,6 +1505,18 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     // POD of the current snapshots (Algorithm 4); in three-stage mode also the augmenting
     // basis Y, whose first w columns are W (nested POD bases)
     const bool three = h->cfg.three_stage != 0;
+    // cap on w for this solve (w_select = 1): a candidate while they are timed, then the choice
+    int cap = h->cfg.w_max;
+    h->wsel_slot = -1;
+    if (h->cfg.w_select && !h->kry_on) {
+        if (h->wsel_done) cap = h->w_cap;
+        else if (h->s_count >= std::min(8, h->cfg.s_max)) {
+            h->wsel_slot = h->wsel_order[h->wsel_pos];
+            cap = h->wsel_caps[h->wsel_slot];
+        }
+    }
+    if (cap != h->cap_now) h->pod_dirty = h->s_count > 0;
+    h->cap_now = cap;
     if (h->cfg.pod_metric == 1 && h->s_count > 0) h->pod_dirty = true;   // the metric is this system's A
     if (h->kry_on) {
         pod_cg_status ks = krylov_gather(h);
@@ -1503,7 +1535,7 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
             Gpod = h->GA;
             launches += 4;
         }
-        PODCG_CK(h, launch_pod_eig(Gpod, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, h->cfg.w_max, h->C,
+        PODCG_CK(h, launch_pod_eig(Gpod, kSMax, h->s_count, h->cfg.energy, h->cfg.rank_tol, cap, h->C,
                                    h->sigma2, h->st, h->Vprev, h->vprev_s, s, h->cfg.energy_y,
                                    three ? h->cfg.y_max : 0));
         h->vprev_s = h->s_count;
@@ -1669,11 +1701,27 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     }
     pod_cg_status ps = choose_proj_form(h, wb, L);
     if (ps != POD_CG_OK) return ps;
+    PODCG_CK(h, cudaEventRecord(h->ev[5], s));
     pod_cg_status ls = run_loop(h, wb, L);
     if (ls != POD_CG_OK) return ls;
     const int sysid = h->system_counter++;
     pod_cg_status fs = finish_solve(h, x_out, w, launches, stats, sysid);
     if (fs == POD_CG_OK && h->kry_on && !h->kc.frozen) fs = krylov_update(h, A, b);
+    if (fs == POD_CG_OK && h->wsel_slot >= 0) {
+        // device time of this solve without the one-time projection-form timing
+        float t0 = 0.0f, t1 = 0.0f;
+        cudaEventElapsedTime(&t0, h->ev[0], h->ev[3]);
+        cudaEventElapsedTime(&t1, h->ev[5], h->ev[4]);
+        h->wsel_ms[h->wsel_slot] += double(t0) + double(t1);
+        h->wsel_n[h->wsel_slot] += 1;
+        if (++h->wsel_pos == (int)h->wsel_order.size()) {
+            int best = 0;
+            for (int i = 1; i < (int)h->wsel_caps.size(); ++i)
+                if (h->wsel_ms[i] / h->wsel_n[i] < h->wsel_ms[best] / h->wsel_n[best]) best = i;
+            h->w_cap = h->wsel_caps[best];
+            h->wsel_done = true;
+        }
+    }
 
     // keep this system's factors for the adjoint
     if (h->cfg.keep_factors > 0 && !h->mixed && fs == POD_CG_OK) {
@@ -1919,6 +1967,18 @@ pod_cg_status pod_cg_proj_tuning(const pod_cg_t* h, int* forms, float* ms)
         if (ms)
             for (int f = 0; f < 2; ++f)
                 for (int k = 0; k < 2; ++k) ms[4 * b + 2 * f + k] = h->proj_ms[b][f][k];
+    }
+    return POD_CG_OK;
+}
+
+pod_cg_status pod_cg_w_tuning(const pod_cg_t* h, int* cap, int* caps, float* ms)
+{
+    if (!h) return POD_CG_ERR_ARG;
+    if (cap) *cap = h->wsel_done ? h->w_cap : h->cfg.w_max;
+    for (int i = 0; i < 8; ++i) {
+        const bool ok = i < (int)h->wsel_caps.size();
+        if (caps) caps[i] = ok ? h->wsel_caps[i] : 0;
+        if (ms) ms[i] = (ok && h->wsel_n[i] > 0) ? float(h->wsel_ms[i] / h->wsel_n[i]) : 0.0f;
     }
     return POD_CG_OK;
 }

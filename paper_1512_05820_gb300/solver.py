@@ -173,7 +173,13 @@ class PodCG:
                              "ms_update_direct": pms[4 * b], "ms_direction_direct": pms[4 * b + 1],
                              "ms_update_staged": pms[4 * b + 2], "ms_direction_staged": pms[4 * b + 3]}
                 for b, wb in enumerate((0, 8, 16, 32, 48, 64)) if forms[b] >= 0}
-        return {"spmv_lanes": L.value, "lane_ms": {str(1 << k): ms[k] for k in range(6)}, "projection": proj}
+        cap = ctypes.c_int(0)
+        caps = (ctypes.c_int * 8)()
+        cms = (ctypes.c_float * 8)()
+        _check(self.L.pod_cg_w_tuning(self.h, ctypes.byref(cap), caps, cms), self.h)
+        wsel = {"cap": cap.value, "ms_per_solve": {str(caps[i]): cms[i] for i in range(8) if caps[i] > 0}}
+        return {"spmv_lanes": L.value, "lane_ms": {str(1 << k): ms[k] for k in range(6)}, "projection": proj,
+                "w_cap": wsel}
 
     @property
     def last_w(self) -> int:
