@@ -97,6 +97,17 @@ struct ProbDesc {
     int krec_cap;
 };
 
+// Programmatic dependent launch inside the stage-three loop's graphs: the update and
+// direction kernels hang off their predecessor by a programmatic edge, so their blocks may
+// be scheduled while the predecessor's last blocks still run. Every loop kernel therefore
+// waits for its prerequisite grids (completion and memory visibility) before its first
+// access (a no-op when launched without such an edge), then lets its own dependents be
+// scheduled: they too wait before touching anything this kernel writes.
+__device__ __forceinline__ void pdl_wait_then_release()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // The scalar step after the CG product (Algorithm 1): gamma = (A p, p) given, the last
 // block records it, flags a breakdown when it is not positive (an FP32 inner pass ends
 // instead of the solve in mixed precision) and forms alpha = (r, z)/gamma. Thread 0 only.

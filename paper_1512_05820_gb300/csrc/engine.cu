@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -120,6 +121,32 @@ cudaError_t add_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, K
     p.kernelParams = k.a.ptrs;
     p.extra = nullptr;
     return cudaGraphAddKernelNode(out, g, deps, ndeps, &p);
+}
+
+// A kernel node hanging off `dep` by a programmatic edge (programmatic dependent launch):
+// its blocks may be scheduled once every block of `dep` has started; the loop kernels wait
+// for their prerequisites' completion before their first access. PODCG_PDL=0 in the
+// environment makes it a plain edge (the same graph without the overlap, for comparison).
+cudaError_t add_node_after(cudaGraph_t g, cudaGraphNode_t dep, KSpec& k, cudaGraphNode_t* out)
+{
+    static const bool pdl = [] {
+        const char* e = std::getenv("PODCG_PDL");
+        return !(e && e[0] == '0');
+    }();
+    if (!pdl) return add_node(g, &dep, 1, k, out);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeKernel;
+    np.kernel.func = k.f;
+    np.kernel.gridDim = dim3(k.grid);
+    np.kernel.blockDim = dim3(k.block);
+    np.kernel.sharedMemBytes = (unsigned int)k.smem;
+    np.kernel.kernelParams = k.a.ptrs;
+    np.kernel.extra = nullptr;
+    cudaGraphEdgeData ed = {};
+    ed.from_port = cudaGraphKernelNodePortProgrammatic;
+    ed.to_port = cudaGraphKernelNodePortDefault;
+    ed.type = cudaGraphDependencyTypeProgrammatic;
+    return cudaGraphAddNode(out, g, &dep, &ed, 1, &np);
 }
 
 cudaError_t add_while(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, cudaGraphConditionalHandle h,
@@ -602,8 +629,8 @@ pod_cg_status build_conditional(pod_cg_t* h, int wb, int L, GraphSlot& gs)
         PODCG_CK(h, add_node(O, &f, 1, pl.mxaccum, &g));
     }
     PODCG_CK(h, add_node(I, nullptr, 0, pl.spmv, &m1));
-    PODCG_CK(h, add_node(I, &m1, 1, pl.upd, &m2));
-    PODCG_CK(h, add_node(I, &m2, 1, pl.dir, &m3));
+    PODCG_CK(h, add_node_after(I, m1, pl.upd, &m2));
+    PODCG_CK(h, add_node_after(I, m2, pl.dir, &m3));
     cudaGraphExec_t exec = nullptr;
     PODCG_CK(h, cudaGraphInstantiate(&exec, P, 0));
     gs.graph = P;
@@ -623,11 +650,12 @@ pod_cg_status build_chunk(pod_cg_t* h, int wb, int L, GraphSlot& gs)
     make_plan(h, wb, L, h->mixed, 0, 0, 0, pl);
     cudaGraphNode_t prev = nullptr, cur;
     for (int it = 0; it < kChunk; ++it) {
-        PODCG_CK(h, add_node(P, prev ? &prev : nullptr, prev ? 1 : 0, pl.spmv, &cur));
+        if (prev) PODCG_CK(h, add_node_after(P, prev, pl.spmv, &cur));
+        else PODCG_CK(h, add_node(P, nullptr, 0, pl.spmv, &cur));
         prev = cur;
-        PODCG_CK(h, add_node(P, &prev, 1, pl.upd, &cur));
+        PODCG_CK(h, add_node_after(P, prev, pl.upd, &cur));
         prev = cur;
-        PODCG_CK(h, add_node(P, &prev, 1, pl.dir, &cur));
+        PODCG_CK(h, add_node_after(P, prev, pl.dir, &cur));
         prev = cur;
     }
     cudaGraphExec_t exec = nullptr;

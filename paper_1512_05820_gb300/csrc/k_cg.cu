@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kBlock) k_update(int n, int ld, T* __restrict_
                                                    double* __restrict__ partials, unsigned int* counter,
                                                    DevState* st, cudaGraphConditionalHandle h_inner, int use_cond)
 {
+    pdl_wait_then_release();
     if (st->done) return;   // uniform: only this kernel's last block writes `done`
     constexpr int CPW = WB > 0 ? (WB + kWarps - 1) / kWarps : 1;
     const int w = st->w;
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(kBlock) k_dir(int n, int ld, T* __restrict__ x
                                                 const T* __restrict__ W, const double* __restrict__ Rinv,
                                                 const DevState* st)
 {
+    pdl_wait_then_release();
     if (!FIRST && !st->dir_pending) return;
     if (FIRST && st->outer_done) return;
     const int w = st->w;
@@ -420,6 +422,7 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_update_tma(int n, int ld, int
                                                               double* __restrict__ partials, int g_spmv,
                                                               DevState* st)
 {
+    pdl_wait_then_release();
     if (st->done) return;   // uniform: `done` is written by k_init / the direction pass only
     constexpr int CPW = (WB + kTmConsumers - 1) / kTmConsumers;
     extern __shared__ __align__(1024) unsigned char tm_raw[];
@@ -546,6 +549,7 @@ __global__ void __launch_bounds__(kTmThreads, 2) k_dir_tma(int n, int ld, int ri
                                                            const double* __restrict__ partials, int g_upd, DevState* st,
                                                            cudaGraphConditionalHandle h_inner, int use_cond)
 {
+    pdl_wait_then_release();
     if (!FIRST && !st->dir_pending) return;
     if (FIRST && st->outer_done) return;
     constexpr int NV = FIRST ? 3 : 4;
@@ -708,6 +712,7 @@ __global__ void __launch_bounds__(kBlock, WB <= 8 ? 4 : 2) k_update_v4(int n, in
                                                                      double* __restrict__ partials, int g_spmv,
                                                                      DevState* st)
 {
+    pdl_wait_then_release();
     if (st->done) return;   // uniform: `done` is written by k_init / the direction pass only
     constexpr int NA = WB > 0 ? WB : 1;
     __shared__ float s_red[kWarps][WB + 2];
@@ -791,6 +796,7 @@ __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4
                                                               DevState* st, cudaGraphConditionalHandle h_inner,
                                                               int use_cond)
 {
+    pdl_wait_then_release();
     if (!FIRST && !st->dir_pending) return;
     if (FIRST && st->outer_done) return;
     constexpr int NB = WB > 0 ? WB : 1;

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
                                                     T* __restrict__ q, double* __restrict__ partials,
                                                     unsigned int* counter, DevState* st)
 {
+    pdl_wait_then_release();
     if (blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;
     if (st->done) return;   // uniform: `done` is written by k_init / k_update only
     const int n = pd->n;
