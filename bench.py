@@ -86,6 +86,9 @@ def parse_args():
     ap.add_argument("--bsr", type=int, default=-1, choices=[-1, 0, 1],
                     help="CG product in 3x3 block form: -1 when the pattern allows (default), 0 never, 1 required")
     ap.add_argument("--batch-seqs", type=int, default=256)
+    ap.add_argument("--batch-profile", type=int, default=0, metavar="N",
+                    help="a short launch sequence for kernel profilers of the batched solver: N sequences of "
+                         "the batch workload, cluster 4, 1 lane per CSR row, 4 rows per thread, two solves")
     ap.add_argument("--krylov", action="store_true",
                     help="the paper's Krylov-vector snapshots (Algorithm 3): the 128^3 sequence against "
                          "POD of previous solutions, and the POD-weights study (ideal / previous / RBF)")
@@ -405,6 +408,33 @@ def batch_section(args, rank=0, world=1):
                                    "ms": t_single}
     out["speedup_vs_single_fp64"] = out["systems_per_s"] / out["single_sequence_fp64"]["systems_per_s"]
     return out
+
+
+def batch_profile(args):
+    """Two launches of the batched persistent kernel with fixed settings (no autotuning, so a
+    profiled run launches the same kernel as a plain one): the first N sequences of the
+    batch workload, cluster 4, tiles lanes 1 / rows 4. Prints the second launch's device time
+    and the algorithmic bytes of its inner FP32 iterations."""
+    from paper_1512_05820_gb300 import workloads as wl
+    from paper_1512_05820_gb300.batch import BatchSolver
+    seqs = wl.batch_sequences(nseq=args.batch_profile)
+    bs = BatchSolver(seqs, cluster=4)
+    bs.set_tiles(1, 4)
+    bs.solve()
+    stats, ms = bs.solve()
+    it_bytes, k = 0.0, 0
+    for sq in seqs:
+        for _ in range(sq.p):
+            it_bytes += stats[k]["iters"] * (8 * sq.nnz + 4 * (sq.n + 1) + 52 * sq.n + 8 * stats[k]["w"] * sq.n)
+            k += 1
+    peak, _ = peaks()
+    bs.close()
+    print(json.dumps({"batch_profile": True, "sequences": len(seqs), "systems": len(stats), "ms": ms,
+                      "inner_bytes": it_bytes, "GB/s": it_bytes / (ms / 1e3) / 1e9,
+                      "frac_hbm": it_bytes / (ms / 1e3) / 1e9 / peak,
+                      "n_total": int(sum(sq.n for sq in seqs)),
+                      "converged": sum(1 for st in stats if st["status"] == "ok")}), flush=True)
+    return 0
 
 
 def cpu_baseline(args, seq, gpu_xs):
@@ -986,6 +1016,8 @@ def main():
         return elasticity_bench(args)
     if args.krylov:
         return krylov_bench(args)
+    if args.batch_profile:
+        return batch_profile(args)
 
     import torch
     from paper_1512_05820_gb300.sequence import DeviceSequence, run_sequence
