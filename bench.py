@@ -1111,6 +1111,7 @@ def main():
                        "ms_stage2_mean": float(np.mean([s["ms_stage2"] for s in last])),
                        "ms_stage3_mean": float(np.mean([s["ms_stage3"] for s in last])),
                        "spmv_per_step": spmv_per_step,
+                       "stage_one_gram_tensor_core_solves": sum(1 for s in last if s.get("gram_tc")),
                        "first_pass_systems_per_s": (seq.p / (first_ms / 1e3)) if first_ms else None}}
 
     # one timed pass each: POD-aug in the other precision, plain Jacobi CG (no recycling)
@@ -1239,8 +1240,13 @@ def main():
             out[key] = out.pop(key)
     if batch_out is not None and "err_vs_fp64_oracle" in batch_out:
         out["batch_err_vs_fp64_oracle"] = batch_out["err_vs_fp64_oracle"]
+    n_tc = out["pod_aug"]["stage_one_gram_tensor_core_solves"]
     out["headline"] = {"pod_aug_" + ("mixed" if prec == 1 else "fp64"): value, "roofline_frac": out["roofline"]["frac"],
-                       "roofline_kernel": out["roofline"]["kernel"]}
+                       "roofline_kernel": out["roofline"]["kernel"],
+                       "stage_one_gram": f"tensor cores (split bf16) in {n_tc} of {seq.p} solves, CUDA cores in the rest",
+                       "w_cap": out["autotune"].get("w_cap", {}).get("cap")}
+    if "plain_cg_mixed" in out and prec == 1:
+        out["headline"]["vs_plain_cg_mixed"] = value / world / out["plain_cg_mixed"]["systems_per_s"]
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

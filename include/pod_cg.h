@@ -83,13 +83,16 @@ typedef struct {
     double inner_tol;    /* MIXED: each inner solve reduces its residual by this factor, or
                             only by half the factor that reaches the tolerance when that is
                             larger (the last refinement step stops where it is needed) */
-    int    use_tc_gram;  /* MIXED only (else ERR_ARG at create): stage-one Gram W^T [AW, b] of
-                            the FP32 panels on the tensor cores with split-bf16 products
-                            (pod_cg_gram_tc); 0 = CUDA cores. Solves that run stage two keep
-                            the CUDA-core Gram (its reduced residual cancels). FP64 mode keeps
-                            the FP64 Gram:
-                            an FP32-rounded W^T A W leaves the directions A-orthogonal to W
-                            only to ~1e-7 cond(W^T A W), too loose for FP64 tolerances */
+    int    use_tc_gram;  /* stage-one Gram W^T [AW, b] of a MIXED two-stage solve: 1 = on the
+                            tensor cores with split-bf16 products (pod_cg_gram_tc; MIXED only,
+                            else ERR_ARG at create), 0 = on the CUDA cores (FP32 panels, FP64
+                            sums), -1 = the faster of the two, timed on the actual panels once
+                            per basis width on the first system of >= 65,536 rows (smaller
+                            systems: CUDA cores); stats.gram_tc reports which ran. Solves that
+                            run stage two keep the CUDA-core Gram (its reduced residual
+                            cancels). FP64 mode keeps the FP64 Gram whatever the setting: an
+                            FP32-rounded W^T A W leaves the directions A-orthogonal to W only to
+                            ~1e-7 cond(W^T A W), too loose for FP64 tolerances */
     int    cond_diag;    /* 1: compute cond_2(W^T A W) per solve (diagnostic, Section 5.2) */
     int    keep_factors; /* systems whose W, AW, R are kept for pod_cg_solve_adjoint (0..) */
     int    loop_mode;    /* 0: the CG loop is one conditional CUDA graph (no host round trip);
@@ -182,13 +185,14 @@ typedef struct {
     float  ms_stage1;       /* device time of stage one (A W, Gram, Cholesky) */
     float  ms_stage2;       /* device time of stage two and the start x0, r0 of stage three */
     float  ms_stage3;       /* device time of the stage-three CG iteration */
+    int    gram_tc;         /* 1 if the stage-one Gram ran on the tensor cores */
 } pod_cg_stats;
 
 /* ------------------------------------------------------------------ handle lifecycle */
 
 /* Handle lifecycle: no counterpart in the paper (a library's housekeeping).
  * Defaults: w_max 32, s_max 40, energy 0.9999, rank_tol 1e-13, k_max 100000,
- * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram 0, cond_diag 0, keep_factors 0,
+ * max_refine 5, FP64, inner_tol 1e-5, use_tc_gram -1, cond_diag 0, keep_factors 0,
  * loop_mode 0, proj_form -1, spmv_lanes 0, three_stage 0, y_max 40, energy_y 0.99999999,
  * tol_stage2 1e-4, tol_inner 1e-12, bsr -1, pod_metric 0, w_select 0. */
 pod_cg_status pod_cg_config_default(pod_cg_config* cfg /* host, out */);

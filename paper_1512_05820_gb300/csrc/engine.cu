@@ -304,6 +304,11 @@ struct pod_cg_t {
     bool wsel_done = false;
     int w_cap = 0;              // cap chosen (valid when wsel_done)
     int cap_now = 0;            // cap of the current solve
+    // stage-one Gram of MIXED two-stage solves (use_tc_gram = -1): per basis width, -1 = not
+    // timed yet, 0 = CUDA cores (FP32 panels), 1 = tensor cores; the times that chose it
+    signed char gram_choice[kWMax + 1];
+    float gram_ms[kWMax + 1][2] = {};
+    int last_gram_tc = 0;       // the last solve's stage-one Gram ran on the tensor cores
     int wsel_slot = -1;         // candidate index timed by the current solve (-1: none)
     cudaEvent_t tev[2] = {nullptr, nullptr};                              // autotuner timing
     int system_counter = 0;
@@ -1037,6 +1042,7 @@ pod_cg_status finish_solve(pod_cg_t* h, double* out, int w_pod, int launches, po
         stats->stage1_relres = d.bb > 0.0 ? std::sqrt(std::max(d.rr_stage1, 0.0) / d.bb) : 0.0;
         stats->final_relres = d.bb > 0.0 ? std::sqrt(d.rr_true / d.bb) : 0.0;
         stats->cond_gram = d.cond;
+        stats->gram_tc = h->last_gram_tc;
         cudaEventElapsedTime(&stats->ms_pod, h->ev[0], h->ev[1]);
         cudaEventElapsedTime(&stats->ms_stage1, h->ev[1], h->ev[2]);
         cudaEventElapsedTime(&stats->ms_stage2, h->ev[2], h->ev[3]);
@@ -1162,7 +1168,7 @@ pod_cg_status pod_cg_config_default(pod_cg_config* c)
     c->max_refine = 5;
     c->precision = POD_CG_FP64;
     c->inner_tol = 1e-5;
-    c->use_tc_gram = 0;
+    c->use_tc_gram = -1;
     c->cond_diag = 0;
     c->keep_factors = 0;
     c->loop_mode = 0;
@@ -1238,9 +1244,10 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     if (c.w_select < 0 || c.w_select > 1) return fail(nullptr, POD_CG_ERR_ARG, "w_select must be 0 or 1");
     if (c.three_stage == 2 && c.precision != POD_CG_FP64)
         return fail(nullptr, POD_CG_ERR_ARG, "three_stage = 2 (stage three over the whole Y) runs in FP64 only");
-    if (c.use_tc_gram != 0 && (c.use_tc_gram != 1 || c.precision != POD_CG_MIXED))
+    if (c.use_tc_gram < -1 || c.use_tc_gram > 1 || (c.use_tc_gram == 1 && c.precision != POD_CG_MIXED))
         return fail(nullptr, POD_CG_ERR_ARG,
-                    "use_tc_gram needs precision MIXED: the tensor-core Gram rounds W and AW to FP32");
+                    "use_tc_gram is -1, 0 or 1, and 1 needs precision MIXED: the tensor-core Gram rounds W and AW "
+                    "to FP32");
     pod_cg_t* h = new (std::nothrow) pod_cg_t();
     if (!h) return fail(nullptr, POD_CG_ERR_OOM, "host allocation failed");
     h->n = n;
@@ -1249,6 +1256,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     h->mixed = c.precision == POD_CG_MIXED;
     // three-stage mode appends up to y - w stage-two directions after W: room for kWMax
     h->wcap = c.three_stage ? kWMax : c.w_max;
+    for (auto& g : h->gram_choice) g = -1;
     if (c.w_select) {   // caps 2, 4, 8, ... below w_max, then w_max; visited c1 .. ck ck .. c1
         for (int cp = 2; cp < c.w_max && h->wsel_caps.size() < 7; cp *= 2) h->wsel_caps.push_back(cp);
         h->wsel_caps.push_back(c.w_max);
@@ -1335,7 +1343,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
         if (c.three_stage && h->mixed)   // the re-formed stage-three Gram, up to kWMax columns
             for (int k = 1; k <= kWMax; ++k)
                 h->gram_work_bytes = std::max(h->gram_work_bytes, gram_workspace_bytes(n, k, k + 1, h->sms));
-        if (c.use_tc_gram)
+        if (c.use_tc_gram != 0 && h->mixed)
             h->gram_work_bytes = std::max(h->gram_work_bytes, gram_tc_workspace_bytes(n, gp, c.w_max + 1, h->sms));
         e = cudaMalloc((void**)&h->gram_work, h->gram_work_bytes);
     }
@@ -1616,7 +1624,8 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         // cancels, and the split-bf16 products' error (2^-16 of sum |y| |A w| per entry)
         // left its deflation terms too loose for the block-diagonal stage-three factor.
         const double* bt = b;
-        if (h->cfg.use_tc_gram && !gram_tc_aligned(b, 16)) {
+        h->last_gram_tc = 0;
+        if (h->mixed && h->cfg.use_tc_gram != 0 && !gram_tc_aligned(b, 16)) {
             PODCG_CK(h, cudaMemcpyAsync(h->r, b, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
             bt = h->r;
         }
@@ -1637,7 +1646,34 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
         } else if (h->mixed) {
             const float* X32 = y > w ? h->Y32 : h->W32;
             PODCG_CK(h, launch_spmm_f32(A->row_ptr, A->col, h->val32, h->W32, h->ld, h->AW32, h->ld, n, w, h->sms, s));
-            if (h->cfg.use_tc_gram && y <= w)
+            bool tc = h->cfg.use_tc_gram == 1 && y <= w;
+            if (h->cfg.use_tc_gram == -1 && y <= w && n >= 65536) {
+                // timed once per basis width on the actual panels (the last call writes G again)
+                if (h->gram_choice[w] < 0) {
+                    for (int form = 0; form < 2; ++form) {
+                        float tot = 0.0f;
+                        for (int rep = 0; rep < 4; ++rep) {
+                            PODCG_CK(h, cudaEventRecord(h->tev[0], s));
+                            if (form == 1)
+                                PODCG_CK(h, launch_gram_tc(n, X32, h->ld, p, h->AW32, h->ld, w, bt, h->G, kWMax + 1,
+                                                           h->gram_work, h->gram_work_bytes, tc_err, h->sms, s));
+                            else
+                                PODCG_CK(h, launch_gram32(n, X32, h->ld, p, h->AW32, h->ld, w, b, h->G, kWMax + 1,
+                                                          upper, h->gram_work, h->gram_work_bytes, h->sms, s));
+                            PODCG_CK(h, cudaEventRecord(h->tev[1], s));
+                            PODCG_CK(h, cudaEventSynchronize(h->tev[1]));
+                            float ms = 0.0f;
+                            cudaEventElapsedTime(&ms, h->tev[0], h->tev[1]);
+                            if (rep > 0) tot += ms;
+                        }
+                        h->gram_ms[w][form] = tot / 3.0f;
+                    }
+                    h->gram_choice[w] = h->gram_ms[w][1] < h->gram_ms[w][0] ? 1 : 0;
+                }
+                tc = h->gram_choice[w] == 1;
+            }
+            h->last_gram_tc = tc ? 1 : 0;
+            if (tc)
                 PODCG_CK(h, launch_gram_tc(n, X32, h->ld, p, h->AW32, h->ld, w, bt, h->G, kWMax + 1, h->gram_work,
                                            h->gram_work_bytes, tc_err, h->sms, s));
             else

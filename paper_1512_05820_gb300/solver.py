@@ -60,7 +60,7 @@ class DeviceCSR:
 
 
 DEFAULTS = dict(w_max=32, s_max=40, energy=0.9999, rank_tol=1e-13, k_max=100000, max_refine=5,
-                precision=0, inner_tol=1e-5, use_tc_gram=0, cond_diag=0, keep_factors=0)
+                precision=0, inner_tol=1e-5, use_tc_gram=-1, cond_diag=0, keep_factors=0)
 
 
 def make_config(**kw) -> _lib.Config:

@@ -51,7 +51,8 @@ def test_config_default_is_host_only():
 
 
 STRUCTS = {"pod_cg_config": "Config", "pod_cg_csr": "CSRStruct", "pod_cg_stats": "Stats",
-           "pod_cg_batch_seq": "BatchSeq", "pod_cg_batch_sysstat": "BatchSysStat"}
+           "pod_cg_batch_seq": "BatchSeq", "pod_cg_batch_sysstat": "BatchSysStat",
+           "pod_cg_krylov_config": "KrylovConfig"}
 
 
 def test_struct_layouts_match_header(tmp_path):
@@ -89,7 +90,7 @@ BAD_CONFIGS = [
     dict(three_stage=1, energy_y=1.5), dict(three_stage=1, tol_stage2=-1.0),
     dict(three_stage=1, tol_stage2=float("inf")), dict(three_stage=2, tol_inner=1.0),
     dict(three_stage=2, precision=1), dict(bsr=2), dict(pod_metric=2), dict(use_tc_gram=1, precision=0),
-    dict(use_tc_gram=2, precision=1),
+    dict(use_tc_gram=2, precision=1), dict(use_tc_gram=-2), dict(w_select=2), dict(w_select=-1),
 ]
 
 

@@ -137,3 +137,43 @@ def test_solves_with_tc_gram(dev, precision):
         assert s1["iters"] <= 1.05 * s0["iters"] + 3, (s0["iters"], s1["iters"])
         if s0["w"] > 0:
             assert abs(s1["stage1_relres"] - s0["stage1_relres"]) <= 1e-3 * s0["stage1_relres"]
+
+
+def test_auto_gram_choice(dev):
+    """use_tc_gram = -1 (the default): on a system of >= 65,536 rows the handle times both
+    stage-one Grams once per basis width and reports which ran (stats gram_tc); the solve
+    matches the forced CUDA-core and tensor-core runs' basis width and accuracy. Below 65,536
+    rows the CUDA-core Gram runs without timing."""
+    from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
+    seq = wl.diffusion3d_moving(m=42, p=4, s_max=4, w_max=8, period=10)   # n = 74,088
+    assert seq.n >= 65536
+    systems = seq.all_systems()
+    A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
+    runs = {}
+    for tc in (-1, 0, 1):
+        solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=1, use_tc_gram=tc)
+        sts = []
+        for j, val, b in systems:
+            x, st = solver.solve(A0.with_values(torch.as_tensor(val, device=dev)), torch.as_tensor(b, device=dev),
+                                 seq.tol)
+            assert st["status"] == "ok" and st["final_relres"] <= seq.tol, st
+            solver.add_snapshots(x)
+            sts.append(st)
+        solver.close()
+        runs[tc] = sts
+    for k, st in enumerate(runs[-1]):
+        if st["w"] == 0:
+            assert st["gram_tc"] == 0
+        assert st["gram_tc"] in (0, 1)
+        assert st["w"] == runs[0][k]["w"] == runs[1][k]["w"]
+    assert all(st["gram_tc"] == 1 for st in runs[1] if st["w"] > 0)
+    assert all(st["gram_tc"] == 0 for st in runs[0])
+    small = wl.diffusion2d_drift(m=40, p=3)
+    solver = PodCG(small.n, w_max=small.w_max, s_max=small.s_max, energy=small.energy, precision=1)
+    A0 = DeviceCSR.from_numpy(small.row_ptr, small.col, np.zeros(small.nnz), device=dev)
+    for j, val, b in small.systems():
+        x, st = solver.solve(A0.with_values(torch.as_tensor(val, device=dev)), torch.as_tensor(b, device=dev),
+                             small.tol)
+        solver.add_snapshots(x)
+        assert st["gram_tc"] == 0
+    solver.close()
