@@ -97,7 +97,11 @@ typedef struct {
     int    keep_factors; /* systems whose W, AW, R are kept for pod_cg_solve_adjoint (0..) */
     int    loop_mode;    /* 0: the CG loop is one conditional CUDA graph (no host round trip);
                             1: plain graphs of 16 unrolled iterations, host check per chunk
-                            (same kernels; a form that kernel profilers can attribute) */
+                            (same kernels; a form that kernel profilers can attribute);
+                            2: as 0, with the MIXED inner loop of bases up to 8 wide and one
+                            lane per CSR row run as one persistent cooperative launch per
+                            refinement step (grid barriers between its passes; the same
+                            iterates as 0, bit for bit; stats.ms_loop reports its time) */
     int    proj_form;    /* MIXED, FP32 update/direction passes: -1 = timed once per basis-
                             width bucket on the handle's first system of >= 65,536 rows in
                             it (else row-parallel); 0 = row-parallel float4; 1 = 256-row
@@ -186,6 +190,8 @@ typedef struct {
     float  ms_stage2;       /* device time of stage two and the start x0, r0 of stage three */
     float  ms_stage3;       /* device time of the stage-three CG iteration */
     int    gram_tc;         /* 1 if the stage-one Gram ran on the tensor cores */
+    float  ms_loop;         /* device time of the FP32 inner loop when it ran as one
+                               persistent launch per refinement step (else 0) */
 } pod_cg_stats;
 
 /* ------------------------------------------------------------------ handle lifecycle */
@@ -409,8 +415,10 @@ pod_cg_status pod_cg_gram_tc(int n, int elem_bytes, const void* X, int p, const 
  * use_tc_gram solves) or bit 2 (the FP32 update and direction passes staged by the TMA engine,
  * proj_form = 1) is set in `mask`, those kernels issue no copies and every wait of theirs
  * gives up after `cycles` SM clocks (1e3 .. 4e9), so each runs its timeout path with nothing
- * in flight: a solve then ends with ERR_TIMEOUT (the handle stays usable) and
- * pod_cg_gram_tc leaves NaN in G. mask = 0 restores normal operation (4e9-clock waits).
+ * in flight; while bit 4 (the persistent FP32 loop's grid barrier) is set, the last CTA to
+ * arrive at a barrier does not release it and every wait gives up after about `cycles`
+ * nanoseconds. A solve then ends with ERR_TIMEOUT (the handle stays usable) and
+ * pod_cg_gram_tc leaves NaN in G. mask = 0 restores normal operation.
  * Applies to the current device, from the next launch on, captured graphs included; meant
  * for tests of the failure path only. Errors: ERR_ARG, ERR_CUDA. */
 pod_cg_status pod_cg_debug_wait_timeout(int mask, long long cycles);

@@ -20,7 +20,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libpodcg.so")
 
 SOURCES = ["k_sparse.cu", "k_dense.cu", "k_cg.cu", "k_mixed.cu", "k_adjoint.cu", "k_batch.cu", "engine.cu", "noalloc.cu",
-           "k_gram_tc.cu", "k_stage2.cu", "k_bsr.cu"]
+           "k_gram_tc.cu", "k_stage2.cu", "k_bsr.cu", "k_loop.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                 "-I", INCLUDE, "-I", CSRC]

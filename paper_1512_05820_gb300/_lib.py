@@ -61,7 +61,8 @@ class Stats(ctypes.Structure):
                 ("inner_iters", ctypes.c_int),
                 ("stage1_relres", ctypes.c_double), ("final_relres", ctypes.c_double),
                 ("cond_gram", ctypes.c_double), ("ms_pod", ctypes.c_float), ("ms_stage1", ctypes.c_float),
-                ("ms_stage2", ctypes.c_float), ("ms_stage3", ctypes.c_float), ("gram_tc", ctypes.c_int)]
+                ("ms_stage2", ctypes.c_float), ("ms_stage3", ctypes.c_float), ("gram_tc", ctypes.c_int),
+                ("ms_loop", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         d = {f: getattr(self, f) for f, _ in self._fields_}

@@ -69,6 +69,7 @@ struct DevState {
     double rho_prev;   // (r, z) before this iteration
     int iters_prev;    // iterations before this iteration
     int inner_prev;    // inner iterations before this iteration
+    unsigned long long loop_ns;   // device time of the persistent inner-loop launches (ns)
 };
 
 // Borrowed problem pointers of the current solve, read by the kernels of a captured
@@ -139,7 +140,8 @@ struct WaitTest {
     int pad_;
 };
 constexpr int kWaitTestGramTc = 1;   // k_gram_tc
-constexpr int kWaitTestStaged = 2;   // k_update_bulk, k_dir_bulk
+constexpr int kWaitTestStaged = 2;   // k_update_tma, k_dir_tma
+constexpr int kWaitTestLoop = 4;     // k_cg_loop's grid barrier
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)

@@ -19,6 +19,8 @@
 //                 FP32 init; first direction; inner { ... in FP32 }; x += d }
 //     loop_mode 1: the same kernels, the inner loop as a plain graph of 16 unrolled
 //        iterations (later ones return at once after convergence), host check per chunk.
+//     loop_mode 2: as 0, the mixed inner loop (bases up to 8 wide, one lane per CSR row)
+//        as one persistent cooperative launch per refinement step (k_loop.cu).
 // The host synchronises once to learn w (which selects the kernel width bucket) and once
 // at the end for the statistics.
 #include <cuda_runtime.h>
@@ -96,6 +98,8 @@ struct KSpec {
 
 struct Plan {
     KSpec init, dir0, spmv, upd, dir, res, mxproj, mxstart, mxaccum;
+    KSpec loop;               // the FP32 inner loop as one persistent cooperative kernel
+    bool persistent = false;  // the inner loop body is `loop` alone
 };
 
 struct Stage2Plan {
@@ -251,6 +255,7 @@ struct pod_cg_t {
     // reductions
     double* partials = nullptr;
     unsigned int* counters = nullptr;   // 8 reduction sites x kCounterStride
+    unsigned int* gbar = nullptr;       // the persistent loop's grid barrier (count, generation)
     double* gram_work = nullptr;
     size_t gram_work_bytes = 0;
 
@@ -560,6 +565,16 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
         P.dir.set(f_dir, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
                   (const float*)h->W32, Rinv, M, (const double*)h->partials, gu, st, h_inner, use_cond);
         P.mxaccum.set(f_acc, occ_grid(h, f_acc, n, kBlock), n, h->x, (const float*)h->d32, cst);
+        // loop_mode 2: the whole inner loop in one cooperative launch (CSR product with one
+        // thread per row, bases up to 8 wide) inside the conditional graph
+        const bool allow = h->cfg.loop_mode == 2;
+        const int gl = (allow && use_cond && !h->use_bsr && L == 1 && wb <= 8) ? cg_loop_grid(wb, h->sms) : 0;
+        if (gl > 0) {
+            P.loop.set(kernel_cg_loop(wb), gl, pd, h->p32, h->q32, h->r32, h->d32, (const float*)h->dinv32,
+                       (const float*)h->AW32, (const float*)h->W32, (const double*)h->Mmu, h->partials, h->gbar, st,
+                       h_inner, use_cond);
+            P.persistent = true;
+        }
     }
     P.upd.smem = sm_upd;
     P.dir0.smem = sm_dir;
@@ -633,9 +648,16 @@ pod_cg_status build_conditional(pod_cg_t* h, int wb, int L, GraphSlot& gs)
         PODCG_CK(h, add_while(O, &e, 1, h_inner, &f, &I));
         PODCG_CK(h, add_node(O, &f, 1, pl.mxaccum, &g));
     }
-    PODCG_CK(h, add_node(I, nullptr, 0, pl.spmv, &m1));
-    PODCG_CK(h, add_node_after(I, m1, pl.upd, &m2));
-    PODCG_CK(h, add_node_after(I, m2, pl.dir, &m3));
+    if (pl.persistent) {   // one body pass runs every inner iteration, then clears the condition
+        PODCG_CK(h, add_node(I, nullptr, 0, pl.loop, &m1));
+        cudaLaunchAttributeValue v = {};
+        v.cooperative = 1;
+        PODCG_CK(h, cudaGraphKernelNodeSetAttribute(m1, cudaLaunchAttributeCooperative, &v));
+    } else {
+        PODCG_CK(h, add_node(I, nullptr, 0, pl.spmv, &m1));
+        PODCG_CK(h, add_node_after(I, m1, pl.upd, &m2));
+        PODCG_CK(h, add_node_after(I, m2, pl.dir, &m3));
+    }
     cudaGraphExec_t exec = nullptr;
     PODCG_CK(h, cudaGraphInstantiate(&exec, P, 0));
     gs.graph = P;
@@ -839,7 +861,7 @@ pod_cg_status read_state(pod_cg_t* h);
 pod_cg_status run_stage2(pod_cg_t* h, int L)
 {
     cudaStream_t s = h->stream;
-    if (h->cfg.loop_mode == 0) {
+    if (h->cfg.loop_mode != 1) {
         GraphSlot& gs = h->s2graph;
         if (gs.valid && (gs.L != L || gs.yb != s2_bucket(h->pod_y))) destroy_graph(gs);
         if (!gs.valid) {
@@ -941,7 +963,7 @@ pod_cg_status run_loop(pod_cg_t* h, int wb, int L)
 {
     const int bi = bucket_index(wb);
     cudaStream_t s = h->stream;
-    if (h->cfg.loop_mode == 0) {
+    if (h->cfg.loop_mode != 1) {
         GraphSlot& gs = h->graphs[bi];
         if (gs.valid && (gs.L != L || gs.bsr != h->use_bsr)) destroy_graph(gs);
         if (!gs.valid) {
@@ -1043,6 +1065,7 @@ pod_cg_status finish_solve(pod_cg_t* h, double* out, int w_pod, int launches, po
         stats->final_relres = d.bb > 0.0 ? std::sqrt(d.rr_true / d.bb) : 0.0;
         stats->cond_gram = d.cond;
         stats->gram_tc = h->last_gram_tc;
+        stats->ms_loop = float(double(d.loop_ns) * 1e-6);
         cudaEventElapsedTime(&stats->ms_pod, h->ev[0], h->ev[1]);
         cudaEventElapsedTime(&stats->ms_stage1, h->ev[1], h->ev[2]);
         cudaEventElapsedTime(&stats->ms_stage2, h->ev[2], h->ev[3]);
@@ -1202,7 +1225,7 @@ pod_cg_status pod_cg_destroy(pod_cg_t* h)
                     h->G, h->Rinv, h->Mmu,
                     h->x, h->r, h->p, h->q, h->dinv, h->dinv32, h->r32, h->p32, h->q32, h->d32, h->val32,
                     h->partials, h->counters, h->gram_work, h->st, h->st_save, h->pd, h->kW, h->kAW, h->kG,
-                    h->Z, h->Zalt, h->AZ, h->kgam, h->zG, h->zG2, h->zcoord, h->zeta};
+                    h->Z, h->Zalt, h->AZ, h->kgam, h->zG, h->zG2, h->zcoord, h->zeta, h->gbar};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->tm_dev) cudaFree(h->tm_dev);
@@ -1227,7 +1250,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     else pod_cg_config_default(&c);
     if (c.w_max < 1 || c.w_max > kWMax || c.s_max < 1 || c.s_max > kSMax || !(c.energy >= 0.0 && c.energy <= 1.0) ||
         c.k_max < 0 || c.max_refine < 0 || (c.precision != POD_CG_FP64 && c.precision != POD_CG_MIXED) ||
-        c.keep_factors < 0 || c.keep_factors > 4096 || (c.loop_mode != 0 && c.loop_mode != 1) ||
+        c.keep_factors < 0 || c.keep_factors > 4096 || (c.loop_mode < 0 || c.loop_mode > 2) ||
         c.proj_form < -1 || c.proj_form > 1 ||
         (c.spmv_lanes != 0 && (c.spmv_lanes < 1 || c.spmv_lanes > 32 || (c.spmv_lanes & (c.spmv_lanes - 1)))) ||
         !(c.inner_tol > 0.0 && c.inner_tol < 1.0))
@@ -1304,6 +1327,7 @@ pod_cg_status pod_cg_create(int n, const pod_cg_config* cfg, void* cuda_stream, 
     PODCG_ALLOC(h->dinv32, ld)
     PODCG_ALLOC(h->partials, (size_t)kPartialRows * kPartialStride)
     PODCG_ALLOC(h->counters, (size_t)8 * kCounterStride)
+    PODCG_ALLOC(h->gbar, (size_t)32)
     PODCG_ALLOC(h->st, 1)
     PODCG_ALLOC(h->st_save, 1)
     PODCG_ALLOC(h->pd, 1)
@@ -1522,6 +1546,7 @@ pod_cg_status pod_cg_solve(pod_cg_t* h, const pod_cg_csr* A, const double* b, do
     }
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    PODCG_CK(h, cudaMemsetAsync(h->gbar, 0, 2 * sizeof(unsigned int), s));   // the persistent loop's barrier
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
     PODCG_CK(h, launch_dinv(h->pd, n, h->dinv, h->dinv32, h->st, h->sms, s));
     int launches = 2;   // dinv, stage-one lift
@@ -1839,6 +1864,7 @@ pod_cg_status pod_cg_solve_adjoint(pod_cg_t* h, int system_id, const pod_cg_csr*
     if (bst != POD_CG_OK) return bst;
     PODCG_CK(h, cudaMemcpyAsync(h->pd, h->pd_host, sizeof(ProbDesc), cudaMemcpyHostToDevice, s));
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
+    PODCG_CK(h, cudaMemsetAsync(h->gbar, 0, 2 * sizeof(unsigned int), s));   // the persistent loop's barrier
     PODCG_CK(h, cudaEventRecord(h->ev[0], s));
     PODCG_CK(h, launch_dinv(h->pd, n, h->dinv, h->dinv32, h->st, h->sms, s));
     PODCG_CK(h, cudaEventRecord(h->ev[1], s));
@@ -2089,11 +2115,13 @@ size_t pod_cg_gram_workspace(int n, int p, int q)
 
 pod_cg_status pod_cg_debug_wait_timeout(int mask, long long cycles)
 {
-    if (mask < 0 || mask > (kWaitTestGramTc | kWaitTestStaged) || (mask != 0 && (cycles < 1000 || cycles > 4000000000LL)))
-        return fail(nullptr, POD_CG_ERR_ARG, "pod_cg_debug_wait_timeout: mask 0..3 and 1e3 <= cycles <= 4e9");
+    const int all = kWaitTestGramTc | kWaitTestStaged | kWaitTestLoop;
+    if (mask < 0 || mask > all || (mask != 0 && (cycles < 1000 || cycles > 4000000000LL)))
+        return fail(nullptr, POD_CG_ERR_ARG, "pod_cg_debug_wait_timeout: mask 0..7 and 1e3 <= cycles <= 4e9");
     const long long c = mask ? cycles : 0;
     cudaError_t e = gram_tc_set_wait_test(mask & kWaitTestGramTc, c);
     if (e == cudaSuccess) e = cg_set_wait_test(mask & kWaitTestStaged, c);
+    if (e == cudaSuccess) e = loop_set_wait_test(mask & kWaitTestLoop, c);
     if (e != cudaSuccess) return cuda_fail(nullptr, "pod_cg_debug_wait_timeout", e);
     return POD_CG_OK;
 }

@@ -121,6 +121,12 @@ cudaError_t launch_gram32(int n, const float* X, int ldx, int p, const float* Y,
 // the wait override of pod_cg_debug_wait_timeout for the current device, per unit
 cudaError_t gram_tc_set_wait_test(int mask, long long cycles);
 cudaError_t cg_set_wait_test(int mask, long long cycles);
+cudaError_t loop_set_wait_test(int mask, long long cycles);
+
+// the FP32 inner loop as one persistent cooperative kernel (k_loop.cu): kernel pointer for a
+// basis-width bucket (0 or 8; NULL otherwise) and its grid (every CTA resident; 0 = none)
+void* kernel_cg_loop(int wb);
+int cg_loop_grid(int wb, int sms);
 
 // tensor-core Gram with split-bf16 products (k_gram_tc.cu); G = X^T [Y, extra]
 size_t gram_tc_workspace_bytes(int n, int p, int q, int sms);

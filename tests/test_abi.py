@@ -84,7 +84,7 @@ def test_struct_layouts_match_header(tmp_path):
 
 BAD_CONFIGS = [
     dict(w_max=0), dict(w_max=65), dict(s_max=0), dict(s_max=65), dict(energy=1.5), dict(energy=float("nan")),
-    dict(k_max=-1), dict(max_refine=-1), dict(precision=2), dict(keep_factors=-1), dict(loop_mode=2),
+    dict(k_max=-1), dict(max_refine=-1), dict(precision=2), dict(keep_factors=-1), dict(loop_mode=3),
     dict(proj_form=2), dict(spmv_lanes=3), dict(spmv_lanes=64), dict(inner_tol=0.0), dict(inner_tol=1.0),
     dict(three_stage=3), dict(three_stage=1, y_max=41), dict(three_stage=1, y_max=0),
     dict(three_stage=1, energy_y=1.5), dict(three_stage=1, tol_stage2=-1.0),

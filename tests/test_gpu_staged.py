@@ -58,16 +58,20 @@ def test_mixed_staged_widths(dev, nsnap, w_max, form):
     assert _a_err(orc, A, x, xo) <= 1e-5
 
 
-@pytest.mark.parametrize("form", [0, 1])
-def test_mixed_loop_modes_bitwise_equal(dev, form):
-    """Mixed precision: the conditional-graph loop and the chunked loop launch the same
-    kernels with the same shapes, so the iterates agree bit for bit."""
+@pytest.mark.parametrize("form,lanes,graph_mode", [(0, 1, 0), (1, 1, 0), (0, 1, 2), (1, 2, 2)])
+def test_mixed_loop_modes_bitwise_equal(dev, form, lanes, graph_mode):
+    """Mixed precision: the conditional-graph loop and the chunked loop agree bit for bit.
+    Loop mode 0 launches the same three kernels per iteration as the chunked loop. Loop mode
+    2 with one lane per CSR row (bases up to 8 wide) runs the whole inner loop as one
+    persistent launch while the chunked loop launches the row-parallel kernels: the
+    persistent kernel repeats their arithmetic and reduction order, so the iterates are the
+    same (with 2 lanes it falls back to the three kernels)."""
     from paper_1512_05820_gb300.solver import DeviceCSR, PodCG
     seq = wl.diffusion3d_moving(m=19, p=5, s_max=6, w_max=8, period=10)
-    outs = []
-    for mode in (0, 1):
+    outs, loop_ms = [], []
+    for mode in (graph_mode, 1):
         solver = PodCG(seq.n, w_max=seq.w_max, s_max=seq.s_max, energy=seq.energy, precision=1, loop_mode=mode,
-                       proj_form=form)
+                       proj_form=form, spmv_lanes=lanes)
         A0 = DeviceCSR.from_numpy(seq.row_ptr, seq.col, np.zeros(seq.nnz), device=dev)
         xs, its = [], []
         for j, val, b in seq.systems():
@@ -76,11 +80,16 @@ def test_mixed_loop_modes_bitwise_equal(dev, form):
             solver.add_snapshots(x)
             xs.append(x.clone())
             its.append((st["iters"], st["w"]))
+            if mode != 1:
+                loop_ms.append(st["ms_loop"])
         solver.close()
         outs.append((xs, its))
     assert outs[0][1] == outs[1][1]
     for a, c in zip(outs[0][0], outs[1][0]):
         assert torch.equal(a, c)
+    # the graph-mode solves ran the persistent loop exactly in loop mode 2 with one lane per row
+    persistent = graph_mode == 2 and lanes == 1
+    assert all((t > 0.0) == persistent for t in loop_ms), loop_ms
 
 
 def test_projection_form_is_timed(dev):

@@ -3,7 +3,9 @@
 The tensor-core Gram and the FP32 passes staged by the TMA engine wait on mbarriers that their
 own copies complete. pod_cg_debug_wait_timeout makes those kernels issue no copies and cut
 every wait to 2e6 SM clocks (about a millisecond), so each wait expires with nothing in
-flight: the kernel records the timeout status (7) and returns. The tests check that the
+flight: the kernel records the timeout status (7) and returns. The persistent FP32 loop waits
+at grid barriers; with its bit set the last CTA to arrive does not release the barrier, so
+every wait runs out (about 2e6 ns) and each CTA leaves the loop. The tests check that the
 status reaches the caller (ERR_TIMEOUT from a solve, NaN from the stateless Gram), and that
 with the override cleared the same handle, or the same call, gives the normal result: the
 context and the handle stay usable.
@@ -38,7 +40,7 @@ def override(lib):
 
 
 def test_override_rejects_bad_arguments(lib):
-    assert lib.pod_cg_debug_wait_timeout(4, CYCLES) == 1
+    assert lib.pod_cg_debug_wait_timeout(8, CYCLES) == 1
     assert lib.pod_cg_debug_wait_timeout(1, 10) == 1
     assert lib.pod_cg_debug_wait_timeout(-1, CYCLES) == 1
 
@@ -93,8 +95,8 @@ def _solve_pair(mask, override, **cfg):
     return bad, again, fresh, seq
 
 
-@pytest.mark.parametrize("mask,cfg", [(2, dict(proj_form=1)), (1, dict(use_tc_gram=1))],
-                         ids=["staged-passes", "tensor-core-gram"])
+@pytest.mark.parametrize("mask,cfg", [(2, dict(proj_form=1)), (1, dict(use_tc_gram=1)), (4, dict(loop_mode=2))],
+                         ids=["staged-passes", "tensor-core-gram", "persistent-loop-barrier"])
 def test_solve_wait_expires_then_recovers(lib, override, mask, cfg):
     (xb, stb), (xa, sta), (xf, stf), seq = _solve_pair(mask, override, **cfg)
     assert stb["status"] == "timeout", stb
