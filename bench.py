@@ -1158,9 +1158,8 @@ def main():
     n, nnz = seq.n, seq.nnz
     # algorithmic bytes per launch (each datum once): FP64 or FP32 vectors/panels
     e = 4 if prec == 1 else 8
-    # the staged direction pass of a two-stage mixed solve reads the 16-bit copy of W
-    rec_b = out["autotune"].get("projection", {}).get(f"w<={next(b for b in (0, 8, 16, 32, 48, 64) if w_meas <= b)}", {})
-    e_w = 2 if (prec == 1 and rec_b.get("direction") == "staged") else e
+    # the direction pass of a two-stage mixed solve (either form) reads the 16-bit copy of W
+    e_w = 2 if prec == 1 else e
     kbytes = {"spmv_cg": b_spmv(n, nnz, fp32=(prec == 1)),
               "update": 4 * e * n + e * w_meas * n,          # read r, q, dinv, AW; write r
               "direction": 6 * e * n + e_w * w_meas * n,     # read x, p, r, dinv, W; write x, p

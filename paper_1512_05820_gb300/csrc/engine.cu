@@ -461,7 +461,16 @@ pod_cg_status choose_proj_form(pod_cg_t* h, int wb, int L)
     for (int a = 0; a < kWMax; ++a) t.c[a] = 0.0;
     *h->st_host = t;
     // each form times its update pass, then its direction pass (which reads the partials of
-    // the update pass of the same form); each pass keeps its faster form
+    // the update pass of the same form); each pass keeps its faster form. Before every timed
+    // launch 256 MB are written, so the panels are not left in L2 by the previous launch (in
+    // the loop the CG product streams the matrix between two passes; a narrow basis would
+    // otherwise be timed from L2)
+    void* flush = nullptr;
+    const size_t flush_bytes = size_t(256) << 20;
+    if (cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        flush = nullptr;
+    }
     for (int form = kProjDirect; form <= kProjStaged; ++form) {
         h->proj_form[bi] = form == kProjStaged ? 3 : 0;
         Plan pl;
@@ -471,6 +480,7 @@ pod_cg_status choose_proj_form(pod_cg_t* h, int wb, int L)
             float total = 0.0f;
             for (int rep = 0; rep < 4; ++rep) {
                 PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_host, sizeof(DevState), cudaMemcpyHostToDevice, s));
+                if (flush) PODCG_CK(h, cudaMemsetAsync(flush, rep, flush_bytes, s));
                 PODCG_CK(h, cudaEventRecord(h->tev[0], s));
                 PODCG_CK(h, launch_spec(*ks[k], s));
                 PODCG_CK(h, cudaEventRecord(h->tev[1], s));
@@ -482,6 +492,7 @@ pod_cg_status choose_proj_form(pod_cg_t* h, int wb, int L)
             h->proj_ms[bi][form][k] = total / 3.0f;
         }
     }
+    if (flush) cudaFree(flush);
     h->proj_form[bi] = (h->proj_ms[bi][kProjStaged][0] < h->proj_ms[bi][kProjDirect][0] ? 1 : 0) |
                        (h->proj_ms[bi][kProjStaged][1] < h->proj_ms[bi][kProjDirect][1] ? 2 : 0);
     PODCG_CK(h, cudaMemcpyAsync(h->st, h->st_save, sizeof(DevState), cudaMemcpyDeviceToDevice, s));
@@ -561,9 +572,11 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
         P.upd.set(f_upd, gu, n, ld, h->r32, (const float*)h->q32, (const float*)h->dinv32, (const float*)h->AW32,
                   h->partials, g_spmv, st);
         P.dir0.set(f_dir0, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
-                   (const float*)h->W32, Rinv, M, (const double*)h->partials, gu, st, h_inner, 0);
+                   (const float*)h->W32, (const __half*)h->W16, (const float*)h->wscale, Rinv, M,
+                   (const double*)h->partials, gu, st, h_inner, 0);
         P.dir.set(f_dir, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
-                  (const float*)h->W32, Rinv, M, (const double*)h->partials, gu, st, h_inner, use_cond);
+                  (const float*)h->W32, (const __half*)h->W16, (const float*)h->wscale, Rinv, M,
+                  (const double*)h->partials, gu, st, h_inner, use_cond);
         P.mxaccum.set(f_acc, occ_grid(h, f_acc, n, kBlock), n, h->x, (const float*)h->d32, cst);
         // loop_mode 2: the whole inner loop in one cooperative launch (CSR product with one
         // thread per row, bases up to 8 wide) inside the conditional graph
@@ -605,11 +618,11 @@ void make_plan(pod_cg_t* h, int wb, int L, bool mixed, int use_cond, cudaGraphCo
             P.dir0.smem = P.dir.smem = sd;
         } else {
             P.dir0.set(f_dir0, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
-                       (const float*)h->W32, Rinv, (const double*)h->Mmu, (const double*)h->partials, gu, st, h_inner,
-                       0);
+                       (const float*)h->W32, (const __half*)h->W16, (const float*)h->wscale, Rinv,
+                       (const double*)h->Mmu, (const double*)h->partials, gu, st, h_inner, 0);
             P.dir.set(f_dir, g_dir, n, ld, h->d32, h->p32, (const float*)h->r32, (const float*)h->dinv32,
-                      (const float*)h->W32, Rinv, (const double*)h->Mmu, (const double*)h->partials, gu, st, h_inner,
-                      use_cond);
+                      (const float*)h->W32, (const __half*)h->W16, (const float*)h->wscale, Rinv,
+                      (const double*)h->Mmu, (const double*)h->partials, gu, st, h_inner, use_cond);
         }
     }
 }

@@ -785,11 +785,13 @@ __global__ void __launch_bounds__(kBlock, WB <= 8 ? 4 : 2) k_update_v4(int n, in
 // totals come from its partials (chain_direction, which also takes the exit decisions and,
 // with COND, sets the graph condition), then mu = R^{-1} R^{-T} c, x += alpha p and
 // p = z + beta p - W mu.
-template <int WB, bool FIRST, bool COND>
-__global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4(int n, int ld, float* __restrict__ x,
+template <int WB, bool FIRST, bool COND, bool H = false>
+__global__ void __launch_bounds__(kBlock, WB <= 8 ? 4 : WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4(int n, int ld, float* __restrict__ x,
                                                               float* __restrict__ p, const float* __restrict__ r,
                                                               const float* __restrict__ dinv,
                                                               const float* __restrict__ W,
+                                                              const __half* __restrict__ W16,
+                                                              const float* __restrict__ wscale,
                                                               const double* __restrict__ Rinv,
                                                               const double* __restrict__ M,
                                                               const double* __restrict__ partials, int g_upd,
@@ -807,6 +809,17 @@ __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4
     __shared__ float s_mu[NB];
     float alpha = 0.0f, beta = 0.0f;
     bool upd_p = true;
+    // narrow bases: the thread's first group of p, x, r and M^{-1} is loaded before the
+    // prologue (which needs none of them), so its latency hides behind the partials' sums
+    constexpr bool kPre = !FIRST && WB <= 8;
+    const int g_first = blockIdx.x * blockDim.x + threadIdx.x;
+    float4 pre_p = make_float4(0.f, 0.f, 0.f, 0.f), pre_x = pre_p, pre_r = pre_p, pre_d = pre_p;
+    if (kPre && g_first < (n >> 2)) {
+        pre_p = reinterpret_cast<const float4*>(p)[g_first];
+        pre_x = reinterpret_cast<const float4*>(x)[g_first];
+        pre_r = __ldg(reinterpret_cast<const float4*>(r) + g_first);
+        pre_d = __ldg(reinterpret_cast<const float4*>(dinv) + g_first);
+    }
     if constexpr (!FIRST) {
         const ChainStep cs = chain_direction<WB, COND>(st, partials, g_upd, w, M, s_tot, s_M, s_mud, h_inner, use_cond);
         alpha = float(cs.alpha);
@@ -815,17 +828,22 @@ __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4
     } else if (WB > 0) {
         block_mu_global(Rinv, st->c, w, s_t, s_mud);
     }
+    __shared__ float s_sc[NB];   // H: the 16-bit basis's column scales (W = W16 * scale exactly)
     if (WB > 0 && upd_p) {
-        for (int j = threadIdx.x; j < WB; j += blockDim.x) s_mu[j] = (j < w) ? float(s_mud[j]) : 0.0f;
+        for (int j = threadIdx.x; j < WB; j += blockDim.x) {
+            s_mu[j] = (j < w) ? float(s_mud[j]) : 0.0f;
+            if (H) s_sc[j] = (j < w) ? wscale[j] : 0.0f;
+        }
         __syncthreads();
     }
     const int wc = upd_p ? w : 0;
     const int n4 = n >> 2;
     const int stride = gridDim.x * blockDim.x;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += stride) {
-        const float4 p4 = reinterpret_cast<const float4*>(p)[g];
+        const bool first = kPre && g == g_first;
+        const float4 p4 = first ? pre_p : reinterpret_cast<const float4*>(p)[g];
         if (!FIRST) {
-            float4 x4 = reinterpret_cast<const float4*>(x)[g];
+            float4 x4 = first ? pre_x : reinterpret_cast<const float4*>(x)[g];
             x4.x += alpha * p4.x;
             x4.y += alpha * p4.y;
             x4.z += alpha * p4.z;
@@ -833,8 +851,8 @@ __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4
             reinterpret_cast<float4*>(x)[g] = x4;
         }
         if (upd_p) {
-            const float4 r4 = __ldg(reinterpret_cast<const float4*>(r) + g);
-            const float4 d4 = __ldg(reinterpret_cast<const float4*>(dinv) + g);
+            const float4 r4 = first ? pre_r : __ldg(reinterpret_cast<const float4*>(r) + g);
+            const float4 d4 = first ? pre_d : __ldg(reinterpret_cast<const float4*>(dinv) + g);
             float4 v = make_float4(d4.x * r4.x, d4.y * r4.y, d4.z * r4.z, d4.w * r4.w);
             if (!FIRST) {
                 v.x += beta * p4.x;
@@ -845,7 +863,16 @@ __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4
             if constexpr (WB > 0) {
 #pragma unroll 4
                 for (int j = 0; j < wc; ++j) {
-                    const float4 a = __ldg(reinterpret_cast<const float4*>(W + (size_t)j * ld) + g);
+                    float4 a;
+                    if constexpr (H) {   // four 16-bit entries, dequantised exactly
+                        const uint2 u = __ldg(reinterpret_cast<const uint2*>(W16 + (size_t)j * ld) + g);
+                        const float sc = s_sc[j];
+                        const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+                        const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+                        a = make_float4(lo.x * sc, lo.y * sc, hi.x * sc, hi.y * sc);
+                    } else {
+                        a = __ldg(reinterpret_cast<const float4*>(W + (size_t)j * ld) + g);
+                    }
                     const float m = s_mu[j];
                     v.x -= a.x * m;
                     v.y -= a.y * m;
@@ -864,7 +891,10 @@ __global__ void __launch_bounds__(kBlock, WB <= 32 ? kV4Blocks - 1 : 4) k_dir_v4
             if (!FIRST) v += beta * pi;
 #pragma unroll
             for (int j = 0; j < WB; ++j)
-                if (j < wc) v -= W[(size_t)j * ld + i] * s_mu[j];
+                if (j < wc) {
+                    const float a = H ? __half2float(W16[(size_t)j * ld + i]) * s_sc[j] : W[(size_t)j * ld + i];
+                    v -= a * s_mu[j];
+                }
             p[i] = v;
         }
     }
@@ -920,22 +950,22 @@ static void pick_tma_wb(int wb, bool w16, void** upd, void** dir0, void** dir)
 
 // FP32 with a basis, row-parallel float4 form.
 template <int WB, bool COND>
-static void pick_v4(void** upd, void** dir0, void** dir)
+static void pick_v4(bool w16, void** upd, void** dir0, void** dir)
 {
     *upd = (void*)k_update_v4<WB>;
-    *dir0 = (void*)k_dir_v4<WB, true, false>;
-    *dir = (void*)k_dir_v4<WB, false, COND>;
+    *dir0 = w16 ? (void*)k_dir_v4<WB, true, false, true> : (void*)k_dir_v4<WB, true, false, false>;
+    *dir = w16 ? (void*)k_dir_v4<WB, false, COND, true> : (void*)k_dir_v4<WB, false, COND, false>;
 }
 
 template <bool COND>
-static void pick_v4_wb(int wb, void** upd, void** dir0, void** dir)
+static void pick_v4_wb(int wb, bool w16, void** upd, void** dir0, void** dir)
 {
-    if (wb <= 0) pick_v4<0, COND>(upd, dir0, dir);
-    else if (wb <= 8) pick_v4<8, COND>(upd, dir0, dir);
-    else if (wb <= 16) pick_v4<16, COND>(upd, dir0, dir);
-    else if (wb <= 32) pick_v4<32, COND>(upd, dir0, dir);
-    else if (wb <= 48) pick_v4<48, COND>(upd, dir0, dir);
-    else pick_v4<64, COND>(upd, dir0, dir);
+    if (wb <= 0) pick_v4<0, COND>(false, upd, dir0, dir);
+    else if (wb <= 8) pick_v4<8, COND>(w16, upd, dir0, dir);
+    else if (wb <= 16) pick_v4<16, COND>(w16, upd, dir0, dir);
+    else if (wb <= 32) pick_v4<32, COND>(w16, upd, dir0, dir);
+    else if (wb <= 48) pick_v4<48, COND>(w16, upd, dir0, dir);
+    else pick_v4<64, COND>(w16, upd, dir0, dir);
 }
 
 void cg_kernels(int wb, bool fp32, bool cond, int form, bool w16, void** init, void** upd, void** dir0, void** dir,
@@ -952,8 +982,8 @@ void cg_kernels(int wb, bool fp32, bool cond, int form, bool w16, void** init, v
             *smem_upd = kTmSmemMax;
             *smem_dir = kTmSmemMax;
         } else {   // every FP32 width, 0 included: row-parallel float4, reductions without tails
-            if (cond) pick_v4_wb<true>(wb, upd, dir0, dir);
-            else pick_v4_wb<false>(wb, upd, dir0, dir);
+            if (cond) pick_v4_wb<true>(wb, w16, upd, dir0, dir);
+            else pick_v4_wb<false>(wb, w16, upd, dir0, dir);
         }
     } else {
         if (cond) pick<double, true>(wb, init, upd, dir0, dir);
