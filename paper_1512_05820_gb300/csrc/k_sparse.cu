@@ -96,18 +96,64 @@ __global__ void __launch_bounds__(kBlock) k_spmv_cg(const ProbDesc* __restrict__
         }
     }
     T dot = T(0);
-    for (int base = blockIdx.x * gpb + wg0; base < n; base += stride) {
-        const int row = base + (g - wg0);
-        T s;
-        if constexpr (std::is_same<T, double>::value)
-            spmv_rows<L, double, double>(rp, col, pd->val, p, n, row, row < n, s);
-        else
-            spmv_rows<L, float, float>(rp, col, pd->val32, p, n, row, row < n, s);
-        if ((threadIdx.x & (L - 1)) == 0 && row < n) {
+    if constexpr (L == 1 && CHAIN) {
+        // FP32, one thread per row: the next row's bounds are loaded before this row's entries, so
+        // every row after a thread's first starts with its bounds already in registers (the
+        // rows, and the order of each row's sum, are those of the general loop below)
+        const T* __restrict__ val;
+        if constexpr (std::is_same<T, double>::value) val = pd->val;
+        else val = pd->val32;
+        int row = blockIdx.x * gpb + threadIdx.x;
+        int beg = 0, end = 0;
+        if (row < n) {
+            beg = __ldg(rp + row);
+            end = __ldg(rp + row + 1);
+        }
+        for (; row < n; row += stride) {
+            const int nrow = row + stride;
+            int nbeg = 0, nend = 0;
+            if (nrow < n) {
+                nbeg = __ldg(rp + nrow);
+                nend = __ldg(rp + nrow + 1);
+            }
+            T s = T(0);
+            const int len = end - beg;
+            if (len <= 8) {
+                int c[8];
+                T v[8], gx[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    c[t] = (t < len) ? __ldg(col + beg + t) : 0;
+                    v[t] = (t < len) ? __ldg(val + beg + t) : T(0);
+                }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) gx[t] = (t < len) ? __ldg(p + c[t]) : T(0);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) s += v[t] * gx[t];
+            } else {
+                for (int k = beg; k < end; ++k) s += __ldg(val + k) * __ldg(p + __ldg(col + k));
+            }
             const T pr = p[row];
             q[row] = s;
             dot += s * pr;
             if (rec) rec[row] = double(pr);
+            beg = nbeg;
+            end = nend;
+        }
+    } else {
+        for (int base = blockIdx.x * gpb + wg0; base < n; base += stride) {
+            const int row = base + (g - wg0);
+            T s;
+            if constexpr (std::is_same<T, double>::value)
+                spmv_rows<L, double, double>(rp, col, pd->val, p, n, row, row < n, s);
+            else
+                spmv_rows<L, float, float>(rp, col, pd->val32, p, n, row, row < n, s);
+            if ((threadIdx.x & (L - 1)) == 0 && row < n) {
+                const T pr = p[row];
+                q[row] = s;
+                dot += s * pr;
+                if (rec) rec[row] = double(pr);
+            }
         }
     }
     if constexpr (CHAIN) {
