@@ -137,3 +137,14 @@ def test_krylov_mode_rejects_bad_settings(dev):
     with pytest.raises(PodCGError):
         h.set_krylov()                                  # two-stage handle
     h.close()
+
+
+def test_krylov_sequence_3d_matches_oracle(dev):
+    """A 3D sequence (24^3 moving source) with 32 directions per system, a storage threshold
+    of 32, compression to 16 after every system past the first (W = the first 6 modes) and
+    ν = 0.05 (a few new directions join W between compressions): system by system against
+    the oracle, as in the 2D cases."""
+    seq = wl.diffusion3d_moving(m=24, p=5, period=10)
+    out, orc = _run(seq, seq.all_systems(), y_threshold=32, y_keep=16, w_keep=6, nu=0.05, weights="rbf", p_cap=32)
+    _check(seq, out, orc)
+    assert out[-1][2]["compressions"] == 4
